@@ -1,0 +1,446 @@
+"""Plain CPU TT-cross quadrature (oracle, test infrastructure only).
+
+Follows the paper step by step:
+  * TT cross interpolation, Eq. (3): A ~ A(i_1, I_>1) [A(I_<=1, I_>1)]^-1
+    A(I_<=1, i_2, I_>2) ... A(I_<=d-1, i_d), with nested index sets, Eq. (4).
+  * Weights folded into the tensor, Sec. 4.1: A = w_{i_1}...w_{i_d} f(t).
+  * One sweep of the dimension-parallel greedy cross, Alg. 6 with one
+    superblock per "process": for every interface k at once, Alg. 2 is applied
+    to the superblock A(I_<=k-1 i_k, i_{k+1} I_>k+1) built from the index sets
+    of the previous sweep, and all new pivots are appended after the sweep.
+  * Alg. 2: random samples, then alternating column / row partial pivoting
+    until the rook condition, Eq. (2), holds or the round budget is spent.
+  * The cross matrix is applied through QR: L_k = Q R, B_k = Q Q(P_k,:)^-1 =
+    L_k A(I_<=k, I_>k)^-1, the coefficient matrix of Alg. 1's first step.
+  * The integral is the product of (2d-1) matrices of Sec. 4.1:
+    (sum_i A(i, I_>1)) G_1^-1 (sum_i A(I_<=1, i, I_>2)) ... (sum_i A(I_<=d-1, i)).
+
+Readings where the paper is silent (each one is also listed in the design doc):
+  * initial index set: one multi-index, the largest |A| among `init_samples`
+    seeded random points (first in draw order on ties);
+  * random samples: `samples_for(k)` draws per interface from the counter-based
+    SplitMix64 of oracle/rng.py, keyed by (seed, sweep, k); samples that land
+    in a row or column of the current cross are skipped (the error is zero
+    there, Sec. 2.4);
+  * ties in every argmax go to the first candidate in scan order (samples in
+    draw order, rows by rho = alpha * N_k + i, columns by gamma = j * r_{k+1} + beta);
+  * a pivot is accepted when |E*| > tol * scale, scale = largest |entry| of the
+    current cores, and r_k < rank cap;
+  * stopping: relative internal convergence |I_s - I_{s-1}| <= tol |I_s|, or
+    no pivot accepted in a sweep, or every interface at the rank cap, or the
+    sweep limit.
+"""
+from __future__ import annotations
+
+import dataclasses
+from fractions import Fraction
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import rng
+from .integrands import family_constant, tensor_entries
+
+STATUS_CONVERGED = 0
+STATUS_NO_PIVOT = 1
+STATUS_RANK_CAP = 2
+STATUS_MAX_SWEEPS = 3
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def neumaier_sum(a: np.ndarray, axis: int) -> np.ndarray:
+    """Neumaier-compensated sum along one axis."""
+    a = np.moveaxis(np.asarray(a, dtype=np.float64), axis, 0)
+    s = np.zeros(a.shape[1:])
+    c = np.zeros(a.shape[1:])
+    for x in a:
+        t = s + x
+        c = c + np.where(np.abs(s) >= np.abs(x), (s - t) + x, (x - t) + s)
+        s = t
+    return s + c
+
+
+@dataclasses.dataclass
+class CrossState:
+    """Nested index sets, Eq. (4): left[k] holds I_<=k as an (r_k, k) array of
+    node indices of modes 1..k; right[k] holds I_>k as an (r_k, d-k) array of
+    node indices of modes k+1..d.  left[0] and right[d] are the empty tuple."""
+    left: List[np.ndarray]
+    right: List[np.ndarray]
+
+    @property
+    def d(self) -> int:
+        return len(self.left)
+
+    def rank(self, k: int) -> int:
+        if k == 0 or k == self.d:
+            return 1
+        return self.left[k].shape[0]
+
+    def ranks(self) -> List[int]:
+        return [self.rank(k) for k in range(self.d + 1)]
+
+    def copy(self) -> "CrossState":
+        return CrossState([x.copy() for x in self.left], [x.copy() for x in self.right])
+
+
+def _row_of(table: np.ndarray, row: np.ndarray) -> int:
+    hits = np.nonzero(np.all(table == row[None, :], axis=1))[0]
+    if len(hits) != 1:
+        raise AssertionError("index sets are not nested")
+    return int(hits[0])
+
+
+def cross_rows(problem, st: CrossState, k: int) -> np.ndarray:
+    """P_k: positions of I_<=k among the rows (alpha, i) of the k-th fiber
+    matrix, rho = alpha * N_k + i (nestedness, Eq. (4), makes them exist)."""
+    Nk = problem.N[k - 1]
+    out = []
+    for a in range(st.rank(k)):
+        alpha = _row_of(st.left[k - 1], st.left[k][a, :k - 1])
+        out.append(alpha * Nk + int(st.left[k][a, k - 1]))
+    return np.array(out, dtype=np.int64)
+
+
+def cross_cols(problem, st: CrossState, k: int) -> np.ndarray:
+    """Q_k: positions of I_>k among the columns (j, beta) of superblock k,
+    gamma = j * r_{k+1} + beta."""
+    r_next = st.rank(k + 1)
+    out = []
+    for b in range(st.rank(k)):
+        beta = _row_of(st.right[k + 1], st.right[k][b, 1:])
+        out.append(int(st.right[k][b, 0]) * r_next + beta)
+    return np.array(out, dtype=np.int64)
+
+
+def to_parents(problem, st: CrossState) -> Dict[str, List[np.ndarray]]:
+    """Parent-pointer form of the nested sets: I_<=k[a] = (I_<=k-1[lpar], lnode),
+    I_>k[b] = (rnode, I_>k+1[rpar]), for k = 1..d-1."""
+    lpar, lnode, rpar, rnode = [], [], [], []
+    for k in range(1, problem.d):
+        P = cross_rows(problem, st, k)
+        Nk = problem.N[k - 1]
+        lpar.append(P // Nk)
+        lnode.append(P % Nk)
+        Q = cross_cols(problem, st, k)
+        rn = st.rank(k + 1)
+        rnode.append(Q // rn)
+        rpar.append(Q % rn)
+    return {"lpar": lpar, "lnode": lnode, "rpar": rpar, "rnode": rnode}
+
+
+def from_parents(problem, lpar, lnode, rpar, rnode) -> CrossState:
+    """Inverse of to_parents: rebuild the full multi-index sets."""
+    d = problem.d
+    left = [np.zeros((1, 0), dtype=np.int64)]
+    for k in range(1, d):
+        rows = [np.concatenate([left[k - 1][int(p)], [int(i)]]) for p, i in zip(lpar[k - 1], lnode[k - 1])]
+        left.append(np.array(rows, dtype=np.int64).reshape(len(rows), k))
+    right = [np.zeros((0, d), dtype=np.int64)] * (d + 1)
+    right[d] = np.zeros((1, 0), dtype=np.int64)
+    for k in range(d - 1, 0, -1):
+        rows = [np.concatenate([[int(j)], right[k + 1][int(p)]]) for p, j in zip(rpar[k - 1], rnode[k - 1])]
+        right[k] = np.array(rows, dtype=np.int64).reshape(len(rows), d - k)
+    return CrossState(left, right)
+
+
+# ---------------------------------------------------------------------------
+# evaluations
+# ---------------------------------------------------------------------------
+
+def eval_points(problem, idx: np.ndarray, chunk: int = 1 << 20) -> np.ndarray:
+    out = np.empty(idx.shape[0])
+    for a in range(0, idx.shape[0], chunk):
+        out[a:a + chunk] = tensor_entries(problem, idx[a:a + chunk])
+    return out
+
+
+def core(problem, st: CrossState, k: int) -> np.ndarray:
+    """Fiber tensor Y_k = A(I_<=k-1, i_k, I_>k), shape (r_{k-1}, N_k, r_k), Eq. (3)."""
+    d = problem.d
+    Lset = st.left[k - 1]                  # (r_{k-1}, k-1)
+    Rset = st.right[k]                     # (r_k, d-k)
+    r0, r1, Nk = Lset.shape[0], Rset.shape[0], problem.N[k - 1]
+    idx = np.empty((r0, Nk, r1, d), dtype=np.int64)
+    idx[..., :k - 1] = Lset[:, None, None, :]
+    idx[..., k - 1] = np.arange(Nk)[None, :, None]
+    idx[..., k:] = Rset[None, None, :, :]
+    return eval_points(problem, idx.reshape(-1, d)).reshape(r0, Nk, r1)
+
+
+def superblock_entries(problem, st: CrossState, k: int, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+    """Fresh entries A(I_<=k-1[alpha], i, j, I_>k+1[beta]) of superblock k at
+    flattened rows rho = alpha*N_k + i and columns gamma = j*r_{k+1} + beta."""
+    d = problem.d
+    Nk = problem.N[k - 1]
+    rn = st.rank(k + 1)
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    idx = np.empty((len(rows), d), dtype=np.int64)
+    idx[:, :k - 1] = st.left[k - 1][rows // Nk]
+    idx[:, k - 1] = rows % Nk
+    idx[:, k] = cols // rn
+    idx[:, k + 1:] = st.right[k + 1][cols % rn]
+    return eval_points(problem, idx)
+
+
+# ---------------------------------------------------------------------------
+# QR + maxvol coefficients, contraction
+# ---------------------------------------------------------------------------
+
+def maxvol_coefficients(Yk: np.ndarray, P: np.ndarray) -> np.ndarray:
+    """B_k = L_k A(I_<=k, I_>k)^-1 computed stably as Q Q(P,:)^-1 from the thin
+    QR of the fiber matrix L_k = Y_k as (r_{k-1} N_k) x r_k (Alg. 1, first step:
+    B(P, :) = identity)."""
+    r = Yk.shape[2]
+    Lk = Yk.reshape(-1, r)
+    Q, _ = np.linalg.qr(Lk)
+    return np.linalg.solve(Q[P, :].T, Q.T).T
+
+
+def integral_plain(problem, st: CrossState, cores: List[np.ndarray]) -> float:
+    """Sec. 4.1: (sum_i A(i,I_>1)) G_1^-1 (sum_i A(I_<=1,i,I_>2)) ... (sum_i A(I_<=d-1,i)),
+    G_k = A(I_<=k, I_>k); weights are already folded into A; node sums compensated."""
+    d = problem.d
+    x = neumaier_sum(cores[0], axis=1)                    # 1 x r_1
+    for k in range(1, d):
+        P = cross_rows(problem, st, k)
+        G = cores[k - 1].reshape(-1, st.rank(k))[P, :]
+        x = np.linalg.solve(G.T, x.T).T                   # x G_k^-1
+        x = x @ neumaier_sum(cores[k], axis=1)            # x V_{k+1}
+    return family_constant(problem.family, problem.form, problem.n) * float(x[0, 0])
+
+
+def integral_from_coefficients(problem, Bs: List[np.ndarray], Yd: np.ndarray) -> float:
+    """Same product written with the coefficient cores: prod_k (sum_i B_k(:, i, :)) times sum_i Y_d."""
+    x = np.ones((1, 1))
+    for B in Bs:
+        x = x @ neumaier_sum(B, axis=1)
+    x = x @ neumaier_sum(Yd, axis=1)
+    return family_constant(problem.family, problem.form, problem.n) * float(x[0, 0])
+
+
+def contract_exact(Bs: List[np.ndarray], Yd: np.ndarray) -> Fraction:
+    """The contraction of given FP64 cores in exact rational arithmetic (no
+    constant): the reference for the double-double contraction."""
+    x = [Fraction(1)]
+    for T in list(Bs) + [Yd]:
+        r0, Nk, r1 = T.shape
+        W = [[sum((Fraction(float(T[a, i, b])) for i in range(Nk)), Fraction(0)) for b in range(r1)]
+             for a in range(r0)]
+        x = [sum((x[a] * W[a][b] for a in range(r0)), Fraction(0)) for b in range(r1)]
+    return x[0]
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2 on one superblock
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Pivot:
+    k: int
+    row: int            # rho = alpha * N_k + i
+    col: int            # gamma = j * r_{k+1} + beta
+    err: float          # residual A - A~ at the pivot
+    accepted: bool
+    rounds: int
+    evals: int
+
+
+def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarray,
+                 sweep: int, scale: float) -> Optional[Pivot]:
+    """Alg. 2 on superblock k with the index sets of the previous sweep (Alg. 6).
+    Residual E(rho, gamma) = A(rho, gamma) - B_k(rho, :) R_{k+1}(:, gamma),
+    R_{k+1} = Y_{k+1} as r_k x (N_{k+1} r_{k+1})."""
+    Nk = problem.N[k - 1]
+    rk = st.rank(k)
+    M = st.rank(k - 1) * Nk
+    R = Ynext.reshape(rk, -1)
+    Ncol = R.shape[1]
+    if M <= rk or Ncol <= rk:
+        return None                                       # superblock already fully crossed
+    P = cross_rows(problem, st, k)
+    Q = cross_cols(problem, st, k)
+    row_ok = np.ones(M, dtype=bool)
+    row_ok[P] = False
+    col_ok = np.ones(Ncol, dtype=bool)
+    col_ok[Q] = False
+
+    def residual(rows, cols):
+        rows = np.asarray(rows, dtype=np.int64)
+        cols = np.asarray(cols, dtype=np.int64)
+        A = superblock_entries(problem, st, k, rows, cols)
+        approx = np.einsum("tb,bt->t", B[rows, :], R[:, cols])
+        return A - approx
+
+    evals = 0
+    # random samples
+    S = problem.samples_for(k)
+    stream = rng.stream_id(sweep, k, rng.PURPOSE_SAMPLE)
+    srows = np.array([rng.draw_index(problem.seed, stream, 2 * t, M) for t in range(S)], dtype=np.int64)
+    scols = np.array([rng.draw_index(problem.seed, stream, 2 * t + 1, Ncol) for t in range(S)], dtype=np.int64)
+    ok = row_ok[srows] & col_ok[scols]
+    score = np.full(S, -1.0)
+    if ok.any():
+        score[ok] = np.abs(residual(srows[ok], scols[ok]))
+        evals += int(ok.sum())
+    t = int(np.argmax(score))
+    if score[t] < 0:
+        return None
+    row, col = int(srows[t]), int(scols[t])
+
+    # rook pivoting: alternate column and row searches, Eq. (2)
+    rows_all = np.arange(M)
+    cols_all = np.arange(Ncol)
+    err = 0.0
+    rounds = 0
+    for _ in range(max(1, problem.rook_max)):
+        rounds += 1
+        cscore = np.full(M, -1.0)
+        cscore[row_ok] = np.abs(residual(rows_all[row_ok], np.full(int(row_ok.sum()), col)))
+        evals += int(row_ok.sum())
+        row = int(np.argmax(cscore))
+        rres = np.zeros(Ncol)
+        rres[col_ok] = residual(np.full(int(col_ok.sum()), row), cols_all[col_ok])
+        evals += int(col_ok.sum())
+        rscore = np.where(col_ok, np.abs(rres), -1.0)
+        new_col = int(np.argmax(rscore))
+        err = float(rres[new_col])
+        if new_col == col:
+            break
+        col = new_col
+    accepted = abs(err) > problem.pivot_tol * scale and rk < problem.rank_cap
+    return Pivot(k=k, row=row, col=col, err=err, accepted=bool(accepted), rounds=rounds, evals=evals)
+
+
+# ---------------------------------------------------------------------------
+# initial set, sweeps, driver
+# ---------------------------------------------------------------------------
+
+def initial_state(problem) -> CrossState:
+    """One seeded multi-index: the largest |A| among init_samples random points."""
+    d = problem.d
+    stream = rng.stream_id(0, 0, rng.PURPOSE_INIT)
+    pts = np.array([[rng.draw_index(problem.seed, stream, p * d + k, problem.N[k]) for k in range(d)]
+                    for p in range(problem.init_samples)], dtype=np.int64)
+    vals = np.abs(eval_points(problem, pts))
+    vals = np.where(np.isfinite(vals), vals, -1.0)
+    p = int(np.argmax(vals))
+    if not vals[p] > 0:
+        raise ValueError("no nonzero entry among the initial samples")
+    x = pts[p]
+    left = [x[:k].reshape(1, k).copy() for k in range(d)]
+    right = [np.zeros((0, d), dtype=np.int64)] + [x[k:].reshape(1, d - k).copy() for k in range(1, d + 1)]
+    return CrossState(left, right)
+
+
+def apply_pivots(problem, st: CrossState, pivots: List[Pivot]) -> CrossState:
+    """Append every accepted pivot after the whole sweep (Alg. 6): the new row
+    (alpha*, i*) extends I_<=k, the new column (j*, beta*) extends I_>k; both are
+    nested in the previous sweep's neighbours by construction."""
+    new = st.copy()
+    for pv in pivots:
+        if pv is None or not pv.accepted:
+            continue
+        k = pv.k
+        Nk = problem.N[k - 1]
+        rn = st.rank(k + 1)
+        alpha, i = divmod(pv.row, Nk)
+        j, beta = divmod(pv.col, rn)
+        lrow = np.concatenate([st.left[k - 1][alpha], [i]]).reshape(1, k)
+        rrow = np.concatenate([[j], st.right[k + 1][beta]]).reshape(1, problem.d - k)
+        new.left[k] = np.vstack([new.left[k], lrow])
+        new.right[k] = np.vstack([new.right[k], rrow])
+    return new
+
+
+@dataclasses.dataclass
+class SweepRecord:
+    value: float
+    ranks: List[int]
+    pivots: List[Optional[Pivot]]
+    scale: float
+
+
+def search_all(problem, st: CrossState, s: int, cores: List[np.ndarray], scale: float) -> List[Optional[Pivot]]:
+    """Alg. 6 with one superblock per interface: Alg. 2 on every interface k
+    (independently, on the sets of this sweep); interfaces at the cap skip."""
+    pivots: List[Optional[Pivot]] = []
+    for k in range(1, problem.d):
+        if st.rank(k) >= problem.rank_cap:
+            pivots.append(None)
+            continue
+        B = maxvol_coefficients(cores[k - 1], cross_rows(problem, st, k))
+        pivots.append(pivot_search(problem, st, k, B, cores[k], s, scale))
+    return pivots
+
+
+def sweep(problem, st: CrossState, s: int, search: bool = True):
+    """One sweep: cores, their largest |entry|, the integral, then (optionally)
+    the pivot search on every interface."""
+    cores = [core(problem, st, k) for k in range(1, problem.d + 1)]
+    scale = max(float(np.max(np.abs(c))) for c in cores)
+    value = integral_plain(problem, st, cores)
+    pivots = search_all(problem, st, s, cores, scale) if search else []
+    return value, cores, scale, pivots
+
+
+def integrate(problem, state: Optional[CrossState] = None, record: bool = True):
+    """Run sweeps until a stopping rule fires.  Returns a dict with the value,
+    status, sweeps, N_eval (core entries + search evaluations + initial scan),
+    final ranks, per-sweep history and the final state."""
+    d = problem.d
+    if d < 2:
+        raise ValueError("the cross needs d >= 2")
+    st = state.copy() if state is not None else initial_state(problem)
+    history: List[SweepRecord] = []
+    search_evals = 0
+    prev = None
+    changes: List[float] = []
+    status = STATUS_MAX_SWEEPS
+    value = float("nan")
+    conv = float("inf")
+    limit = problem.sweeps_limit()
+    for s in range(limit):
+        at_cap = all(st.rank(k) >= problem.rank_cap for k in range(1, d))
+        last = (s == limit - 1)
+        value, cores, scale, _ = sweep(problem, st, s, search=False)
+        if prev is not None:
+            conv = abs(value - prev) / abs(value) if value != 0 else abs(value - prev)
+            changes.append(conv)
+        if len(changes) >= problem.conv_window and max(changes[-problem.conv_window:]) <= problem.tol:
+            status = STATUS_CONVERGED
+            history.append(SweepRecord(value, st.ranks(), [], scale))
+            break
+        if at_cap:
+            status = STATUS_RANK_CAP
+            history.append(SweepRecord(value, st.ranks(), [], scale))
+            break
+        if last:
+            status = STATUS_MAX_SWEEPS
+            history.append(SweepRecord(value, st.ranks(), [], scale))
+            break
+        pivots = search_all(problem, st, s, cores, scale)
+        search_evals += sum(p.evals for p in pivots if p is not None)
+        history.append(SweepRecord(value, st.ranks(), pivots, scale))
+        if not any(p is not None and p.accepted for p in pivots):
+            status = STATUS_NO_PIVOT
+            break
+        st = apply_pivots(problem, st, pivots)
+        prev = value
+    ranks = st.ranks()
+    core_entries = sum(ranks[k - 1] * problem.N[k - 1] * ranks[k] for k in range(1, d + 1))
+    return {
+        "value": value,
+        "status": status,
+        "sweeps": len(history),
+        "internal_conv": conv,
+        "n_eval": core_entries + search_evals + problem.init_samples,
+        "ranks": ranks,
+        "max_rank": max(ranks),
+        "history": history if record else None,
+        "state": st,
+    }
