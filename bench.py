@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 TT-cross quadrature on the D_12 workload.
+
+A step is one whole integral: the initial index set, then sweeps of the
+dimension-parallel cross (new core entries, QR of the cross matrices,
+contraction, Alg. 2 on every interface, set update) until a stopping rule
+fires.  The workload is D_12 in R^12 (trapezoid on [-24, 24], 385 nodes per
+mode, rank cap 64, tol 1e-12, seed 12); the problem's node tables stay
+resident in HBM across steps and L2 is flushed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload d12|c4|e16]
+
+One JSON line on rank 0.  Under torchrun every rank runs its own replica of the
+workload on its own GPU (the path does not shard: replicas only, weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "integrals/s & fiber evals/s at rel.err<=1e-12 vs plain sweep; p50/p99 latency"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup")
+
+
+def workload(name):
+    from paper_1903_11554_gb300 import inputs
+    return {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16}[name]()
+
+
+def workload_config(p):
+    return {"workload": "%s: %s_%d, %s form, N=%d/mode, d=%d, rank cap %d, tol %g, %s contraction, seed %d"
+            % (p.name, p.family, p.n, "R^n trapezoid" if p.form == "rn" else "unit-cube Gauss-Legendre",
+               p.N[0], p.d, p.rank_cap, p.tol, p.precision, p.seed),
+            "family": p.family, "n": p.n, "d": p.d, "nodes_per_mode": p.N[0], "rank_cap": p.rank_cap,
+            "tol": p.tol, "precision": p.precision, "l2": "flushed between steps (256 MB write)"}
+
+
+def golden(name):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_full.json")
+    if not os.path.exists(path):
+        return None
+    g = json.load(open(path))
+    return g.get(name)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class Clocks:
+    def __init__(self, index):
+        self.path = tempfile.mktemp(prefix="ttq_clk_", suffix=".csv")
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        load = [v for v in sm if v > 0.5 * mx] or sm
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the workload
+
+BASELINE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import ttcross
+from paper_1903_11554_gb300 import inputs
+p = {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16}[%(wl)r]()
+budget = %(budget)f
+st = ttcross.initial_state(p)
+rows = []
+t0 = time.time()
+for s in range(p.sweeps_limit()):
+    t = time.time()
+    value, cores, scale, piv = ttcross.sweep(p, st, s, search=True)
+    rows.append([s, max(st.ranks()), time.time() - t])
+    st = ttcross.apply_pivots(p, st, piv)
+    if time.time() - t0 > budget or all(x is None or not x.accepted for x in piv):
+        break
+print(json.dumps(rows))
+"""
+
+
+def cpu_baseline(wl, ranks_traj, budget):
+    """Time the oracle's first sweeps of the workload on one host core, fit
+    t(r) = a + b r^2 + c r^3 to the per-sweep times, and sum it over the rank
+    trajectory the GPU run took (the oracle re-evaluates its cores every sweep,
+    so its sweep cost grows with the rank)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = BASELINE_SNIPPET % {"root": ROOT, "wl": wl, "budget": budget}
+    t = time.time()
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=budget * 4 + 120)
+    wall = time.time() - t
+    rows = json.loads(out.stdout.strip().splitlines()[-1])
+    import numpy as np
+    r = np.array([row[1] for row in rows], dtype=float)
+    ts = np.array([row[2] for row in rows], dtype=float)
+    if len(rows) >= 3:
+        A = np.stack([np.ones_like(r), r ** 2, r ** 3], axis=1)
+        coef, *_ = np.linalg.lstsq(A, ts, rcond=None)
+        coef = np.maximum(coef, 0.0)
+        model = lambda x: coef[0] + coef[1] * x * x + coef[2] * x ** 3
+    else:
+        model = lambda x: ts.mean()
+    if len(ranks_traj) <= len(rows):
+        est = float(ts[:len(ranks_traj)].sum())
+    else:
+        est = float(ts.sum() + sum(model(x) for x in ranks_traj[len(rows):]))
+    return {"value": 1.0 / est, "unit": "integrals/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle sweeps 0..%d of the same workload (ranks 1..%d) timed in %.1f s on one host core; "
+                      "seconds per integral = measured sweeps + t(r) = a + b r^2 + c r^3 fitted to them, summed over "
+                      "the %d-sweep rank trajectory of the GPU run (%.0f s estimated)"
+                      % (len(rows) - 1, int(r.max()), float(ts.sum()), len(ranks_traj), est),
+            "seconds_sampled": round(wall, 1)}
+
+
+# --------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = workload(args.workload)
+    g = golden(args.workload)
+    traj = list(range(1, (g["sweeps"] if g else p.rank_cap) + 1))
+    traj = [min(x, p.rank_cap) for x in traj]
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(args.workload, traj, budget=max(5.0, 60.0 / max(1, args.steps + args.warmup))))
+    timed = vals[args.warmup:]
+    v = statistics.median(x["value"] for x in timed)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "integrals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(p),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": timed[0]["sample"], "value": v,
+                             "unit": "integrals/s"},
+            "e2e": {"value": v, "unit": "integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="d12", choices=["d12", "c4", "e16"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1903_11554_gb300 import binding, build
+    if rank == 0:
+        build.build()
+    barrier()
+    build.build()
+    p = workload(args.workload)
+    plan = binding.Plan(p)
+    stream = plan.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    res = None
+    for _ in range(max(3, args.warmup)):
+        res = plan.run()
+
+    # ---- device-timed region: inputs resident, K whole integrals
+    plan.set_timing(True)
+    plan.kernel_times(reset=True)
+    k0 = plan.kernel_times()
+    l0 = plan.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    results = []
+    lat = []
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            results.append(plan.run())
+            b.record(stream)
+            lat.append((a, b))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    launches = plan.launches - l0
+    k1 = plan.kernel_times()
+    plan.set_timing(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = args.steps * world / (ms / 1000.0)
+    n_eval = sum(r["n_eval"] for r in results)
+    evals_per_s = n_eval * world / (ms / 1000.0)
+
+    # ---- roofline of the dominant kernel
+    kt = {}
+    for name in KERNELS:
+        kt[name] = {"ms": k1[name]["ms"] - k0[name]["ms"], "launches": k1[name]["launches"] - k0[name]["launches"],
+                    "flops": k1[name]["flops"] - k0[name]["flops"]}
+    dom = max(kt, key=lambda n: kt[n]["ms"])
+    d = kt[dom]
+    achieved = d["flops"] / (d["ms"] / 1000.0) / 1e12 if d["ms"] > 0 else 0.0
+    per_launch_ms = d["ms"] / max(1, d["launches"])
+    roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                           "(nominal 1.25 TFLOP/s)",
+            "algorithmic_flops_per_launch": d["flops"] / max(1, d["launches"]),
+            "avg_launch_ms": per_launch_ms,
+            "time_share": d["ms"] / max(1e-9, sum(v["ms"] for v in kt.values())),
+            "kernels": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                            "tflops": (v["flops"] / (v["ms"] / 1000.0) / 1e12) if v["ms"] > 0 else 0.0}
+                        for k, v in kt.items() if v["launches"]}}
+
+    # ---- end to end through the C ABI with host buffers
+    h2d0, d2h0 = 0, 0
+    torch.cuda.synchronize()
+    ws = plan.workspace
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = d2h = 0
+    barrier()
+    t_host = time.time()
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        flush.zero_()
+        q = binding.Plan(p, workspace=ws, stream=stream)   # host nodes/weights -> device inside the call
+        r = q.run()                                          # result read back to the host
+        hb, db = q.transfer_bytes()
+        h2d += hb
+        d2h += db
+        q.close()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max(f0.elapsed_time(f1), (time.time() - t_host) * 1000.0)
+    e2e = {"value": e2e_steps * world / (e2e_ms / 1000.0), "unit": "integrals/s",
+           "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
+
+    if rank != 0:
+        return 0
+    g = golden(args.workload)
+    check = {}
+    if g is not None:
+        ref = float(g["value"])
+        check = {"oracle_value": ref, "rel_err_vs_oracle": abs(results[-1]["value"] - ref) / abs(ref),
+                 "oracle_sweeps": g["sweeps"], "oracle_seconds": g.get("oracle_seconds")}
+    traj = list(range(1, results[-1]["sweeps"] + 1))
+    traj = [min(x, p.rank_cap) for x in traj]
+    cpu = cpu_baseline(args.workload, traj, args.cpu_budget)
+    line = {
+        "metric": METRIC, "value": value, "unit": "integrals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(p),
+        "fiber_evals_per_s": evals_per_s,
+        "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)]},
+        "result": {"value": results[-1]["value"], "value_lo": results[-1]["value_lo"], "sweeps": results[-1]["sweeps"],
+                   "max_rank": results[-1]["max_rank"], "status": results[-1]["status_name"],
+                   "n_eval": results[-1]["n_eval"], "internal_conv": results[-1]["internal_conv"], **check},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * ttq.h - C ABI of the GB300 TT-cross quadrature library (libttq.so).
+ *
+ * The library computes tensor-product quadratures (Sec. 4.1, Eq. 5 of
+ * Dolgov & Savostyanov, arXiv:1903.11554)
+ *
+ *     I = c * sum_{i_1..i_d} w_{1,i_1} ... w_{d,i_d} g(t_{1,i_1}, ..., t_{d,i_d})
+ *
+ * of the Ising-class integrands C_n, D_n, E_n (Sec. 5.1, Eqs. 9-11) by the
+ * dimension-parallel greedy tensor-train cross (Alg. 6 with Alg. 2 on every
+ * superblock at once), with the quadrature weights folded into the tensor
+ * (Sec. 4.1) and the integral contracted from the TT cores and the inverse
+ * cross matrices (Sec. 4.1, product of 2d-1 matrices).
+ *
+ * Conventions
+ *  - All entry points return an int status: 0 = TTQ_OK, > 0 a warning,
+ *    < 0 an error (see ttq_status).  No C++ exception crosses the ABI.
+ *  - "host" pointers are read during the call only; the caller keeps
+ *    ownership.  "device" pointers must stay valid while a plan uses them.
+ *  - Streams are passed as void* (a cudaStream_t; NULL = legacy default).
+ *  - All compute runs in the library's own CUDA kernels (sm_103a); there is
+ *    no CPU fallback: without a usable GPU every entry point that computes
+ *    returns TTQ_ERR_CUDA.
+ *  - A plan is not thread-safe; use one plan per thread.
+ */
+#ifndef TTQ_H
+#define TTQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Integrand families, Sec. 5.1 (Eqs. 9-11).  TEST is a separable tensor of
+ * exact TT rank n (g = sum_{t=1}^n exp(-t * mean(x))), used to check the exact
+ * recovery theorem (Thm. 2); it has no counterpart among the paper's integrals. */
+typedef enum { TTQ_FAMILY_C = 0, TTQ_FAMILY_D = 1, TTQ_FAMILY_E = 2, TTQ_FAMILY_TEST = 3 } ttq_family;
+
+/* Variables of the integral.
+ *  TTQ_FORM_RN:   s in R^n, d = n modes; C_n = 4/n! int (sum 2cosh s_j)^-2,
+ *                 D_n adds prod_{i<j} tanh^2((s_i - s_j)/2).  Nodes are s values.
+ *  TTQ_FORM_CUBE: the paper's form on [0,1]^(n-1), d = n-1 modes x_2..x_n
+ *                 (Eqs. 9-11), constant 2.  Nodes are x values in [0,1].     */
+typedef enum { TTQ_FORM_RN = 0, TTQ_FORM_CUBE = 1 } ttq_form;
+
+/* Arithmetic of the final contraction (Sec. 4.1): plain FP64, or double-double
+ * node sums and chain products (compensated TwoSum / FMA-based TwoProd).  The
+ * integrand, the QR of the cross matrices and the interface solves are FP64
+ * in both modes. */
+typedef enum { TTQ_PREC_FP64 = 0, TTQ_PREC_DD = 1 } ttq_precision;
+
+typedef enum {
+  TTQ_OK = 0,
+  TTQ_WARN_NO_PIVOT = 1,      /* stopped: no interface accepted a pivot            */
+  TTQ_WARN_RANK_CAP = 2,      /* stopped: every interface at the rank cap          */
+  TTQ_WARN_MAX_SWEEPS = 3,    /* stopped: sweep limit reached before convergence   */
+  TTQ_PENDING = 4,            /* serving: request not finished yet                 */
+  TTQ_ERR_INVALID_ARG = -1,
+  TTQ_ERR_NONFINITE = -2,     /* the integrand produced inf/nan                    */
+  TTQ_ERR_SINGULAR = -3,      /* a cross matrix A(I<=k, I>k) became singular       */
+  TTQ_ERR_WORKSPACE = -4,     /* workspace too small or misaligned                 */
+  TTQ_ERR_CUDA = -5,          /* a CUDA call failed (message: ttq_last_error)      */
+  TTQ_ERR_ADMISSION = -6,     /* serving: request larger than the memory budget    */
+  TTQ_ERR_NOT_FOUND = -7
+} ttq_status;
+
+#define TTQ_MAX_MODES 32      /* d <= 32 */
+#define TTQ_MAX_RANK 128      /* rank cap <= 128 */
+#define TTQ_MAX_NODES 2048    /* N_k <= 2048 */
+
+/* The problem statement (Sec. 4.1: integrand, per-mode nodes and weights;
+ * Alg. 6 inputs: rank cap and stopping tolerance). */
+typedef struct ttq_problem {
+  int32_t family;             /* ttq_family */
+  int32_t form;               /* ttq_form */
+  int32_t n;                  /* Ising index (TEST: number of separable terms) */
+  int32_t d;                  /* number of modes: n (RN), n-1 (CUBE), any (TEST) */
+  const int32_t *nodes_per_mode;  /* host [d], N_k in 2..TTQ_MAX_NODES */
+  const double *nodes;        /* [sum N_k] node values, mode-major; host or device */
+  const double *weights;      /* [sum N_k] quadrature weights, same layout */
+  int32_t inputs_on_device;   /* 1: nodes/weights are device pointers */
+  int32_t rank_cap;           /* 1..TTQ_MAX_RANK */
+  double tol;                 /* stop when |I_s - I_{s-1}| <= tol |I_s| in conv_window sweeps in a row */
+  double pivot_tol;           /* keep a pivot when |E*| > pivot_tol * max|core entry| */
+  int32_t conv_window;        /* >= 1 */
+  int32_t max_sweeps;         /* > 0 */
+  uint64_t seed;              /* counter-based SplitMix64 key of the random samples */
+  int32_t n_samples;          /* random samples per interface; 0 -> N_k + N_{k+1} */
+  int32_t rook_max;           /* column/row rounds of rook pivoting, >= 1 */
+  int32_t init_samples;       /* random points scanned for the first pivot, >= 1 */
+  int32_t precision;          /* ttq_precision */
+} ttq_problem;
+
+typedef struct ttq_result {
+  double value;               /* integral (family constant included) */
+  double value_lo;            /* double-double tail (0 in FP64 mode) */
+  double internal_conv;       /* last relative change |I_s - I_{s-1}| / |I_s| */
+  int64_t n_eval;             /* integrand evaluations: core entries + search + initial scan */
+  int32_t sweeps;             /* sweeps run (each with its own integral value) */
+  int32_t max_rank;
+  int32_t status;             /* ttq_status of the run */
+  int32_t reserved;
+} ttq_result;
+
+/* Per-interface outcome of one pivot search (Alg. 2 on superblock k).  The
+ * argmax of every step treats candidates whose |E| lies within
+ * 1e-10 * max + 1e-14 * max|core entry| of the maximum as tied and takes the
+ * first in scan order (the paper does not define ties). */
+typedef struct ttq_pivot {
+  int32_t k;                  /* interface 1..d-1 */
+  int32_t searched;           /* 0 if the interface was at the cap or stopped */
+  int32_t row;                /* rho = alpha * N_k + i */
+  int32_t col;                /* gamma = j * r_{k+1} + beta */
+  double err;                 /* residual A - A~ at the pivot */
+  int32_t accepted;
+  int32_t rounds;             /* rook rounds run */
+  int64_t evals;              /* integrand evaluations of this search */
+} ttq_pivot;
+
+typedef struct ttq_plan ttq_plan;
+
+/* Device workspace (bytes, 256-byte aligned) a plan for this problem needs.
+ * It holds the node tables, index sets, cores, QR factors and search state;
+ * its size grows as sum_k cap^2 N_k. */
+int ttq_workspace_bytes(const ttq_problem *p, size_t *bytes);
+
+/* Create a plan over caller-owned device memory `workspace` (>= the size
+ * above, 256-byte aligned).  Copies the problem's nodes/weights to the
+ * workspace on `stream` (host->device when inputs_on_device == 0) and builds
+ * the derived node tables.  The plan object itself lives in host memory. */
+int ttq_plan_create(const ttq_problem *p, void *workspace, size_t bytes, void *stream, ttq_plan **out);
+int ttq_plan_destroy(ttq_plan *plan);
+
+/* Full run: initial index set, then sweeps until a stopping rule fires
+ * (Alg. 6 repeated).  Blocks until the result is on the host. */
+int ttq_plan_run(ttq_plan *plan, ttq_result *out);
+
+/* --- stage-level entry points (replay and inspection) ------------------- */
+
+/* Initial index set: the largest |A| among init_samples seeded random points. */
+int ttq_plan_init(ttq_plan *plan);
+
+/* Replace the index sets by the given nested sets in parent-pointer form
+ * (Eq. 4): I<=k[a] = (I<=k-1[lpar[k-1][a]], lnode[k-1][a]) and
+ * I>k[b] = (rnode[k-1][b], I>k+1[rpar[k-1][b]]), host arrays concatenated over
+ * k = 1..d-1 with ranks[k] entries each (ranks has d+1 entries, ranks[0] =
+ * ranks[d] = 1).  The next sweep re-evaluates every core and refactors every
+ * cross matrix from scratch. */
+int ttq_plan_set_state(ttq_plan *plan, const int32_t *ranks, const int32_t *lpar, const int32_t *lnode,
+                       const int32_t *rpar, const int32_t *rnode);
+int ttq_plan_get_state(ttq_plan *plan, int32_t *ranks, int32_t *lpar, int32_t *lnode,
+                       int32_t *rpar, int32_t *rnode);
+
+/* One sweep: evaluate the new core entries, factor the cross matrices,
+ * contract the integral, then (search != 0) run Alg. 2 on every interface on
+ * the sets of this sweep and append the accepted pivots (Alg. 6).  Writes the
+ * sweep's integral to *value (and its double-double tail to *value_lo) and,
+ * if pivots != NULL, d-1 ttq_pivot records.  No stopping rule is applied. */
+int ttq_plan_sweep(ttq_plan *plan, int sweep_index, int search, double *value, double *value_lo,
+                   ttq_pivot *pivots);
+
+/* Copy core k (1..d) Y_k = A(I<=k-1, i_k, I>k) to host memory as a dense
+ * row-major r_{k-1} x N_k x r_k array (valid after a sweep). */
+int ttq_plan_get_core(ttq_plan *plan, int k, double *host_out);
+
+/* Weighted tensor entries A = prod_k w_k[i_k] g(t) (no family constant) at
+ * npts multi-indices idx (device, row-major npts x d int32) into out (device
+ * npts doubles), on the plan's stream. */
+int ttq_plan_eval_points(ttq_plan *plan, const int32_t *idx, int64_t npts, double *out);
+
+/* Number of the library's kernel launches issued by this plan so far. */
+int64_t ttq_plan_launches(const ttq_plan *plan);
+
+/* Bytes this plan has copied host->device (problem inputs, descriptor) and
+ * device->host (state and flags read back) since it was created. */
+int ttq_plan_transfer_bytes(const ttq_plan *plan, int64_t *h2d, int64_t *d2h);
+
+/* Per-kernel timing.  With timing enabled every launch of a sweep is
+ * bracketed by CUDA events on the plan's stream; ttq_plan_kernel_times writes,
+ * for each of the TTQ_NUM_KERNELS kernels (index order: eval_slabs, qr,
+ * contract, samples, rook_col, rook_row, update, init, setup), the summed
+ * device time in ms and the launch count since the last reset, and the
+ * algorithmic FP64 operations the kernel has done since the plan's state was
+ * last set (cumulative; a division, exp or cosh counts as one operation, an
+ * FMA as two).  Any output array may be NULL.  Synchronizes the stream. */
+#define TTQ_NUM_KERNELS 9
+int ttq_plan_set_timing(ttq_plan *plan, int enable);
+int ttq_plan_kernel_times(ttq_plan *plan, double *ms, int64_t *launches, double *flops, int reset);
+
+const char *ttq_status_string(int status);
+const char *ttq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTQ_H */

@@ -22,8 +22,12 @@ Readings where the paper is silent (each one is also listed in the design doc):
     SplitMix64 of oracle/rng.py, keyed by (seed, sweep, k); samples that land
     in a row or column of the current cross are skipped (the error is zero
     there, Sec. 2.4);
-  * ties in every argmax go to the first candidate in scan order (samples in
-    draw order, rows by rho = alpha * N_k + i, columns by gamma = j * r_{k+1} + beta);
+  * ties in the argmax of Alg. 2: candidates whose |E| is within a noise
+    window of the maximum, |E| >= max - (TIE_REL * max + TIE_ABS * scale), are
+    tied, and the first in scan order wins (samples in draw order, rows by
+    rho = alpha * N_k + i, columns by gamma = j * r_{k+1} + beta); residuals that
+    are equal in exact arithmetic (e.g. by the permutation symmetry of C_n and
+    D_n) then pick the same pivot whatever the rounding;
   * a pivot is accepted when |E*| > tol * scale, scale = largest |entry| of the
     current cores, and r_k < rank cap;
   * stopping: relative internal convergence |I_s - I_{s-1}| <= tol |I_s|, or
@@ -40,6 +44,9 @@ import numpy as np
 
 from . import rng
 from .integrands import family_constant, tensor_entries
+
+TIE_REL = 1e-10
+TIE_ABS = 1e-14
 
 STATUS_CONVERGED = 0
 STATUS_NO_PIVOT = 1
@@ -239,6 +246,17 @@ def contract_exact(Bs: List[np.ndarray], Yd: np.ndarray) -> Fraction:
 # Alg. 2 on one superblock
 # ---------------------------------------------------------------------------
 
+def tie_argmax(score: np.ndarray, scale: float) -> int:
+    """First index whose score is within the tie window of the maximum;
+    scores < 0 mark candidates that are not eligible.  -1 if none is."""
+    ok = score >= 0
+    if not ok.any():
+        return -1
+    smax = float(score[ok].max())
+    thr = smax - (TIE_REL * smax + TIE_ABS * scale)
+    return int(np.nonzero(ok & (score >= thr))[0][0])
+
+
 @dataclasses.dataclass
 class Pivot:
     k: int
@@ -287,8 +305,8 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
     if ok.any():
         score[ok] = np.abs(residual(srows[ok], scols[ok]))
         evals += int(ok.sum())
-    t = int(np.argmax(score))
-    if score[t] < 0:
+    t = tie_argmax(score, scale)
+    if t < 0:
         return None
     row, col = int(srows[t]), int(scols[t])
 
@@ -302,12 +320,12 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
         cscore = np.full(M, -1.0)
         cscore[row_ok] = np.abs(residual(rows_all[row_ok], np.full(int(row_ok.sum()), col)))
         evals += int(row_ok.sum())
-        row = int(np.argmax(cscore))
+        row = tie_argmax(cscore, scale)
         rres = np.zeros(Ncol)
         rres[col_ok] = residual(np.full(int(col_ok.sum()), row), cols_all[col_ok])
         evals += int(col_ok.sum())
         rscore = np.where(col_ok, np.abs(rres), -1.0)
-        new_col = int(np.argmax(rscore))
+        new_col = tie_argmax(rscore, scale)
         err = float(rres[new_col])
         if new_col == col:
             break

@@ -1,0 +1,272 @@
+"""Thin Python binding of libttq.so (include/ttq.h): argument marshalling only.
+
+Every step of the quadrature runs in the library's CUDA kernels.  PyTorch is
+used for device memory (the plan's workspace) and the current CUDA stream.
+There is no CPU fallback: if the library or a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttq.so")
+
+STATUS_NAMES = {0: "converged", 1: "no_pivot", 2: "rank_cap", 3: "max_sweeps", 4: "pending",
+                -1: "invalid_arg", -2: "nonfinite", -3: "singular", -4: "workspace", -5: "cuda",
+                -6: "admission", -7: "not_found"}
+
+# function name -> (restype, argtypes); the exported surface of include/ttq.h
+_c = ctypes
+_vp = _c.c_void_p
+
+
+class TTQProblem(_c.Structure):
+    _fields_ = [("family", _c.c_int32), ("form", _c.c_int32), ("n", _c.c_int32), ("d", _c.c_int32),
+                ("nodes_per_mode", _c.POINTER(_c.c_int32)), ("nodes", _c.c_void_p), ("weights", _c.c_void_p),
+                ("inputs_on_device", _c.c_int32), ("rank_cap", _c.c_int32), ("tol", _c.c_double),
+                ("pivot_tol", _c.c_double), ("conv_window", _c.c_int32), ("max_sweeps", _c.c_int32),
+                ("seed", _c.c_uint64), ("n_samples", _c.c_int32), ("rook_max", _c.c_int32),
+                ("init_samples", _c.c_int32), ("precision", _c.c_int32)]
+
+
+class TTQResult(_c.Structure):
+    _fields_ = [("value", _c.c_double), ("value_lo", _c.c_double), ("internal_conv", _c.c_double),
+                ("n_eval", _c.c_int64), ("sweeps", _c.c_int32), ("max_rank", _c.c_int32),
+                ("status", _c.c_int32), ("reserved", _c.c_int32)]
+
+
+class TTQPivot(_c.Structure):
+    _fields_ = [("k", _c.c_int32), ("searched", _c.c_int32), ("row", _c.c_int32), ("col", _c.c_int32),
+                ("err", _c.c_double), ("accepted", _c.c_int32), ("rounds", _c.c_int32),
+                ("evals", _c.c_int64)]
+
+
+_i32p = _c.POINTER(_c.c_int32)
+_dp = _c.POINTER(_c.c_double)
+SIGNATURES = {
+    "ttq_workspace_bytes": (_c.c_int, [_c.POINTER(TTQProblem), _c.POINTER(_c.c_size_t)]),
+    "ttq_plan_create": (_c.c_int, [_c.POINTER(TTQProblem), _vp, _c.c_size_t, _vp, _c.POINTER(_vp)]),
+    "ttq_plan_destroy": (_c.c_int, [_vp]),
+    "ttq_plan_run": (_c.c_int, [_vp, _c.POINTER(TTQResult)]),
+    "ttq_plan_init": (_c.c_int, [_vp]),
+    "ttq_plan_set_state": (_c.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "ttq_plan_get_state": (_c.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "ttq_plan_sweep": (_c.c_int, [_vp, _c.c_int, _c.c_int, _dp, _dp, _c.POINTER(TTQPivot)]),
+    "ttq_plan_get_core": (_c.c_int, [_vp, _c.c_int, _dp]),
+    "ttq_plan_eval_points": (_c.c_int, [_vp, _vp, _c.c_int64, _vp]),
+    "ttq_plan_launches": (_c.c_int64, [_vp]),
+    "ttq_plan_transfer_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
+    "ttq_plan_set_timing": (_c.c_int, [_vp, _c.c_int]),
+    "ttq_plan_kernel_times": (_c.c_int, [_vp, _dp, _c.POINTER(_c.c_int64), _dp, _c.c_int]),
+    "ttq_status_string": (_c.c_char_p, [_c.c_int]),
+    "ttq_last_error": (_c.c_char_p, []),
+}
+
+KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libttq.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libttq.so not built: run __graft_entry__.build() (or python -m "
+                               "paper_1903_11554_gb300.build)")
+        lib = _c.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class TTQError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        lib = load()
+        raise TTQError("%s failed: %s (%s)" % (what, STATUS_NAMES.get(rc, rc),
+                                               lib.ttq_last_error().decode(errors="replace")))
+    return rc
+
+
+class _Arrays:
+    """Keeps the host arrays a ttq_problem points to alive."""
+
+    def __init__(self, p: inputs.Problem, nodes=None, weights=None):
+        self.N = np.ascontiguousarray(p.N, dtype=np.int32)
+        if nodes is None:
+            self.nodes = np.ascontiguousarray(np.concatenate(p.nodes), dtype=np.float64)
+            self.weights = np.ascontiguousarray(np.concatenate(p.weights), dtype=np.float64)
+            self.on_device = 0
+            self.nptr = self.nodes.ctypes.data
+            self.wptr = self.weights.ctypes.data
+        else:
+            self.nodes, self.weights = nodes, weights
+            self.on_device = 1
+            self.nptr = nodes.data_ptr()
+            self.wptr = weights.data_ptr()
+
+
+def make_struct(p: inputs.Problem, arrays: _Arrays) -> TTQProblem:
+    s = TTQProblem()
+    s.family = inputs.FAMILY_CODE[p.family]
+    s.form = inputs.FORM_CODE[p.form]
+    s.n = p.n
+    s.d = p.d
+    s.nodes_per_mode = arrays.N.ctypes.data_as(_i32p)
+    s.nodes = arrays.nptr
+    s.weights = arrays.wptr
+    s.inputs_on_device = arrays.on_device
+    s.rank_cap = p.rank_cap
+    s.tol = p.tol
+    s.pivot_tol = p.pivot_tol
+    s.conv_window = p.conv_window
+    s.max_sweeps = p.sweeps_limit()
+    s.seed = p.seed & ((1 << 64) - 1)
+    s.n_samples = p.n_samples
+    s.rook_max = p.rook_max
+    s.init_samples = p.init_samples
+    s.precision = inputs.PREC_CODE[p.precision]
+    return s
+
+
+def workspace_bytes(p: inputs.Problem) -> int:
+    lib = load()
+    arrays = _Arrays(p)
+    st = make_struct(p, arrays)
+    out = _c.c_size_t(0)
+    _check(lib.ttq_workspace_bytes(_c.byref(st), _c.byref(out)), "ttq_workspace_bytes")
+    return int(out.value)
+
+
+class Plan:
+    """One integral on the GPU: workspace (torch) + plan handle (library)."""
+
+    def __init__(self, p: inputs.Problem, workspace=None, stream=None, device_inputs=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise TTQError("no CUDA device: the TT-cross quadrature runs only on the GPU")
+        self.lib = load()
+        self.problem = p
+        self.arrays = _Arrays(p, *(device_inputs or (None, None)))
+        self.struct = make_struct(p, self.arrays)
+        nbytes = _c.c_size_t(0)
+        _check(self.lib.ttq_workspace_bytes(_c.byref(self.struct), _c.byref(nbytes)), "ttq_workspace_bytes")
+        self.nbytes = int(nbytes.value)
+        if workspace is None:
+            workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _vp()
+        _check(self.lib.ttq_plan_create(_c.byref(self.struct), _vp(workspace.data_ptr()), self.nbytes,
+                                        _vp(self.stream.cuda_stream), _c.byref(h)), "ttq_plan_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ttq_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- full run ---------------------------------------------------------
+    def run(self) -> Dict:
+        res = TTQResult()
+        _check(self.lib.ttq_plan_run(self.h, _c.byref(res)), "ttq_plan_run")
+        return {"value": res.value, "value_lo": res.value_lo, "internal_conv": res.internal_conv,
+                "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
+                "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
+
+    # -- stages -----------------------------------------------------------
+    def init(self):
+        _check(self.lib.ttq_plan_init(self.h), "ttq_plan_init")
+
+    def sweep(self, s: int, search: bool = True):
+        v, vlo = _c.c_double(0), _c.c_double(0)
+        piv = (TTQPivot * max(1, self.problem.d - 1))()
+        _check(self.lib.ttq_plan_sweep(self.h, s, 1 if search else 0, _c.byref(v), _c.byref(vlo), piv),
+               "ttq_plan_sweep")
+        pivots = [{"k": q.k, "searched": q.searched, "row": q.row, "col": q.col, "err": q.err,
+                   "accepted": q.accepted, "rounds": q.rounds, "evals": int(q.evals)}
+                  for q in piv[:self.problem.d - 1]]
+        return v.value, vlo.value, pivots
+
+    def set_state(self, ranks, lpar, lnode, rpar, rnode):
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in
+                (ranks, np.concatenate([np.asarray(x) for x in lpar]), np.concatenate([np.asarray(x) for x in lnode]),
+                 np.concatenate([np.asarray(x) for x in rpar]), np.concatenate([np.asarray(x) for x in rnode]))]
+        _check(self.lib.ttq_plan_set_state(self.h, *[a.ctypes.data_as(_i32p) for a in arrs]), "ttq_plan_set_state")
+
+    def get_state(self):
+        d = self.problem.d
+        cap = self.problem.rank_cap
+        ranks = np.zeros(d + 1, dtype=np.int32)
+        bufs = [np.zeros(cap * (d - 1), dtype=np.int32) for _ in range(4)]
+        _check(self.lib.ttq_plan_get_state(self.h, ranks.ctypes.data_as(_i32p),
+                                           *[b.ctypes.data_as(_i32p) for b in bufs]), "ttq_plan_get_state")
+        out = {"ranks": ranks.tolist(), "lpar": [], "lnode": [], "rpar": [], "rnode": []}
+        o = 0
+        for k in range(1, d):
+            r = int(ranks[k])
+            for name, b in zip(("lpar", "lnode", "rpar", "rnode"), bufs):
+                out[name].append(b[o:o + r].copy())
+            o += r
+        return out
+
+    def get_core(self, k: int, shape) -> np.ndarray:
+        out = np.zeros(int(np.prod(shape)), dtype=np.float64)
+        _check(self.lib.ttq_plan_get_core(self.h, k, out.ctypes.data_as(_dp)), "ttq_plan_get_core")
+        return out.reshape(shape)
+
+    def eval_points(self, idx) -> "object":
+        """idx: torch int32 (npts x d) on the GPU -> torch float64 values."""
+        import torch
+        idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(idx.shape[0], dtype=torch.float64, device="cuda")
+        _check(self.lib.ttq_plan_eval_points(self.h, _vp(idx.data_ptr()), idx.shape[0], _vp(out.data_ptr())),
+               "ttq_plan_eval_points")
+        return out
+
+    def transfer_bytes(self):
+        a, b = _c.c_int64(0), _c.c_int64(0)
+        _check(self.lib.ttq_plan_transfer_bytes(self.h, _c.byref(a), _c.byref(b)), "ttq_plan_transfer_bytes")
+        return int(a.value), int(b.value)
+
+    def set_timing(self, on: bool):
+        _check(self.lib.ttq_plan_set_timing(self.h, 1 if on else 0), "ttq_plan_set_timing")
+
+    def kernel_times(self, reset: bool = False) -> Dict[str, Dict]:
+        ms = (_c.c_double * len(KERNELS))()
+        n = (_c.c_int64 * len(KERNELS))()
+        fl = (_c.c_double * len(KERNELS))()
+        _check(self.lib.ttq_plan_kernel_times(self.h, ms, n, fl, 1 if reset else 0), "ttq_plan_kernel_times")
+        return {name: {"ms": ms[q], "launches": int(n[q]), "flops": fl[q]} for q, name in enumerate(KERNELS)}
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.ttq_plan_launches(self.h))
+
+
+def integrate(p: inputs.Problem) -> Dict:
+    """Convenience: one plan, one full run."""
+    plan = Plan(p)
+    try:
+        return plan.run()
+    finally:
+        plan.close()

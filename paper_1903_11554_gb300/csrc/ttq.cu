@@ -1,0 +1,580 @@
+// libttq: C ABI of the GB300 TT-cross quadrature (declarations and contracts in include/ttq.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ttq.h"
+#include "ttq_kernels.cuh"
+
+using namespace ttq;
+
+static thread_local std::string g_last_error;
+
+static int set_err(int code, const char *msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+      return TTQ_ERR_CUDA;                                                         \
+    }                                                                              \
+  } while (0)
+
+// kernel ids of the timing counters (ttq_plan_kernel_times)
+enum { KT_EVAL = 0, KT_QR, KT_CONTRACT, KT_SAMPLES, KT_ROOK_COL, KT_ROOK_ROW, KT_UPDATE, KT_INIT, KT_SETUP, KT_N };
+
+struct TimedLaunch {
+  int kid;
+  cudaEvent_t a, b;
+};
+
+struct ttq_plan {
+  Dev h;                    // host copy of the descriptor (device pointers inside)
+  Dev *dev;                 // descriptor in the workspace
+  State *st;                // mutable state in the workspace
+  cudaStream_t stream;
+  int grid_eval, qr_smem;
+  long long launches;
+  State *hst;               // pinned host mirror of the state
+  int timing;               // 1: bracket every launch with CUDA events
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  double kt_ms[KT_N];
+  long long kt_n[KT_N];
+  long long h2d, d2h;       // bytes copied host<->device by this plan
+};
+
+static cudaEvent_t ev_get(ttq_plan *P) {
+  if (!P->pool.empty()) {
+    cudaEvent_t e = P->pool.back();
+    P->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// launch helper: counts the launch and, when timing, records events around it
+template <typename F>
+static void timed(ttq_plan *P, int kid, F &&launch) {
+  if (P->timing) {
+    TimedLaunch t{kid, ev_get(P), ev_get(P)};
+    cudaEventRecord(t.a, P->stream);
+    launch();
+    cudaEventRecord(t.b, P->stream);
+    P->pending.push_back(t);
+  } else {
+    launch();
+  }
+  P->launches++;
+  P->kt_n[kid]++;
+}
+
+// fold the completed launches' durations into the counters (stream must be idle)
+static void harvest(ttq_plan *P) {
+  for (auto &t : P->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) P->kt_ms[t.kid] += ms;
+    P->pool.push_back(t.a);
+    P->pool.push_back(t.b);
+  }
+  P->pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// validation and layout
+
+static int validate(const ttq_problem *p) {
+  if (!p) return set_err(TTQ_ERR_INVALID_ARG, "null problem");
+  if (p->family < 0 || p->family > 3) return set_err(TTQ_ERR_INVALID_ARG, "bad family");
+  if (p->form < 0 || p->form > 1) return set_err(TTQ_ERR_INVALID_ARG, "bad form");
+  if (p->d < 2 || p->d > TTQ_MAX_MODES) return set_err(TTQ_ERR_INVALID_ARG, "d must be in 2..32");
+  if (p->family == TTQ_FAMILY_TEST) {
+    if (p->n < 1) return set_err(TTQ_ERR_INVALID_ARG, "TEST needs n >= 1 terms");
+  } else if (p->form == TTQ_FORM_RN) {
+    if (p->family == TTQ_FAMILY_E) return set_err(TTQ_ERR_INVALID_ARG, "E_n has no R^n form");
+    if (p->d != p->n) return set_err(TTQ_ERR_INVALID_ARG, "R^n form needs d == n");
+  } else if (p->d != p->n - 1) {
+    return set_err(TTQ_ERR_INVALID_ARG, "unit-cube form needs d == n - 1");
+  }
+  if (!p->nodes_per_mode || !p->nodes || !p->weights) return set_err(TTQ_ERR_INVALID_ARG, "null arrays");
+  for (int k = 0; k < p->d; ++k)
+    if (p->nodes_per_mode[k] < 2 || p->nodes_per_mode[k] > TTQ_MAX_NODES)
+      return set_err(TTQ_ERR_INVALID_ARG, "N_k must be in 2..2048");
+  if (p->rank_cap < 1 || p->rank_cap > TTQ_MAX_RANK) return set_err(TTQ_ERR_INVALID_ARG, "rank_cap must be in 1..128");
+  if (!(p->tol >= 0.0) || !(p->pivot_tol >= 0.0)) return set_err(TTQ_ERR_INVALID_ARG, "negative tolerance");
+  if (p->conv_window < 1 || p->conv_window > 8) return set_err(TTQ_ERR_INVALID_ARG, "conv_window must be in 1..8");
+  if (p->max_sweeps < 1) return set_err(TTQ_ERR_INVALID_ARG, "max_sweeps must be >= 1");
+  if (p->rook_max < 1) return set_err(TTQ_ERR_INVALID_ARG, "rook_max must be >= 1");
+  if (p->init_samples < 1) return set_err(TTQ_ERR_INVALID_ARG, "init_samples must be >= 1");
+  if (p->n_samples < 0 || p->n_samples > (1 << 20)) return set_err(TTQ_ERR_INVALID_ARG, "bad n_samples");
+  if (p->precision < 0 || p->precision > 1) return set_err(TTQ_ERR_INVALID_ARG, "bad precision");
+  return TTQ_OK;
+}
+
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = (off + 255) & ~(size_t)255;
+    off = o + bytes;
+    return o;
+  }
+};
+
+struct Layout {
+  size_t dev, st, x, w, c, T, part;
+  size_t lidx[TTQ_MAXD], ridx[TTQ_MAXD], lpar[TTQ_MAXD], lnode[TTQ_MAXD], rpar[TTQ_MAXD], rnode[TTQ_MAXD];
+  size_t Y[TTQ_MAXD + 1], V[TTQ_MAXD + 1], Vlo[TTQ_MAXD + 1];
+  size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], rinv[TTQ_MAXD], zvec[TTQ_MAXD];
+  size_t cs[TTQ_MAXD], ce[TTQ_MAXD];
+  size_t total;
+  int sblocks, cblocks, rblocks;
+};
+
+static int samples_for(const ttq_problem *p, int k) {  // interface k = 1..d-1
+  return p->n_samples > 0 ? p->n_samples : p->nodes_per_mode[k - 1] + p->nodes_per_mode[k];
+}
+
+static void make_layout(const ttq_problem *p, Layout *L) {
+  const int d = p->d, cap = p->rank_cap;
+  size_t sumN = 0;
+  int maxN = 0, maxS = 0;
+  for (int k = 0; k < d; ++k) { sumN += p->nodes_per_mode[k]; maxN = p->nodes_per_mode[k] > maxN ? p->nodes_per_mode[k] : maxN; }
+  for (int k = 1; k < d; ++k) maxS = samples_for(p, k) > maxS ? samples_for(p, k) : maxS;
+  int capL[TTQ_MAXD + 1];
+  for (int k = 0; k <= d; ++k) capL[k] = (k == 0 || k == d) ? 1 : cap;
+  Bump b;
+  L->dev = b.take(sizeof(Dev));
+  L->st = b.take(sizeof(State));
+  L->x = b.take(sumN * 8);
+  L->w = b.take(sumN * 8);
+  L->c = b.take(sumN * 8);
+  L->T = b.take((size_t)maxN * 8);
+  for (int k = 1; k < d; ++k) {
+    L->lidx[k] = b.take((size_t)cap * d * 4);
+    L->ridx[k] = b.take((size_t)cap * d * 4);
+    L->lpar[k] = b.take((size_t)cap * 4);
+    L->lnode[k] = b.take((size_t)cap * 4);
+    L->rpar[k] = b.take((size_t)cap * 4);
+    L->rnode[k] = b.take((size_t)cap * 4);
+  }
+  for (int k = 1; k <= d; ++k) {
+    L->Y[k] = b.take((size_t)capL[k - 1] * p->nodes_per_mode[k - 1] * capL[k] * 8);
+    L->V[k] = b.take((size_t)capL[k - 1] * capL[k] * 8);
+    L->Vlo[k] = b.take((size_t)capL[k - 1] * capL[k] * 8);
+  }
+  for (int k = 1; k < d; ++k) {
+    L->Qr[k] = b.take((size_t)cap * cap * 8);
+    L->Qc[k] = b.take((size_t)cap * cap * 8);
+    L->Rc[k] = b.take((size_t)cap * cap * 8);
+    L->Rr[k] = b.take((size_t)cap * cap * 8);
+    L->rinv[k] = b.take((size_t)cap * 8);
+    L->zvec[k] = b.take((size_t)cap * 8);
+    size_t nc = (size_t)samples_for(p, k);
+    size_t ncol = (size_t)cap * p->nodes_per_mode[k - 1], nrow = (size_t)p->nodes_per_mode[k] * cap;
+    nc = nc > ncol ? nc : ncol;
+    nc = nc > nrow ? nc : nrow;
+    L->cs[k] = b.take(nc * 8);
+    L->ce[k] = b.take(nc * 8);
+  }
+  const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;
+  auto clampi = [](long v, long lo, long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
+  L->sblocks = clampi((maxS + TTQ_WARPS - 1) / TTQ_WARPS, 1, 64);
+  L->cblocks = clampi(((long)cap * nch + TTQ_WARPS - 1) / TTQ_WARPS, 1, 96);
+  L->rblocks = L->cblocks;
+  int mb = L->sblocks > L->cblocks ? L->sblocks : L->cblocks;
+  L->part = b.take((size_t)(d - 1) * mb * 3 * 8);
+  L->total = (b.off + 255) & ~(size_t)255;
+}
+
+extern "C" int ttq_workspace_bytes(const ttq_problem *p, size_t *bytes) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!bytes) return set_err(TTQ_ERR_INVALID_ARG, "null bytes");
+  Layout L;
+  make_layout(p, &L);
+  *bytes = L.total;
+  return TTQ_OK;
+}
+
+static bool uniform_pair_table(const ttq_problem *p, const std::vector<double> &x) {
+  if (p->family != TTQ_FAMILY_D || p->form != TTQ_FORM_RN) return false;
+  const int d = p->d, N = p->nodes_per_mode[0];
+  for (int k = 1; k < d; ++k) {
+    if (p->nodes_per_mode[k] != N) return false;
+    for (int i = 0; i < N; ++i)
+      if (x[(size_t)k * N + i] != x[i]) return false;
+  }
+  // every difference x[a] - x[b] must equal +-(x[|a-b|] - x[0]) exactly
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      double dlt = x[a] - x[b];
+      double ref = (a >= b) ? (x[a - b] - x[0]) : -(x[b - a] - x[0]);
+      if (dlt != ref) return false;
+    }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+
+extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t bytes, void *stream, ttq_plan **out) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!out) return set_err(TTQ_ERR_INVALID_ARG, "null out");
+  Layout L;
+  make_layout(p, &L);
+  if (!workspace || bytes < L.total || ((uintptr_t)workspace & 255))
+    return set_err(TTQ_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
+  const int d = p->d;
+  size_t sumN = 0;
+  for (int k = 0; k < d; ++k) sumN += p->nodes_per_mode[k];
+  std::vector<double> hx(sumN), hw(sumN);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->inputs_on_device) {
+    CK(cudaMemcpyAsync(hx.data(), p->nodes, sumN * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hw.data(), p->weights, sumN * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    memcpy(hx.data(), p->nodes, sumN * 8);
+    memcpy(hw.data(), p->weights, sumN * 8);
+  }
+  for (size_t q = 0; q < sumN; ++q)
+    if (!isfinite(hx[q]) || !isfinite(hw[q])) return set_err(TTQ_ERR_INVALID_ARG, "non-finite node or weight");
+
+  ttq_plan *P = new ttq_plan();
+  char *base = (char *)workspace;
+  Dev &D = P->h;
+  memset(&D, 0, sizeof(D));
+  D.d = d; D.family = p->family; D.form = p->form; D.n = p->n; D.cap = p->rank_cap;
+  D.rook_max = p->rook_max; D.init_samples = p->init_samples; D.conv_window = p->conv_window;
+  D.max_sweeps = p->max_sweeps; D.prec = p->precision;
+  D.tol = p->tol; D.pivot_tol = p->pivot_tol; D.seed = p->seed;
+  if (p->family == TTQ_FAMILY_TEST) D.constant = 1.0;
+  else if (p->form == TTQ_FORM_RN) { double f = 1.0; for (int q = 2; q <= p->n; ++q) f *= q; D.constant = 4.0 / f; }
+  else D.constant = 2.0;
+  D.uniformT = uniform_pair_table(p, hx) ? 1 : 0;
+  D.sblocks = L.sblocks; D.cblocks = L.cblocks; D.rblocks = L.rblocks;
+  int off = 0;
+  for (int k = 0; k < d; ++k) { D.N[k] = p->nodes_per_mode[k]; D.off[k] = off; off += D.N[k]; }
+  for (int k = 1; k < d; ++k) D.S[k] = samples_for(p, k);
+  for (int k = 0; k <= d; ++k) D.capL[k] = (k == 0 || k == d) ? 1 : p->rank_cap;
+  D.x = (const double *)(base + L.x); D.w = (const double *)(base + L.w);
+  D.c = (const double *)(base + L.c); D.T = (const double *)(base + L.T);
+  for (int k = 1; k < d; ++k) {
+    D.lidx[k] = (int *)(base + L.lidx[k]); D.ridx[k] = (int *)(base + L.ridx[k]);
+    D.lpar[k] = (int *)(base + L.lpar[k]); D.lnode[k] = (int *)(base + L.lnode[k]);
+    D.rpar[k] = (int *)(base + L.rpar[k]); D.rnode[k] = (int *)(base + L.rnode[k]);
+    D.Qr[k] = (double *)(base + L.Qr[k]); D.Qc[k] = (double *)(base + L.Qc[k]);
+    D.Rc[k] = (double *)(base + L.Rc[k]); D.Rr[k] = (double *)(base + L.Rr[k]);
+    D.rinv[k] = (double *)(base + L.rinv[k]); D.zvec[k] = (double *)(base + L.zvec[k]);
+    D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
+  }
+  for (int k = 1; k <= d; ++k) {
+    D.Y[k] = (double *)(base + L.Y[k]); D.V[k] = (double *)(base + L.V[k]); D.Vlo[k] = (double *)(base + L.Vlo[k]);
+  }
+  D.part = (double *)(base + L.part);
+  D.st = (State *)(base + L.st);
+  P->dev = (Dev *)(base + L.dev);
+  P->st = D.st;
+  P->stream = s;
+  P->launches = 0;
+  size_t maxfib = 0;
+  for (int k = 1; k <= d; ++k) maxfib += (size_t)D.capL[k - 1] * D.capL[k];
+  size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
+  P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
+  P->qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + p->rank_cap) * 8);
+  if (cudaMallocHost((void **)&P->hst, sizeof(State)) != cudaSuccess) {
+    delete P;
+    return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
+  }
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpyAsync(base + L.x, hx.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpyAsync(base + L.w, hw.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
+  P->h2d += (long long)(2 * sumN * 8 + sizeof(Dev));
+  if (p->inputs_on_device) P->d2h += (long long)(2 * sumN * 8);
+  if ((e = cudaMemsetAsync(D.st, 0, sizeof(State), s)) != cudaSuccess) goto fail;
+  if ((e = cudaMemsetAsync(D.part, 0, (size_t)(d - 1) * (L.sblocks > L.cblocks ? L.sblocks : L.cblocks) * 24, s)) != cudaSuccess) goto fail;
+  if ((e = cudaMemcpyAsync(P->dev, &D, sizeof(Dev), cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
+  timed(P, KT_SETUP, [&] { k_setup<<<(int)((sumN + 255) / 256), 256, 0, s>>>(P->dev, (int)sumN); });
+  if ((e = cudaGetLastError()) != cudaSuccess) goto fail;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto fail;
+  *out = P;
+  return TTQ_OK;
+fail:
+  g_last_error = std::string("plan setup: ") + cudaGetErrorString(e);
+  cudaFreeHost(P->hst);
+  delete P;
+  return TTQ_ERR_CUDA;
+}
+
+extern "C" int ttq_plan_destroy(ttq_plan *P) {
+  if (!P) return TTQ_OK;
+  if (!P->pending.empty()) cudaStreamSynchronize(P->stream);
+  harvest(P);
+  for (cudaEvent_t e : P->pool) cudaEventDestroy(e);
+  cudaFreeHost(P->hst);
+  delete P;
+  return TTQ_OK;
+}
+
+static int launch_sweep(ttq_plan *P) {
+  const Dev &D = P->h;
+  cudaStream_t s = P->stream;
+  const int ni = D.d - 1;
+  Dev *dv = P->dev;
+  timed(P, KT_EVAL, [&] { k_eval_slabs<<<P->grid_eval, TTQ_WARPS * 32, 0, s>>>(dv); });
+  timed(P, KT_QR, [&] { k_qr<<<ni, 256, P->qr_smem, s>>>(dv); });
+  timed(P, KT_CONTRACT, [&] { k_contract<<<1, 32, 0, s>>>(dv); });
+  timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(D.sblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
+  for (int q = 0; q < D.rook_max; ++q) {
+    timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(D.cblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
+    timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(D.rblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
+  }
+  timed(P, KT_UPDATE, [&] { k_update<<<1, 32, 0, s>>>(dv); });
+  CK(cudaGetLastError());
+  return TTQ_OK;
+}
+
+static int read_state(ttq_plan *P) {
+  CK(cudaMemcpyAsync(P->hst, P->st, sizeof(State), cudaMemcpyDeviceToHost, P->stream));
+  P->d2h += sizeof(State);
+  CK(cudaStreamSynchronize(P->stream));
+  harvest(P);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_init(ttq_plan *P) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  timed(P, KT_INIT, [&] { k_init<<<1, TTQ_WARPS * 32, 0, P->stream>>>(P->dev); });
+  CK(cudaGetLastError());
+  return TTQ_OK;
+}
+
+static void fill_result(const ttq_plan *P, ttq_result *out) {
+  const State &S = *P->hst;
+  const Dev &D = P->h;
+  out->value = S.value;
+  out->value_lo = S.value_lo;
+  out->internal_conv = S.conv;
+  long long core = 0;
+  int mr = 0;
+  for (int k = 1; k <= D.d; ++k) core += (long long)S.r[k - 1] * D.N[k - 1] * S.r[k];
+  for (int k = 0; k <= D.d; ++k) mr = S.r[k] > mr ? S.r[k] : mr;
+  out->n_eval = core + S.search_evals + S.init_evals;
+  out->sweeps = S.nchanges + 1;
+  out->max_rank = mr;
+  out->status = S.status;
+  out->reserved = 0;
+}
+
+extern "C" int ttq_plan_run(ttq_plan *P, ttq_result *out) {
+  if (!P || !out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  int rc = ttq_plan_init(P);
+  if (rc) return rc;
+  k_begin<<<1, 1, 0, P->stream>>>(P->dev, 0, 1, 1);
+  P->launches++;
+  CK(cudaGetLastError());
+  const int batch = 2;
+  for (int s = 0; s < P->h.max_sweeps; s += batch) {
+    for (int b = 0; b < batch; ++b)
+      if ((rc = launch_sweep(P))) return rc;
+    CK(cudaMemcpyAsync(&P->hst->stop, &P->st->stop, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    P->d2h += sizeof(int);
+    CK(cudaStreamSynchronize(P->stream));
+    harvest(P);
+    if (P->hst->stop) break;
+  }
+  if ((rc = read_state(P))) return rc;
+  fill_result(P, out);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *value, double *value_lo,
+                              ttq_pivot *pivots) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  k_begin<<<1, 1, 0, P->stream>>>(P->dev, sweep_index, 0, search ? 1 : 0);
+  P->launches++;
+  int rc = launch_sweep(P);
+  if (rc) return rc;
+  if ((rc = read_state(P))) return rc;
+  const State &S = *P->hst;
+  if (value) *value = S.value;
+  if (value_lo) *value_lo = S.value_lo;
+  if (pivots) {
+    for (int k = 1; k < P->h.d; ++k) {
+      const IfaceState &I = S.it[k];
+      ttq_pivot &pv = pivots[k - 1];
+      pv.k = k;
+      pv.searched = I.active;
+      pv.row = I.row;
+      pv.col = I.col;
+      pv.err = I.err;
+      pv.accepted = I.accepted;
+      pv.rounds = I.rounds;
+      pv.evals = (int64_t)I.evals;
+    }
+  }
+  if (S.status < 0) return set_err(S.status, S.status == ST_ERR_SINGULAR ? "singular cross matrix" : "non-finite integrand");
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_set_state(ttq_plan *P, const int32_t *ranks, const int32_t *lpar, const int32_t *lnode,
+                                  const int32_t *rpar, const int32_t *rnode) {
+  if (!P || !ranks || !lpar || !lnode || !rpar || !rnode) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  const Dev &D = P->h;
+  const int d = D.d;
+  if (ranks[0] != 1 || ranks[d] != 1) return set_err(TTQ_ERR_INVALID_ARG, "ranks[0] and ranks[d] must be 1");
+  std::vector<std::vector<int>> L(d + 1), R(d + 2);
+  L[0] = std::vector<int>();
+  size_t o = 0;
+  std::vector<size_t> offs(d + 1, 0);
+  for (int k = 1; k < d; ++k) {
+    if (ranks[k] < 1 || ranks[k] > D.cap) return set_err(TTQ_ERR_INVALID_ARG, "rank out of range");
+    offs[k] = o;
+    o += ranks[k];
+  }
+  // rebuild the full multi-index rows and validate nestedness
+  std::vector<std::vector<int>> lrows(d + 1), rrows(d + 2);
+  lrows[0] = std::vector<int>(d, -1);
+  for (int k = 1; k < d; ++k) {
+    lrows[k].assign((size_t)ranks[k] * d, -1);
+    for (int a = 0; a < ranks[k]; ++a) {
+      int par = lpar[offs[k] + a], nd = lnode[offs[k] + a];
+      if (par < 0 || par >= ranks[k - 1] || nd < 0 || nd >= D.N[k - 1]) return set_err(TTQ_ERR_INVALID_ARG, "bad left parent");
+      for (int m = 0; m < k - 1; ++m) lrows[k][(size_t)a * d + m] = lrows[k - 1][(size_t)par * d + m];
+      lrows[k][(size_t)a * d + k - 1] = nd;
+    }
+  }
+  rrows[d] = std::vector<int>(d, -1);
+  for (int k = d - 1; k >= 1; --k) {
+    rrows[k].assign((size_t)ranks[k] * d, -1);
+    for (int b = 0; b < ranks[k]; ++b) {
+      int par = rpar[offs[k] + b], nd = rnode[offs[k] + b];
+      if (par < 0 || par >= ranks[k + 1] || nd < 0 || nd >= D.N[k]) return set_err(TTQ_ERR_INVALID_ARG, "bad right parent");
+      rrows[k][(size_t)b * d + k] = nd;
+      for (int m = k + 1; m < d; ++m) rrows[k][(size_t)b * d + m] = rrows[k + 1][(size_t)par * d + m];
+    }
+  }
+  cudaStream_t s = P->stream;
+  for (int k = 1; k < d; ++k) {
+    CK(cudaMemcpyAsync(D.lidx[k], lrows[k].data(), lrows[k].size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.ridx[k], rrows[k].data(), rrows[k].size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.lpar[k], lpar + offs[k], ranks[k] * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.lnode[k], lnode + offs[k], ranks[k] * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.rpar[k], rpar + offs[k], ranks[k] * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(D.rnode[k], rnode + offs[k], ranks[k] * 4, cudaMemcpyHostToDevice, s));
+  }
+  State *h = P->hst;
+  memset(h, 0, sizeof(State));
+  for (int k = 0; k <= d; ++k) { h->r[k] = ranks[k]; h->ro[k] = 0; }
+  h->conv = INFINITY;
+  CK(cudaMemcpyAsync(P->st, h, sizeof(State), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_get_state(ttq_plan *P, int32_t *ranks, int32_t *lpar, int32_t *lnode, int32_t *rpar,
+                                  int32_t *rnode) {
+  if (!P || !ranks) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  int rc = read_state(P);
+  if (rc) return rc;
+  const Dev &D = P->h;
+  const int d = D.d;
+  for (int k = 0; k <= d; ++k) ranks[k] = P->hst->r[k];
+  size_t o = 0;
+  for (int k = 1; k < d; ++k) {
+    int r = ranks[k];
+    if (lpar) CK(cudaMemcpy(lpar + o, D.lpar[k], r * 4, cudaMemcpyDeviceToHost));
+    if (lnode) CK(cudaMemcpy(lnode + o, D.lnode[k], r * 4, cudaMemcpyDeviceToHost));
+    if (rpar) CK(cudaMemcpy(rpar + o, D.rpar[k], r * 4, cudaMemcpyDeviceToHost));
+    if (rnode) CK(cudaMemcpy(rnode + o, D.rnode[k], r * 4, cudaMemcpyDeviceToHost));
+    o += r;
+  }
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_get_core(ttq_plan *P, int k, double *host_out) {
+  if (!P || !host_out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  const Dev &D = P->h;
+  if (k < 1 || k > D.d) return set_err(TTQ_ERR_INVALID_ARG, "k out of range");
+  int rc = read_state(P);
+  if (rc) return rc;
+  const int rl = P->hst->ro[k - 1], rr = P->hst->ro[k], Nk = D.N[k - 1];
+  std::vector<double> buf((size_t)D.capL[k - 1] * Nk * D.capL[k]);
+  CK(cudaMemcpy(buf.data(), D.Y[k], buf.size() * 8, cudaMemcpyDeviceToHost));
+  for (int a = 0; a < rl; ++a)
+    for (int i = 0; i < Nk; ++i)
+      for (int b = 0; b < rr; ++b)
+        host_out[((size_t)a * Nk + i) * rr + b] = buf[((size_t)b * D.capL[k - 1] + a) * Nk + i];
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_eval_points(ttq_plan *P, const int32_t *idx, int64_t npts, double *out) {
+  if (!P || (!idx && npts) || (!out && npts) || npts < 0) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
+  if (npts == 0) return TTQ_OK;
+  long long blocks = (npts + TTQ_WARPS - 1) / TTQ_WARPS;
+  if (blocks > 4096) blocks = 4096;
+  k_eval_points<<<(int)blocks, TTQ_WARPS * 32, 0, P->stream>>>(P->dev, idx, npts, out);
+  P->launches++;   // not part of a sweep: counted, not timed
+  CK(cudaGetLastError());
+  return TTQ_OK;
+}
+
+extern "C" int64_t ttq_plan_launches(const ttq_plan *P) { return P ? P->launches : 0; }
+
+extern "C" int ttq_plan_transfer_bytes(const ttq_plan *P, int64_t *h2d, int64_t *d2h) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (h2d) *h2d = P->h2d;
+  if (d2h) *d2h = P->d2h;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_set_timing(ttq_plan *P, int enable) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  P->timing = enable ? 1 : 0;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_kernel_times(ttq_plan *P, double *ms, int64_t *launches, double *flops, int reset) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  int rc = read_state(P);               // synchronizes and harvests the pending events
+  if (rc) return rc;
+  for (int q = 0; q < KT_N; ++q) {
+    if (ms) ms[q] = P->kt_ms[q];
+    if (launches) launches[q] = P->kt_n[q];
+    if (flops) flops[q] = (double)P->hst->flops[q];
+    if (reset) { P->kt_ms[q] = 0.0; P->kt_n[q] = 0; }
+  }
+  return TTQ_OK;
+}
+
+extern "C" const char *ttq_status_string(int s) {
+  switch (s) {
+    case TTQ_OK: return "ok (converged)";
+    case TTQ_WARN_NO_PIVOT: return "stopped: no pivot accepted";
+    case TTQ_WARN_RANK_CAP: return "stopped: rank cap reached on every interface";
+    case TTQ_WARN_MAX_SWEEPS: return "stopped: sweep limit reached";
+    case TTQ_PENDING: return "pending";
+    case TTQ_ERR_INVALID_ARG: return "invalid argument";
+    case TTQ_ERR_NONFINITE: return "non-finite integrand value";
+    case TTQ_ERR_SINGULAR: return "singular cross matrix";
+    case TTQ_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case TTQ_ERR_CUDA: return "CUDA error";
+    case TTQ_ERR_ADMISSION: return "request exceeds the memory budget";
+    case TTQ_ERR_NOT_FOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char *ttq_last_error(void) { return g_last_error.c_str(); }

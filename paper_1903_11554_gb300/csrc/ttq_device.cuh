@@ -1,0 +1,373 @@
+// Device-side data layout and building blocks of the TT-cross quadrature.
+//
+// Layout of one plan in HBM (all inside the caller's workspace):
+//   node tables   x[sum N], w[sum N], c[sum N] (2cosh s for the R^n form),
+//                 T[N] = tanh^2(m h / 2) when every mode shares one uniform grid
+//   index sets    per interface k = 1..d-1, capacity `cap` rows:
+//                 lidx[k][a*d + m], m < k        node indices of I<=k (modes 1..k)
+//                 ridx[k][b*d + m], m >= k       node indices of I>k  (modes k+1..d)
+//                 lpar/lnode, rpar/rnode         parent-pointer form (Eq. 4)
+//   cores         Y_k(alpha, i, beta) at ((beta * capL[k-1] + alpha) * N_k + i):
+//                 the fiber matrix L_k = (r_{k-1} N_k) x r_k is column-major with
+//                 leading dimension capL[k-1] * N_k, so a warp with lanes over
+//                 the node index i reads and writes contiguous memory
+//   node sums     V_k(alpha, beta) = sum_i Y_k(alpha, i, beta)  (+ double-double tail)
+//   QR factors    of the cross matrix G_k = A(I<=k, I>k), r_k x r_k, ld = cap:
+//                 Qr (row-major), Qc (col-major), Rc (col-major), Rr (row-major), 1/R_jj
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define TTQ_MAXD 32
+#define TTQ_MAXR 128
+#define TTQ_WARPS 8                      // warps per CTA in the fiber kernels
+#define TTQ_CHUNK 128                    // nodes per work item in the rook kernels
+#define TTQ_TIE_REL 1e-10                // Alg. 2 argmax: |E| >= max - (REL*max + ABS*scale) is a tie
+#define TTQ_TIE_ABS 1e-14
+#define TTQ_MAXPAIR 288                  // varying pairs of one cube-form fiber, <= (n/2)^2 for n <= 33
+
+namespace ttq {
+
+enum { FAM_C = 0, FAM_D = 1, FAM_E = 2, FAM_TEST = 3 };
+enum { FORM_RN = 0, FORM_CUBE = 1 };
+
+// status codes, mirror include/ttq.h
+enum { ST_OK = 0, ST_NO_PIVOT = 1, ST_RANK_CAP = 2, ST_MAX_SWEEPS = 3,
+       ST_ERR_NONFINITE = -2, ST_ERR_SINGULAR = -3 };
+
+struct IfaceState {
+  int active;          // a pivot search is running on this interface this sweep
+  int rook_done;       // rook condition met
+  int row, col;        // current rook position (rho, gamma)
+  int rounds;
+  int accepted;
+  double err;          // residual at (row, col)
+  unsigned int counter;// last-CTA-done counter of the running reduction
+  int pad;
+  unsigned long long evals;   // integrand evaluations of this sweep's search
+};
+
+struct State {
+  int r[TTQ_MAXD + 1];      // current ranks, r[0] = r[d] = 1
+  int ro[TTQ_MAXD + 1];     // ranks whose core entries are already evaluated
+  int sweep;
+  int status;               // ST_*
+  int stop;                 // 1: the run is over; later kernels of the sweep do nothing
+  int rules;                // 1: apply the stopping rules (full run); 0: stage calls
+  int search;               // 1: run the pivot search this sweep
+  int nonfinite;
+  int singular;
+  int nchanges;
+  unsigned long long scale_bits;   // max |core entry| as IEEE bits (non-negative)
+  double value, value_lo, prev, conv;
+  double changes[8];
+  long long search_evals;
+  long long init_evals;
+  unsigned long long flops[16];    // algorithmic FP64 operations per kernel id (see ttq.cu)
+  IfaceState it[TTQ_MAXD];
+};
+
+struct Dev {
+  int d, family, form, n, cap, rook_max, init_samples, conv_window, max_sweeps, prec;
+  int uniformT;             // 1: D in R^n on one shared uniform grid -> pair table T
+  int sblocks, cblocks, rblocks;   // CTAs per interface of the sample / column / row kernels
+  double tol, pivot_tol, constant;
+  unsigned long long seed;
+  int N[TTQ_MAXD], off[TTQ_MAXD], S[TTQ_MAXD];
+  int capL[TTQ_MAXD + 1];
+  const double *x, *w, *c, *T;
+  int *lidx[TTQ_MAXD], *ridx[TTQ_MAXD];
+  int *lpar[TTQ_MAXD], *lnode[TTQ_MAXD], *rpar[TTQ_MAXD], *rnode[TTQ_MAXD];
+  double *Y[TTQ_MAXD + 1];
+  double *V[TTQ_MAXD + 1], *Vlo[TTQ_MAXD + 1];
+  double *Qr[TTQ_MAXD], *Qc[TTQ_MAXD], *Rc[TTQ_MAXD], *Rr[TTQ_MAXD], *rinv[TTQ_MAXD];
+  double *zvec[TTQ_MAXD];   // per interface: G^{-1} y or G^{-T} l of the next rook step
+  double *cs[TTQ_MAXD];     // per interface: scores |E| of the current candidates (-1: not eligible)
+  double *ce[TTQ_MAXD];     // per interface: residuals E of the current candidates
+  double *part;             // reduction partials: [iface][block][3] (score, idx, value)
+  State *st;
+};
+
+// ---------------------------------------------------------------------------
+// warp helpers (fixed butterfly order: every lane gets the same, reproducible result)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// argmax with ties to the lowest index; score -1 marks "no candidate"
+struct Best {
+  double score;
+  int idx;
+  double val;
+};
+__device__ __forceinline__ bool better(double s1, int i1, double s2, int i2) {
+  return s1 > s2 || (s1 == s2 && i1 < i2);
+}
+__device__ __forceinline__ Best warp_best(Best b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double s = __shfl_xor_sync(0xffffffffu, b.score, o);
+    int i = __shfl_xor_sync(0xffffffffu, b.idx, o);
+    double v = __shfl_xor_sync(0xffffffffu, b.val, o);
+    if (better(s, i, b.score, b.idx)) { b.score = s; b.idx = i; b.val = v; }
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// double-double arithmetic (Dekker 1971; Knuth's TwoSum; TwoProd through FMA)
+
+struct dd { double hi, lo; };
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dd fast_two_sum(double a, double b) {
+  double s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_mul_d(dd a, double b) {
+  double p = a.hi * b;
+  double e = fma(a.hi, b, -p);
+  e = fma(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  double p = a.hi * b.hi;
+  double e = fma(a.hi, b.hi, -p);
+  e = fma(a.hi, b.lo, e);
+  e = fma(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_div_d(dd a, double b) {
+  double q1 = a.hi / b;
+  dd p = {q1 * b, fma(q1, b, -(q1 * b))};      // q1*b exactly
+  dd r = dd_add(a, {-p.hi, -p.lo});
+  double q2 = r.hi / b;
+  return fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ dd warp_sum_dd(dd v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    // combine in a lane-order-independent way: lower lane's value first
+    int lane = threadIdx.x & 31;
+    v = ((lane & o) == 0) ? dd_add(v, u) : dd_add(u, v);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): m-th output from state s is mix(s + m*GAMMA)
+
+__device__ __forceinline__ unsigned long long sm_mix(unsigned long long z) {
+  z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ULL;
+  z ^= z >> 27; z *= 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long sm_out(unsigned long long s, unsigned long long m) {
+  return sm_mix(s + m * 0x9E3779B97F4A7C15ULL);
+}
+__device__ __forceinline__ unsigned long long stream_id(int sweep, int k, int purpose) {
+  return ((unsigned long long)(unsigned)sweep << 32) | ((unsigned long long)(k & 0xFFFFFF) << 8) |
+         (unsigned long long)(purpose & 0xFF);
+}
+__device__ __forceinline__ int draw_index(unsigned long long seed, unsigned long long stream,
+                                          unsigned long long counter, unsigned long long M) {
+  unsigned long long s1 = sm_out(seed, 1);
+  unsigned long long s2 = sm_out(s1, stream + 1);
+  unsigned long long v = sm_out(s2, counter + 1);
+  return (int)__umul64hi(v, M);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// Fiber evaluation (kernel (a)'s core routine).
+//
+// One warp evaluates the weighted tensor A at the points that share every node
+// index except the free mode f: (m_0, .., m_{f-1}, i, m_{f+1}, .., m_{d-1}) for a
+// range of i.  The factors that do not involve mode f (the weights and node
+// terms of the other modes, and for D / E every pair of other modes) are the
+// same for the whole fiber; the warp computes them once, cooperatively (lanes
+// split the modes and pairs, butterfly reductions combine them), and each lane
+// then adds only the factors that involve its own node i.  Every entry is still
+// exactly the integrand at that point, up to rounding.
+
+struct FiberU {
+  double W;       // prod of weights of the other modes
+  double S;       // R^n: sum 2cosh s of other modes; TEST: sum of x
+  double P;       // product of the pair factors among the other modes
+  double aL, bL, aR, bR;   // unit-cube B_n: left/right sums as a + b * x_F
+  int npair;      // unit-cube A_n: number of pairs (i, j) whose product contains x_F
+  int fl_node;    // FP64 operations per node of this fiber (the lane-local part)
+  int fl_uniform; // FP64 operations of the fiber's shared part
+};
+
+// m: warp-uniform node indices (shared memory); plist: per-warp scratch of TTQ_MAXPAIR doubles
+__device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m, double *plist) {
+  const int lane = threadIdx.x & 31;
+  const int d = D.d;
+  FiberU u;
+  u.P = 1.0; u.S = 0.0; u.aL = u.bL = u.aR = u.bR = 0.0; u.npair = 0;
+  double wj = 1.0;
+  if (lane < d && lane != f) wj = D.w[D.off[lane] + m[lane]];
+  u.W = warp_prod(wj);
+  u.fl_uniform = d - 1;
+  if (D.family == FAM_TEST) {
+    double xj = (lane < d && lane != f) ? D.x[D.off[lane] + m[lane]] : 0.0;
+    u.S = warp_sum(xj);
+    u.fl_uniform += d - 1;
+    u.fl_node = 2 * D.n + 5;
+    return u;
+  }
+  if (D.form == FORM_RN) {
+    double cj = (lane < d && lane != f) ? D.c[D.off[lane] + m[lane]] : 0.0;
+    u.S = warp_sum(cj);
+    u.fl_uniform += d - 1;
+    u.fl_node = 5;
+    if (D.family == FAM_D) {
+      u.fl_node += d;
+      u.fl_uniform += (d - 1) * (d - 2) / 2 * (D.uniformT ? 1 : 4);
+      double p = 1.0;
+      if (lane < d && lane != f) {
+        for (int b = lane + 1; b < d; ++b) {
+          if (b == f) continue;
+          double t2;
+          if (D.uniformT) {
+            int dm = m[lane] - m[b];
+            t2 = D.T[dm < 0 ? -dm : dm];
+          } else {
+            double t = tanh((D.x[D.off[lane] + m[lane]] - D.x[D.off[b] + m[b]]) * 0.5);
+            t2 = t * t;
+          }
+          p *= t2;
+        }
+      }
+      u.P = warp_prod(p);
+    }
+    return u;
+  }
+  // unit cube: variable x_v (v = 2..n) lives in mode v-2; free variable F = f + 2
+  const int n = D.n, F = f + 2;
+#define XV(v) (D.x[D.off[(v) - 2] + m[(v) - 2]])
+  if (D.family == FAM_C || D.family == FAM_D) {
+    if (lane == 0) {
+      double p = 1.0, aL = 1.0;
+      for (int v = 2; v <= F - 1; ++v) { p *= XV(v); aL += p; }
+      double PL = p, t = 1.0;
+      p = 1.0;
+      for (int v = F + 1; v <= n; ++v) { p *= XV(v); t += p; }
+      double aR = 1.0;
+      p = 1.0;
+      for (int v = n; v >= F + 1; --v) { p *= XV(v); aR += p; }
+      double PR = p, h = 1.0;
+      p = 1.0;
+      for (int v = F - 1; v >= 2; --v) { p *= XV(v); h += p; }
+      u.aL = aL; u.bL = PL * t; u.aR = aR; u.bR = PR * h;
+    }
+    u.fl_uniform += 4 * n;
+    u.fl_node = 8;
+    u.aL = __shfl_sync(0xffffffffu, u.aL, 0);
+    u.bL = __shfl_sync(0xffffffffu, u.bL, 0);
+    u.aR = __shfl_sync(0xffffffffu, u.aR, 0);
+    u.bR = __shfl_sync(0xffffffffu, u.bR, 0);
+  }
+  if (D.family == FAM_D || D.family == FAM_E) {
+    // pairs 1 <= i < j <= n with p_ij = x_{i+1} ... x_j; lane handles row i = lane + 1
+    double pu = 1.0;
+    const int i = lane + 1;
+    const int width = n - F + 1;
+    if (i <= n - 1) {
+      double p = 1.0;
+      for (int j = i + 1; j <= n; ++j) {
+        if (j != F) p *= XV(j);
+        if (i < F && F <= j) {
+          plist[(i - 1) * width + (j - F)] = p;        // x_F * p is this pair's product
+        } else {
+          double q = (1.0 - p) / (1.0 + p);
+          pu *= q * q;
+        }
+      }
+    }
+    u.P = warp_prod(pu);
+    u.npair = (F - 1) * width;
+    u.fl_uniform += 6 * (n * (n - 1) / 2 - u.npair);
+    u.fl_node = (D.family == FAM_D ? 11 : 5) + 6 * u.npair;
+    __syncwarp();
+  }
+#undef XV
+  return u;
+}
+
+// value at node i of the free mode f (lane-local)
+__device__ __forceinline__ double fiber_value(const Dev &D, int f, const int *m, const FiberU &u,
+                                              const double *plist, int i) {
+  const int o = D.off[f] + i;
+  const double wi = D.w[o];
+  if (D.family == FAM_TEST) {
+    double e = exp(-(u.S + D.x[o]) / (double)D.d);
+    double g = 0.0;
+    for (int t = 0; t < D.n; ++t) g = (g + 1.0) * e;
+    return u.W * wi * g;
+  }
+  if (D.form == FORM_RN) {
+    double s = u.S + D.c[o];
+    double g = 1.0 / (s * s);
+    if (D.family == FAM_D) {
+      double p = u.P;
+      const int d = D.d;
+      if (D.uniformT) {
+        for (int j = 0; j < d; ++j) {
+          if (j == f) continue;
+          int dm = i - m[j];
+          p *= D.T[dm < 0 ? -dm : dm];
+        }
+      } else {
+        const double si = D.x[o];
+        for (int j = 0; j < d; ++j) {
+          if (j == f) continue;
+          double t = tanh((si - D.x[D.off[j] + m[j]]) * 0.5);
+          p *= t * t;
+        }
+      }
+      g *= p;
+    }
+    return u.W * wi * g;
+  }
+  const double xf = D.x[o];
+  double g = 1.0;
+  if (D.family == FAM_D || D.family == FAM_E) {
+    double num = 1.0, den = 1.0;
+    for (int t = 0; t < u.npair; ++t) {
+      double cx = plist[t];
+      num *= fma(-xf, cx, 1.0);
+      den *= fma(xf, cx, 1.0);
+    }
+    double q = num / den;
+    g = u.P * q * q;
+  }
+  if (D.family == FAM_C || D.family == FAM_D) {
+    g = g / ((u.aL + u.bL * xf) * (u.aR + u.bR * xf));
+  }
+  return u.W * wi * g;
+}
+
+}  // namespace ttq

@@ -62,7 +62,7 @@ class Problem:
     rank_cap: int = 16
     tol: float = 1e-12          # relative internal convergence of the integral
     pivot_tol: float = 1e-14    # a pivot is kept when |E*| > pivot_tol * max|core entry|
-    conv_window: int = 2        # sweeps in a row whose relative change must be <= tol
+    conv_window: int = 3        # sweeps in a row whose relative change must be <= tol
     max_sweeps: int = 0         # 0 -> rank_cap + 8
     seed: int = 1
     n_samples: int = 0          # random samples per interface; 0 -> N_k + N_{k+1}

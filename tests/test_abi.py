@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/ttq.h declares; the binding's struct layouts match the header (no GPU
+needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_1903_11554_gb300 import binding, build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ttq.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ttq_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists(build.LIB):
+        pytest.skip("no nvcc and no prebuilt library")
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for must in ("ttq_workspace_bytes", "ttq_plan_create", "ttq_plan_run", "ttq_plan_sweep",
+                 "ttq_plan_eval_points", "ttq_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    assert set(binding.SIGNATURES) >= set(declared_functions()) - set()
+
+
+def test_struct_sizes_match_c_layout():
+    # natural alignment of the C structs in include/ttq.h
+    assert ctypes.sizeof(binding.TTQProblem) == 96
+    assert ctypes.sizeof(binding.TTQResult) == 48
+    assert ctypes.sizeof(binding.TTQPivot) == 40
+
+
+def test_workspace_size_and_validation(lib):
+    p = inputs.config_d12()
+    nb = binding.workspace_bytes(p)
+    # cores of the 10 interior modes dominate: 64 * 385 * 64 doubles each
+    assert nb >= 10 * 64 * 385 * 64 * 8
+    assert nb % 256 == 0
+    bad = inputs.config_c4(rank_cap=500)
+    with pytest.raises(binding.TTQError):
+        binding.workspace_bytes(bad)
+    bad = inputs.make_problem("C", "rn", 4, 41, L=10.0)
+    bad.nodes = bad.nodes[:3]
+    bad.weights = bad.weights[:3]
+    with pytest.raises(binding.TTQError):
+        binding.workspace_bytes(bad)          # R^n form needs d == n
+
+
+def test_status_strings(lib):
+    for code in (0, 1, 2, 3, -1, -2, -3, -5):
+        assert lib.ttq_status_string(code)
