@@ -189,6 +189,27 @@ int ttq_plan_transfer_bytes(const ttq_plan *plan, int64_t *h2d, int64_t *d2h);
 int ttq_plan_set_timing(ttq_plan *plan, int enable);
 int ttq_plan_kernel_times(ttq_plan *plan, double *ms, int64_t *launches, double *flops, int reset);
 
+/* Whole integral without allocating anything, for callers that must not call
+ * cudaMalloc (code running under another component's memory pool or a fixed
+ * memory budget, plugins handed only a stream, paths that must not fail on
+ * allocation).  The paper has no counterpart: this is a deployment variant of
+ * ttq_plan_create + ttq_plan_run.
+ *  - Device scratch: one fixed array of TTQ_NOALLOC_SCRATCH_BYTES (16 MiB),
+ *    declared in the library, which every GPU that loads the library holds
+ *    until the process exits.  A problem whose plan needs more
+ *    (ttq_workspace_bytes) is rejected with TTQ_ERR_WORKSPACE.
+ *  - nodes/weights must be host arrays (inputs_on_device == 0).
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device uses the same scratch, which keeps the previous
+ *    call's contents (the call resets what it reads).  Calls that overlap on
+ *    the GPU (other streams, other host threads) race on it: serialize them.
+ *  - Blocks until the result is on the host.  Same result as
+ *    ttq_plan_create + ttq_plan_run on the same problem and stream. */
+#define TTQ_NOALLOC_SCRATCH_BYTES (16u << 20)
+int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_result *out);
+
 const char *ttq_status_string(int status);
 const char *ttq_last_error(void);
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "ttq_plan_transfer_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
     "ttq_plan_set_timing": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_kernel_times": (_c.c_int, [_vp, _dp, _c.POINTER(_c.c_int64), _dp, _c.c_int]),
+    "ttq_integrate_noalloc": (_c.c_int, [_c.POINTER(TTQProblem), _vp, _c.POINTER(TTQResult)]),
     "ttq_status_string": (_c.c_char_p, [_c.c_int]),
     "ttq_last_error": (_c.c_char_p, []),
 }

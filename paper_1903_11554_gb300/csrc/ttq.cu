@@ -578,3 +578,118 @@ extern "C" const char *ttq_status_string(int s) {
 }
 
 extern "C" const char *ttq_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Entry point for callers that cannot allocate device memory.
+//
+// Some callers are not allowed to call cudaMalloc: code that runs while another
+// component owns the device's memory pool (a framework's caching allocator or
+// a memory-capped serving process), plugins that are handed a stream and must
+// not grow the process footprint, or code paths that must not fail on
+// allocation at run time.  For them the library keeps one fixed scratch area
+// in device memory, declared below; every GPU that loads the library holds it
+// until the process exits.  This entry point allocates nothing (no cudaMalloc,
+// cudaFree, cudaMallocHost or allocating library routine): the plan, the host
+// copy of its state and the node checks live on the stack, and the device
+// scratch is this array.
+// size: TTQ_NOALLOC_SCRATCH_BYTES (16 MiB), include/ttq.h
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TTQ_NOALLOC_SCRATCH_BYTES];
+static void *g_noalloc_ptr[256];           // device address of the scratch, per device id
+
+static bool uniform_pair_table_host(const ttq_problem *p, const double *x) {
+  if (p->family != TTQ_FAMILY_D || p->form != TTQ_FORM_RN) return false;
+  const int d = p->d, N = p->nodes_per_mode[0];
+  for (int k = 1; k < d; ++k) {
+    if (p->nodes_per_mode[k] != N) return false;
+    for (int i = 0; i < N; ++i)
+      if (x[(size_t)k * N + i] != x[i]) return false;
+  }
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      double dlt = x[a] - x[b];
+      double ref = (a >= b) ? (x[a - b] - x[0]) : -(x[b - a] - x[0]);
+      if (dlt != ref) return false;
+    }
+  return true;
+}
+
+extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_result *out) {
+  int rc = validate(p);
+  if (rc) return rc;
+  if (!out) return set_err(TTQ_ERR_INVALID_ARG, "null result");
+  if (p->inputs_on_device) return set_err(TTQ_ERR_INVALID_ARG, "ttq_integrate_noalloc takes host nodes and weights");
+  Layout L;
+  make_layout(p, &L);
+  if (L.total > TTQ_NOALLOC_SCRATCH_BYTES)
+    return set_err(TTQ_ERR_WORKSPACE, "problem needs more device scratch than the 16 MiB the "
+                                      "no-allocation entry point holds; use ttq_plan_create");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return set_err(TTQ_ERR_INVALID_ARG, "device id out of range");
+  if (!g_noalloc_ptr[dev]) {                // first call on this device: look up the scratch address
+    void *ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  char *base = (char *)g_noalloc_ptr[dev];
+  const int d = p->d;
+  size_t sumN = 0;
+  for (int k = 0; k < d; ++k) sumN += p->nodes_per_mode[k];
+  for (size_t q = 0; q < sumN; ++q)
+    if (!isfinite(p->nodes[q]) || !isfinite(p->weights[q])) return set_err(TTQ_ERR_INVALID_ARG, "non-finite node or weight");
+
+  ttq_plan P{};                             // on the stack, zeroed; its vectors stay empty (timing off)
+  State host_state;
+  Dev &D = P.h;
+  memset(&D, 0, sizeof(D));
+  D.d = d; D.family = p->family; D.form = p->form; D.n = p->n; D.cap = p->rank_cap;
+  D.rook_max = p->rook_max; D.init_samples = p->init_samples; D.conv_window = p->conv_window;
+  D.max_sweeps = p->max_sweeps; D.prec = p->precision;
+  D.tol = p->tol; D.pivot_tol = p->pivot_tol; D.seed = p->seed;
+  if (p->family == TTQ_FAMILY_TEST) D.constant = 1.0;
+  else if (p->form == TTQ_FORM_RN) { double f = 1.0; for (int q = 2; q <= p->n; ++q) f *= q; D.constant = 4.0 / f; }
+  else D.constant = 2.0;
+  D.uniformT = uniform_pair_table_host(p, p->nodes) ? 1 : 0;
+  D.sblocks = L.sblocks; D.cblocks = L.cblocks; D.rblocks = L.rblocks;
+  int off = 0;
+  for (int k = 0; k < d; ++k) { D.N[k] = p->nodes_per_mode[k]; D.off[k] = off; off += D.N[k]; }
+  for (int k = 1; k < d; ++k) D.S[k] = samples_for(p, k);
+  for (int k = 0; k <= d; ++k) D.capL[k] = (k == 0 || k == d) ? 1 : p->rank_cap;
+  D.x = (const double *)(base + L.x); D.w = (const double *)(base + L.w);
+  D.c = (const double *)(base + L.c); D.T = (const double *)(base + L.T);
+  for (int k = 1; k < d; ++k) {
+    D.lidx[k] = (int *)(base + L.lidx[k]); D.ridx[k] = (int *)(base + L.ridx[k]);
+    D.lpar[k] = (int *)(base + L.lpar[k]); D.lnode[k] = (int *)(base + L.lnode[k]);
+    D.rpar[k] = (int *)(base + L.rpar[k]); D.rnode[k] = (int *)(base + L.rnode[k]);
+    D.Qr[k] = (double *)(base + L.Qr[k]); D.Qc[k] = (double *)(base + L.Qc[k]);
+    D.Rc[k] = (double *)(base + L.Rc[k]); D.Rr[k] = (double *)(base + L.Rr[k]);
+    D.rinv[k] = (double *)(base + L.rinv[k]); D.zvec[k] = (double *)(base + L.zvec[k]);
+    D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
+  }
+  for (int k = 1; k <= d; ++k) {
+    D.Y[k] = (double *)(base + L.Y[k]); D.V[k] = (double *)(base + L.V[k]); D.Vlo[k] = (double *)(base + L.Vlo[k]);
+  }
+  D.part = (double *)(base + L.part);
+  D.st = (State *)(base + L.st);
+  P.dev = (Dev *)(base + L.dev);
+  P.st = D.st;
+  P.stream = (cudaStream_t)stream;
+  P.hst = &host_state;
+  size_t maxfib = 0;
+  for (int k = 1; k <= d; ++k) maxfib += (size_t)D.capL[k - 1] * D.capL[k];
+  size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
+  P.grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
+  P.qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + p->rank_cap) * 8);
+  cudaStream_t s = P.stream;
+  // the scratch keeps the previous call's contents: everything read before it is
+  // written (node tables, descriptor, state, reduction partials) is set here
+  CK(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P.qr_smem));
+  CK(cudaMemcpyAsync(base + L.x, p->nodes, sumN * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(base + L.w, p->weights, sumN * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(D.st, 0, sizeof(State), s));
+  CK(cudaMemsetAsync(D.part, 0, (size_t)(d - 1) * (L.sblocks > L.cblocks ? L.sblocks : L.cblocks) * 24, s));
+  CK(cudaMemcpyAsync(P.dev, &D, sizeof(Dev), cudaMemcpyHostToDevice, s));
+  k_setup<<<(int)((sumN + 255) / 256), 256, 0, s>>>(P.dev, (int)sumN);
+  CK(cudaGetLastError());
+  return ttq_plan_run(&P, out);
+}
