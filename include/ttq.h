@@ -48,7 +48,9 @@ typedef enum { TTQ_FORM_RN = 0, TTQ_FORM_CUBE = 1 } ttq_form;
 /* Arithmetic of the final contraction (Sec. 4.1): plain FP64, or double-double
  * node sums and chain products (compensated TwoSum / FMA-based TwoProd).  The
  * integrand, the QR of the cross matrices and the interface solves are FP64
- * in both modes. */
+ * in both modes.  In double-double mode the per-sweep values that drive the
+ * stopping rule are FP64 contractions; the reported value (and value_lo) is
+ * the double-double contraction of the final index sets. */
 typedef enum { TTQ_PREC_FP64 = 0, TTQ_PREC_DD = 1 } ttq_precision;
 
 typedef enum {
@@ -134,7 +136,10 @@ int ttq_plan_create(const ttq_problem *p, void *workspace, size_t bytes, void *s
 int ttq_plan_destroy(ttq_plan *plan);
 
 /* Full run: initial index set, then sweeps until a stopping rule fires
- * (Alg. 6 repeated).  Blocks until the result is on the host. */
+ * (Alg. 6 repeated).  Blocks until the result is on the host.  On a stream
+ * other than the legacy default stream, one sweep is captured once into a
+ * CUDA graph and replayed; the contraction runs on a second stream of the
+ * plan, beside the pivot search. */
 int ttq_plan_run(ttq_plan *plan, ttq_result *out);
 
 /* --- stage-level entry points (replay and inspection) ------------------- */
@@ -156,8 +161,10 @@ int ttq_plan_get_state(ttq_plan *plan, int32_t *ranks, int32_t *lpar, int32_t *l
 /* One sweep: evaluate the new core entries, factor the cross matrices,
  * contract the integral, then (search != 0) run Alg. 2 on every interface on
  * the sets of this sweep and append the accepted pivots (Alg. 6).  Writes the
- * sweep's integral to *value (and its double-double tail to *value_lo) and,
- * if pivots != NULL, d-1 ttq_pivot records.  No stopping rule is applied. */
+ * sweep's integral to *value and, if pivots != NULL, d-1 ttq_pivot records.
+ * In double-double mode with search == 0, *value / *value_lo are the
+ * double-double contraction; with search != 0 the FP64 one.  No stopping rule
+ * is applied. */
 int ttq_plan_sweep(ttq_plan *plan, int sweep_index, int search, double *value, double *value_lo,
                    ttq_pivot *pivots);
 
@@ -180,12 +187,12 @@ int ttq_plan_transfer_bytes(const ttq_plan *plan, int64_t *h2d, int64_t *d2h);
 /* Per-kernel timing.  With timing enabled every launch of a sweep is
  * bracketed by CUDA events on the plan's stream; ttq_plan_kernel_times writes,
  * for each of the TTQ_NUM_KERNELS kernels (index order: eval_slabs, qr,
- * contract, samples, rook_col, rook_row, update, init, setup), the summed
+ * contract, samples, rook_col, rook_row, update, init, setup, solve), the summed
  * device time in ms and the launch count since the last reset, and the
  * algorithmic FP64 operations the kernel has done since the plan's state was
  * last set (cumulative; a division, exp or cosh counts as one operation, an
  * FMA as two).  Any output array may be NULL.  Synchronizes the stream. */
-#define TTQ_NUM_KERNELS 9
+#define TTQ_NUM_KERNELS 10
 int ttq_plan_set_timing(ttq_plan *plan, int enable);
 int ttq_plan_kernel_times(ttq_plan *plan, double *ms, int64_t *launches, double *flops, int reset);
 

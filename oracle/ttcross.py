@@ -10,8 +10,8 @@ Follows the paper step by step:
     of the previous sweep, and all new pivots are appended after the sweep.
   * Alg. 2: random samples, then alternating column / row partial pivoting
     until the rook condition, Eq. (2), holds or the round budget is spent.
-  * The cross matrix is applied through QR: L_k = Q R, B_k = Q Q(P_k,:)^-1 =
-    L_k A(I_<=k, I_>k)^-1, the coefficient matrix of Alg. 1's first step.
+  * The coefficient matrix of Alg. 1's first step, B_k = L_k A(I_<=k, I_>k)^-1,
+    is one solve with the r_k x r_k cross matrix (LAPACK, partial pivoting).
   * The integral is the product of (2d-1) matrices of Sec. 4.1:
     (sum_i A(i, I_>1)) G_1^-1 (sum_i A(I_<=1, i, I_>2)) ... (sum_i A(I_<=d-1, i)).
 
@@ -199,13 +199,12 @@ def superblock_entries(problem, st: CrossState, k: int, rows: np.ndarray, cols: 
 # ---------------------------------------------------------------------------
 
 def maxvol_coefficients(Yk: np.ndarray, P: np.ndarray) -> np.ndarray:
-    """B_k = L_k A(I_<=k, I_>k)^-1 computed stably as Q Q(P,:)^-1 from the thin
-    QR of the fiber matrix L_k = Y_k as (r_{k-1} N_k) x r_k (Alg. 1, first step:
-    B(P, :) = identity)."""
+    """B_k = A(:, I_>k) A(I_<=k, I_>k)^-1 = L_k G_k^-1 with L_k = Y_k as
+    (r_{k-1} N_k) x r_k and G_k = L_k(P_k, :): the coefficient matrix of Alg. 1,
+    first step (B(P, :) = identity), as one LAPACK solve with the cross matrix."""
     r = Yk.shape[2]
     Lk = Yk.reshape(-1, r)
-    Q, _ = np.linalg.qr(Lk)
-    return np.linalg.solve(Q[P, :].T, Q.T).T
+    return np.linalg.solve(Lk[P, :].T, Lk.T).T
 
 
 def integral_plain(problem, st: CrossState, cores: List[np.ndarray]) -> float:

@@ -69,7 +69,8 @@ SIGNATURES = {
     "ttq_last_error": (_c.c_char_p, []),
 }
 
-KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup")
+KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup",
+           "solve")
 
 _lib = None
 
@@ -169,7 +170,10 @@ class Plan:
         if workspace is None:
             workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
         self.workspace = workspace
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        if stream is None:
+            stream = torch.cuda.Stream()
+            stream.wait_stream(torch.cuda.current_stream())     # the workspace allocation is ordered before use
+        self.stream = stream
         h = _vp()
         _check(self.lib.ttq_plan_create(_c.byref(self.struct), _vp(workspace.data_ptr()), self.nbytes,
                                         _vp(self.stream.cuda_stream), _c.byref(h)), "ttq_plan_create")
@@ -240,8 +244,13 @@ class Plan:
         import torch
         idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
         out = torch.empty(idx.shape[0], dtype=torch.float64, device="cuda")
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)                 # inputs ready before the plan's stream reads them
         _check(self.lib.ttq_plan_eval_points(self.h, _vp(idx.data_ptr()), idx.shape[0], _vp(out.data_ptr())),
                "ttq_plan_eval_points")
+        cur.wait_stream(self.stream)                 # results ready before torch reads them
+        idx.record_stream(self.stream)
+        out.record_stream(self.stream)
         return out
 
     def transfer_bytes(self):

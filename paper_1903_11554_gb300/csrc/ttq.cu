@@ -30,7 +30,8 @@ static int set_err(int code, const char *msg) {
   } while (0)
 
 // kernel ids of the timing counters (ttq_plan_kernel_times)
-enum { KT_EVAL = 0, KT_QR, KT_CONTRACT, KT_SAMPLES, KT_ROOK_COL, KT_ROOK_ROW, KT_UPDATE, KT_INIT, KT_SETUP, KT_N };
+enum { KT_EVAL = 0, KT_QR, KT_CONTRACT, KT_SAMPLES, KT_ROOK_COL, KT_ROOK_ROW, KT_UPDATE, KT_INIT, KT_SETUP,
+       KT_SOLVE, KT_N };
 
 struct TimedLaunch {
   int kid;
@@ -51,6 +52,15 @@ struct ttq_plan {
   double kt_ms[KT_N];
   long long kt_n[KT_N];
   long long h2d, d2h;       // bytes copied host<->device by this plan
+  cudaStream_t s2;          // side stream: the contraction runs beside the pivot search
+  cudaEvent_t fork, join;
+  int use_graph;            // replay one captured sweep graph (timing off)
+  cudaGraphExec_t sweep_exec;
+  cudaGraphExec_t run_exec; // whole run: WHILE(not stopped) { one sweep }
+  cudaGraphConditionalHandle cond;
+  int in_loop;              // enqueueing the body of the WHILE node
+  int sweep_kernels;        // kernels in one sweep
+  int samples_smem, contract_smem, solve_smem;
 };
 
 static cudaEvent_t ev_get(ttq_plan *P) {
@@ -66,18 +76,22 @@ static cudaEvent_t ev_get(ttq_plan *P) {
 
 // launch helper: counts the launch and, when timing, records events around it
 template <typename F>
-static void timed(ttq_plan *P, int kid, F &&launch) {
+static void timed_on(ttq_plan *P, cudaStream_t s, int kid, F &&launch) {
   if (P->timing) {
     TimedLaunch t{kid, ev_get(P), ev_get(P)};
-    cudaEventRecord(t.a, P->stream);
+    cudaEventRecord(t.a, s);
     launch();
-    cudaEventRecord(t.b, P->stream);
+    cudaEventRecord(t.b, s);
     P->pending.push_back(t);
   } else {
     launch();
   }
   P->launches++;
   P->kt_n[kid]++;
+}
+template <typename F>
+static void timed(ttq_plan *P, int kid, F &&launch) {
+  timed_on(P, P->stream, kid, launch);
 }
 
 // fold the completed launches' durations into the counters (stream must be idle)
@@ -227,6 +241,24 @@ static bool uniform_pair_table(const ttq_problem *p, const std::vector<double> &
 
 // ---------------------------------------------------------------------------
 
+static void set_smem_sizes(ttq_plan *P) {
+  const size_t cap = P->h.cap;
+  P->h.q_in_smem = cap <= 96 ? 1 : 0;
+  P->samples_smem = (int)((P->h.q_in_smem ? 2 : 1) * cap * cap * 8);
+  P->contract_smem = (int)(cap * cap * 8);
+  P->solve_smem = (int)(cap * cap * 8);
+}
+
+static cudaError_t set_smem_attributes(ttq_plan *P) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
+}
+
 extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t bytes, void *stream, ttq_plan **out) {
   int rc = validate(p);
   if (rc) return rc;
@@ -292,13 +324,18 @@ extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t byt
   for (int k = 1; k <= d; ++k) maxfib += (size_t)D.capL[k - 1] * D.capL[k];
   size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
   P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
-  P->qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + p->rank_cap) * 8);
+  P->qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + 4 * (size_t)p->rank_cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+4r
+  set_smem_sizes(P);
   if (cudaMallocHost((void **)&P->hst, sizeof(State)) != cudaSuccess) {
     delete P;
     return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
   }
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) goto fail;
+  if ((e = set_smem_attributes(P)) != cudaSuccess) goto fail;
+  if ((e = cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking)) != cudaSuccess) goto fail;
+  if ((e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming)) != cudaSuccess) goto fail;
+  if ((e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming)) != cudaSuccess) goto fail;
+  P->use_graph = s != nullptr ? 1 : 0;   // no capture on the legacy default stream
   if ((e = cudaMemcpyAsync(base + L.x, hx.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
   if ((e = cudaMemcpyAsync(base + L.w, hw.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
   P->h2d += (long long)(2 * sumN * 8 + sizeof(Dev));
@@ -313,6 +350,9 @@ extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t byt
   return TTQ_OK;
 fail:
   g_last_error = std::string("plan setup: ") + cudaGetErrorString(e);
+  if (P->s2) cudaStreamDestroy(P->s2);
+  if (P->fork) cudaEventDestroy(P->fork);
+  if (P->join) cudaEventDestroy(P->join);
   cudaFreeHost(P->hst);
   delete P;
   return TTQ_ERR_CUDA;
@@ -323,25 +363,105 @@ extern "C" int ttq_plan_destroy(ttq_plan *P) {
   if (!P->pending.empty()) cudaStreamSynchronize(P->stream);
   harvest(P);
   for (cudaEvent_t e : P->pool) cudaEventDestroy(e);
+  if (P->sweep_exec) cudaGraphExecDestroy(P->sweep_exec);
+  if (P->run_exec) cudaGraphExecDestroy(P->run_exec);
+  if (P->s2) { cudaStreamSynchronize(P->s2); cudaStreamDestroy(P->s2); }
+  if (P->fork) cudaEventDestroy(P->fork);
+  if (P->join) cudaEventDestroy(P->join);
   cudaFreeHost(P->hst);
   delete P;
   return TTQ_OK;
 }
 
-static int launch_sweep(ttq_plan *P) {
+// One sweep: eval -> qr -> { contract (side stream) | samples -> rook rounds } -> update.
+static void enqueue_sweep(ttq_plan *P) {
   const Dev &D = P->h;
   cudaStream_t s = P->stream;
   const int ni = D.d - 1;
   Dev *dv = P->dev;
   timed(P, KT_EVAL, [&] { k_eval_slabs<<<P->grid_eval, TTQ_WARPS * 32, 0, s>>>(dv); });
   timed(P, KT_QR, [&] { k_qr<<<ni, 256, P->qr_smem, s>>>(dv); });
-  timed(P, KT_CONTRACT, [&] { k_contract<<<1, 32, 0, s>>>(dv); });
-  timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(D.sblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
+  if (P->s2) {
+    cudaEventRecord(P->fork, s);
+    cudaStreamWaitEvent(P->s2, P->fork, 0);
+    timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->s2>>>(dv, 0); });
+    cudaEventRecord(P->join, P->s2);
+  } else {
+    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, s>>>(dv, 0); });
+  }
+  timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(D.sblocks, ni), TTQ_WARPS * 32, P->samples_smem, s>>>(dv); });
   for (int q = 0; q < D.rook_max; ++q) {
+    timed(P, KT_SOLVE, [&] { k_solve<<<ni, 256, P->solve_smem, s>>>(dv, 0); });
     timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(D.cblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
+    timed(P, KT_SOLVE, [&] { k_solve<<<ni, 256, P->solve_smem, s>>>(dv, 1); });
     timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(D.rblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
   }
-  timed(P, KT_UPDATE, [&] { k_update<<<1, 32, 0, s>>>(dv); });
+  if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
+  timed(P, KT_UPDATE, [&] { k_update<<<1, 32, 0, s>>>(dv, P->cond, P->in_loop); });
+}
+
+// Whole run as one graph: a conditional WHILE node whose body is one sweep;
+// k_update sets the condition, so a run needs no host round trip per sweep.
+static int build_run_graph(ttq_plan *P) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); g_last_error = std::string("conditional handle: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+  alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+  memset(npbuf, 0, sizeof(npbuf));
+  cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); g_last_error = std::string("while node: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const long long l0 = P->launches;
+  long long n0[KT_N];
+  memcpy(n0, P->kt_n, sizeof(n0));
+  P->cond = h;
+  P->in_loop = 1;
+  e = cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_sweep(P);
+    e = cudaStreamEndCapture(P->stream, &body);
+  }
+  P->in_loop = 0;
+  P->sweep_kernels = (int)(P->launches - l0);
+  P->launches = l0;
+  memcpy(P->kt_n, n0, sizeof(n0));
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->run_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { g_last_error = std::string("run graph: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+  return TTQ_OK;
+}
+
+static int launch_sweep(ttq_plan *P) {
+  if (P->use_graph && !P->timing) {
+    if (!P->sweep_exec) {
+      cudaGraph_t g = nullptr;
+      const long long l0 = P->launches;
+      long long n0[KT_N];
+      memcpy(n0, P->kt_n, sizeof(n0));
+      CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_sweep(P);
+      cudaError_t e = cudaStreamEndCapture(P->stream, &g);
+      if (e != cudaSuccess) { g_last_error = std::string("sweep capture: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+      P->sweep_kernels = (int)(P->launches - l0);
+      P->launches = l0;
+      memcpy(P->kt_n, n0, sizeof(n0));
+      e = cudaGraphInstantiate(&P->sweep_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { g_last_error = std::string("sweep graph: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+    }
+    CK(cudaGraphLaunch(P->sweep_exec, P->stream));
+    P->launches += P->sweep_kernels;
+    return TTQ_OK;
+  }
+  enqueue_sweep(P);
   CK(cudaGetLastError());
   return TTQ_OK;
 }
@@ -385,6 +505,19 @@ extern "C" int ttq_plan_run(ttq_plan *P, ttq_result *out) {
   k_begin<<<1, 1, 0, P->stream>>>(P->dev, 0, 1, 1);
   P->launches++;
   CK(cudaGetLastError());
+  if (P->use_graph && !P->timing) {
+    if (!P->run_exec && (rc = build_run_graph(P))) return rc;
+    CK(cudaGraphLaunch(P->run_exec, P->stream));
+    if ((rc = read_state(P))) return rc;
+    P->launches += (long long)P->sweep_kernels * P->hst->loop_guard;
+    if (P->h.prec) {
+      timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
+      CK(cudaGetLastError());
+      if ((rc = read_state(P))) return rc;
+    }
+    fill_result(P, out);
+    return TTQ_OK;
+  }
   const int batch = 2;
   for (int s = 0; s < P->h.max_sweeps; s += batch) {
     for (int b = 0; b < batch; ++b)
@@ -394,6 +527,10 @@ extern "C" int ttq_plan_run(ttq_plan *P, ttq_result *out) {
     CK(cudaStreamSynchronize(P->stream));
     harvest(P);
     if (P->hst->stop) break;
+  }
+  if (P->h.prec) {                          // double-double contraction of the final sets
+    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
+    CK(cudaGetLastError());
   }
   if ((rc = read_state(P))) return rc;
   fill_result(P, out);
@@ -407,6 +544,11 @@ extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *
   P->launches++;
   int rc = launch_sweep(P);
   if (rc) return rc;
+  if (P->h.prec && !search) {               // this sweep's sets, contracted in double-double
+    if (P->s2) CK(cudaStreamSynchronize(P->s2));
+    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
+    CK(cudaGetLastError());
+  }
   if ((rc = read_state(P))) return rc;
   const State &S = *P->hst;
   if (value) *value = S.value;
@@ -679,11 +821,12 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
   for (int k = 1; k <= d; ++k) maxfib += (size_t)D.capL[k - 1] * D.capL[k];
   size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
   P.grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
-  P.qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + p->rank_cap) * 8);
+  P.qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + 4 * (size_t)p->rank_cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+4r
   cudaStream_t s = P.stream;
   // the scratch keeps the previous call's contents: everything read before it is
   // written (node tables, descriptor, state, reduction partials) is set here
-  CK(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P.qr_smem));
+  set_smem_sizes(&P);
+  CK(set_smem_attributes(&P));
   CK(cudaMemcpyAsync(base + L.x, p->nodes, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(base + L.w, p->weights, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(D.st, 0, sizeof(State), s));

@@ -58,6 +58,10 @@ struct State {
   int nonfinite;
   int singular;
   int nchanges;
+  int stop_pending;         // a stopping rule fired in this sweep's contraction; applied by k_update
+  int loop_guard;           // sweeps run by the device-side loop of this run (bounded by max_sweeps)
+  int pending_status;
+  int qr_rank[TTQ_MAXD];    // size of the stored QR factors of G_k (0: none)
   unsigned long long scale_bits;   // max |core entry| as IEEE bits (non-negative)
   double value, value_lo, prev, conv;
   double changes[8];
@@ -71,6 +75,7 @@ struct Dev {
   int d, family, form, n, cap, rook_max, init_samples, conv_window, max_sweeps, prec;
   int uniformT;             // 1: D in R^n on one shared uniform grid -> pair table T
   int sblocks, cblocks, rblocks;   // CTAs per interface of the sample / column / row kernels
+  int q_in_smem;            // the sample kernel stages Q_k in shared memory too (cap <= 96)
   double tol, pivot_tol, constant;
   unsigned long long seed;
   int N[TTQ_MAXD], off[TTQ_MAXD], S[TTQ_MAXD];

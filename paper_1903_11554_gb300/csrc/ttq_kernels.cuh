@@ -23,40 +23,25 @@ __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 // ---------------------------------------------------------------------------
 // solves with the QR factors of G_k (one warp; buf/tmp: per-warp shared scratch)
 
-// buf <- G^{-1} buf  (G = Q R: Q^T y, then back substitution with R)
-__device__ void warp_col_solve(const Dev &D, int k, int r, double *buf, double *tmp) {
+// buf <- G^{-1} buf with factors staged in shared memory: Qs row-major (ld r)
+// or, if Qs == nullptr, Q from global; Rs column-major (ld r)
+__device__ void warp_col_solve_s(const Dev &D, int k, int r, const double *Qs, const double *Rs,
+                                 double *buf, double *tmp) {
   const int lane = lane_id(), ld = D.cap;
-  const double *Qr = D.Qr[k], *Rc = D.Rc[k], *ri = D.rinv[k];
+  const double *ri = D.rinv[k];
   for (int i = lane; i < r; i += 32) {
     double acc = 0.0;
-    for (int b = 0; b < r; ++b) acc = fma(Qr[b * ld + i], buf[b], acc);
+    if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], buf[b], acc);
+    else for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], buf[b], acc);
     tmp[i] = acc;
   }
   __syncwarp();
   for (int j = r - 1; j >= 0; --j) {
     double zj = tmp[j] * ri[j];
-    for (int i = lane; i < j; i += 32) tmp[i] = fma(-Rc[i + j * ld], zj, tmp[i]);
+    for (int i = lane; i < j; i += 32) tmp[i] = fma(-Rs[i + j * r], zj, tmp[i]);
     if (lane == 0) buf[j] = zj;
     __syncwarp();
   }
-}
-
-// buf <- G^{-T} buf  (forward substitution with R^T, then Q t)
-__device__ void warp_row_solve(const Dev &D, int k, int r, double *buf, double *tmp) {
-  const int lane = lane_id(), ld = D.cap;
-  const double *Qc = D.Qc[k], *Rr = D.Rr[k], *ri = D.rinv[k];
-  for (int i = 0; i < r; ++i) {
-    double ti = buf[i] * ri[i];
-    for (int j = i + 1 + lane; j < r; j += 32) buf[j] = fma(-Rr[i * ld + j], ti, buf[j]);
-    if (lane == 0) tmp[i] = ti;
-    __syncwarp();
-  }
-  for (int i = lane; i < r; i += 32) {
-    double acc = 0.0;
-    for (int j = 0; j < r; ++j) acc = fma(Qc[i + j * ld], tmp[j], acc);
-    buf[i] = acc;
-  }
-  __syncwarp();
 }
 
 // core entry Y_k(alpha, i, beta)
@@ -185,6 +170,8 @@ __global__ void k_init(Dev *Dp) {
     for (int k = 0; k <= d; ++k) { st->r[k] = 1; st->ro[k] = 0; }
     st->sweep = 0; st->status = ST_OK; st->stop = 0; st->nonfinite = 0; st->singular = 0;
     st->nchanges = 0; st->scale_bits = 0ULL; st->value = st->value_lo = st->prev = 0.0;
+    st->stop_pending = 0; st->pending_status = 0;
+    for (int k = 0; k < TTQ_MAXD; ++k) st->qr_rank[k] = 0;
     st->conv = __longlong_as_double(0x7ff0000000000000LL);
     st->search_evals = 0; st->init_evals = D.init_samples;
     if (!(c.score > 0.0)) { st->status = ST_ERR_NONFINITE; st->stop = 1; }
@@ -281,26 +268,43 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *Dp) {
   if (lane == 0 && fl) atomicAdd(&st->flops[0], fl);
 }
 
-// Kernel (b): Householder QR of G_k = A(I<=k, I>k) (r_k x r_k), one CTA per interface.
-// Stores Q (both orders), R (both orders) and 1/R_jj for the solves.
-__global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
-  const Dev &D = *Dp;
-  State *st = D.st;
-  if (st->stop) return;
-  extern __shared__ double sm[];
-  const int k = blockIdx.x + 1;
-  const int r = st->r[k];
-  const int ls = r + 1;                     // leading dimension in shared memory
-  double *G = sm;                           // r x ls, column-major
+// Kernel (b): QR factors G_k = Q R of every cross matrix G_k = A(I<=k, I>k)
+// (r_k x r_k), one CTA per interface.  G_k only grows by bordering: the pivot
+// interface k accepted in the previous sweep appends the last row (its new
+// element of I<=k) and the last column (its new element of I>k), and nothing
+// else changes.  The stored factors are then updated in O(r^2): r - 1 Givens
+// rotations fold the new row into R (Q gains a row and a column), and the new
+// column of R is Q'^T times the new column of G.  A full Householder QR
+// (O(r^3), LAPACK dgeqr2/dorg2r conventions) runs when no factors are stored
+// (first sweep, or index sets replaced from outside).
+// Stored: Q column-major (Qc) and row-major (Qr), R column- and row-major,
+// 1/R_jj; leading dimension cap.
+
+__device__ void qr_store_R(const Dev &D, int k, int r, const double *Rs, int lds, bool rowmajor) {
+  const int ld = D.cap;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    int i = e / r, j = e % r;
+    double v = (i <= j) ? (rowmajor ? Rs[i * lds + j] : Rs[i + j * lds]) : 0.0;
+    D.Rc[k][i + j * ld] = v;
+    D.Rr[k][i * ld + j] = v;
+  }
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    double rjj = rowmajor ? Rs[j * lds + j] : Rs[j + j * lds];
+    if (!(fabs(rjj) > 0.0) || !isfinite(rjj)) D.st->singular = 1;
+    D.rinv[k][j] = 1.0 / rjj;
+  }
+}
+
+__device__ void qr_full(const Dev &D, int k, int r, double *sm) {
+  const int ls = r + 1;
+  double *G = sm;
   double *tau = sm + (size_t)r * ls;
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
-  if (tid == 0) atomicAdd(&st->flops[1], (unsigned long long)(8.0 / 3.0 * r * (double)r * r));
   for (int e = tid; e < r * r; e += nt) {
     int a = e % r, b = e / r;
     G[a + b * ls] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], b)];
   }
   __syncthreads();
-  // factorization (LAPACK dgeqr2 / dlarfg conventions)
   for (int j = 0; j < r; ++j) {
     if (warp == 0) {
       double ss = 0.0;
@@ -331,25 +335,13 @@ __global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
     }
     __syncthreads();
   }
-  const int ld = D.cap;
-  for (int e = tid; e < r * r; e += nt) {
-    int i = e % r, j = e / r;
-    double v = (i <= j) ? G[i + j * ls] : 0.0;
-    D.Rc[k][i + j * ld] = v;
-    D.Rr[k][i * ld + j] = v;
-  }
-  for (int j = tid; j < r; j += nt) {
-    double rjj = G[j + j * ls];
-    if (!(fabs(rjj) > 0.0) || !isfinite(rjj)) st->singular = 1;
-    D.rinv[k][j] = 1.0 / rjj;
-  }
+  qr_store_R(D, k, r, G, ls, false);
   __syncthreads();
-  // form Q in place (LAPACK dorg2r)
   for (int j = r - 1; j >= 0; --j) {
     const double tj = tau[j];
     if (j < r - 1 && tj != 0.0) {
       for (int c = j + 1 + tid; c < r; c += nt) {
-        double w = G[j + c * ls];               // v_j = 1
+        double w = G[j + c * ls];
         for (int i = j + 1; i < r; ++i) w = fma(G[i + j * ls], G[i + c * ls], w);
         w *= tj;
         G[j + c * ls] -= w;
@@ -364,6 +356,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
     if (tid == 0) G[j + j * ls] = 1.0 - tj;
     __syncthreads();
   }
+  const int ld = D.cap;
   for (int e = tid; e < r * r; e += nt) {
     int i = e % r, j = e / r;
     double v = G[i + j * ls];
@@ -372,71 +365,181 @@ __global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
   }
 }
 
-// Kernel (c): contraction of the weighted cores with the inverse cross matrices
-// (Sec. 4.1), one warp; then the stopping rules.
-__global__ void k_contract(Dev *Dp) {
+// factors of the (r-1) x (r-1) leading block are stored; G gained row and column r-1
+__device__ void qr_border(const Dev &D, int k, int r, double *sm) {
+  const int n = r - 1, ls = r, ld = D.cap;
+  double *Rs = sm;                       // r x r row-major
+  double *h = Rs + (size_t)r * ls;       // new row of G, reduced by the rotations
+  double *cn = h + r;                    // new column of G (length r)
+  double *gc = cn + r;                   // rotation cosines
+  double *gs = gc + r;                   // rotation sines
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
+  const int anew = D.lpar[k][n], inew = D.lnode[k][n];
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, j = e % n;
+    Rs[i * ls + j] = D.Rr[k][i * ld + j];
+  }
+  for (int c = tid; c < n; c += nt) h[c] = D.Y[k][core_at(D, k, anew, inew, c)];
+  for (int a = tid; a < r; a += nt) cn[a] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], n)];
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < n; ++j) {
+      const double x = Rs[j * ls + j], y = h[j];
+      double c = 1.0, sn = 0.0, rho = x;
+      if (y != 0.0) {
+        rho = copysign(hypot(x, y), x);
+        const double inv = 1.0 / rho;
+        c = x * inv;
+        sn = y * inv;
+      }
+      for (int q = j + 1 + lane; q < n; q += 32) {
+        const double t1 = Rs[j * ls + q], t2 = h[q];
+        Rs[j * ls + q] = fma(c, t1, sn * t2);
+        h[q] = fma(-sn, t1, c * t2);
+      }
+      if (lane == 0) { Rs[j * ls + j] = rho; h[j] = 0.0; gc[j] = c; gs[j] = sn; }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // Q' = [[Q, 0], [0, 1]] J_0^T ... J_{n-1}^T, one row per thread
+  for (int i = tid; i < r; i += nt) {
+    double qlast = (i == n) ? 1.0 : 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double qa = (i < n) ? D.Qc[k][i + j * ld] : 0.0;
+      const double c = gc[j], sn = gs[j];
+      D.Qc[k][i + j * ld] = fma(c, qa, sn * qlast);
+      qlast = fma(-sn, qa, c * qlast);
+    }
+    D.Qc[k][i + n * ld] = qlast;
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += nt) {
+    int i = e / r, j = e % r;
+    D.Qr[k][i * ld + j] = D.Qc[k][i + j * ld];
+  }
+  __syncthreads();
+  // new column of R: Q'^T [G(:, n)]
+  for (int a = tid; a < r; a += nt) {
+    double acc = 0.0;
+    for (int i = 0; i < r; ++i) acc = fma(D.Qr[k][i * ld + a], cn[i], acc);
+    Rs[a * ls + n] = acc;
+  }
+  for (int j = tid; j < n; j += nt) Rs[n * ls + j] = 0.0;
+  __syncthreads();
+  qr_store_R(D, k, r, Rs, ls, true);
+}
+
+__global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
   const Dev &D = *Dp;
   State *st = D.st;
   if (st->stop) return;
+  extern __shared__ double sm[];
+  const int k = blockIdx.x + 1;
+  const int r = st->r[k];
+  const int have = st->qr_rank[k];
+  if (threadIdx.x == 0) {
+    IfaceState &I = st->it[k];
+    I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
+    I.err = 0.0; I.evals = 0;
+  }
+  if (have == r) return;
+  if (have >= 1 && have == r - 1) {
+    qr_border(D, k, r, sm);
+    if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * r * (double)r));
+  } else {
+    qr_full(D, k, r, sm);
+    if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(8.0 / 3.0 * r * (double)r * r));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st->qr_rank[k] = r;
+}
+
+// Kernel (c): contraction of the weighted cores with the inverse cross matrices
+// (Sec. 4.1): x <- V_1; for k: x <- x G_k^-1 = (Q R^-T x^T)^T; x <- x V_{k+1}.
+// One CTA; R_k staged in shared memory for the sequential substitution (one
+// warp), the products with Q_k and V_{k+1} spread over all threads.  It only
+// feeds the stopping rule, so it runs beside the pivot search; a rule that
+// fires is recorded as pending and applied at the end of the sweep.
+__global__ void __launch_bounds__(256) k_contract(Dev *Dp, int final_dd) {
+  const Dev &D = *Dp;
+  State *st = D.st;
+  // per sweep: FP64 contraction for the stopping rule; final_dd: the
+  // double-double contraction of the final sets (after the run stopped)
+  if (st->stop && !final_dd) return;
+  if (final_dd && (st->nonfinite || st->singular)) return;
+  const int prec = final_dd;
+  extern __shared__ double sm[];
   __shared__ double xh[TTQ_MAXR], xl[TTQ_MAXR], th[TTQ_MAXR], tl[TTQ_MAXR];
-  const int lane = lane_id(), d = D.d, ld = D.cap;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
+  const int d = D.d, ld = D.cap;
   if (st->nonfinite || st->singular) {
-    if (lane == 0) { st->status = st->nonfinite ? ST_ERR_NONFINITE : ST_ERR_SINGULAR; st->stop = 1; }
+    if (tid == 0) {
+      st->pending_status = st->nonfinite ? ST_ERR_NONFINITE : ST_ERR_SINGULAR;
+      st->stop_pending = 1;
+    }
     return;
   }
-  for (int b = lane; b < st->r[1]; b += 32) { xh[b] = D.V[1][b]; xl[b] = D.Vlo[1][b]; }
-  if (lane == 0) {
+  double *Rs = sm;                               // r x r row-major
+  for (int b = tid; b < st->r[1]; b += nt) { xh[b] = D.V[1][b]; xl[b] = D.Vlo[1][b]; }
+  if (tid == 0) {
     unsigned long long fl = 0;
     for (int k = 1; k <= d - 1; ++k) {
       unsigned long long r = st->r[k], rn = st->r[k + 1];
-      fl += (3 * r * r + 2 * r * rn) * (D.prec ? 15 : 1);
+      fl += (3 * r * r + 2 * r * rn) * (prec ? 15 : 1);
     }
     atomicAdd(&st->flops[2], fl);
   }
-  __syncwarp();
   for (int k = 1; k <= d - 1; ++k) {
     const int r = st->r[k], rn = st->r[k + 1];
-    const double *Qc = D.Qc[k], *Rr = D.Rr[k], *Rc = D.Rc[k];
-    if (!D.prec) {
-      // x <- x G^-1 = (G^-T x^T)^T: forward substitution with R^T, then Q
-      for (int i = 0; i < r; ++i) {
-        double ti = xh[i] * D.rinv[k][i];
-        for (int j = i + 1 + lane; j < r; j += 32) xh[j] = fma(-Rr[i * ld + j], ti, xh[j]);
-        if (lane == 0) th[i] = ti;
-        __syncwarp();
+    const double *Qc = D.Qc[k];
+    for (int e = tid; e < r * r; e += nt) {
+      int i = e / r, j = e % r;
+      Rs[i * r + j] = (j >= i) ? D.Rr[k][i * ld + j] : 0.0;
+    }
+    __syncthreads();
+    // forward substitution R^T t = x (one warp, from shared memory)
+    if (warp == 0) {
+      if (!prec) {
+        for (int i = 0; i < r; ++i) {
+          double ti = xh[i] * D.rinv[k][i];
+          for (int j = i + 1 + lane; j < r; j += 32) xh[j] = fma(-Rs[i * r + j], ti, xh[j]);
+          if (lane == 0) th[i] = ti;
+          __syncwarp();
+        }
+      } else {
+        for (int i = 0; i < r; ++i) {
+          dd ti = dd_div_d({xh[i], xl[i]}, Rs[i * r + i]);
+          for (int j = i + 1 + lane; j < r; j += 32) {
+            dd v = dd_add({xh[j], xl[j]}, dd_mul_d(ti, -Rs[i * r + j]));
+            xh[j] = v.hi; xl[j] = v.lo;
+          }
+          if (lane == 0) { th[i] = ti.hi; tl[i] = ti.lo; }
+          __syncwarp();
+        }
       }
-      for (int i = lane; i < r; i += 32) {
+    }
+    __syncthreads();
+    // x <- Q t
+    for (int i = tid; i < r; i += nt) {
+      if (!prec) {
         double acc = 0.0;
         for (int j = 0; j < r; ++j) acc = fma(Qc[i + j * ld], th[j], acc);
         xh[i] = acc;
-      }
-      __syncwarp();
-      // x <- x V_{k+1}
-      for (int b = lane; b < rn; b += 32) {
-        double acc = 0.0;
-        for (int a = 0; a < r; ++a) acc = fma(xh[a], D.V[k + 1][(size_t)a * D.capL[k + 1] + b], acc);
-        th[b] = acc;
-      }
-      __syncwarp();
-      for (int b = lane; b < rn; b += 32) xh[b] = th[b];
-      __syncwarp();
-    } else {
-      for (int i = 0; i < r; ++i) {
-        dd ti = dd_div_d({xh[i], xl[i]}, Rc[i + i * ld]);
-        for (int j = i + 1 + lane; j < r; j += 32) {
-          dd v = dd_add({xh[j], xl[j]}, dd_mul_d(ti, -Rr[i * ld + j]));
-          xh[j] = v.hi; xl[j] = v.lo;
-        }
-        if (lane == 0) { th[i] = ti.hi; tl[i] = ti.lo; }
-        __syncwarp();
-      }
-      for (int i = lane; i < r; i += 32) {
+      } else {
         dd acc = {0.0, 0.0};
         for (int j = 0; j < r; ++j) acc = dd_add(acc, dd_mul_d({th[j], tl[j]}, Qc[i + j * ld]));
         xh[i] = acc.hi; xl[i] = acc.lo;
       }
-      __syncwarp();
-      for (int b = lane; b < rn; b += 32) {
+    }
+    __syncthreads();
+    // x <- x V_{k+1}
+    for (int b = tid; b < rn; b += nt) {
+      if (!prec) {
+        double acc = 0.0;
+        for (int a = 0; a < r; ++a) acc = fma(xh[a], D.V[k + 1][(size_t)a * D.capL[k + 1] + b], acc);
+        th[b] = acc;
+      } else {
         dd acc = {0.0, 0.0};
         for (int a = 0; a < r; ++a) {
           size_t vi = (size_t)a * D.capL[k + 1] + b;
@@ -444,22 +547,23 @@ __global__ void k_contract(Dev *Dp) {
         }
         th[b] = acc.hi; tl[b] = acc.lo;
       }
-      __syncwarp();
-      for (int b = lane; b < rn; b += 32) { xh[b] = th[b]; xl[b] = tl[b]; }
-      __syncwarp();
     }
+    __syncthreads();
+    for (int b = tid; b < rn; b += nt) { xh[b] = th[b]; xl[b] = tl[b]; }
+    __syncthreads();
   }
-  if (lane == 0) {
-    dd v = D.prec ? dd_mul_d({xh[0], xl[0]}, D.constant) : dd{xh[0] * D.constant, 0.0};
+  if (tid == 0 && final_dd) {
+    dd v = dd_mul_d({xh[0], xl[0]}, D.constant);
+    st->value = v.hi;
+    st->value_lo = v.lo;
+    return;
+  }
+  if (tid == 0) {
+    dd v = prec ? dd_mul_d({xh[0], xl[0]}, D.constant) : dd{xh[0] * D.constant, 0.0};
     const double val = v.hi;
     st->value = val;
     st->value_lo = v.lo;
     for (int k = 0; k <= d; ++k) st->ro[k] = st->r[k];
-    for (int k = 1; k < d; ++k) {
-      IfaceState &I = st->it[k];
-      I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
-      I.err = 0.0; I.evals = 0;
-    }
     const int s = st->sweep;
     if (st->rules) {
       if (s > 0) {
@@ -480,10 +584,75 @@ __global__ void k_contract(Dev *Dp) {
         if (allcap) { stop = 1; status = ST_RANK_CAP; }
       }
       if (!stop && s >= D.max_sweeps - 1) { stop = 1; status = ST_MAX_SWEEPS; }
-      if (stop) { st->stop = 1; st->status = status; }
+      if (stop) { st->pending_status = status; st->stop_pending = 1; }
     }
     st->prev = val;
   }
+}
+
+// The solve of the next rook step, one CTA per interface with R_k staged in
+// shared memory: mode 0 z = G^-1 y for the column step, y = R_{k+1}(:, gamma*);
+// mode 1 b = G^-T l for the row step, l = L_k(rho*, :)^T.  Result in zvec[k].
+__global__ void __launch_bounds__(256) k_solve(Dev *Dp, int mode) {
+  const Dev &D = *Dp;
+  State *st = D.st;
+  const int k = blockIdx.x + 1;
+  if (st->stop || !st->search) return;
+  IfaceState &I = st->it[k];
+  if (!I.active || I.rook_done) return;
+  extern __shared__ double sm[];
+  __shared__ double v[TTQ_MAXR], t[TTQ_MAXR];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
+  const int r = st->r[k];
+  double *Rs = sm;                               // r x r, orientation of the substitution
+  if (mode == 0) {
+    const int rn = st->r[k + 1], j = I.col / rn, beta = I.col % rn;
+    for (int e = tid; e < r * r; e += nt) {
+      int i = e % r, c = e / r;                  // column-major: R[i][c] at Rs[i + c r]
+      Rs[i + c * r] = D.Rc[k][i + c * ld];
+    }
+    for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
+    __syncthreads();
+    for (int i = tid; i < r; i += nt) {          // t = Q^T y
+      double acc = 0.0;
+      for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], v[b], acc);
+      t[i] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {                             // back substitution R z = t
+      for (int jj = r - 1; jj >= 0; --jj) {
+        double zj = t[jj] * D.rinv[k][jj];
+        for (int i = lane; i < jj; i += 32) t[i] = fma(-Rs[i + jj * r], zj, t[i]);
+        if (lane == 0) v[jj] = zj;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b];
+  } else {
+    const int Nk = D.N[k - 1], alpha = I.row / Nk, i0 = I.row % Nk;
+    for (int e = tid; e < r * r; e += nt) {
+      int i = e / r, c = e % r;                  // row-major: R[i][c] at Rs[i r + c]
+      Rs[i * r + c] = D.Rr[k][i * ld + c];
+    }
+    for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
+    __syncthreads();
+    if (warp == 0) {                             // forward substitution R^T t = l
+      for (int i = 0; i < r; ++i) {
+        double ti = v[i] * D.rinv[k][i];
+        for (int jj = i + 1 + lane; jj < r; jj += 32) v[jj] = fma(-Rs[i * r + jj], ti, v[jj]);
+        if (lane == 0) t[i] = ti;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < r; i += nt) {          // b = Q t
+      double acc = 0.0;
+      for (int jj = 0; jj < r; ++jj) acc = fma(D.Qc[k][i + jj * ld], t[jj], acc);
+      D.zvec[k][i] = acc;
+    }
+  }
+  if (tid == 0) atomicAdd(&st->flops[3], (unsigned long long)(3 * r * r));
 }
 
 // shared per-warp scratch of the search kernels
@@ -492,6 +661,14 @@ struct SearchSmem {
   double pl[TTQ_WARPS][TTQ_MAXPAIR];
   double buf[TTQ_WARPS][TTQ_MAXR];
   double tmp[TTQ_WARPS][TTQ_MAXR];
+  int exc[TTQ_WARPS][TTQ_MAXR];
+  double z[TTQ_MAXR];
+};
+
+// per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
+struct RookSmem {
+  int ms[TTQ_WARPS][TTQ_MAXD];
+  double pl[TTQ_WARPS][TTQ_MAXPAIR];
   int exc[TTQ_WARPS][TTQ_MAXR];
   double z[TTQ_MAXR];
 };
@@ -512,10 +689,19 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *Dp) {
   const int k = blockIdx.y + 1;
   if (!iface_searchable(D, st, k)) return;
   __shared__ SearchSmem sh;
+  extern __shared__ double fac[];
   const int lane = lane_id(), warp = warp_id(), d = D.d;
   const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
   const int Nk = D.N[k - 1], Nk1 = D.N[k];
   const int M = rl * Nk, Ncol = Nk1 * rn, S = D.S[k];
+  double *Rs = fac;                                  // R column-major, ld rk
+  double *Qs = D.q_in_smem ? fac + (size_t)rk * rk : nullptr;   // Q row-major, ld rk
+  for (int e = threadIdx.x; e < rk * rk; e += blockDim.x) {
+    int i = e % rk, c = e / rk;
+    Rs[i + c * rk] = D.Rc[k][i + c * D.cap];
+    if (Qs) Qs[c * rk + i] = D.Qr[k][c * D.cap + i];
+  }
+  __syncthreads();
   const unsigned long long sid = stream_id(st->sweep, k, 1);
   double best = -1.0;
   long long evals = 0;
@@ -548,7 +734,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *Dp) {
     double A = 0.0;
     if (lane == 0) A = fiber_value(D, k - 1, sh.ms[warp], u, sh.pl[warp], i);
     A = __shfl_sync(0xffffffffu, A, 0);
-    warp_col_solve(D, k, rk, sh.buf[warp], sh.tmp[warp]);
+    warp_col_solve_s(D, k, rk, Qs, Rs, sh.buf[warp], sh.tmp[warp]);
     double acc = 0.0;
     for (int b = lane; b < rk; b += 32) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], sh.buf[warp][b], acc);
     acc = warp_sum(acc);
@@ -566,31 +752,25 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *Dp) {
   double epick;
   if (!cta_pick_last(best, D, k, S, &pick, &epick)) return;
   if (pick < 0) return;                        // nothing to search from
-  if (warp == 0) {
+  if (threadIdx.x == 0) {
     const int t = pick;
-    const int rho = draw_index(D.seed, sid, 2ULL * t, (unsigned long long)M);
-    const int gam = draw_index(D.seed, sid, 2ULL * t + 1, (unsigned long long)Ncol);
-    const int j = gam / rn, beta = gam % rn;
-    for (int b = lane; b < rk; b += 32) sh.buf[0][b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
-    __syncwarp();
-    warp_col_solve(D, k, rk, sh.buf[0], sh.tmp[0]);
-    for (int b = lane; b < rk; b += 32) D.zvec[k][b] = sh.buf[0][b];
-    if (lane == 0) {
-      IfaceState &I = st->it[k];
-      I.active = 1; I.row = rho; I.col = gam; I.err = epick;
-    }
+    IfaceState &I = st->it[k];
+    I.row = draw_index(D.seed, sid, 2ULL * t, (unsigned long long)M);
+    I.col = draw_index(D.seed, sid, 2ULL * t + 1, (unsigned long long)Ncol);
+    I.err = epick;
+    I.active = 1;
   }
 }
 
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i); argmax -> rho*.
-__global__ void __launch_bounds__(TTQ_WARPS * 32) k_rook_col(Dev *Dp) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_col(Dev *Dp) {
   const Dev &D = *Dp;
   State *st = D.st;
   const int k = blockIdx.y + 1;
   if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
   if (!I.active || I.rook_done) return;
-  __shared__ SearchSmem sh;
+  __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
   const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
   const int Nk = D.N[k - 1];
@@ -650,31 +830,22 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_rook_col(Dev *Dp) {
   int pick;
   double epick;
   if (!cta_pick_last(best, D, k, rl * Nk, &pick, &epick)) return;
-  if (warp == 0) {
-    if (pick < 0) {
-      if (lane == 0) I.active = 0;
-      return;
-    }
-    const int rho = pick, alpha = rho / Nk, i = rho % Nk;
-    // row coefficients b = G^{-T} L_k(rho, :)^T for the row step
-    for (int b = lane; b < rk; b += 32) sh.buf[0][b] = D.Y[k][core_at(D, k, alpha, i, b)];
-    __syncwarp();
-    warp_row_solve(D, k, rk, sh.buf[0], sh.tmp[0]);
-    for (int b = lane; b < rk; b += 32) D.zvec[k][b] = sh.buf[0][b];
-    if (lane == 0) I.row = rho;
+  if (threadIdx.x == 0) {
+    if (pick < 0) I.active = 0;
+    else I.row = pick;
   }
 }
 
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta); argmax -> gamma_new,
 // then the rook test (Eq. 2): gamma_new == gamma* ends the search.
-__global__ void __launch_bounds__(TTQ_WARPS * 32) k_rook_row(Dev *Dp) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_row(Dev *Dp) {
   const Dev &D = *Dp;
   State *st = D.st;
   const int k = blockIdx.y + 1;
   if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
   if (!I.active || I.rook_done) return;
-  __shared__ SearchSmem sh;
+  __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
   const int rk = st->r[k], rn = st->r[k + 1];
   const int Nk = D.N[k - 1], Nk1 = D.N[k];
@@ -732,24 +903,14 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_rook_row(Dev *Dp) {
   int pick;
   double epick;
   if (!cta_pick_last(best, D, k, Nk1 * rn, &pick, &epick)) return;
-  if (warp == 0) {
+  if (threadIdx.x == 0) {
     if (pick < 0) {
-      if (lane == 0) I.active = 0;
-      return;
-    }
-    const int gnew = pick;
-    const int rounds = I.rounds + 1;
-    const bool done = (gnew == I.col) || rounds >= D.rook_max;
-    if (!done) {
-      const int j = gnew / rn, beta = gnew % rn;
-      for (int b = lane; b < rk; b += 32) sh.buf[0][b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
-      __syncwarp();
-      warp_col_solve(D, k, rk, sh.buf[0], sh.tmp[0]);
-      for (int b = lane; b < rk; b += 32) D.zvec[k][b] = sh.buf[0][b];
-    }
-    if (lane == 0) {
+      I.active = 0;
+    } else {
+      const int rounds = I.rounds + 1;
+      const bool done = (pick == I.col) || rounds >= D.rook_max;
       I.rounds = rounds;
-      I.col = gnew;
+      I.col = pick;
       I.err = epick;
       I.rook_done = done ? 1 : 0;
     }
@@ -757,47 +918,64 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_rook_row(Dev *Dp) {
 }
 
 // End of sweep (Alg. 6): append every accepted pivot, nested by construction.
-__global__ void k_update(Dev *Dp) {
+// Inside the whole-run graph it also sets the WHILE condition: continue while
+// the run is not over, never past max_sweeps (every path reaches the end).
+__global__ void k_update(Dev *Dp, cudaGraphConditionalHandle h, int use_cond) {
   const Dev &D = *Dp;
   State *st = D.st;
-  if (st->stop) return;
-  if (!st->search) { if (threadIdx.x == 0) st->sweep++; return; }
   const int d = D.d;
   const int k = threadIdx.x + 1;            // one thread per interface (d - 1 <= 31)
   __shared__ int rold[TTQ_MAXD + 1];
   __shared__ int nacc;
   __shared__ long long ev;
-  if (threadIdx.x == 0) { nacc = 0; ev = 0; }
-  for (int q = threadIdx.x; q <= d; q += blockDim.x) rold[q] = st->r[q];
-  __syncthreads();
-  const double scale = __longlong_as_double((long long)st->scale_bits);
-  if (k <= d - 1) {
-    IfaceState &I = st->it[k];
-    atomicAdd((unsigned long long *)&ev, (unsigned long long)I.evals);
-    if (I.active) {
-      const bool acc = fabs(I.err) > D.pivot_tol * scale && rold[k] < D.cap;
-      I.accepted = acc ? 1 : 0;
-      if (acc) {
-        atomicAdd(&nacc, 1);
-        const int Nk = D.N[k - 1], rn = rold[k + 1];
-        const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
-        const int a = rold[k];
-        int *L = D.lidx[k] + (size_t)a * d, *R = D.ridx[k] + (size_t)a * d;
-        for (int m = 0; m < d; ++m) {
-          L[m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
-          R[m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
-        }
-        D.lpar[k][a] = alpha; D.lnode[k][a] = i;
-        D.rpar[k][a] = beta; D.rnode[k][a] = j;
-      }
-    }
+  __shared__ int mode;                      // 0: nothing to do, 1: apply pending stop, 2: no search, 3: append
+  if (threadIdx.x == 0) {
+    nacc = 0; ev = 0;
+    if (st->stop) mode = 0;
+    else if (st->stop_pending) mode = 1;
+    else if (!st->search) mode = 2;
+    else mode = 3;
   }
   __syncthreads();
-  if (k <= d - 1 && st->it[k].accepted) st->r[k] = rold[k] + 1;
-  if (threadIdx.x == 0) {
-    st->search_evals += ev;
-    if (st->rules && nacc == 0) { st->stop = 1; st->status = ST_NO_PIVOT; }
-    st->sweep++;
+  if (mode == 1 && threadIdx.x == 0) { st->stop = 1; st->status = st->pending_status; }
+  if (mode == 2 && threadIdx.x == 0) st->sweep++;
+  if (mode == 3) {
+    for (int q = threadIdx.x; q <= d; q += blockDim.x) rold[q] = st->r[q];
+    __syncthreads();
+    const double scale = __longlong_as_double((long long)st->scale_bits);
+    if (k <= d - 1) {
+      IfaceState &I = st->it[k];
+      atomicAdd((unsigned long long *)&ev, (unsigned long long)I.evals);
+      if (I.active) {
+        const bool acc = fabs(I.err) > D.pivot_tol * scale && rold[k] < D.cap;
+        I.accepted = acc ? 1 : 0;
+        if (acc) {
+          atomicAdd(&nacc, 1);
+          const int Nk = D.N[k - 1], rn = rold[k + 1];
+          const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
+          const int a = rold[k];
+          int *L = D.lidx[k] + (size_t)a * d, *R = D.ridx[k] + (size_t)a * d;
+          for (int m = 0; m < d; ++m) {
+            L[m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
+            R[m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
+          }
+          D.lpar[k][a] = alpha; D.lnode[k][a] = i;
+          D.rpar[k][a] = beta; D.rnode[k][a] = j;
+        }
+      }
+    }
+    __syncthreads();
+    if (k <= d - 1 && st->it[k].accepted) st->r[k] = rold[k] + 1;
+    if (threadIdx.x == 0) {
+      st->search_evals += ev;
+      if (st->rules && nacc == 0) { st->stop = 1; st->status = ST_NO_PIVOT; }
+      st->sweep++;
+    }
+  }
+  if (use_cond && threadIdx.x == 0) {
+    const int guard = ++st->loop_guard;
+    const int cont = !st->stop && st->sweep < D.max_sweeps && guard < D.max_sweeps + 2;
+    cudaGraphSetConditional(h, cont ? 1u : 0u);
   }
 }
 
@@ -806,6 +984,8 @@ __global__ void k_begin(Dev *Dp, int sweep, int rules, int search) {
   st->sweep = sweep;
   st->rules = rules;
   st->search = search;
+  st->stop_pending = 0;
+  st->loop_guard = 0;
   if (!rules) st->stop = 0;
 }
 
