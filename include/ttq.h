@@ -142,6 +142,16 @@ int ttq_plan_destroy(ttq_plan *plan);
  * plan, beside the pivot search. */
 int ttq_plan_run(ttq_plan *plan, ttq_result *out);
 
+/* Asynchronous pair: ttq_plan_launch enqueues a whole run on the plan's
+ * stream (one CUDA graph) followed by a copy of its final state into result
+ * slot `slot` (0..63, pinned host memory owned by the plan) and returns at
+ * once; ttq_plan_result waits for the stream and reads that slot.  Runs of
+ * one plan execute in launch order; a slot is valid until it is launched
+ * into again.  Without graphs (legacy default stream, or graphs switched off)
+ * ttq_plan_launch runs synchronously. */
+int ttq_plan_launch(ttq_plan *plan, int slot);
+int ttq_plan_result(ttq_plan *plan, int slot, ttq_result *out);
+
 /* --- stage-level entry points (replay and inspection) ------------------- */
 
 /* Initial index set: the largest |A| among init_samples seeded random points. */
@@ -179,6 +189,12 @@ int ttq_plan_eval_points(ttq_plan *plan, const int32_t *idx, int64_t npts, doubl
 
 /* Number of the library's kernel launches issued by this plan so far. */
 int64_t ttq_plan_launches(const ttq_plan *plan);
+
+/* Graph execution on (default, except on the legacy default stream) or off:
+ * off, every kernel of a sweep is a plain stream launch and the host checks
+ * the stopping flag every two sweeps (same work and results; for profilers
+ * that replay individual launches). */
+int ttq_plan_set_graphs(ttq_plan *plan, int enable);
 
 /* Bytes this plan has copied host->device (problem inputs, descriptor) and
  * device->host (state and flags read back) since it was created. */

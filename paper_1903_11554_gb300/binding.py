@@ -55,6 +55,8 @@ SIGNATURES = {
     "ttq_plan_destroy": (_c.c_int, [_vp]),
     "ttq_plan_run": (_c.c_int, [_vp, _c.POINTER(TTQResult)]),
     "ttq_plan_init": (_c.c_int, [_vp]),
+    "ttq_plan_launch": (_c.c_int, [_vp, _c.c_int]),
+    "ttq_plan_result": (_c.c_int, [_vp, _c.c_int, _c.POINTER(TTQResult)]),
     "ttq_plan_set_state": (_c.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "ttq_plan_get_state": (_c.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p]),
     "ttq_plan_sweep": (_c.c_int, [_vp, _c.c_int, _c.c_int, _dp, _dp, _c.POINTER(TTQPivot)]),
@@ -62,6 +64,7 @@ SIGNATURES = {
     "ttq_plan_eval_points": (_c.c_int, [_vp, _vp, _c.c_int64, _vp]),
     "ttq_plan_launches": (_c.c_int64, [_vp]),
     "ttq_plan_transfer_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
+    "ttq_plan_set_graphs": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_set_timing": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_kernel_times": (_c.c_int, [_vp, _dp, _c.POINTER(_c.c_int64), _dp, _c.c_int]),
     "ttq_integrate_noalloc": (_c.c_int, [_c.POINTER(TTQProblem), _vp, _c.POINTER(TTQResult)]),
@@ -198,6 +201,17 @@ class Plan:
                 "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
                 "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
 
+    def launch(self, slot: int = 0):
+        """Enqueue a whole run; its result lands in `slot` (read with result())."""
+        _check(self.lib.ttq_plan_launch(self.h, slot), "ttq_plan_launch")
+
+    def result(self, slot: int = 0) -> Dict:
+        res = TTQResult()
+        _check(self.lib.ttq_plan_result(self.h, slot, _c.byref(res)), "ttq_plan_result")
+        return {"value": res.value, "value_lo": res.value_lo, "internal_conv": res.internal_conv,
+                "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
+                "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
+
     # -- stages -----------------------------------------------------------
     def init(self):
         _check(self.lib.ttq_plan_init(self.h), "ttq_plan_init")
@@ -257,6 +271,9 @@ class Plan:
         a, b = _c.c_int64(0), _c.c_int64(0)
         _check(self.lib.ttq_plan_transfer_bytes(self.h, _c.byref(a), _c.byref(b)), "ttq_plan_transfer_bytes")
         return int(a.value), int(b.value)
+
+    def set_graphs(self, on: bool):
+        _check(self.lib.ttq_plan_set_graphs(self.h, 1 if on else 0), "ttq_plan_set_graphs")
 
     def set_timing(self, on: bool):
         _check(self.lib.ttq_plan_set_timing(self.h, 1 if on else 0), "ttq_plan_set_timing")

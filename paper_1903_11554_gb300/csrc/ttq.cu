@@ -61,7 +61,10 @@ struct ttq_plan {
   int in_loop;              // enqueueing the body of the WHILE node
   int sweep_kernels;        // kernels in one sweep
   int samples_smem, contract_smem, solve_smem;
+  State *slots;             // pinned host copies of the final state of launched runs
+  int nslots;
 };
+#define TTQ_RESULT_SLOTS 64
 
 static cudaEvent_t ev_get(ttq_plan *P) {
   if (!P->pool.empty()) {
@@ -246,7 +249,7 @@ static void set_smem_sizes(ttq_plan *P) {
   P->h.q_in_smem = cap <= 96 ? 1 : 0;
   P->samples_smem = (int)((P->h.q_in_smem ? 2 : 1) * cap * cap * 8);
   P->contract_smem = (int)(cap * cap * 8);
-  P->solve_smem = (int)(cap * cap * 8);
+  P->solve_smem = (int)((P->h.q_in_smem ? 2 : 1) * cap * cap * 8);
 }
 
 static cudaError_t set_smem_attributes(ttq_plan *P) {
@@ -330,6 +333,7 @@ extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t byt
     delete P;
     return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
   }
+
   cudaError_t e;
   if ((e = set_smem_attributes(P)) != cudaSuccess) goto fail;
   if ((e = cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking)) != cudaSuccess) goto fail;
@@ -365,6 +369,7 @@ extern "C" int ttq_plan_destroy(ttq_plan *P) {
   for (cudaEvent_t e : P->pool) cudaEventDestroy(e);
   if (P->sweep_exec) cudaGraphExecDestroy(P->sweep_exec);
   if (P->run_exec) cudaGraphExecDestroy(P->run_exec);
+  if (P->slots) cudaFreeHost(P->slots);
   if (P->s2) { cudaStreamSynchronize(P->s2); cudaStreamDestroy(P->s2); }
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->join) cudaEventDestroy(P->join);
@@ -481,8 +486,7 @@ extern "C" int ttq_plan_init(ttq_plan *P) {
   return TTQ_OK;
 }
 
-static void fill_result(const ttq_plan *P, ttq_result *out) {
-  const State &S = *P->hst;
+static void fill_result_from(const ttq_plan *P, const State &S, ttq_result *out) {
   const Dev &D = P->h;
   out->value = S.value;
   out->value_lo = S.value_lo;
@@ -496,6 +500,48 @@ static void fill_result(const ttq_plan *P, ttq_result *out) {
   out->max_rank = mr;
   out->status = S.status;
   out->reserved = 0;
+}
+
+static void fill_result(const ttq_plan *P, ttq_result *out) { fill_result_from(P, *P->hst, out); }
+
+extern "C" int ttq_plan_launch(ttq_plan *P, int slot) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (slot < 0 || slot >= TTQ_RESULT_SLOTS) return set_err(TTQ_ERR_INVALID_ARG, "slot out of range");
+  if (!P->slots) {                          // first launch: pinned result slots (warm up before timing)
+    if (cudaMallocHost((void **)&P->slots, sizeof(State) * TTQ_RESULT_SLOTS) != cudaSuccess)
+      return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
+  }
+  int rc;
+  if (!(P->use_graph && !P->timing)) {      // plain launches need the host in the loop: run now
+    ttq_result tmp;
+    if ((rc = ttq_plan_run(P, &tmp))) return rc;
+    memcpy(&P->slots[slot], P->hst, sizeof(State));
+    return TTQ_OK;
+  }
+  if ((rc = ttq_plan_init(P))) return rc;
+  k_begin<<<1, 1, 0, P->stream>>>(P->dev, 0, 1, 1);
+  P->launches++;
+  CK(cudaGetLastError());
+  if (!P->run_exec && (rc = build_run_graph(P))) return rc;
+  CK(cudaGraphLaunch(P->run_exec, P->stream));
+  if (P->h.prec) {
+    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(&P->slots[slot], P->st, sizeof(State), cudaMemcpyDeviceToHost, P->stream));
+  P->d2h += sizeof(State);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_result(ttq_plan *P, int slot, ttq_result *out) {
+  if (!P || !out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  if (slot < 0 || slot >= TTQ_RESULT_SLOTS || !P->slots) return set_err(TTQ_ERR_INVALID_ARG, "bad slot");
+  CK(cudaStreamSynchronize(P->stream));
+  harvest(P);
+  const State &S = P->slots[slot];
+  P->launches += (long long)P->sweep_kernels * S.loop_guard;
+  fill_result_from(P, S, out);
+  return TTQ_OK;
 }
 
 extern "C" int ttq_plan_run(ttq_plan *P, ttq_result *out) {
@@ -679,6 +725,12 @@ extern "C" int ttq_plan_transfer_bytes(const ttq_plan *P, int64_t *h2d, int64_t 
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
   if (h2d) *h2d = P->h2d;
   if (d2h) *d2h = P->d2h;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_set_graphs(ttq_plan *P, int enable) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  P->use_graph = (enable && P->stream != nullptr) ? 1 : 0;
   return TTQ_OK;
 }
 

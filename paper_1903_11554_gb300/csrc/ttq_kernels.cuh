@@ -605,17 +605,20 @@ __global__ void __launch_bounds__(256) k_solve(Dev *Dp, int mode) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
   const int r = st->r[k];
   double *Rs = sm;                               // r x r, orientation of the substitution
+  double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
   if (mode == 0) {
     const int rn = st->r[k + 1], j = I.col / rn, beta = I.col % rn;
     for (int e = tid; e < r * r; e += nt) {
       int i = e % r, c = e / r;                  // column-major: R[i][c] at Rs[i + c r]
       Rs[i + c * r] = D.Rc[k][i + c * ld];
+      if (Qs) Qs[c * r + i] = D.Qr[k][c * ld + i];   // row-major Q[c][i]
     }
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
     __syncthreads();
     for (int i = tid; i < r; i += nt) {          // t = Q^T y
       double acc = 0.0;
-      for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], v[b], acc);
+      if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], v[b], acc);
+      else for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], v[b], acc);
       t[i] = acc;
     }
     __syncthreads();
@@ -634,6 +637,7 @@ __global__ void __launch_bounds__(256) k_solve(Dev *Dp, int mode) {
     for (int e = tid; e < r * r; e += nt) {
       int i = e / r, c = e % r;                  // row-major: R[i][c] at Rs[i r + c]
       Rs[i * r + c] = D.Rr[k][i * ld + c];
+      if (Qs) Qs[i + c * r] = D.Qc[k][i + c * ld];   // column-major Q[i][c]
     }
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
     __syncthreads();
@@ -648,7 +652,8 @@ __global__ void __launch_bounds__(256) k_solve(Dev *Dp, int mode) {
     __syncthreads();
     for (int i = tid; i < r; i += nt) {          // b = Q t
       double acc = 0.0;
-      for (int jj = 0; jj < r; ++jj) acc = fma(D.Qc[k][i + jj * ld], t[jj], acc);
+      if (Qs) for (int jj = 0; jj < r; ++jj) acc = fma(Qs[i + jj * r], t[jj], acc);
+      else for (int jj = 0; jj < r; ++jj) acc = fma(D.Qc[k][i + jj * ld], t[jj], acc);
       D.zvec[k][i] = acc;
     }
   }
@@ -763,7 +768,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *Dp) {
 }
 
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i); argmax -> rho*.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_col(Dev *Dp) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *Dp) {
   const Dev &D = *Dp;
   State *st = D.st;
   const int k = blockIdx.y + 1;
@@ -804,17 +809,40 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_col(Dev *Dp) {
     FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
     const int i0 = ch * TTQ_CHUNK, i1 = min(Nk, i0 + TTQ_CHUNK);
     fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + 2 * rk + 1);
-    for (int i = i0 + lane; i < i1; i += 32) {
-      const int rho = alpha * Nk + i;
+    // each lane takes 4 nodes of the chunk at once: 4 independent loads per step
+    // of the product L_k(rho, :) z over the core
+    int iq[4];
+    bool ok[4];
+    double A[4], acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      iq[q] = i0 + lane + 32 * q;
       bool ex = false;
-      for (int q = 0; q < nex; ++q) ex |= (sh.exc[warp][q] == i);
-      if (ex) { D.cs[k][rho] = -1.0; D.ce[k][rho] = 0.0; continue; }
-      double A = fiber_value(D, k - 1, sh.ms[warp], u, sh.pl[warp], i);
-      double acc = 0.0;
-      const double *Yc = D.Y[k] + core_at(D, k, alpha, i, 0);
+      for (int e = 0; e < nex; ++e) ex |= (sh.exc[warp][e] == iq[q]);
+      ok[q] = iq[q] < i1 && !ex;
+      A[q] = ok[q] ? fiber_value(D, k - 1, sh.ms[warp], u, sh.pl[warp], iq[q]) : 0.0;
+      acc[q] = 0.0;
+    }
+    {
+      const double *Yc = D.Y[k] + core_at(D, k, alpha, 0, 0);
       const size_t cst = (size_t)D.capL[k - 1] * Nk;
-      for (int b = 0; b < rk; ++b) acc = fma(Yc[b * cst], sh.z[b], acc);
-      const double E = A - acc;
+      const int c0 = min(iq[0], Nk - 1), c1 = min(iq[1], Nk - 1), c2 = min(iq[2], Nk - 1), c3 = min(iq[3], Nk - 1);
+#pragma unroll 4
+      for (int b = 0; b < rk; ++b) {
+        const double zb = sh.z[b];
+        const double *row = Yc + b * cst;
+        acc[0] = fma(row[c0], zb, acc[0]);
+        acc[1] = fma(row[c1], zb, acc[1]);
+        acc[2] = fma(row[c2], zb, acc[2]);
+        acc[3] = fma(row[c3], zb, acc[3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (iq[q] >= i1) continue;
+      const int rho = alpha * Nk + iq[q];
+      if (!ok[q]) { D.cs[k][rho] = -1.0; D.ce[k][rho] = 0.0; continue; }
+      const double E = A[q] - acc[q];
       const double sc = isfinite(E) ? fabs(E) : -1.0;
       D.cs[k][rho] = sc;
       D.ce[k][rho] = E;
@@ -838,7 +866,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_col(Dev *Dp) {
 
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta); argmax -> gamma_new,
 // then the rook test (Eq. 2): gamma_new == gamma* ends the search.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_row(Dev *Dp) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *Dp) {
   const Dev &D = *Dp;
   State *st = D.st;
   const int k = blockIdx.y + 1;
@@ -878,16 +906,37 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 4) k_rook_row(Dev *Dp) {
     FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
     const int j0 = ch * TTQ_CHUNK, j1 = min(Nk1, j0 + TTQ_CHUNK);
     fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node + 2 * rk + 1);
-    for (int jj = j0 + lane; jj < j1; jj += 32) {
-      const int g = jj * rn + beta;
+    int jq[4];
+    bool ok[4];
+    double A[4], acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      jq[q] = j0 + lane + 32 * q;
       bool ex = false;
-      for (int q = 0; q < nex; ++q) ex |= (sh.exc[warp][q] == jj);
-      if (ex) { D.cs[k][g] = -1.0; D.ce[k][g] = 0.0; continue; }
-      double A = fiber_value(D, k, sh.ms[warp], u, sh.pl[warp], jj);
-      double acc = 0.0;
-      const double *Yr = D.Y[k + 1] + core_at(D, k + 1, 0, jj, beta);
-      for (int a = 0; a < rk; ++a) acc = fma(Yr[(size_t)a * Nk1], sh.z[a], acc);
-      const double E = A - acc;
+      for (int e = 0; e < nex; ++e) ex |= (sh.exc[warp][e] == jq[q]);
+      ok[q] = jq[q] < j1 && !ex;
+      A[q] = ok[q] ? fiber_value(D, k, sh.ms[warp], u, sh.pl[warp], jq[q]) : 0.0;
+      acc[q] = 0.0;
+    }
+    {
+      const double *Yr = D.Y[k + 1] + core_at(D, k + 1, 0, 0, beta);
+      const int c0 = min(jq[0], Nk1 - 1), c1 = min(jq[1], Nk1 - 1), c2 = min(jq[2], Nk1 - 1), c3 = min(jq[3], Nk1 - 1);
+#pragma unroll 4
+      for (int a = 0; a < rk; ++a) {
+        const double za = sh.z[a];
+        const double *row = Yr + (size_t)a * Nk1;
+        acc[0] = fma(row[c0], za, acc[0]);
+        acc[1] = fma(row[c1], za, acc[1]);
+        acc[2] = fma(row[c2], za, acc[2]);
+        acc[3] = fma(row[c3], za, acc[3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (jq[q] >= j1) continue;
+      const int g = jq[q] * rn + beta;
+      if (!ok[q]) { D.cs[k][g] = -1.0; D.ce[k][g] = 0.0; continue; }
+      const double E = A[q] - acc[q];
       const double sc = isfinite(E) ? fabs(E) : -1.0;
       D.cs[k][g] = sc;
       D.ce[k][g] = E;

@@ -249,3 +249,24 @@ def test_double_double_contraction_vs_exact():
     v64, lo64, _ = plan64.sweep(0, search=False)
     assert lo64 == 0.0
     assert float(abs(Fraction(v64) - ex) / abs(ex)) < 1e-13
+
+
+def test_async_launch_matches_run():
+    """ttq_plan_launch / ttq_plan_result (several runs enqueued back to back,
+    results read afterwards) give exactly what ttq_plan_run gives."""
+    p = FULL["E_cube"]()
+    plan = B().Plan(p)
+    ref = plan.run()
+    for slot in range(3):
+        plan.launch(slot)
+    for slot in range(3):
+        assert plan.result(slot) == ref
+
+
+def test_plain_launches_match_graph():
+    p = FULL["D_rn"]()
+    plan = B().Plan(p)
+    a = plan.run()
+    plan.set_graphs(False)
+    b = plan.run()
+    assert a == b
