@@ -15,7 +15,7 @@ Follows the paper step by step:
   * The integral is the product of (2d-1) matrices of Sec. 4.1:
     (sum_i A(i, I_>1)) G_1^-1 (sum_i A(I_<=1, i, I_>2)) ... (sum_i A(I_<=d-1, i)).
 
-Readings where the paper is silent (each one is also listed in the design doc):
+Readings where the paper is silent:
   * initial index set: one multi-index, the largest |A| among `init_samples`
     seeded random points (first in draw order on ties);
   * random samples: `samples_for(k)` draws per interface from the counter-based

@@ -1,6 +1,6 @@
 """GPU path vs the CPU oracle, through the C ABI (needs a GB300).
 
-Tolerances (derived in the design doc):
+Tolerances:
   * integrand entries: |gpu - oracle| <= 1e-13 |oracle| + 1e-15 max|A|
     (both sides round a product of <= n(n-1)/2 + 2n + 3 factors; the unit-cube
     pair factors 1 - x_{i+1}..x_j lose relative accuracy near x = 1, where the
