@@ -152,6 +152,27 @@ int ttq_plan_run(ttq_plan *plan, ttq_result *out);
 int ttq_plan_launch(ttq_plan *plan, int slot);
 int ttq_plan_result(ttq_plan *plan, int slot, ttq_result *out);
 
+/* --- batches ---------------------------------------------------------------
+ * Many integrals with uneven families, n, node counts and rank caps advance
+ * together: every kernel launch of a sweep covers all instances (one
+ * persistent-style launch per stage, instance = grid z), and the whole batch
+ * runs as one CUDA graph whose WHILE loop continues while any instance is
+ * running.  A batch is a ttq_plan with count instances (destroy with
+ * ttq_plan_destroy); stage calls need count == 1.  Each instance's result is
+ * exactly what a single plan gives for that problem. */
+int ttq_batch_workspace_bytes(const ttq_problem *probs, int count, size_t *bytes);
+int ttq_batch_create(const ttq_problem *probs, int count, void *workspace, size_t bytes, void *stream,
+                     ttq_plan **out);
+int ttq_batch_run(ttq_plan *batch, ttq_result *results /* [count] */);
+
+/* Autotuner: times the evaluation, sample and rook kernels over `sweeps`
+ * sweeps for candidate grid shapes (CTAs per interface of the sample / rook
+ * kernels, CTAs per instance of the evaluation kernel), keeps the fastest and
+ * writes them to chosen[0..2] (rook, sample, eval) if chosen != NULL.  Grid
+ * shapes never change results.  ttq_plan_set_config sets them directly. */
+int ttq_batch_autotune(ttq_plan *plan, int sweeps, int32_t *chosen);
+int ttq_plan_set_config(ttq_plan *plan, int rook_ctas, int sample_ctas, int eval_ctas);
+
 /* --- stage-level entry points (replay and inspection) ------------------- */
 
 /* Initial index set: the largest |A| among init_samples seeded random points. */

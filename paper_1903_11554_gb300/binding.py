@@ -68,6 +68,11 @@ SIGNATURES = {
     "ttq_plan_set_timing": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_kernel_times": (_c.c_int, [_vp, _dp, _c.POINTER(_c.c_int64), _dp, _c.c_int]),
     "ttq_integrate_noalloc": (_c.c_int, [_c.POINTER(TTQProblem), _vp, _c.POINTER(TTQResult)]),
+    "ttq_batch_workspace_bytes": (_c.c_int, [_c.POINTER(TTQProblem), _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ttq_batch_create": (_c.c_int, [_c.POINTER(TTQProblem), _c.c_int, _vp, _c.c_size_t, _vp, _c.POINTER(_vp)]),
+    "ttq_batch_run": (_c.c_int, [_vp, _c.POINTER(TTQResult)]),
+    "ttq_batch_autotune": (_c.c_int, [_vp, _c.c_int, _i32p]),
+    "ttq_plan_set_config": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
     "ttq_status_string": (_c.c_char_p, [_c.c_int]),
     "ttq_last_error": (_c.c_char_p, []),
 }
@@ -271,6 +276,82 @@ class Plan:
         a, b = _c.c_int64(0), _c.c_int64(0)
         _check(self.lib.ttq_plan_transfer_bytes(self.h, _c.byref(a), _c.byref(b)), "ttq_plan_transfer_bytes")
         return int(a.value), int(b.value)
+
+    def set_graphs(self, on: bool):
+        _check(self.lib.ttq_plan_set_graphs(self.h, 1 if on else 0), "ttq_plan_set_graphs")
+
+    def set_timing(self, on: bool):
+        _check(self.lib.ttq_plan_set_timing(self.h, 1 if on else 0), "ttq_plan_set_timing")
+
+    def kernel_times(self, reset: bool = False) -> Dict[str, Dict]:
+        ms = (_c.c_double * len(KERNELS))()
+        n = (_c.c_int64 * len(KERNELS))()
+        fl = (_c.c_double * len(KERNELS))()
+        _check(self.lib.ttq_plan_kernel_times(self.h, ms, n, fl, 1 if reset else 0), "ttq_plan_kernel_times")
+        return {name: {"ms": ms[q], "launches": int(n[q]), "flops": fl[q]} for q, name in enumerate(KERNELS)}
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.ttq_plan_launches(self.h))
+
+
+def _result_dict(res) -> Dict:
+    return {"value": res.value, "value_lo": res.value_lo, "internal_conv": res.internal_conv,
+            "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
+            "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
+
+
+class Batch:
+    """Many integrals advancing together: one launch per stage for all of them."""
+
+    def __init__(self, problems: List[inputs.Problem], workspace=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise TTQError("no CUDA device: the TT-cross quadrature runs only on the GPU")
+        self.lib = load()
+        self.problems = list(problems)
+        self.arrays = [_Arrays(p) for p in self.problems]
+        self.structs = (TTQProblem * len(self.problems))(*[make_struct(p, a) for p, a in
+                                                          zip(self.problems, self.arrays)])
+        nbytes = _c.c_size_t(0)
+        _check(self.lib.ttq_batch_workspace_bytes(self.structs, len(self.problems), _c.byref(nbytes)),
+               "ttq_batch_workspace_bytes")
+        self.nbytes = int(nbytes.value)
+        if workspace is None:
+            workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        if stream is None:
+            stream = torch.cuda.Stream()
+            stream.wait_stream(torch.cuda.current_stream())
+        self.stream = stream
+        h = _vp()
+        _check(self.lib.ttq_batch_create(self.structs, len(self.problems), _vp(workspace.data_ptr()), self.nbytes,
+                                         _vp(self.stream.cuda_stream), _c.byref(h)), "ttq_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ttq_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self) -> List[Dict]:
+        res = (TTQResult * len(self.problems))()
+        _check(self.lib.ttq_batch_run(self.h, res), "ttq_batch_run")
+        return [_result_dict(r) for r in res]
+
+    def autotune(self, sweeps: int = 3):
+        chosen = (_c.c_int32 * 3)()
+        _check(self.lib.ttq_batch_autotune(self.h, sweeps, chosen), "ttq_batch_autotune")
+        return {"rook_ctas": chosen[0], "sample_ctas": chosen[1], "eval_ctas": chosen[2]}
+
+    def set_config(self, rook_ctas: int, sample_ctas: int, eval_ctas: int):
+        _check(self.lib.ttq_plan_set_config(self.h, rook_ctas, sample_ctas, eval_ctas), "ttq_plan_set_config")
 
     def set_graphs(self, on: bool):
         _check(self.lib.ttq_plan_set_graphs(self.h, 1 if on else 0), "ttq_plan_set_graphs")

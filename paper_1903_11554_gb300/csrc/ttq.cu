@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <string>
@@ -33,19 +34,33 @@ static int set_err(int code, const char *msg) {
 enum { KT_EVAL = 0, KT_QR, KT_CONTRACT, KT_SAMPLES, KT_ROOK_COL, KT_ROOK_ROW, KT_UPDATE, KT_INIT, KT_SETUP,
        KT_SOLVE, KT_N };
 
+#define TTQ_MAX_CTAS_PER_IFACE 128   // reduction partials reserved per interface
+#define TTQ_RESULT_SLOTS 64
+
 struct TimedLaunch {
   int kid;
   cudaEvent_t a, b;
 };
 
+// A plan is a set of `count` instances (one integral each) that share every
+// kernel launch: instance q is blockIdx.z == q.  A single-integral plan is a
+// set of one; a batch is a set of many with uneven d, N and rank caps.
 struct ttq_plan {
-  Dev h;                    // host copy of the descriptor (device pointers inside)
-  Dev *dev;                 // descriptor in the workspace
-  State *st;                // mutable state in the workspace
+  int count;
+  Dev h;                    // host copy of instance 0's descriptor
+  Dev *dev;                 // instance 0's descriptor (device)
+  State *st;                // instance 0's state (device)
+  Dev **devs;               // device array of every instance's descriptor
+  Dev *hs;                  // host copies of every descriptor (&h when count == 1)
+  State **sts;              // every instance's state, device (&st when count == 1)
+  unsigned *guard;          // device loop counter of a batch's WHILE node
   cudaStream_t stream;
-  int grid_eval, qr_smem;
+  // launch configuration (batch maxima)
+  int max_ni, rook_max, max_sweeps, max_cap;
+  int grid_eval, sblocks, cblocks, rblocks, max_sum_n;
+  int qr_smem, samples_smem, contract_smem, solve_smem;
   long long launches;
-  State *hst;               // pinned host mirror of the state
+  State *hst;               // pinned host mirror of the states (count entries)
   int timing;               // 1: bracket every launch with CUDA events
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> pool;
@@ -54,17 +69,14 @@ struct ttq_plan {
   long long h2d, d2h;       // bytes copied host<->device by this plan
   cudaStream_t s2;          // side stream: the contraction runs beside the pivot search
   cudaEvent_t fork, join;
-  int use_graph;            // replay one captured sweep graph (timing off)
+  int use_graph;            // whole run as one graph (timing off, not the legacy stream)
   cudaGraphExec_t sweep_exec;
-  cudaGraphExec_t run_exec; // whole run: WHILE(not stopped) { one sweep }
+  cudaGraphExec_t run_exec; // WHILE(any instance running) { one sweep }
   cudaGraphConditionalHandle cond;
   int in_loop;              // enqueueing the body of the WHILE node
   int sweep_kernels;        // kernels in one sweep
-  int samples_smem, contract_smem, solve_smem;
   State *slots;             // pinned host copies of the final state of launched runs
-  int nslots;
 };
-#define TTQ_RESULT_SLOTS 64
 
 static cudaEvent_t ev_get(ttq_plan *P) {
   if (!P->pool.empty()) {
@@ -154,6 +166,7 @@ struct Layout {
   size_t Y[TTQ_MAXD + 1], V[TTQ_MAXD + 1], Vlo[TTQ_MAXD + 1];
   size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], rinv[TTQ_MAXD], zvec[TTQ_MAXD];
   size_t cs[TTQ_MAXD], ce[TTQ_MAXD];
+  size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
   int sblocks, cblocks, rblocks;
 };
@@ -209,8 +222,8 @@ static void make_layout(const ttq_problem *p, Layout *L) {
   L->sblocks = clampi((maxS + TTQ_WARPS - 1) / TTQ_WARPS, 1, 64);
   L->cblocks = clampi(((long)cap * nch + TTQ_WARPS - 1) / TTQ_WARPS, 1, 96);
   L->rblocks = L->cblocks;
-  int mb = L->sblocks > L->cblocks ? L->sblocks : L->cblocks;
-  L->part = b.take((size_t)(d - 1) * mb * 3 * 8);
+  L->part = b.take((size_t)(d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8);
+  L->devs = b.take(sizeof(Dev *));
   L->total = (b.off + 255) & ~(size_t)255;
 }
 
@@ -224,7 +237,7 @@ extern "C" int ttq_workspace_bytes(const ttq_problem *p, size_t *bytes) {
   return TTQ_OK;
 }
 
-static bool uniform_pair_table(const ttq_problem *p, const std::vector<double> &x) {
+static bool uniform_pair_table(const ttq_problem *p, const double *x) {
   if (p->family != TTQ_FAMILY_D || p->form != TTQ_FORM_RN) return false;
   const int d = p->d, N = p->nodes_per_mode[0];
   for (int k = 1; k < d; ++k) {
@@ -244,61 +257,29 @@ static bool uniform_pair_table(const ttq_problem *p, const std::vector<double> &
 
 // ---------------------------------------------------------------------------
 
-static void set_smem_sizes(ttq_plan *P) {
-  const size_t cap = P->h.cap;
-  P->h.q_in_smem = cap <= 96 ? 1 : 0;
-  P->samples_smem = (int)((P->h.q_in_smem ? 2 : 1) * cap * cap * 8);
-  P->contract_smem = (int)(cap * cap * 8);
-  P->solve_smem = (int)((P->h.q_in_smem ? 2 : 1) * cap * cap * 8);
-}
-
-static cudaError_t set_smem_attributes(ttq_plan *P) {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
-}
-
-extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t bytes, void *stream, ttq_plan **out) {
-  int rc = validate(p);
-  if (rc) return rc;
-  if (!out) return set_err(TTQ_ERR_INVALID_ARG, "null out");
-  Layout L;
-  make_layout(p, &L);
-  if (!workspace || bytes < L.total || ((uintptr_t)workspace & 255))
-    return set_err(TTQ_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
-  const int d = p->d;
-  size_t sumN = 0;
-  for (int k = 0; k < d; ++k) sumN += p->nodes_per_mode[k];
-  std::vector<double> hx(sumN), hw(sumN);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (p->inputs_on_device) {
-    CK(cudaMemcpyAsync(hx.data(), p->nodes, sumN * 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hw.data(), p->weights, sumN * 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-  } else {
-    memcpy(hx.data(), p->nodes, sumN * 8);
-    memcpy(hw.data(), p->weights, sumN * 8);
+static double family_constant(const ttq_problem *p) {
+  if (p->family == TTQ_FAMILY_TEST) return 1.0;
+  if (p->form == TTQ_FORM_RN) {
+    double f = 1.0;
+    for (int q = 2; q <= p->n; ++q) f *= q;
+    return 4.0 / f;
   }
-  for (size_t q = 0; q < sumN; ++q)
-    if (!isfinite(hx[q]) || !isfinite(hw[q])) return set_err(TTQ_ERR_INVALID_ARG, "non-finite node or weight");
+  return 2.0;
+}
 
-  ttq_plan *P = new ttq_plan();
-  char *base = (char *)workspace;
-  Dev &D = P->h;
+// Host descriptor of one instance laid out at `base` (device pointers only; nothing is copied).
+static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, const Layout &L,
+                            int q_in_smem, Dev &D) {
+  const int d = p->d;
   memset(&D, 0, sizeof(D));
   D.d = d; D.family = p->family; D.form = p->form; D.n = p->n; D.cap = p->rank_cap;
   D.rook_max = p->rook_max; D.init_samples = p->init_samples; D.conv_window = p->conv_window;
   D.max_sweeps = p->max_sweeps; D.prec = p->precision;
   D.tol = p->tol; D.pivot_tol = p->pivot_tol; D.seed = p->seed;
-  if (p->family == TTQ_FAMILY_TEST) D.constant = 1.0;
-  else if (p->form == TTQ_FORM_RN) { double f = 1.0; for (int q = 2; q <= p->n; ++q) f *= q; D.constant = 4.0 / f; }
-  else D.constant = 2.0;
+  D.constant = family_constant(p);
   D.uniformT = uniform_pair_table(p, hx) ? 1 : 0;
   D.sblocks = L.sblocks; D.cblocks = L.cblocks; D.rblocks = L.rblocks;
+  D.q_in_smem = q_in_smem;
   int off = 0;
   for (int k = 0; k < d; ++k) { D.N[k] = p->nodes_per_mode[k]; D.off[k] = off; off += D.N[k]; }
   for (int k = 1; k < d; ++k) D.S[k] = samples_for(p, k);
@@ -319,94 +300,244 @@ extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t byt
   }
   D.part = (double *)(base + L.part);
   D.st = (State *)(base + L.st);
-  P->dev = (Dev *)(base + L.dev);
-  P->st = D.st;
-  P->stream = s;
-  P->launches = 0;
-  size_t maxfib = 0;
-  for (int k = 1; k <= d; ++k) maxfib += (size_t)D.capL[k - 1] * D.capL[k];
-  size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
-  P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
-  P->qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + 4 * (size_t)p->rank_cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+4r
-  set_smem_sizes(P);
-  if (cudaMallocHost((void **)&P->hst, sizeof(State)) != cudaSuccess) {
-    delete P;
-    return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
-  }
-
-  cudaError_t e;
-  if ((e = set_smem_attributes(P)) != cudaSuccess) goto fail;
-  if ((e = cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking)) != cudaSuccess) goto fail;
-  if ((e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming)) != cudaSuccess) goto fail;
-  if ((e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming)) != cudaSuccess) goto fail;
-  P->use_graph = s != nullptr ? 1 : 0;   // no capture on the legacy default stream
-  if ((e = cudaMemcpyAsync(base + L.x, hx.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
-  if ((e = cudaMemcpyAsync(base + L.w, hw.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
-  P->h2d += (long long)(2 * sumN * 8 + sizeof(Dev));
-  if (p->inputs_on_device) P->d2h += (long long)(2 * sumN * 8);
-  if ((e = cudaMemsetAsync(D.st, 0, sizeof(State), s)) != cudaSuccess) goto fail;
-  if ((e = cudaMemsetAsync(D.part, 0, (size_t)(d - 1) * (L.sblocks > L.cblocks ? L.sblocks : L.cblocks) * 24, s)) != cudaSuccess) goto fail;
-  if ((e = cudaMemcpyAsync(P->dev, &D, sizeof(Dev), cudaMemcpyHostToDevice, s)) != cudaSuccess) goto fail;
-  timed(P, KT_SETUP, [&] { k_setup<<<(int)((sumN + 255) / 256), 256, 0, s>>>(P->dev, (int)sumN); });
-  if ((e = cudaGetLastError()) != cudaSuccess) goto fail;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) goto fail;
-  *out = P;
-  return TTQ_OK;
-fail:
-  g_last_error = std::string("plan setup: ") + cudaGetErrorString(e);
-  if (P->s2) cudaStreamDestroy(P->s2);
-  if (P->fork) cudaEventDestroy(P->fork);
-  if (P->join) cudaEventDestroy(P->join);
-  cudaFreeHost(P->hst);
-  delete P;
-  return TTQ_ERR_CUDA;
 }
 
-extern "C" int ttq_plan_destroy(ttq_plan *P) {
-  if (!P) return TTQ_OK;
+// host copies of a problem's nodes and weights (checked finite)
+static int host_inputs(const ttq_problem *p, cudaStream_t s, std::vector<double> &hx, std::vector<double> &hw) {
+  size_t sumN = 0;
+  for (int k = 0; k < p->d; ++k) sumN += p->nodes_per_mode[k];
+  hx.resize(sumN);
+  hw.resize(sumN);
+  if (p->inputs_on_device) {
+    CK(cudaMemcpyAsync(hx.data(), p->nodes, sumN * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hw.data(), p->weights, sumN * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    memcpy(hx.data(), p->nodes, sumN * 8);
+    memcpy(hw.data(), p->weights, sumN * 8);
+  }
+  for (size_t q = 0; q < sumN; ++q)
+    if (!isfinite(hx[q]) || !isfinite(hw[q])) return set_err(TTQ_ERR_INVALID_ARG, "non-finite node or weight");
+  return TTQ_OK;
+}
+
+// launch configuration from the instances' problems (maxima over the set)
+static void configure(ttq_plan *P, const ttq_problem *probs, int count, const Layout *Ls) {
+  P->max_ni = 0; P->rook_max = 1; P->max_sweeps = 1; P->max_cap = 1; P->max_sum_n = 1;
+  P->sblocks = P->cblocks = P->rblocks = 1;
+  size_t maxfib = 0;
+  for (int q = 0; q < count; ++q) {
+    const ttq_problem *p = probs + q;
+    const int cap = p->rank_cap;
+    P->max_ni = p->d - 1 > P->max_ni ? p->d - 1 : P->max_ni;
+    P->rook_max = p->rook_max > P->rook_max ? p->rook_max : P->rook_max;
+    P->max_sweeps = p->max_sweeps > P->max_sweeps ? p->max_sweeps : P->max_sweeps;
+    P->max_cap = cap > P->max_cap ? cap : P->max_cap;
+    int sn = 0;
+    for (int k = 0; k < p->d; ++k) sn += p->nodes_per_mode[k];
+    P->max_sum_n = sn > P->max_sum_n ? sn : P->max_sum_n;
+    size_t fib = 0;
+    for (int k = 1; k <= p->d; ++k) fib += (size_t)((k == 1) ? 1 : cap) * ((k == p->d) ? 1 : cap);
+    maxfib = fib > maxfib ? fib : maxfib;
+    P->sblocks = Ls[q].sblocks > P->sblocks ? Ls[q].sblocks : P->sblocks;
+    P->cblocks = Ls[q].cblocks > P->cblocks ? Ls[q].cblocks : P->cblocks;
+  }
+  P->rblocks = P->cblocks;
+  size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
+  P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
+  const size_t cap = P->max_cap;
+  const int q_in = cap <= 96 ? 1 : 0;
+  P->qr_smem = (int)((cap * (cap + 1) + 4 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+4r
+  P->samples_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
+  P->contract_smem = (int)(cap * cap * 8);
+  P->solve_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
+}
+
+static cudaError_t set_smem_attributes(ttq_plan *P) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
+}
+
+static void plan_free(ttq_plan *P) {
+  if (!P) return;
   if (!P->pending.empty()) cudaStreamSynchronize(P->stream);
   harvest(P);
   for (cudaEvent_t e : P->pool) cudaEventDestroy(e);
   if (P->sweep_exec) cudaGraphExecDestroy(P->sweep_exec);
   if (P->run_exec) cudaGraphExecDestroy(P->run_exec);
-  if (P->slots) cudaFreeHost(P->slots);
   if (P->s2) { cudaStreamSynchronize(P->s2); cudaStreamDestroy(P->s2); }
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->join) cudaEventDestroy(P->join);
-  cudaFreeHost(P->hst);
+  if (P->slots) cudaFreeHost(P->slots);
+  if (P->hst) cudaFreeHost(P->hst);
+  if (P->count > 1) {
+    delete[] P->hs;
+    delete[] P->sts;
+  }
   delete P;
+}
+
+// Instances laid out one after another in `workspace`: an optional array of
+// descriptor pointers for the set, then each instance's own layout.
+static int plan_build(const ttq_problem *probs, int count, void *workspace, size_t bytes, void *stream,
+                      ttq_plan **out) {
+  if (count < 1 || count > 65535) return set_err(TTQ_ERR_INVALID_ARG, "count must be in 1..65535");
+  if (!out) return set_err(TTQ_ERR_INVALID_ARG, "null out");
+  std::vector<Layout> Ls(count);
+  size_t need = count > 1 ? (((size_t)count * sizeof(Dev *) + 255) & ~(size_t)255) : 0;
+  std::vector<size_t> offs(count);
+  for (int q = 0; q < count; ++q) {
+    int rc = validate(probs + q);
+    if (rc) return rc;
+    make_layout(probs + q, &Ls[q]);
+    offs[q] = need;
+    need += Ls[q].total;
+  }
+  if (!workspace || bytes < need || ((uintptr_t)workspace & 255))
+    return set_err(TTQ_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  ttq_plan *P = new ttq_plan();
+  P->count = count;
+  P->stream = s;
+  configure(P, probs, count, Ls.data());
+  P->hs = count == 1 ? &P->h : new Dev[count];
+  P->sts = count == 1 ? &P->st : new State *[count];
+  char *base0 = (char *)workspace;
+  std::vector<Dev *> devp(count);
+  cudaError_t e = cudaSuccess;
+  int rc = TTQ_OK;
+  if (cudaMallocHost((void **)&P->hst, sizeof(State) * count) != cudaSuccess) {
+    P->hst = nullptr;
+    plan_free(P);
+    return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
+  }
+  for (int q = 0; q < count && !rc; ++q) {
+    const ttq_problem *p = probs + q;
+    char *base = base0 + offs[q];
+    std::vector<double> hx, hw;
+    if ((rc = host_inputs(p, s, hx, hw))) break;
+    fill_descriptor(p, hx.data(), base, Ls[q], P->max_cap <= 96 ? 1 : 0, P->hs[q]);
+    devp[q] = (Dev *)(base + Ls[q].dev);
+    P->sts[q] = P->hs[q].st;
+    const size_t sumN = hx.size();
+    if ((e = cudaMemcpyAsync(base + Ls[q].x, hx.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(base + Ls[q].w, hw.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(P->hs[q].st, 0, sizeof(State), s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(P->hs[q].part, 0, (size_t)(p->d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(devp[q], &P->hs[q], sizeof(Dev), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    P->h2d += (long long)(2 * sumN * 8 + sizeof(Dev));
+    if (p->inputs_on_device) P->d2h += (long long)(2 * sumN * 8);
+    // this instance's own one-entry descriptor array
+    Dev **own = (Dev **)(base + Ls[q].devs);
+    if ((e = cudaMemcpyAsync(own, &devp[q], sizeof(Dev *), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if (count == 1) P->devs = own;
+    // each host copy's transfers must finish before hx/hw go out of scope
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+  }
+  if (!rc && e == cudaSuccess && count > 1) {
+    P->devs = (Dev **)base0;
+    e = cudaMemcpyAsync(P->devs, devp.data(), count * sizeof(Dev *), cudaMemcpyHostToDevice, s);
+    P->h2d += (long long)(count * sizeof(Dev *));
+  }
+  if (!rc && e == cudaSuccess) {
+    P->h = P->hs[0];
+    P->dev = devp[0];
+    P->st = P->sts[0];
+    P->guard = (unsigned *)((char *)P->sts[0] + offsetof(State, batch_guard));
+    if ((e = set_smem_attributes(P)) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming)) == cudaSuccess &&
+        (e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming)) == cudaSuccess) {
+      P->use_graph = s != nullptr ? 1 : 0;   // no capture on the legacy default stream
+      timed(P, KT_SETUP, [&] {
+        k_setup<<<dim3((P->max_sum_n + 255) / 256, 1, count), 256, 0, s>>>(P->devs);
+      });
+      if ((e = cudaGetLastError()) == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+  }
+  if (rc || e != cudaSuccess) {
+    if (!rc) {
+      g_last_error = std::string("plan setup: ") + cudaGetErrorString(e);
+      rc = TTQ_ERR_CUDA;
+    }
+    plan_free(P);
+    return rc;
+  }
+  *out = P;
   return TTQ_OK;
 }
 
-// One sweep: eval -> qr -> { contract (side stream) | samples -> rook rounds } -> update.
+extern "C" int ttq_plan_create(const ttq_problem *p, void *workspace, size_t bytes, void *stream, ttq_plan **out) {
+  return plan_build(p, 1, workspace, bytes, stream, out);
+}
+
+extern "C" int ttq_plan_destroy(ttq_plan *P) {
+  plan_free(P);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_batch_workspace_bytes(const ttq_problem *probs, int count, size_t *bytes) {
+  if (!probs || !bytes || count < 1 || count > 65535) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
+  size_t need = count > 1 ? (((size_t)count * sizeof(Dev *) + 255) & ~(size_t)255) : 0;
+  for (int q = 0; q < count; ++q) {
+    int rc = validate(probs + q);
+    if (rc) return rc;
+    Layout L;
+    make_layout(probs + q, &L);
+    need += L.total;
+  }
+  *bytes = need;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_batch_create(const ttq_problem *probs, int count, void *workspace, size_t bytes, void *stream,
+                                ttq_plan **out) {
+  if (!probs) return set_err(TTQ_ERR_INVALID_ARG, "null problems");
+  return plan_build(probs, count, workspace, bytes, stream, out);
+}
+
+// ---------------------------------------------------------------------------
+// One sweep for every instance: eval -> qr -> { contract (side stream) |
+// samples -> rook rounds } -> update.  Every launch covers all instances
+// (grid z); CTAs of instances or interfaces with no work exit at once.
 static void enqueue_sweep(ttq_plan *P) {
-  const Dev &D = P->h;
   cudaStream_t s = P->stream;
-  const int ni = D.d - 1;
-  Dev *dv = P->dev;
-  timed(P, KT_EVAL, [&] { k_eval_slabs<<<P->grid_eval, TTQ_WARPS * 32, 0, s>>>(dv); });
-  timed(P, KT_QR, [&] { k_qr<<<ni, 256, P->qr_smem, s>>>(dv); });
+  const int ni = P->max_ni, nb = P->count;
+  Dev *const *dv = P->devs;
+  timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+  timed(P, KT_QR, [&] { k_qr<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
   if (P->s2) {
     cudaEventRecord(P->fork, s);
     cudaStreamWaitEvent(P->s2, P->fork, 0);
-    timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->s2>>>(dv, 0); });
+    timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, nb), 256, P->contract_smem, P->s2>>>(dv, 0); });
     cudaEventRecord(P->join, P->s2);
   } else {
-    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, s>>>(dv, 0); });
+    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
-  timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(D.sblocks, ni), TTQ_WARPS * 32, P->samples_smem, s>>>(dv); });
-  for (int q = 0; q < D.rook_max; ++q) {
-    timed(P, KT_SOLVE, [&] { k_solve<<<ni, 256, P->solve_smem, s>>>(dv, 0); });
-    timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(D.cblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
-    timed(P, KT_SOLVE, [&] { k_solve<<<ni, 256, P->solve_smem, s>>>(dv, 1); });
-    timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(D.rblocks, ni), TTQ_WARPS * 32, 0, s>>>(dv); });
+  timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), TTQ_WARPS * 32, P->samples_smem, s>>>(dv); });
+  for (int q = 0; q < P->rook_max; ++q) {
+    timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 0); });
+    timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, ni, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+    timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 1); });
+    timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, ni, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
   }
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
-  timed(P, KT_UPDATE, [&] { k_update<<<1, 32, 0, s>>>(dv, P->cond, P->in_loop); });
+  const int single_cond = P->in_loop && nb == 1;
+  timed(P, KT_UPDATE, [&] { k_update<<<dim3(1, 1, nb), 32, 0, s>>>(dv, P->cond, single_cond); });
+  if (P->in_loop && nb > 1) {
+    k_batch_cond<<<1, 256, 0, s>>>(dv, nb, P->max_sweeps, P->guard, P->cond);
+    P->launches++;
+  }
 }
 
 // Whole run as one graph: a conditional WHILE node whose body is one sweep;
-// k_update sets the condition, so a run needs no host round trip per sweep.
+// the condition is set on the device (k_update for one instance, k_batch_cond
+// for a batch), so a run needs no host round trip per sweep.
 static int build_run_graph(ttq_plan *P) {
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
@@ -445,7 +576,7 @@ static int build_run_graph(ttq_plan *P) {
 }
 
 static int launch_sweep(ttq_plan *P) {
-  if (P->use_graph && !P->timing) {
+  if (P->use_graph && !P->timing && P->count == 1) {
     if (!P->sweep_exec) {
       cudaGraph_t g = nullptr;
       const long long l0 = P->launches;
@@ -455,12 +586,13 @@ static int launch_sweep(ttq_plan *P) {
       enqueue_sweep(P);
       cudaError_t e = cudaStreamEndCapture(P->stream, &g);
       if (e != cudaSuccess) { g_last_error = std::string("sweep capture: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
-      P->sweep_kernels = (int)(P->launches - l0);
+      const int nk = (int)(P->launches - l0);
       P->launches = l0;
       memcpy(P->kt_n, n0, sizeof(n0));
       e = cudaGraphInstantiate(&P->sweep_exec, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) { g_last_error = std::string("sweep graph: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+      P->sweep_kernels = nk;
     }
     CK(cudaGraphLaunch(P->sweep_exec, P->stream));
     P->launches += P->sweep_kernels;
@@ -471,23 +603,25 @@ static int launch_sweep(ttq_plan *P) {
   return TTQ_OK;
 }
 
-static int read_state(ttq_plan *P) {
-  CK(cudaMemcpyAsync(P->hst, P->st, sizeof(State), cudaMemcpyDeviceToHost, P->stream));
-  P->d2h += sizeof(State);
+// copy every instance's state to the host mirror and wait
+static int read_states(ttq_plan *P) {
+  for (int q = 0; q < P->count; ++q)
+    CK(cudaMemcpyAsync(P->hst + q, P->sts[q], sizeof(State), cudaMemcpyDeviceToHost, P->stream));
+  P->d2h += (long long)sizeof(State) * P->count;
   CK(cudaStreamSynchronize(P->stream));
   harvest(P);
   return TTQ_OK;
 }
+static int read_state(ttq_plan *P) { return read_states(P); }
 
 extern "C" int ttq_plan_init(ttq_plan *P) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
-  timed(P, KT_INIT, [&] { k_init<<<1, TTQ_WARPS * 32, 0, P->stream>>>(P->dev); });
+  timed(P, KT_INIT, [&] { k_init<<<dim3(1, 1, P->count), TTQ_WARPS * 32, 0, P->stream>>>(P->devs); });
   CK(cudaGetLastError());
   return TTQ_OK;
 }
 
-static void fill_result_from(const ttq_plan *P, const State &S, ttq_result *out) {
-  const Dev &D = P->h;
+static void fill_result_from(const Dev &D, const State &S, ttq_result *out) {
   out->value = S.value;
   out->value_lo = S.value_lo;
   out->internal_conv = S.conv;
@@ -502,10 +636,83 @@ static void fill_result_from(const ttq_plan *P, const State &S, ttq_result *out)
   out->reserved = 0;
 }
 
-static void fill_result(const ttq_plan *P, ttq_result *out) { fill_result_from(P, *P->hst, out); }
+static int any_prec(const ttq_plan *P) {
+  for (int q = 0; q < P->count; ++q)
+    if (P->hs[q].prec) return 1;
+  return 0;
+}
+
+// enqueue a whole run of every instance (graph path); returns without waiting
+static int enqueue_run(ttq_plan *P) {
+  int rc;
+  if ((rc = ttq_plan_init(P))) return rc;
+  k_begin<<<dim3(1, 1, P->count), 1, 0, P->stream>>>(P->devs, 0, 1, 1);
+  P->launches++;
+  CK(cudaGetLastError());
+  if (P->count > 1) CK(cudaMemsetAsync(P->guard, 0, sizeof(unsigned), P->stream));
+  if (!P->run_exec && (rc = build_run_graph(P))) return rc;
+  CK(cudaGraphLaunch(P->run_exec, P->stream));
+  if (any_prec(P)) {                        // double-double contraction of the final sets
+    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
+    CK(cudaGetLastError());
+  }
+  return TTQ_OK;
+}
+
+// run every instance to its stop (blocking); states land in P->hst
+static int run_all(ttq_plan *P) {
+  int rc;
+  if (P->use_graph && !P->timing) {
+    if ((rc = enqueue_run(P))) return rc;
+    if ((rc = read_states(P))) return rc;
+    int mx = 0;
+    for (int q = 0; q < P->count; ++q) mx = P->hst[q].loop_guard > mx ? P->hst[q].loop_guard : mx;
+    P->launches += (long long)P->sweep_kernels * mx;
+    return TTQ_OK;
+  }
+  if ((rc = ttq_plan_init(P))) return rc;
+  k_begin<<<dim3(1, 1, P->count), 1, 0, P->stream>>>(P->devs, 0, 1, 1);
+  P->launches++;
+  CK(cudaGetLastError());
+  const int batch = 2;
+  for (int s = 0; s < P->max_sweeps; s += batch) {
+    for (int b = 0; b < batch; ++b)
+      if ((rc = launch_sweep(P))) return rc;
+    int all = 1;
+    for (int q = 0; q < P->count; ++q)
+      CK(cudaMemcpyAsync(&P->hst[q].stop, &P->sts[q]->stop, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    P->d2h += (long long)sizeof(int) * P->count;
+    CK(cudaStreamSynchronize(P->stream));
+    harvest(P);
+    for (int q = 0; q < P->count; ++q) all &= P->hst[q].stop ? 1 : 0;
+    if (all) break;
+  }
+  if (any_prec(P)) {
+    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
+    CK(cudaGetLastError());
+  }
+  return read_states(P);
+}
+
+extern "C" int ttq_plan_run(ttq_plan *P, ttq_result *out) {
+  if (!P || !out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  int rc = run_all(P);
+  if (rc) return rc;
+  fill_result_from(P->hs[0], P->hst[0], out);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_batch_run(ttq_plan *P, ttq_result *results) {
+  if (!P || !results) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  int rc = run_all(P);
+  if (rc) return rc;
+  for (int q = 0; q < P->count; ++q) fill_result_from(P->hs[q], P->hst[q], results + q);
+  return TTQ_OK;
+}
 
 extern "C" int ttq_plan_launch(ttq_plan *P, int slot) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "ttq_plan_launch needs a single-instance plan");
   if (slot < 0 || slot >= TTQ_RESULT_SLOTS) return set_err(TTQ_ERR_INVALID_ARG, "slot out of range");
   if (!P->slots) {                          // first launch: pinned result slots (warm up before timing)
     if (cudaMallocHost((void **)&P->slots, sizeof(State) * TTQ_RESULT_SLOTS) != cudaSuccess)
@@ -513,21 +720,11 @@ extern "C" int ttq_plan_launch(ttq_plan *P, int slot) {
   }
   int rc;
   if (!(P->use_graph && !P->timing)) {      // plain launches need the host in the loop: run now
-    ttq_result tmp;
-    if ((rc = ttq_plan_run(P, &tmp))) return rc;
+    if ((rc = run_all(P))) return rc;
     memcpy(&P->slots[slot], P->hst, sizeof(State));
     return TTQ_OK;
   }
-  if ((rc = ttq_plan_init(P))) return rc;
-  k_begin<<<1, 1, 0, P->stream>>>(P->dev, 0, 1, 1);
-  P->launches++;
-  CK(cudaGetLastError());
-  if (!P->run_exec && (rc = build_run_graph(P))) return rc;
-  CK(cudaGraphLaunch(P->run_exec, P->stream));
-  if (P->h.prec) {
-    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
-    CK(cudaGetLastError());
-  }
+  if ((rc = enqueue_run(P))) return rc;
   CK(cudaMemcpyAsync(&P->slots[slot], P->st, sizeof(State), cudaMemcpyDeviceToHost, P->stream));
   P->d2h += sizeof(State);
   return TTQ_OK;
@@ -540,59 +737,93 @@ extern "C" int ttq_plan_result(ttq_plan *P, int slot, ttq_result *out) {
   harvest(P);
   const State &S = P->slots[slot];
   P->launches += (long long)P->sweep_kernels * S.loop_guard;
-  fill_result_from(P, S, out);
+  fill_result_from(P->h, S, out);
   return TTQ_OK;
 }
 
-extern "C" int ttq_plan_run(ttq_plan *P, ttq_result *out) {
-  if (!P || !out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
-  int rc = ttq_plan_init(P);
-  if (rc) return rc;
-  k_begin<<<1, 1, 0, P->stream>>>(P->dev, 0, 1, 1);
-  P->launches++;
-  CK(cudaGetLastError());
-  if (P->use_graph && !P->timing) {
-    if (!P->run_exec && (rc = build_run_graph(P))) return rc;
-    CK(cudaGraphLaunch(P->run_exec, P->stream));
-    if ((rc = read_state(P))) return rc;
-    P->launches += (long long)P->sweep_kernels * P->hst->loop_guard;
-    if (P->h.prec) {
-      timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
-      CK(cudaGetLastError());
-      if ((rc = read_state(P))) return rc;
-    }
-    fill_result(P, out);
-    return TTQ_OK;
-  }
-  const int batch = 2;
-  for (int s = 0; s < P->h.max_sweeps; s += batch) {
-    for (int b = 0; b < batch; ++b)
-      if ((rc = launch_sweep(P))) return rc;
-    CK(cudaMemcpyAsync(&P->hst->stop, &P->st->stop, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-    P->d2h += sizeof(int);
-    CK(cudaStreamSynchronize(P->stream));
-    harvest(P);
-    if (P->hst->stop) break;
-  }
-  if (P->h.prec) {                          // double-double contraction of the final sets
-    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
+// Autotuner: CTAs per interface of the sample and rook kernels and CTAs per
+// instance of the evaluation kernel.  Every candidate computes the same
+// results (the reductions do not depend on the grid); each is timed with CUDA
+// events over `sweeps` sweeps from the initial sets and the fastest kept.
+extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
+  if (!P || sweeps < 1) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
+  const int cand_c[] = {8, 16, 32, 64, 96, 128};
+  const int cand_s[] = {8, 16, 32, 64, 128};
+  const int cand_e[] = {152, 304, 608, 1216};
+  const int save_timing = P->timing;
+  P->timing = 1;
+  auto time_cfg = [&](double *ms_out) -> int {
+    int rc;
+    if ((rc = ttq_plan_init(P))) return rc;
+    k_begin<<<dim3(1, 1, P->count), 1, 0, P->stream>>>(P->devs, 0, 1, 1);
     CK(cudaGetLastError());
+    double before[KT_N];
+    if ((rc = read_states(P))) return rc;
+    memcpy(before, P->kt_ms, sizeof(before));
+    for (int s = 0; s < sweeps; ++s)
+      if ((rc = launch_sweep(P))) return rc;
+    if ((rc = read_states(P))) return rc;
+    *ms_out = (P->kt_ms[KT_EVAL] - before[KT_EVAL]) + (P->kt_ms[KT_SAMPLES] - before[KT_SAMPLES]) +
+              (P->kt_ms[KT_ROOK_COL] - before[KT_ROOK_COL]) + (P->kt_ms[KT_ROOK_ROW] - before[KT_ROOK_ROW]);
+    return TTQ_OK;
+  };
+  int rc = TTQ_OK;
+  double best = 1e300, ms = 0;
+  int bc = P->cblocks, bs = P->sblocks, be = P->grid_eval;
+  for (int c : cand_c) {
+    P->cblocks = P->rblocks = c;
+    if ((rc = time_cfg(&ms))) break;
+    if (ms < best) { best = ms; bc = c; }
   }
-  if ((rc = read_state(P))) return rc;
-  fill_result(P, out);
+  P->cblocks = P->rblocks = bc;
+  best = 1e300;
+  for (int sb : cand_s) {
+    if (rc) break;
+    P->sblocks = sb;
+    if ((rc = time_cfg(&ms))) break;
+    if (ms < best) { best = ms; bs = sb; }
+  }
+  P->sblocks = bs;
+  best = 1e300;
+  for (int ge : cand_e) {
+    if (rc) break;
+    P->grid_eval = ge;
+    if ((rc = time_cfg(&ms))) break;
+    if (ms < best) { best = ms; be = ge; }
+  }
+  P->grid_eval = be;
+  P->timing = save_timing;
+  for (int k = 0; k < KT_N; ++k) { P->kt_ms[k] = 0.0; P->kt_n[k] = 0; }
+  if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
+  if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
+  if (chosen) { chosen[0] = P->cblocks; chosen[1] = P->sblocks; chosen[2] = P->grid_eval; }
+  return rc;
+}
+
+extern "C" int ttq_plan_set_config(ttq_plan *P, int rook_ctas, int sample_ctas, int eval_ctas) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (rook_ctas < 1 || rook_ctas > TTQ_MAX_CTAS_PER_IFACE || sample_ctas < 1 || sample_ctas > TTQ_MAX_CTAS_PER_IFACE ||
+      eval_ctas < 1 || eval_ctas > 65535)
+    return set_err(TTQ_ERR_INVALID_ARG, "CTA counts out of range");
+  P->cblocks = P->rblocks = rook_ctas;
+  P->sblocks = sample_ctas;
+  P->grid_eval = eval_ctas;
+  if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
+  if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
   return TTQ_OK;
 }
 
 extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *value, double *value_lo,
                               ttq_pivot *pivots) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
-  k_begin<<<1, 1, 0, P->stream>>>(P->dev, sweep_index, 0, search ? 1 : 0);
+  if (P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "stage calls need a single-instance plan");
+  k_begin<<<1, 1, 0, P->stream>>>(P->devs, sweep_index, 0, search ? 1 : 0);
   P->launches++;
   int rc = launch_sweep(P);
   if (rc) return rc;
   if (P->h.prec && !search) {               // this sweep's sets, contracted in double-double
     if (P->s2) CK(cudaStreamSynchronize(P->s2));
-    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->dev, 1); });
+    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
   if ((rc = read_state(P))) return rc;
@@ -619,6 +850,7 @@ extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *
 
 extern "C" int ttq_plan_set_state(ttq_plan *P, const int32_t *ranks, const int32_t *lpar, const int32_t *lnode,
                                   const int32_t *rpar, const int32_t *rnode) {
+  if (P && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "stage calls need a single-instance plan");
   if (!P || !ranks || !lpar || !lnode || !rpar || !rnode) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
   const Dev &D = P->h;
   const int d = D.d;
@@ -674,6 +906,7 @@ extern "C" int ttq_plan_set_state(ttq_plan *P, const int32_t *ranks, const int32
 
 extern "C" int ttq_plan_get_state(ttq_plan *P, int32_t *ranks, int32_t *lpar, int32_t *lnode, int32_t *rpar,
                                   int32_t *rnode) {
+  if (P && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "stage calls need a single-instance plan");
   if (!P || !ranks) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
   int rc = read_state(P);
   if (rc) return rc;
@@ -693,6 +926,7 @@ extern "C" int ttq_plan_get_state(ttq_plan *P, int32_t *ranks, int32_t *lpar, in
 }
 
 extern "C" int ttq_plan_get_core(ttq_plan *P, int k, double *host_out) {
+  if (P && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "stage calls need a single-instance plan");
   if (!P || !host_out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
   const Dev &D = P->h;
   if (k < 1 || k > D.d) return set_err(TTQ_ERR_INVALID_ARG, "k out of range");
@@ -709,11 +943,12 @@ extern "C" int ttq_plan_get_core(ttq_plan *P, int k, double *host_out) {
 }
 
 extern "C" int ttq_plan_eval_points(ttq_plan *P, const int32_t *idx, int64_t npts, double *out) {
+  if (P && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "stage calls need a single-instance plan");
   if (!P || (!idx && npts) || (!out && npts) || npts < 0) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
   if (npts == 0) return TTQ_OK;
   long long blocks = (npts + TTQ_WARPS - 1) / TTQ_WARPS;
   if (blocks > 4096) blocks = 4096;
-  k_eval_points<<<(int)blocks, TTQ_WARPS * 32, 0, P->stream>>>(P->dev, idx, npts, out);
+  k_eval_points<<<(int)blocks, TTQ_WARPS * 32, 0, P->stream>>>(P->devs, idx, npts, out);
   P->launches++;   // not part of a sweep: counted, not timed
   CK(cudaGetLastError());
   return TTQ_OK;
@@ -742,12 +977,16 @@ extern "C" int ttq_plan_set_timing(ttq_plan *P, int enable) {
 
 extern "C" int ttq_plan_kernel_times(ttq_plan *P, double *ms, int64_t *launches, double *flops, int reset) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
-  int rc = read_state(P);               // synchronizes and harvests the pending events
+  int rc = read_states(P);               // synchronizes and harvests the pending events
   if (rc) return rc;
   for (int q = 0; q < KT_N; ++q) {
     if (ms) ms[q] = P->kt_ms[q];
     if (launches) launches[q] = P->kt_n[q];
-    if (flops) flops[q] = (double)P->hst->flops[q];
+    if (flops) {
+      double f = 0.0;
+      for (int i = 0; i < P->count; ++i) f += (double)P->hst[i].flops[q];
+      flops[q] = f;
+    }
     if (reset) { P->kt_ms[q] = 0.0; P->kt_n[q] = 0; }
   }
   return TTQ_OK;
@@ -773,6 +1012,7 @@ extern "C" const char *ttq_status_string(int s) {
 
 extern "C" const char *ttq_last_error(void) { return g_last_error.c_str(); }
 
+
 // ---------------------------------------------------------------------------
 // Entry point for callers that cannot allocate device memory.
 //
@@ -789,23 +1029,6 @@ extern "C" const char *ttq_last_error(void) { return g_last_error.c_str(); }
 // size: TTQ_NOALLOC_SCRATCH_BYTES (16 MiB), include/ttq.h
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TTQ_NOALLOC_SCRATCH_BYTES];
 static void *g_noalloc_ptr[256];           // device address of the scratch, per device id
-
-static bool uniform_pair_table_host(const ttq_problem *p, const double *x) {
-  if (p->family != TTQ_FAMILY_D || p->form != TTQ_FORM_RN) return false;
-  const int d = p->d, N = p->nodes_per_mode[0];
-  for (int k = 1; k < d; ++k) {
-    if (p->nodes_per_mode[k] != N) return false;
-    for (int i = 0; i < N; ++i)
-      if (x[(size_t)k * N + i] != x[i]) return false;
-  }
-  for (int a = 0; a < N; ++a)
-    for (int b = 0; b < N; ++b) {
-      double dlt = x[a] - x[b];
-      double ref = (a >= b) ? (x[a - b] - x[0]) : -(x[b - a] - x[0]);
-      if (dlt != ref) return false;
-    }
-  return true;
-}
 
 extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_result *out) {
   int rc = validate(p);
@@ -834,57 +1057,29 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
 
   ttq_plan P{};                             // on the stack, zeroed; its vectors stay empty (timing off)
   State host_state;
-  Dev &D = P.h;
-  memset(&D, 0, sizeof(D));
-  D.d = d; D.family = p->family; D.form = p->form; D.n = p->n; D.cap = p->rank_cap;
-  D.rook_max = p->rook_max; D.init_samples = p->init_samples; D.conv_window = p->conv_window;
-  D.max_sweeps = p->max_sweeps; D.prec = p->precision;
-  D.tol = p->tol; D.pivot_tol = p->pivot_tol; D.seed = p->seed;
-  if (p->family == TTQ_FAMILY_TEST) D.constant = 1.0;
-  else if (p->form == TTQ_FORM_RN) { double f = 1.0; for (int q = 2; q <= p->n; ++q) f *= q; D.constant = 4.0 / f; }
-  else D.constant = 2.0;
-  D.uniformT = uniform_pair_table_host(p, p->nodes) ? 1 : 0;
-  D.sblocks = L.sblocks; D.cblocks = L.cblocks; D.rblocks = L.rblocks;
-  int off = 0;
-  for (int k = 0; k < d; ++k) { D.N[k] = p->nodes_per_mode[k]; D.off[k] = off; off += D.N[k]; }
-  for (int k = 1; k < d; ++k) D.S[k] = samples_for(p, k);
-  for (int k = 0; k <= d; ++k) D.capL[k] = (k == 0 || k == d) ? 1 : p->rank_cap;
-  D.x = (const double *)(base + L.x); D.w = (const double *)(base + L.w);
-  D.c = (const double *)(base + L.c); D.T = (const double *)(base + L.T);
-  for (int k = 1; k < d; ++k) {
-    D.lidx[k] = (int *)(base + L.lidx[k]); D.ridx[k] = (int *)(base + L.ridx[k]);
-    D.lpar[k] = (int *)(base + L.lpar[k]); D.lnode[k] = (int *)(base + L.lnode[k]);
-    D.rpar[k] = (int *)(base + L.rpar[k]); D.rnode[k] = (int *)(base + L.rnode[k]);
-    D.Qr[k] = (double *)(base + L.Qr[k]); D.Qc[k] = (double *)(base + L.Qc[k]);
-    D.Rc[k] = (double *)(base + L.Rc[k]); D.Rr[k] = (double *)(base + L.Rr[k]);
-    D.rinv[k] = (double *)(base + L.rinv[k]); D.zvec[k] = (double *)(base + L.zvec[k]);
-    D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
-  }
-  for (int k = 1; k <= d; ++k) {
-    D.Y[k] = (double *)(base + L.Y[k]); D.V[k] = (double *)(base + L.V[k]); D.Vlo[k] = (double *)(base + L.Vlo[k]);
-  }
-  D.part = (double *)(base + L.part);
-  D.st = (State *)(base + L.st);
-  P.dev = (Dev *)(base + L.dev);
-  P.st = D.st;
+  P.count = 1;
   P.stream = (cudaStream_t)stream;
   P.hst = &host_state;
-  size_t maxfib = 0;
-  for (int k = 1; k <= d; ++k) maxfib += (size_t)D.capL[k - 1] * D.capL[k];
-  size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
-  P.grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
-  P.qr_smem = (int)(((size_t)p->rank_cap * (p->rank_cap + 1) + 4 * (size_t)p->rank_cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+4r
+  P.hs = &P.h;
+  P.sts = &P.st;
+  configure(&P, p, 1, &L);
+  fill_descriptor(p, p->nodes, base, L, P.max_cap <= 96 ? 1 : 0, P.h);
+  P.dev = (Dev *)(base + L.dev);
+  P.st = P.h.st;
+  P.devs = (Dev **)(base + L.devs);
+  Dev *devp = P.dev;
   cudaStream_t s = P.stream;
   // the scratch keeps the previous call's contents: everything read before it is
   // written (node tables, descriptor, state, reduction partials) is set here
-  set_smem_sizes(&P);
   CK(set_smem_attributes(&P));
   CK(cudaMemcpyAsync(base + L.x, p->nodes, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(base + L.w, p->weights, sumN * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemsetAsync(D.st, 0, sizeof(State), s));
-  CK(cudaMemsetAsync(D.part, 0, (size_t)(d - 1) * (L.sblocks > L.cblocks ? L.sblocks : L.cblocks) * 24, s));
-  CK(cudaMemcpyAsync(P.dev, &D, sizeof(Dev), cudaMemcpyHostToDevice, s));
-  k_setup<<<(int)((sumN + 255) / 256), 256, 0, s>>>(P.dev, (int)sumN);
+  CK(cudaMemsetAsync(P.h.st, 0, sizeof(State), s));
+  CK(cudaMemsetAsync(P.h.part, 0, (size_t)(d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8, s));
+  CK(cudaMemcpyAsync(P.dev, &P.h, sizeof(Dev), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.devs, &devp, sizeof(Dev *), cudaMemcpyHostToDevice, s));
+  k_setup<<<dim3((P.max_sum_n + 255) / 256, 1, 1), 256, 0, s>>>(P.devs);
   CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));             // the host sources above live on this stack frame
   return ttq_plan_run(&P, out);
 }

@@ -60,6 +60,7 @@ struct State {
   int nchanges;
   int stop_pending;         // a stopping rule fired in this sweep's contraction; applied by k_update
   int loop_guard;           // sweeps run by the device-side loop of this run (bounded by max_sweeps)
+  unsigned batch_guard;     // sweeps run by a batch's loop (used in instance 0 of a batch)
   int pending_status;
   int qr_rank[TTQ_MAXD];    // size of the stored QR factors of G_k (0: none)
   unsigned long long scale_bits;   // max |core entry| as IEEE bits (non-negative)

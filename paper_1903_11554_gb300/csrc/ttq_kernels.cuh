@@ -111,8 +111,9 @@ __device__ bool cta_pick_last(double myscore, const Dev &D, int k, int count, in
 
 // ---------------------------------------------------------------------------
 
-__global__ void k_setup(Dev *Dp, int total) {
-  const Dev &D = *Dp;
+__global__ void k_setup(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
+  const int total = D.off[D.d - 1] + D.N[D.d - 1];
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < total && D.form == FORM_RN) const_cast<double *>(D.c)[t] = 2.0 * cosh(D.x[t]);
   if (D.uniformT && t < D.N[0]) {
@@ -122,8 +123,8 @@ __global__ void k_setup(Dev *Dp, int total) {
 }
 
 // weighted entries at explicit multi-indices, one warp per point
-__global__ void k_eval_points(Dev *Dp, const int *idx, long long npts, double *out) {
-  const Dev &D = *Dp;
+__global__ void k_eval_points(Dev *const *Dps, const int *idx, long long npts, double *out) {
+  const Dev &D = *Dps[blockIdx.z];
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
   __shared__ double pl[TTQ_WARPS][TTQ_MAXPAIR];
   const int lane = lane_id(), warp = warp_id();
@@ -139,8 +140,8 @@ __global__ void k_eval_points(Dev *Dp, const int *idx, long long npts, double *o
 }
 
 // initial index set: the largest |A| among init_samples seeded points
-__global__ void k_init(Dev *Dp) {
-  const Dev &D = *Dp;
+__global__ void k_init(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
   __shared__ double pl[TTQ_WARPS][TTQ_MAXPAIR];
@@ -194,8 +195,8 @@ __global__ void k_init(Dev *Dp) {
 // Kernel (a): evaluate every core entry that is new since the previous sweep.
 // Fibers (k, alpha, beta) with alpha >= ro[k-1] or beta >= ro[k]; one warp per fiber,
 // lanes over the N_k nodes; writes Y_k and the node sums V_k(alpha, beta).
-__global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *Dp) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   if (st->stop) return;
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
@@ -430,12 +431,13 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
   qr_store_R(D, k, r, Rs, ls, true);
 }
 
-__global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   if (st->stop) return;
   extern __shared__ double sm[];
   const int k = blockIdx.x + 1;
+  if (k > D.d - 1) return;                  // instances with fewer interfaces (batches)
   const int r = st->r[k];
   const int have = st->qr_rank[k];
   if (threadIdx.x == 0) {
@@ -461,13 +463,13 @@ __global__ void __launch_bounds__(256) k_qr(Dev *Dp) {
 // warp), the products with Q_k and V_{k+1} spread over all threads.  It only
 // feeds the stopping rule, so it runs beside the pivot search; a rule that
 // fires is recorded as pending and applied at the end of the sweep.
-__global__ void __launch_bounds__(256) k_contract(Dev *Dp, int final_dd) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   // per sweep: FP64 contraction for the stopping rule; final_dd: the
   // double-double contraction of the final sets (after the run stopped)
   if (st->stop && !final_dd) return;
-  if (final_dd && (st->nonfinite || st->singular)) return;
+  if (final_dd && (!D.prec || st->nonfinite || st->singular)) return;
   const int prec = final_dd;
   extern __shared__ double sm[];
   __shared__ double xh[TTQ_MAXR], xl[TTQ_MAXR], th[TTQ_MAXR], tl[TTQ_MAXR];
@@ -593,10 +595,11 @@ __global__ void __launch_bounds__(256) k_contract(Dev *Dp, int final_dd) {
 // The solve of the next rook step, one CTA per interface with R_k staged in
 // shared memory: mode 0 z = G^-1 y for the column step, y = R_{k+1}(:, gamma*);
 // mode 1 b = G^-T l for the row step, l = L_k(rho*, :)^T.  Result in zvec[k].
-__global__ void __launch_bounds__(256) k_solve(Dev *Dp, int mode) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   const int k = blockIdx.x + 1;
+  if (k > D.d - 1) return;
   if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
   if (!I.active || I.rook_done) return;
@@ -679,6 +682,7 @@ struct RookSmem {
 };
 
 __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, int k) {
+  if (k > D.d - 1) return false;            // instances with fewer interfaces (batches)
   if (st->stop || !st->search) return false;
   const int rk = st->r[k];
   if (rk >= D.cap) return false;
@@ -688,8 +692,8 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
 }
 
 // Alg. 2, first step: residuals E = A - B_k R_{k+1} at seeded random positions.
-__global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *Dp) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   const int k = blockIdx.y + 1;
   if (!iface_searchable(D, st, k)) return;
@@ -768,10 +772,11 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *Dp) {
 }
 
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i); argmax -> rho*.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *Dp) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   const int k = blockIdx.y + 1;
+  if (k > D.d - 1) return;
   if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
   if (!I.active || I.rook_done) return;
@@ -866,10 +871,11 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *Dp) {
 
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta); argmax -> gamma_new,
 // then the rook test (Eq. 2): gamma_new == gamma* ends the search.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *Dp) {
-  const Dev &D = *Dp;
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   const int k = blockIdx.y + 1;
+  if (k > D.d - 1) return;
   if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
   if (!I.active || I.rook_done) return;
@@ -969,8 +975,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *Dp) {
 // End of sweep (Alg. 6): append every accepted pivot, nested by construction.
 // Inside the whole-run graph it also sets the WHILE condition: continue while
 // the run is not over, never past max_sweeps (every path reaches the end).
-__global__ void k_update(Dev *Dp, cudaGraphConditionalHandle h, int use_cond) {
-  const Dev &D = *Dp;
+__global__ void k_update(Dev *const *Dps, cudaGraphConditionalHandle h, int use_cond) {
+  const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   const int d = D.d;
   const int k = threadIdx.x + 1;            // one thread per interface (d - 1 <= 31)
@@ -1028,14 +1034,27 @@ __global__ void k_update(Dev *Dp, cudaGraphConditionalHandle h, int use_cond) {
   }
 }
 
-__global__ void k_begin(Dev *Dp, int sweep, int rules, int search) {
-  State *st = Dp->st;
+__global__ void k_begin(Dev *const *Dps, int sweep, int rules, int search) {
+  State *st = Dps[blockIdx.z]->st;
   st->sweep = sweep;
   st->rules = rules;
   st->search = search;
   st->stop_pending = 0;
   st->loop_guard = 0;
   if (!rules) st->stop = 0;
+}
+
+// End of a batched sweep inside the whole-run graph: continue while any
+// instance of the batch is still running (bounded by the largest max_sweeps).
+__global__ void k_batch_cond(Dev *const *Dps, int count, int max_sweeps, unsigned *guard,
+                             cudaGraphConditionalHandle h) {
+  int running = 0;
+  for (int q = threadIdx.x; q < count; q += blockDim.x) running |= !Dps[q]->st->stop;
+  running = __syncthreads_or(running);
+  if (threadIdx.x == 0) {
+    const unsigned g = ++(*guard);
+    cudaGraphSetConditional(h, (running && g < (unsigned)max_sweeps + 2) ? 1u : 0u);
+  }
 }
 
 }  // namespace ttq

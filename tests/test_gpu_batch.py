@@ -1,0 +1,72 @@
+"""Batches (many integrals advancing together in one launch per stage): every
+instance's result equals what a single plan gives for its problem, bit for
+bit, whatever the mix and the grid shapes (needs a GB300)."""
+import numpy as np
+import pytest
+
+from oracle import ttcross
+from paper_1903_11554_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1903_11554_gb300 import build
+    build.build()
+
+
+def mix():
+    return [
+        inputs.make_problem("C", "rn", 4, 41, L=10.0, rank_cap=12, seed=3),
+        inputs.make_problem("D", "rn", 5, 33, L=8.0, rank_cap=10, seed=4),
+        inputs.make_problem("E", "cube", 6, 33, rank_cap=20, seed=5),
+        inputs.make_problem("D", "cube", 7, 17, rank_cap=8, seed=6),
+        inputs.make_problem("C", "cube", 9, 65, rank_cap=24, seed=7),
+        inputs.make_problem("E", "cube", 5, 48, rank_cap=16, precision="dd", seed=8),
+        inputs.make_problem("TEST", "cube", 4, 33, d=7, rank_cap=8, seed=9),
+        inputs.make_problem("D", "rn", 6, 49, L=12.0, rank_cap=16, seed=10),
+        inputs.make_problem("C", "rn", 3, 129, L=16.0, rank_cap=32, seed=11),
+    ]
+
+
+def test_batch_matches_single_plans():
+    from paper_1903_11554_gb300 import binding
+    probs = mix()
+    singles = [binding.integrate(p) for p in probs]
+    got = binding.Batch(probs).run()
+    for a, b in zip(got, singles):
+        assert a == b
+
+
+def test_batch_matches_oracle():
+    from paper_1903_11554_gb300 import binding
+    probs = mix()[:5]
+    got = binding.Batch(probs).run()
+    for p, g in zip(probs, got):
+        ref = ttcross.integrate(p)["value"]
+        assert abs(g["value"] - ref) <= 1e-12 * abs(ref)
+
+
+def test_grid_shapes_and_autotune_do_not_change_results():
+    from paper_1903_11554_gb300 import binding
+    probs = mix()
+    b = binding.Batch(probs)
+    ref = b.run()
+    b.set_config(7, 5, 33)
+    assert b.run() == ref
+    chosen = b.autotune(sweeps=2)
+    assert all(v >= 1 for v in chosen.values())
+    assert b.run() == ref
+
+
+def test_batch_plain_launches_match_graph():
+    from paper_1903_11554_gb300 import binding
+    probs = mix()[:4]
+    b = binding.Batch(probs)
+    a = b.run()
+    b.set_graphs(False)
+    assert b.run() == a
