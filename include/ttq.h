@@ -173,6 +173,31 @@ int ttq_batch_run(ttq_plan *batch, ttq_result *results /* [count] */);
 int ttq_batch_autotune(ttq_plan *plan, int sweeps, int32_t *chosen);
 int ttq_plan_set_config(ttq_plan *plan, int rook_ctas, int sample_ctas, int eval_ctas);
 
+/* --- serving: continuous batching -----------------------------------------
+ * A server owns a caller-allocated device pool (`pool`, pool_bytes, 256-byte
+ * aligned; its size is the HBM admission budget) and at most max_slots
+ * integrals in flight.  ttq_server_submit copies a request (host arrays) into
+ * the server's arrival queue and returns its id; a request whose plan
+ * footprint (ttq_workspace_bytes, reserved at its rank cap) exceeds the pool
+ * is refused with TTQ_ERR_ADMISSION.  ttq_server_step, at a sweep boundary:
+ * retires the requests that stopped (their memory returns to the pool, their
+ * result becomes available), admits queued requests in arrival order while a
+ * slot and pool memory are free, and enqueues `sweeps` sweeps of every
+ * request in flight, all of them in the same batched kernel launches.  Each
+ * result equals what a single plan gives for the same problem, whatever else
+ * is in flight.  ttq_server_poll returns TTQ_PENDING until a request is done;
+ * ttq_server_drain returns up to max finished results at once.
+ * ttq_server_stats: [in flight, queued, admitted, retired, sweeps run, free
+ * pool bytes].  A server is not thread-safe. */
+typedef struct ttq_server ttq_server;
+int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, void *stream, ttq_server **out);
+int ttq_server_destroy(ttq_server *server);
+int ttq_server_submit(ttq_server *server, const ttq_problem *p, uint64_t *request_id);
+int ttq_server_step(ttq_server *server, int sweeps, int *in_flight, int *queued, int64_t *completed);
+int ttq_server_poll(ttq_server *server, uint64_t request_id, ttq_result *out);
+int ttq_server_drain(ttq_server *server, uint64_t *ids, ttq_result *results, int max, int *n);
+int ttq_server_stats(const ttq_server *server, int64_t *stats /* [6] */);
+
 /* --- stage-level entry points (replay and inspection) ------------------- */
 
 /* Initial index set: the largest |A| among init_samples seeded random points. */

@@ -73,6 +73,15 @@ SIGNATURES = {
     "ttq_batch_run": (_c.c_int, [_vp, _c.POINTER(TTQResult)]),
     "ttq_batch_autotune": (_c.c_int, [_vp, _c.c_int, _i32p]),
     "ttq_plan_set_config": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
+    "ttq_server_create": (_c.c_int, [_vp, _c.c_size_t, _c.c_int, _vp, _c.POINTER(_vp)]),
+    "ttq_server_destroy": (_c.c_int, [_vp]),
+    "ttq_server_submit": (_c.c_int, [_vp, _c.POINTER(TTQProblem), _c.POINTER(_c.c_uint64)]),
+    "ttq_server_step": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
+                                   _c.POINTER(_c.c_int64)]),
+    "ttq_server_poll": (_c.c_int, [_vp, _c.c_uint64, _c.POINTER(TTQResult)]),
+    "ttq_server_drain": (_c.c_int, [_vp, _c.POINTER(_c.c_uint64), _c.POINTER(TTQResult), _c.c_int,
+                                    _c.POINTER(_c.c_int)]),
+    "ttq_server_stats": (_c.c_int, [_vp, _c.POINTER(_c.c_int64)]),
     "ttq_status_string": (_c.c_char_p, [_c.c_int]),
     "ttq_last_error": (_c.c_char_p, []),
 }
@@ -369,6 +378,71 @@ class Batch:
     @property
     def launches(self) -> int:
         return int(self.lib.ttq_plan_launches(self.h))
+
+
+class Server:
+    """Continuous batching: requests join and leave the set in flight at sweep
+    boundaries; admission by the plan footprint against a device pool."""
+
+    def __init__(self, pool_bytes: int, max_slots: int = 512, stream=None, pool=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise TTQError("no CUDA device: the TT-cross quadrature runs only on the GPU")
+        self.lib = load()
+        if pool is None:
+            pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+        self.pool = pool
+        if stream is None:
+            stream = torch.cuda.Stream()
+            stream.wait_stream(torch.cuda.current_stream())
+        self.stream = stream
+        h = _vp()
+        _check(self.lib.ttq_server_create(_vp(pool.data_ptr()), pool_bytes, max_slots, _vp(stream.cuda_stream),
+                                          _c.byref(h)), "ttq_server_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ttq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, p: inputs.Problem) -> int:
+        arrays = _Arrays(p)
+        st = make_struct(p, arrays)
+        rid = _c.c_uint64(0)
+        _check(self.lib.ttq_server_submit(self.h, _c.byref(st), _c.byref(rid)), "ttq_server_submit")
+        return int(rid.value)
+
+    def step(self, sweeps: int = 1):
+        a, q, c = _c.c_int(0), _c.c_int(0), _c.c_int64(0)
+        _check(self.lib.ttq_server_step(self.h, sweeps, _c.byref(a), _c.byref(q), _c.byref(c)), "ttq_server_step")
+        return a.value, q.value, int(c.value)
+
+    def poll(self, rid: int):
+        res = TTQResult()
+        rc = self.lib.ttq_server_poll(self.h, rid, _c.byref(res))
+        if rc == 4:
+            return None
+        _check(rc, "ttq_server_poll")
+        return _result_dict(res)
+
+    def drain(self, max_n: int = 4096):
+        ids = (_c.c_uint64 * max_n)()
+        res = (TTQResult * max_n)()
+        n = _c.c_int(0)
+        _check(self.lib.ttq_server_drain(self.h, ids, res, max_n, _c.byref(n)), "ttq_server_drain")
+        return {int(ids[q]): _result_dict(res[q]) for q in range(n.value)}
+
+    def stats(self):
+        st = (_c.c_int64 * 6)()
+        _check(self.lib.ttq_server_stats(self.h, st), "ttq_server_stats")
+        return dict(zip(("in_flight", "queued", "admitted", "retired", "sweeps", "free_bytes"), list(st)))
 
 
 def integrate(p: inputs.Problem) -> Dict:

@@ -1083,3 +1083,324 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
   CK(cudaStreamSynchronize(s));             // the host sources above live on this stack frame
   return ttq_plan_run(&P, out);
 }
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching.
+//
+// Requests are queued on the host as they arrive.  At every step boundary the
+// server (1) retires the instances that stopped (double-double contraction if
+// asked, state copied back, memory returned to the pool), (2) admits queued
+// requests in arrival order while a slot and pool memory (the plan footprint
+// at the request's rank cap) are free, initializing them on the device, and
+// (3) runs `sweeps` sweeps of every instance in flight with the batched
+// kernels (one launch per stage for the whole set).  Each instance's
+// arithmetic is independent of the others, so a result is the same alone and
+// in any mix.
+#include <map>
+#include <deque>
+#include <unordered_map>
+
+struct Request {
+  uint64_t id;
+  ttq_problem p;                    // host copy; arrays below
+  std::vector<int32_t> N;
+  std::vector<double> x, w;
+  size_t bytes;                     // plan footprint at the rank cap
+};
+
+struct Slot {
+  Request req;
+  size_t off;                       // offset of its workspace in the pool
+  Layout L;
+  Dev h;
+  Dev *dev;
+  Dev **own;                        // its one-entry descriptor array
+  int fresh;                        // admitted at this boundary: not yet initialized
+};
+
+struct ttq_server {
+  char *pool;
+  size_t pool_bytes;
+  int max_slots;
+  cudaStream_t stream;
+  std::map<size_t, size_t> free_list;       // offset -> size, coalesced
+  std::deque<Request> queue;
+  std::vector<Slot> active;
+  std::unordered_map<uint64_t, ttq_result> done;
+  uint64_t next_id;
+  ttq_plan P;                               // launch configuration over the active set
+  Dev **devs;                               // device array of the active descriptors (pool head)
+  State *hst;                               // pinned host states (max_slots)
+  long long sweeps_run, admitted, retired;
+};
+
+static size_t pool_alloc(ttq_server *S, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  for (auto it = S->free_list.begin(); it != S->free_list.end(); ++it) {
+    if (it->second >= bytes) {
+      size_t off = it->first, rest = it->second - bytes;
+      S->free_list.erase(it);
+      if (rest) S->free_list[off + bytes] = rest;
+      return off;
+    }
+  }
+  return (size_t)-1;
+}
+
+static void pool_free(ttq_server *S, size_t off, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  auto it = S->free_list.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != S->free_list.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    S->free_list.erase(nx);
+  }
+  if (it != S->free_list.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      S->free_list.erase(it);
+    }
+  }
+}
+
+extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, void *stream, ttq_server **out) {
+  if (!pool || !out || max_slots < 1 || max_slots > 4096 || ((uintptr_t)pool & 255))
+    return set_err(TTQ_ERR_INVALID_ARG, "bad server arguments");
+  size_t head = ((size_t)max_slots * sizeof(Dev *) + 255) & ~(size_t)255;
+  if (pool_bytes <= head) return set_err(TTQ_ERR_WORKSPACE, "pool too small");
+  ttq_server *S = new ttq_server();
+  S->pool = (char *)pool;
+  S->pool_bytes = pool_bytes;
+  S->max_slots = max_slots;
+  S->stream = (cudaStream_t)stream;
+  S->devs = (Dev **)pool;
+  S->free_list[head] = (pool_bytes - head) & ~(size_t)255;
+  S->next_id = 1;
+  if (cudaMallocHost((void **)&S->hst, sizeof(State) * max_slots) != cudaSuccess) {
+    delete S;
+    return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
+  }
+  S->P.stream = S->stream;
+  S->P.devs = S->devs;
+  S->P.hst = S->hst;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&S->P.s2, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&S->P.fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&S->P.join, cudaEventDisableTiming)) != cudaSuccess) {
+    g_last_error = std::string("server setup: ") + cudaGetErrorString(e);
+    cudaFreeHost(S->hst);
+    delete S;
+    return TTQ_ERR_CUDA;
+  }
+  *out = S;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_destroy(ttq_server *S) {
+  if (!S) return TTQ_OK;
+  cudaStreamSynchronize(S->stream);
+  if (S->P.s2) { cudaStreamSynchronize(S->P.s2); cudaStreamDestroy(S->P.s2); }
+  if (S->P.fork) cudaEventDestroy(S->P.fork);
+  if (S->P.join) cudaEventDestroy(S->P.join);
+  S->P.s2 = nullptr;
+  S->P.hs = nullptr;
+  S->P.sts = nullptr;
+  cudaFreeHost(S->hst);
+  delete S;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_submit(ttq_server *S, const ttq_problem *p, uint64_t *request_id) {
+  if (!S || !p) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  int rc = validate(p);
+  if (rc) return rc;
+  Layout L;
+  make_layout(p, &L);
+  size_t head = ((size_t)S->max_slots * sizeof(Dev *) + 255) & ~(size_t)255;
+  if (L.total > S->pool_bytes - head) return set_err(TTQ_ERR_ADMISSION, "request larger than the server's memory pool");
+  Request r;
+  r.id = S->next_id++;
+  r.p = *p;
+  r.N.assign(p->nodes_per_mode, p->nodes_per_mode + p->d);
+  if ((rc = host_inputs(p, S->stream, r.x, r.w))) return rc;
+  r.p.nodes_per_mode = nullptr;             // re-pointed at admission
+  r.p.inputs_on_device = 0;
+  r.bytes = L.total;
+  S->queue.push_back(std::move(r));
+  if (request_id) *request_id = S->queue.back().id;
+  return TTQ_OK;
+}
+
+static void repoint(Request &r) {
+  r.p.nodes_per_mode = r.N.data();
+  r.p.nodes = r.x.data();
+  r.p.weights = r.w.data();
+}
+
+// admit what fits; build and upload each new instance's descriptor and inputs
+static int server_admit(ttq_server *S) {
+  while (!S->queue.empty() && (int)S->active.size() < S->max_slots) {
+    Request &r = S->queue.front();
+    size_t off = pool_alloc(S, r.bytes);
+    if (off == (size_t)-1) break;           // wait for memory (arrival order is kept)
+    Slot sl;
+    sl.req = std::move(r);
+    S->queue.pop_front();
+    repoint(sl.req);
+    sl.off = off;
+    make_layout(&sl.req.p, &sl.L);
+    char *base = S->pool + off;
+    fill_descriptor(&sl.req.p, sl.req.x.data(), base, sl.L, 0, sl.h);
+    sl.dev = (Dev *)(base + sl.L.dev);
+    sl.own = (Dev **)(base + sl.L.devs);
+    sl.fresh = 1;
+    const size_t sumN = sl.req.x.size();
+    cudaStream_t s = S->stream;
+    CK(cudaMemcpyAsync(base + sl.L.x, sl.req.x.data(), sumN * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(base + sl.L.w, sl.req.w.data(), sumN * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(sl.h.st, 0, sizeof(State), s));
+    CK(cudaMemsetAsync(sl.h.part, 0, (size_t)(sl.req.p.d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8, s));
+    S->active.push_back(std::move(sl));
+    Slot &a = S->active.back();
+    repoint(a.req);                         // vectors moved: pointers refreshed
+    a.h.x = (const double *)(base + a.L.x);
+    CK(cudaMemcpyAsync(a.dev, &a.h, sizeof(Dev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(a.own, &a.dev, sizeof(Dev *), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));           // host sources must outlive the copies
+    S->admitted++;
+  }
+  return TTQ_OK;
+}
+
+// launch configuration and descriptor array of the current active set
+static int server_configure(ttq_server *S) {
+  const int n = (int)S->active.size();
+  if (n == 0) return TTQ_OK;
+  std::vector<ttq_problem> probs(n);
+  std::vector<Layout> Ls(n);
+  std::vector<Dev *> dp(n);
+  for (int q = 0; q < n; ++q) {
+    probs[q] = S->active[q].req.p;
+    Ls[q] = S->active[q].L;
+    dp[q] = S->active[q].dev;
+  }
+  ttq_plan &P = S->P;
+  P.count = n;
+  configure(&P, probs.data(), n, Ls.data());
+  // the search kernels stage Q in shared memory only when the largest cap allows
+  for (int q = 0; q < n; ++q) {
+    Slot &a = S->active[q];
+    int qin = P.max_cap <= 96 ? 1 : 0;
+    if (a.h.q_in_smem != qin) {
+      a.h.q_in_smem = qin;
+      CK(cudaMemcpyAsync(a.dev, &a.h, sizeof(Dev), cudaMemcpyHostToDevice, S->stream));
+    }
+  }
+  CK(cudaMemcpyAsync(S->devs, dp.data(), n * sizeof(Dev *), cudaMemcpyHostToDevice, S->stream));
+  CK(set_smem_attributes(&P));
+  CK(cudaStreamSynchronize(S->stream));
+  return TTQ_OK;
+}
+
+// retire stopped instances: double-double contraction if asked, results, memory
+static int server_retire(ttq_server *S) {
+  const int n = (int)S->active.size();
+  if (n == 0) return TTQ_OK;
+  for (int q = 0; q < n; ++q)
+    CK(cudaMemcpyAsync(&S->hst[q].stop, (char *)S->active[q].h.st + offsetof(State, stop), sizeof(int),
+                       cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  std::vector<Slot> keep;
+  keep.reserve(n);
+  for (int q = 0; q < n; ++q) {
+    Slot &a = S->active[q];
+    if (!S->hst[q].stop) {
+      keep.push_back(std::move(a));
+      continue;
+    }
+    if (a.h.prec) {
+      const int cs = (int)((size_t)a.h.cap * a.h.cap * 8);
+      k_contract<<<1, 256, cs, S->stream>>>(a.own, 1);
+      CK(cudaGetLastError());
+    }
+    State st;
+    CK(cudaMemcpyAsync(&st, a.h.st, sizeof(State), cudaMemcpyDeviceToHost, S->stream));
+    CK(cudaStreamSynchronize(S->stream));
+    ttq_result res;
+    fill_result_from(a.h, st, &res);
+    S->done[a.req.id] = res;
+    pool_free(S, a.off, a.req.bytes);
+    S->retired++;
+  }
+  S->active.swap(keep);
+  for (auto &a : S->active) repoint(a.req);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_step(ttq_server *S, int sweeps, int *active, int *queued, int64_t *completed) {
+  if (!S || sweeps < 1) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
+  int rc;
+  if ((rc = server_retire(S))) return rc;
+  if ((rc = server_admit(S))) return rc;
+  if ((rc = server_configure(S))) return rc;
+  const int n = (int)S->active.size();
+  if (n) {
+    // initialize the instances admitted at this boundary (they join the next sweep)
+    for (auto &a : S->active) {
+      if (!a.fresh) continue;
+      const int sumN = a.h.off[a.h.d - 1] + a.h.N[a.h.d - 1];
+      k_setup<<<(sumN + 255) / 256, 256, 0, S->stream>>>(a.own);
+      k_init<<<1, TTQ_WARPS * 32, 0, S->stream>>>(a.own);
+      k_begin<<<1, 1, 0, S->stream>>>(a.own, 0, 1, 1);
+      a.fresh = 0;
+    }
+    CK(cudaGetLastError());
+    for (int s = 0; s < sweeps; ++s) enqueue_sweep(&S->P);
+    CK(cudaGetLastError());
+    S->sweeps_run += sweeps;
+  }
+  if (active) *active = (int)S->active.size();
+  if (queued) *queued = (int)S->queue.size();
+  if (completed) *completed = S->retired;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_poll(ttq_server *S, uint64_t request_id, ttq_result *out) {
+  if (!S || !out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  auto it = S->done.find(request_id);
+  if (it == S->done.end()) {
+    for (auto &a : S->active) if (a.req.id == request_id) return TTQ_PENDING;
+    for (auto &r : S->queue) if (r.id == request_id) return TTQ_PENDING;
+    return set_err(TTQ_ERR_NOT_FOUND, "unknown request");
+  }
+  *out = it->second;
+  S->done.erase(it);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_drain(ttq_server *S, uint64_t *ids, ttq_result *results, int max, int *n) {
+  if (!S || !n || (max > 0 && (!ids || !results))) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  int q = 0;
+  for (auto it = S->done.begin(); it != S->done.end() && q < max;) {
+    ids[q] = it->first;
+    results[q] = it->second;
+    ++q;
+    it = S->done.erase(it);
+  }
+  *n = q;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_stats(const ttq_server *S, int64_t *stats /* [6] */) {
+  if (!S || !stats) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  size_t free_bytes = 0;
+  for (auto &kv : S->free_list) free_bytes += kv.second;
+  stats[0] = (int64_t)S->active.size();
+  stats[1] = (int64_t)S->queue.size();
+  stats[2] = S->admitted;
+  stats[3] = S->retired;
+  stats[4] = S->sweeps_run;
+  stats[5] = (int64_t)free_bytes;
+  return TTQ_OK;
+}
