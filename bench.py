@@ -174,6 +174,94 @@ def cpu_baseline(wl, ranks_traj, budget):
 
 # --------------------------------------------------------------------------
 
+def measure_batched(binding, inputs, torch, count=256):
+    """The 256-instance mixed batch (families C/D/E cyclic, n in 4..24, N in
+    {65,129,257,513}, rank caps in {8..128}): autotuned, one warm-up run, one
+    timed run; the same problems one at a time on a subsample of 32 for the
+    single-instance comparison (results compared bit for bit)."""
+    probs = inputs.batched_mix(count)
+    b = binding.Batch(probs)
+    tuned = b.autotune(2)
+    b.run()
+    torch.cuda.synchronize()
+    t = time.time()
+    res = b.run()
+    dt = time.time() - t
+    del b
+    torch.cuda.empty_cache()
+    sub = list(range(0, count, max(1, count // 32)))
+    st, same = 0.0, True
+    for q in sub:
+        pl = binding.Plan(probs[q])
+        pl.run()
+        torch.cuda.synchronize()
+        t = time.time()
+        r = pl.run()
+        st += time.time() - t
+        same &= (r == res[q])
+        pl.close()
+    bs = binding.Batch([probs[q] for q in sub])
+    bs.autotune(2)
+    bs.run()
+    t = time.time()
+    bs.run()
+    dts = time.time() - t
+    return {"workload": "%d mixed instances (C/D/E cyclic, n 4..24, N 65..513, rank cap 8..128, tol 1e-12, "
+                        "seed 256+i)" % count,
+            "integrals_per_s": count / dt, "seconds": dt, "autotuned": tuned,
+            "statuses": {k: sum(1 for r in res if r["status_name"] == k) for k in set(r["status_name"] for r in res)},
+            "fiber_evals_per_s": sum(r["n_eval"] for r in res) / dt,
+            "subsample": {"count": len(sub), "batched_integrals_per_s": len(sub) / dts,
+                          "one_at_a_time_integrals_per_s": len(sub) / st,
+                          "results_identical_to_one_at_a_time": bool(same)}}
+
+
+def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120.0, max_slots=1024):
+    """Poisson arrivals (rate per second, seeded), families uniform over C/D/E,
+    n in 4..32, tol log-uniform in [1e-14, 1e-8], N in {129, 257, 513}, rank cap
+    64; HBM admission budget pool_gb.  Latency = completion seen by the host
+    minus scheduled arrival."""
+    arrivals, probs = inputs.serving_stream(count, rate)
+    pool_bytes = int(pool_gb * (1 << 30))
+    srv = binding.Server(pool_bytes, max_slots=max_slots)
+    t0 = time.time()
+    i, lat, when, ids = 0, {}, {}, {}
+    peak_flight, peak_queue = 0, 0
+    results = {}
+    while len(results) < count:
+        now = time.time() - t0
+        while i < count and arrivals[i] <= now:
+            rid = srv.submit(probs[i])
+            ids[rid] = i
+            when[rid] = arrivals[i]
+            i += 1
+        flight, queued, _ = srv.step(1)
+        peak_flight = max(peak_flight, flight)
+        peak_queue = max(peak_queue, queued)
+        done = srv.drain()
+        tnow = time.time() - t0
+        for rid, r in done.items():
+            results[rid] = r
+            lat[rid] = tnow - when[rid]
+        if flight == 0 and queued == 0 and i < count and not done:
+            time.sleep(max(0.0, min(0.01, arrivals[i] - (time.time() - t0))))
+    span = time.time() - t0
+    srv.close()
+    del srv
+    torch.cuda.empty_cache()
+    ls = sorted(lat.values())
+    # a few served results against the same problem run alone
+    same = True
+    for rid in list(results)[:8]:
+        same &= (binding.integrate(probs[ids[rid]]) == results[rid])
+    return {"workload": "Poisson %g req/s, %d requests (seed 2000), C/D/E, n 4..32, tol 1e-14..1e-8, N 129..513, "
+                        "rank cap 64, HBM admission budget %g GB" % (rate, count, pool_gb),
+            "offered_per_s": count / float(arrivals[-1]), "achieved_integrals_per_s": count / span,
+            "latency_s": {"p50": ls[len(ls) // 2], "p99": ls[min(len(ls) - 1, int(math.ceil(0.99 * len(ls))) - 1)]},
+            "peak_in_flight": peak_flight, "peak_queued": peak_queue, "seconds": span,
+            "served_equal_alone_on_8": bool(same)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -206,6 +294,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d12", choices=["d12", "c4", "e16"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-systems", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "plain"],
                     help="graph: one CUDA graph per integral (default); plain: every kernel a stream launch")
     args = ap.parse_args()
@@ -226,7 +316,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    from paper_1903_11554_gb300 import binding, build
+    from paper_1903_11554_gb300 import binding, build, inputs
     if rank == 0:
         build.build()
     barrier()
@@ -342,6 +432,12 @@ def main():
     e2e = {"value": e2e_steps * world / (e2e_ms / 1000.0), "unit": "integrals/s",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
 
+    systems = {}
+    if not args.no_systems and args.launch_mode == "graph":
+        del plan
+        torch.cuda.empty_cache()
+        systems["batched"] = measure_batched(binding, inputs, torch)
+        systems["serving"] = measure_serving(binding, inputs, torch, count=args.serving_requests)
     if rank != 0:
         return 0
     g = golden(args.workload)
@@ -364,6 +460,7 @@ def main():
                    "max_rank": results[-1]["max_rank"], "status": results[-1]["status_name"],
                    "n_eval": results[-1]["n_eval"], "internal_conv": results[-1]["internal_conv"], **check},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        **systems,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
