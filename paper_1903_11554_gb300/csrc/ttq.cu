@@ -34,7 +34,6 @@ static int set_err(int code, const char *msg) {
 enum { KT_EVAL = 0, KT_QR, KT_CONTRACT, KT_SAMPLES, KT_ROOK_COL, KT_ROOK_ROW, KT_UPDATE, KT_INIT, KT_SETUP,
        KT_SOLVE, KT_N };
 
-#define TTQ_MAX_CTAS_PER_IFACE 128   // reduction partials reserved per interface
 #define TTQ_RESULT_SLOTS 64
 
 struct TimedLaunch {
@@ -161,11 +160,11 @@ struct Bump {
 };
 
 struct Layout {
-  size_t dev, st, x, w, c, T, part;
+  size_t dev, st, x, w, c, T, cbuf;
   size_t lidx[TTQ_MAXD], ridx[TTQ_MAXD], lpar[TTQ_MAXD], lnode[TTQ_MAXD], rpar[TTQ_MAXD], rnode[TTQ_MAXD];
   size_t Y[TTQ_MAXD + 1], V[TTQ_MAXD + 1], Vlo[TTQ_MAXD + 1];
-  size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], rinv[TTQ_MAXD], zvec[TTQ_MAXD];
-  size_t cs[TTQ_MAXD], ce[TTQ_MAXD];
+  size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], rinv[TTQ_MAXD], zvec[TTQ_MAXD], pvec[TTQ_MAXD];
+  size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD];
   size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
   int sblocks, cblocks, rblocks;
@@ -210,19 +209,24 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     L->Rr[k] = b.take((size_t)cap * cap * 8);
     L->rinv[k] = b.take((size_t)cap * 8);
     L->zvec[k] = b.take((size_t)cap * 8);
+    L->pvec[k] = b.take((size_t)cap * 8);
     size_t nc = (size_t)samples_for(p, k);
     size_t ncol = (size_t)cap * p->nodes_per_mode[k - 1], nrow = (size_t)p->nodes_per_mode[k] * cap;
     nc = nc > ncol ? nc : ncol;
     nc = nc > nrow ? nc : nrow;
     L->cs[k] = b.take(nc * 8);
     L->ce[k] = b.take(nc * 8);
+    const size_t nchk = (p->nodes_per_mode[k - 1] + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    const size_t nchk1 = (p->nodes_per_mode[k] + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);
   }
   const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;
   auto clampi = [](long v, long lo, long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
   L->sblocks = clampi((maxS + TTQ_WARPS - 1) / TTQ_WARPS, 1, 64);
-  L->cblocks = clampi(((long)cap * nch + TTQ_WARPS - 1) / TTQ_WARPS, 1, 96);
+  // the rook kernels spread every interface's work over one grid per instance
+  L->cblocks = clampi(((long)(d - 1) * cap * nch + TTQ_WARPS - 1) / TTQ_WARPS, 1, 456);
   L->rblocks = L->cblocks;
-  L->part = b.take((size_t)(d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8);
+  L->cbuf = b.take((size_t)4 * cap * 8);
   L->devs = b.take(sizeof(Dev *));
   L->total = (b.off + 255) & ~(size_t)255;
 }
@@ -293,13 +297,15 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
     D.Qr[k] = (double *)(base + L.Qr[k]); D.Qc[k] = (double *)(base + L.Qc[k]);
     D.Rc[k] = (double *)(base + L.Rc[k]); D.Rr[k] = (double *)(base + L.Rr[k]);
     D.rinv[k] = (double *)(base + L.rinv[k]); D.zvec[k] = (double *)(base + L.zvec[k]);
+    D.pvec[k] = (double *)(base + L.pvec[k]);
     D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
+    D.im[k] = (double *)(base + L.im[k]);
   }
   for (int k = 1; k <= d; ++k) {
     D.Y[k] = (double *)(base + L.Y[k]); D.V[k] = (double *)(base + L.V[k]); D.Vlo[k] = (double *)(base + L.Vlo[k]);
   }
-  D.part = (double *)(base + L.part);
   D.st = (State *)(base + L.st);
+  D.cbuf = (double *)(base + L.cbuf);
 }
 
 // host copies of a problem's nodes and weights (checked finite)
@@ -347,7 +353,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
   const size_t cap = P->max_cap;
   const int q_in = cap <= 96 ? 1 : 0;
-  P->qr_smem = (int)((cap * (cap + 1) + 4 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+4r
+  P->qr_smem = (int)((cap * (cap + 1) + 8 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+7r
   P->samples_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
   P->contract_smem = (int)(cap * cap * 8);
   P->solve_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
@@ -428,7 +434,6 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
     if ((e = cudaMemcpyAsync(base + Ls[q].x, hx.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(base + Ls[q].w, hw.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(P->hs[q].st, 0, sizeof(State), s)) != cudaSuccess) break;
-    if ((e = cudaMemsetAsync(P->hs[q].part, 0, (size_t)(p->d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(devp[q], &P->hs[q], sizeof(Dev), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     P->h2d += (long long)(2 * sumN * 8 + sizeof(Dev));
     if (p->inputs_on_device) P->d2h += (long long)(2 * sumN * 8);
@@ -514,21 +519,22 @@ static void enqueue_sweep(ttq_plan *P) {
   if (P->s2) {
     cudaEventRecord(P->fork, s);
     cudaStreamWaitEvent(P->s2, P->fork, 0);
-    timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, nb), 256, P->contract_smem, P->s2>>>(dv, 0); });
+    timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, P->s2>>>(dv, 0); });
     cudaEventRecord(P->join, P->s2);
   } else {
-    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
+    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
   timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), TTQ_WARPS * 32, P->samples_smem, s>>>(dv); });
+  timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 0); });
   for (int q = 0; q < P->rook_max; ++q) {
-    timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 0); });
-    timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, ni, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+    timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
     timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 1); });
-    timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, ni, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+    timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+    timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 2); });
   }
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
   const int single_cond = P->in_loop && nb == 1;
-  timed(P, KT_UPDATE, [&] { k_update<<<dim3(1, 1, nb), 32, 0, s>>>(dv, P->cond, single_cond); });
+  timed(P, KT_UPDATE, [&] { k_update<<<dim3(1, 1, nb), 256, 0, s>>>(dv, P->cond, single_cond); });
   if (P->in_loop && nb > 1) {
     k_batch_cond<<<1, 256, 0, s>>>(dv, nb, P->max_sweeps, P->guard, P->cond);
     P->launches++;
@@ -653,7 +659,7 @@ static int enqueue_run(ttq_plan *P) {
   if (!P->run_exec && (rc = build_run_graph(P))) return rc;
   CK(cudaGraphLaunch(P->run_exec, P->stream));
   if (any_prec(P)) {                        // double-double contraction of the final sets
-    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
+    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
   return TTQ_OK;
@@ -688,7 +694,7 @@ static int run_all(ttq_plan *P) {
     if (all) break;
   }
   if (any_prec(P)) {
-    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(1, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
+    timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
   return read_states(P);
@@ -747,7 +753,7 @@ extern "C" int ttq_plan_result(ttq_plan *P, int slot, ttq_result *out) {
 // events over `sweeps` sweeps from the initial sets and the fastest kept.
 extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
   if (!P || sweeps < 1) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
-  const int cand_c[] = {8, 16, 32, 64, 96, 128};
+  const int cand_c[] = {4, 16, 38, 76, 152, 304, 456};
   const int cand_s[] = {8, 16, 32, 64, 128};
   const int cand_e[] = {152, 304, 608, 1216};
   const int save_timing = P->timing;
@@ -802,8 +808,8 @@ extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
 
 extern "C" int ttq_plan_set_config(ttq_plan *P, int rook_ctas, int sample_ctas, int eval_ctas) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
-  if (rook_ctas < 1 || rook_ctas > TTQ_MAX_CTAS_PER_IFACE || sample_ctas < 1 || sample_ctas > TTQ_MAX_CTAS_PER_IFACE ||
-      eval_ctas < 1 || eval_ctas > 65535)
+  if (rook_ctas < 1 || rook_ctas > 65535 || sample_ctas < 1 || sample_ctas > 65535 || eval_ctas < 1 ||
+      eval_ctas > 65535)
     return set_err(TTQ_ERR_INVALID_ARG, "CTA counts out of range");
   P->cblocks = P->rblocks = rook_ctas;
   P->sblocks = sample_ctas;
@@ -823,7 +829,7 @@ extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *
   if (rc) return rc;
   if (P->h.prec && !search) {               // this sweep's sets, contracted in double-double
     if (P->s2) CK(cudaStreamSynchronize(P->s2));
-    timed(P, KT_CONTRACT, [&] { k_contract<<<1, 256, P->contract_smem, P->stream>>>(P->devs, 1); });
+    timed(P, KT_CONTRACT, [&] { k_contract<<<2, 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
   if ((rc = read_state(P))) return rc;
@@ -1075,7 +1081,6 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
   CK(cudaMemcpyAsync(base + L.x, p->nodes, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(base + L.w, p->weights, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(P.h.st, 0, sizeof(State), s));
-  CK(cudaMemsetAsync(P.h.part, 0, (size_t)(d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8, s));
   CK(cudaMemcpyAsync(P.dev, &P.h, sizeof(Dev), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.devs, &devp, sizeof(Dev *), cudaMemcpyHostToDevice, s));
   k_setup<<<dim3((P.max_sum_n + 255) / 256, 1, 1), 256, 0, s>>>(P.devs);
@@ -1260,7 +1265,6 @@ static int server_admit(ttq_server *S) {
     CK(cudaMemcpyAsync(base + sl.L.x, sl.req.x.data(), sumN * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + sl.L.w, sl.req.w.data(), sumN * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(sl.h.st, 0, sizeof(State), s));
-    CK(cudaMemsetAsync(sl.h.part, 0, (size_t)(sl.req.p.d - 1) * TTQ_MAX_CTAS_PER_IFACE * 8, s));
     S->active.push_back(std::move(sl));
     Slot &a = S->active.back();
     repoint(a.req);                         // vectors moved: pointers refreshed
@@ -1321,7 +1325,7 @@ static int server_retire(ttq_server *S) {
     }
     if (a.h.prec) {
       const int cs = (int)((size_t)a.h.cap * a.h.cap * 8);
-      k_contract<<<1, 256, cs, S->stream>>>(a.own, 1);
+      k_contract<<<2, 256, cs, S->stream>>>(a.own, 1);
       CK(cudaGetLastError());
     }
     State st;

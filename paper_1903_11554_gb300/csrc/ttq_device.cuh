@@ -42,9 +42,11 @@ struct IfaceState {
   int rounds;
   int accepted;
   double err;          // residual at (row, col)
-  unsigned int counter;// last-CTA-done counter of the running reduction
+  unsigned long long evals;       // integrand evaluations of this sweep's search
+  unsigned long long smax_bits;   // max score of the running stage's candidates (IEEE bits, >= 0)
+  unsigned int stage_count;       // eligible candidates of the running stage
+  int prow, prank;                // pvec holds R^-T L_k(prow, :)^T for the rank-prank factors (-1: none)
   int pad;
-  unsigned long long evals;   // integrand evaluations of this sweep's search
 };
 
 struct State {
@@ -62,6 +64,7 @@ struct State {
   int loop_guard;           // sweeps run by the device-side loop of this run (bounded by max_sweeps)
   unsigned batch_guard;     // sweeps run by a batch's loop (used in instance 0 of a batch)
   int pending_status;
+  unsigned contract_arrive;  // CTAs of the two contraction chains that have finished
   int qr_rank[TTQ_MAXD];    // size of the stored QR factors of G_k (0: none)
   unsigned long long scale_bits;   // max |core entry| as IEEE bits (non-negative)
   double value, value_lo, prev, conv;
@@ -75,7 +78,7 @@ struct State {
 struct Dev {
   int d, family, form, n, cap, rook_max, init_samples, conv_window, max_sweeps, prec;
   int uniformT;             // 1: D in R^n on one shared uniform grid -> pair table T
-  int sblocks, cblocks, rblocks;   // CTAs per interface of the sample / column / row kernels
+  int sblocks, cblocks, rblocks;   // CTAs: per interface (samples), per instance (column / row)
   int q_in_smem;            // the sample kernel stages Q_k in shared memory too (cap <= 96)
   double tol, pivot_tol, constant;
   unsigned long long seed;
@@ -88,9 +91,11 @@ struct Dev {
   double *V[TTQ_MAXD + 1], *Vlo[TTQ_MAXD + 1];
   double *Qr[TTQ_MAXD], *Qc[TTQ_MAXD], *Rc[TTQ_MAXD], *Rr[TTQ_MAXD], *rinv[TTQ_MAXD];
   double *zvec[TTQ_MAXD];   // per interface: G^{-1} y or G^{-T} l of the next rook step
+  double *pvec[TTQ_MAXD];   // per interface: R^{-T} l of the last row solve
+  double *cbuf;             // the two contraction chains' vectors (hi, lo) x 2, cap each
   double *cs[TTQ_MAXD];     // per interface: scores |E| of the current candidates (-1: not eligible)
   double *ce[TTQ_MAXD];     // per interface: residuals E of the current candidates
-  double *part;             // reduction partials: [iface][block][3] (score, idx, value)
+  double *im[TTQ_MAXD];     // per interface: max score of each rook work item (-1: none eligible)
   State *st;
 };
 

@@ -24,11 +24,10 @@ __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 // solves with the QR factors of G_k (one warp; buf/tmp: per-warp shared scratch)
 
 // buf <- G^{-1} buf with factors staged in shared memory: Qs row-major (ld r)
-// or, if Qs == nullptr, Q from global; Rs column-major (ld r)
+// or, if Qs == nullptr, Q from global; Rs column-major (ld r); ri = 1 / R_jj
 __device__ void warp_col_solve_s(const Dev &D, int k, int r, const double *Qs, const double *Rs,
-                                 double *buf, double *tmp) {
+                                 const double *ri, double *buf, double *tmp) {
   const int lane = lane_id(), ld = D.cap;
-  const double *ri = D.rinv[k];
   for (int i = lane; i < r; i += 32) {
     double acc = 0.0;
     if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], buf[b], acc);
@@ -44,69 +43,43 @@ __device__ void warp_col_solve_s(const Dev &D, int k, int r, const double *Qs, c
   }
 }
 
+// Stage r x r blocks of the QR factors in shared memory: for e = (row, col) in
+// [0, r)^2, a_dst[row * ldd + col] = a_src[row * ld + col], the same for b if
+// b_dst; whole CTA, with eight independent loads in flight per thread (the
+// copies are latency bound).
+__device__ __forceinline__ void stage_block(double *a_dst, const double *a_src, double *b_dst,
+                                            const double *b_src, int r, int ld, int ldd) {
+  const int n = r * r, nt = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < n; e0 += 4 * nt) {
+    double va[4], vb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * nt;
+      if (e < n) {
+        const int o = (e / r) * ld + e % r;
+        va[u] = a_src[o];
+        if (b_dst) vb[u] = b_src[o];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * nt;
+      if (e < n) {
+        const int o = (e / r) * ldd + e % r;
+        a_dst[o] = va[u];
+        if (b_dst) b_dst[o] = vb[u];
+      }
+    }
+  }
+}
+__device__ __forceinline__ void stage_compact(double *a_dst, const double *a_src, double *b_dst,
+                                              const double *b_src, int r, int ld) {
+  stage_block(a_dst, a_src, b_dst, b_src, r, ld, r);
+}
+
 // core entry Y_k(alpha, i, beta)
 __device__ __forceinline__ size_t core_at(const Dev &D, int k, int alpha, int i, int beta) {
   return ((size_t)beta * D.capL[k - 1] + alpha) * D.N[k - 1] + i;
-}
-
-// ---------------------------------------------------------------------------
-// Argmax of Alg. 2 over the candidates of one interface, spread over the CTAs of
-// a kernel.  Every candidate index in [0, count) has its score |E| (-1 if not
-// eligible) and E stored in D.cs[k] / D.ce[k].  Pass 1: CTA maxima -> per-interface
-// partials -> the last CTA to finish reduces them (deterministic).  Pass 2, in
-// that CTA: the first index whose score is within the tie window of the max.
-// Returns true in the last CTA (all threads) with the chosen index and E.
-__device__ bool cta_pick_last(double myscore, const Dev &D, int k, int count, int *idx_out, double *e_out) {
-  __shared__ double sm[TTQ_WARPS];
-  __shared__ int si[TTQ_WARPS];
-  __shared__ int is_last;
-  const int lane = lane_id(), warp = warp_id();
-  const int nb = gridDim.x, nw = blockDim.x >> 5;
-  __threadfence();                              // publish this thread's candidate writes
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) myscore = fmax(myscore, __shfl_xor_sync(0xffffffffu, myscore, o));
-  if (lane == 0) sm[warp] = myscore;
-  __syncthreads();
-  State *st = D.st;
-  if (threadIdx.x == 0) {
-    double c = sm[0];
-    for (int w = 1; w < nw; ++w) c = fmax(c, sm[w]);
-    D.part[(size_t)(k - 1) * nb + blockIdx.x] = c;
-    __threadfence();
-    unsigned prev = atomicAdd(&st->it[k].counter, 1u);
-    is_last = (prev == (unsigned)nb - 1);
-  }
-  __syncthreads();
-  if (!is_last) return false;
-  __threadfence();
-  double smax = -1.0;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) smax = fmax(smax, __ldcg(D.part + (size_t)(k - 1) * nb + q));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  if (lane == 0) sm[warp] = smax;
-  __syncthreads();
-  smax = sm[0];
-  for (int w = 1; w < nw; ++w) smax = fmax(smax, sm[w]);
-  int first = 0x7fffffff;
-  if (smax >= 0.0) {
-    const double scale = __longlong_as_double((long long)st->scale_bits);
-    const double thr = __dadd_rn(smax, -__dadd_rn(__dmul_rn(TTQ_TIE_REL, smax), __dmul_rn(TTQ_TIE_ABS, scale)));
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-      double v = __ldcg(D.cs[k] + i);
-      if (v >= 0.0 && v >= thr) { first = i; break; }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
-  __syncthreads();
-  if (lane == 0) si[warp] = first;
-  __syncthreads();
-  first = si[0];
-  for (int w = 1; w < nw; ++w) first = min(first, si[w]);
-  if (threadIdx.x == 0) st->it[k].counter = 0;
-  *idx_out = (first == 0x7fffffff) ? -1 : first;
-  *e_out = (first == 0x7fffffff) ? 0.0 : __ldcg(D.ce[k] + first);
-  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,66 +339,127 @@ __device__ void qr_full(const Dev &D, int k, int r, double *sm) {
   }
 }
 
-// factors of the (r-1) x (r-1) leading block are stored; G gained row and column r-1
+// Factors of the (r-1) x (r-1) leading block are stored; G gained row and
+// column n = r-1.  Appending the row h (the new row over the old columns) to R
+// takes the rotations J_j (rows j and n) that zero h_0 .. h_{n-1} in turn.
+// Their parameters follow from p = R^-T h without the sequential chain of the
+// rotations themselves: with t_j^2 = 1 + sum_{i<=j} p_i^2 (t_{-1} = 1),
+// c_j = t_{j-1} / t_j and s_j = p_j / t_j, since the entry J_j zeroes is
+// R_jj p_j / t_{j-1} (Gill, Golub, Murray & Saunders 1974, method C1, for the
+// update R^T R + h h^T).  p comes from the row solve of the search that found
+// the pivot when it is still at hand, else from a forward substitution.  The
+// rotations then run down every column of R and every row of Q independently;
+// the new column of R is Q'^T G(:, n) = J [Q^T G(0:n-1, n); G(n, n)].
 __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
+  IfaceState &I = D.st->it[k];
   const int n = r - 1, ls = r, ld = D.cap;
-  double *Rs = sm;                       // r x r row-major
-  double *h = Rs + (size_t)r * ls;       // new row of G, reduced by the rotations
+  double *Rs = sm;                       // r x r row-major (ld ls)
+  double *h = Rs + (size_t)r * ls;       // new row of G over the old columns
   double *cn = h + r;                    // new column of G (length r)
   double *gc = cn + r;                   // rotation cosines
   double *gs = gc + r;                   // rotation sines
+  double *p = gs + r;                    // R^-T h
+  double *v = p + r;                     // Q^T G(0:n-1, n), then the new column of R
+  double *ri = v + r;                    // 1 / R_jj of the old factor
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
   const int anew = D.lpar[k][n], inew = D.lnode[k][n];
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, j = e % n;
-    Rs[i * ls + j] = D.Rr[k][i * ld + j];
+  const bool cached = I.prank == n && I.prow == anew * D.N[k - 1] + inew;
+  stage_block(Rs, D.Rr[k], nullptr, nullptr, n, ld, ls);
+  for (int c = tid; c < n; c += nt) {
+    h[c] = D.Y[k][core_at(D, k, anew, inew, c)];
+    ri[c] = D.rinv[k][c];
+    if (cached) p[c] = D.pvec[k][c];
   }
-  for (int c = tid; c < n; c += nt) h[c] = D.Y[k][core_at(D, k, anew, inew, c)];
   for (int a = tid; a < r; a += nt) cn[a] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], n)];
   __syncthreads();
   if (warp == 0) {
-    for (int j = 0; j < n; ++j) {
-      const double x = Rs[j * ls + j], y = h[j];
-      double c = 1.0, sn = 0.0, rho = x;
-      if (y != 0.0) {
-        rho = copysign(hypot(x, y), x);
-        const double inv = 1.0 / rho;
-        c = x * inv;
-        sn = y * inv;
-      }
-      for (int q = j + 1 + lane; q < n; q += 32) {
-        const double t1 = Rs[j * ls + q], t2 = h[q];
-        Rs[j * ls + q] = fma(c, t1, sn * t2);
-        h[q] = fma(-sn, t1, c * t2);
-      }
-      if (lane == 0) { Rs[j * ls + j] = rho; h[j] = 0.0; gc[j] = c; gs[j] = sn; }
+    if (!cached) {                         // forward substitution R^T p = h
+      for (int c = lane; c < n; c += 32) p[c] = h[c];
       __syncwarp();
+      for (int i = 0; i < n; ++i) {
+        const double pi = p[i] * ri[i];
+        for (int j = i + 1 + lane; j < n; j += 32) p[j] = fma(-Rs[i * ls + j], pi, p[j]);
+        __syncwarp();
+        if (lane == 0) p[i] = pi;
+        __syncwarp();
+      }
+    }
+    // t_j by an inclusive scan of p_j^2 over chunks of 32, then c_j and s_j
+    double carry = 1.0;
+    for (int base = 0; base < n; base += 32) {
+      const int j = base + lane;
+      const double pj = (j < n) ? p[j] : 0.0;
+      double sc = pj * pj;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += y;
+      }
+      const double tj = sqrt(carry + sc);
+      double tp = __shfl_up_sync(0xffffffffu, tj, 1);
+      if (lane == 0) tp = sqrt(carry);
+      if (j < n) {
+        const double inv = 1.0 / tj;
+        gc[j] = tp * inv;
+        gs[j] = pj * inv;
+      }
+      carry += __shfl_sync(0xffffffffu, sc, 31);
+    }
+  } else {
+    for (int a = tid - 32; a < n; a += nt - 32) {   // v = Q^T G(0:n-1, n), old Q
+      double acc = 0.0;
+#pragma unroll 8
+      for (int i = 0; i < n; ++i) acc = fma(D.Qr[k][i * ld + a], cn[i], acc);
+      v[a] = acc;
     }
   }
   __syncthreads();
-  // Q' = [[Q, 0], [0, 1]] J_0^T ... J_{n-1}^T, one row per thread
-  for (int i = tid; i < r; i += nt) {
-    double qlast = (i == n) ? 1.0 : 0.0;
-    for (int j = 0; j < n; ++j) {
-      const double qa = (i < n) ? D.Qc[k][i + j * ld] : 0.0;
-      const double c = gc[j], sn = gs[j];
-      D.Qc[k][i + j * ld] = fma(c, qa, sn * qlast);
-      qlast = fma(-sn, qa, c * qlast);
+  if (tid < 128) {
+    // column q of R: rotations 0 .. q (the last one makes the diagonal entry)
+    for (int q = tid; q < n; q += 128) {
+      double hq = h[q];
+      for (int j = 0; j <= q; ++j) {
+        const double c = gc[j], sn = gs[j], rjq = Rs[j * ls + q];
+        Rs[j * ls + q] = fma(c, rjq, sn * hq);
+        hq = fma(-sn, rjq, c * hq);
+      }
     }
-    D.Qc[k][i + n * ld] = qlast;
+    if (tid == 0) {                        // new column of R: rotations of [v; G(n, n)]
+      double vl = cn[n];
+      for (int j = 0; j < n; ++j) {
+        const double c = gc[j], sn = gs[j], vj = v[j];
+        v[j] = fma(c, vj, sn * vl);
+        vl = fma(-sn, vj, c * vl);
+      }
+      v[n] = vl;
+    }
+  } else {
+    // Q' = [[Q, 0], [0, 1]] J_0^T ... J_{n-1}^T, one row per thread, old Q read
+    // sixteen columns at a time
+    for (int i = tid - 128; i < r; i += nt - 128) {
+      double qlast = (i == n) ? 1.0 : 0.0;
+      for (int j0 = 0; j0 < n; j0 += 16) {
+        double qa[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) qa[u] = (i < n && j0 + u < n) ? D.Qc[k][i + (j0 + u) * ld] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int j = j0 + u;
+          if (j < n) {
+            const double c = gc[j], sn = gs[j];
+            const double q = fma(c, qa[u], sn * qlast);
+            qlast = fma(-sn, qa[u], c * qlast);
+            D.Qc[k][i + j * ld] = q;
+            D.Qr[k][i * ld + j] = q;
+          }
+        }
+      }
+      D.Qc[k][i + n * ld] = qlast;
+      D.Qr[k][i * ld + n] = qlast;
+    }
   }
   __syncthreads();
-  for (int e = tid; e < r * r; e += nt) {
-    int i = e / r, j = e % r;
-    D.Qr[k][i * ld + j] = D.Qc[k][i + j * ld];
-  }
-  __syncthreads();
-  // new column of R: Q'^T [G(:, n)]
-  for (int a = tid; a < r; a += nt) {
-    double acc = 0.0;
-    for (int i = 0; i < r; ++i) acc = fma(D.Qr[k][i * ld + a], cn[i], acc);
-    Rs[a * ls + n] = acc;
-  }
+  for (int a = tid; a < r; a += nt) Rs[a * ls + n] = v[a];
   for (int j = tid; j < n; j += nt) Rs[n * ls + j] = 0.0;
   __syncthreads();
   qr_store_R(D, k, r, Rs, ls, true);
@@ -443,9 +477,12 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (threadIdx.x == 0) {
     IfaceState &I = st->it[k];
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
-    I.err = 0.0; I.evals = 0;
+    I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0;
   }
-  if (have == r) return;
+  if (have == r) {
+    if (threadIdx.x == 0) st->it[k].prank = -1;
+    return;
+  }
   if (have >= 1 && have == r - 1) {
     qr_border(D, k, r, sm);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * r * (double)r));
@@ -454,37 +491,161 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(8.0 / 3.0 * r * (double)r * r));
   }
   __syncthreads();
-  if (threadIdx.x == 0) st->qr_rank[k] = r;
+  if (threadIdx.x == 0) { st->qr_rank[k] = r; st->it[k].prank = -1; }
 }
 
 // Kernel (c): contraction of the weighted cores with the inverse cross matrices
-// (Sec. 4.1): x <- V_1; for k: x <- x G_k^-1 = (Q R^-T x^T)^T; x <- x V_{k+1}.
-// One CTA; R_k staged in shared memory for the sequential substitution (one
-// warp), the products with Q_k and V_{k+1} spread over all threads.  It only
-// feeds the stopping rule, so it runs beside the pivot search; a rule that
-// fires is recorded as pending and applied at the end of the sweep.
+// (Sec. 4.1), V_1 G_1^-1 V_2 ... G_{d-1}^-1 V_d, as two chains that meet at
+// m = (d+1)/2: CTA 0 forms the row x = V_1 G_1^-1 V_2 ... V_m from the left
+// (x <- x G_k^-1 = (Q R^-T x^T)^T, then x <- x V_{k+1}), CTA 1 the column
+// y = G_m^-1 V_{m+1} ... G_{d-1}^-1 V_d from the right (y <- V_k R^-1 Q^T y),
+// and the CTA that finishes second takes the product x y.  R_k is staged in
+// shared memory for the sequential substitutions (one warp); the products with
+// Q_k and V_k are spread over the threads.  The per-sweep FP64 contraction
+// only feeds the stopping rule, so it runs beside the pivot search; a rule
+// that fires is recorded as pending and applied at the end of the sweep.
+// final_dd: the double-double contraction of the final sets (after the run).
+
+// x <- x G_k^-1 for the row x (hi/lo pairs used when prec)
+__device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *xh, double *xl,
+                                    double *th, double *tl) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
+  stage_compact(Rs, D.Rr[k], nullptr, nullptr, r, ld);      // row-major R
+  __syncthreads();
+  if (warp == 0) {                               // forward substitution R^T t = x
+    if (!prec) {
+      for (int i = 0; i < r; ++i) {
+        const double ti = xh[i] * D.rinv[k][i];
+        for (int j = i + 1 + lane; j < r; j += 32) xh[j] = fma(-Rs[i * r + j], ti, xh[j]);
+        if (lane == 0) th[i] = ti;
+        __syncwarp();
+      }
+    } else {
+      for (int i = 0; i < r; ++i) {
+        const dd ti = dd_div_d({xh[i], xl[i]}, Rs[i * r + i]);
+        for (int j = i + 1 + lane; j < r; j += 32) {
+          const dd v = dd_add({xh[j], xl[j]}, dd_mul_d(ti, -Rs[i * r + j]));
+          xh[j] = v.hi; xl[j] = v.lo;
+        }
+        if (lane == 0) { th[i] = ti.hi; tl[i] = ti.lo; }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) {            // x <- Q t
+    const double *Qrow = D.Qr[k] + (size_t)i * ld;
+    if (!prec) {
+      double acc = 0.0;
+      for (int j = 0; j < r; ++j) acc = fma(Qrow[j], th[j], acc);
+      xh[i] = acc;
+    } else {
+      dd acc = {0.0, 0.0};
+      for (int j = 0; j < r; ++j) acc = dd_add(acc, dd_mul_d({th[j], tl[j]}, Qrow[j]));
+      xh[i] = acc.hi; xl[i] = acc.lo;
+    }
+  }
+  __syncthreads();
+}
+
+// y <- G_k^-1 y for the column y
+__device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *yh, double *yl,
+                                     double *th, double *tl) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
+  stage_compact(Rs, D.Rc[k], nullptr, nullptr, r, ld);      // column-major R: R[i][j] at Rs[i + j r]
+  for (int i = tid; i < r; i += nt) {            // t = Q^T y
+    if (!prec) {
+      double acc = 0.0;
+      for (int j = 0; j < r; ++j) acc = fma(D.Qr[k][(size_t)j * ld + i], yh[j], acc);
+      th[i] = acc;
+    } else {
+      dd acc = {0.0, 0.0};
+      for (int j = 0; j < r; ++j) acc = dd_add(acc, dd_mul_d({yh[j], yl[j]}, D.Qr[k][(size_t)j * ld + i]));
+      th[i] = acc.hi; tl[i] = acc.lo;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {                               // back substitution R z = t
+    if (!prec) {
+      for (int j = r - 1; j >= 0; --j) {
+        const double zj = th[j] * D.rinv[k][j];
+        for (int i = lane; i < j; i += 32) th[i] = fma(-Rs[i + j * r], zj, th[i]);
+        if (lane == 0) yh[j] = zj;
+        __syncwarp();
+      }
+    } else {
+      for (int j = r - 1; j >= 0; --j) {
+        const dd zj = dd_div_d({th[j], tl[j]}, Rs[j + j * r]);
+        for (int i = lane; i < j; i += 32) {
+          const dd v = dd_add({th[i], tl[i]}, dd_mul_d(zj, -Rs[i + j * r]));
+          th[i] = v.hi; tl[i] = v.lo;
+        }
+        if (lane == 0) { yh[j] = zj.hi; yl[j] = zj.lo; }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// value (as hi/lo), the stopping rules (per sweep) or the final value (final_dd)
+__device__ void contract_finish(const Dev &D, State *st, dd v, int final_dd) {
+  const int d = D.d;
+  if (final_dd) {
+    v = dd_mul_d(v, D.constant);
+    st->value = v.hi;
+    st->value_lo = v.lo;
+    return;
+  }
+  const double val = v.hi * D.constant;          // the per-sweep contraction is FP64
+  st->value = val;
+  st->value_lo = 0.0;
+  for (int k = 0; k <= d; ++k) st->ro[k] = st->r[k];
+  const int s = st->sweep;
+  if (st->rules) {
+    if (s > 0) {
+      double c = (val != 0.0) ? fabs(val - st->prev) / fabs(val) : fabs(val - st->prev);
+      st->conv = c;
+      st->changes[st->nchanges & 7] = c;
+      st->nchanges++;
+    }
+    int stop = 0, status = ST_OK;
+    if (st->nchanges >= D.conv_window) {
+      double mx = 0.0;
+      for (int q = 0; q < D.conv_window; ++q) mx = fmax(mx, st->changes[(st->nchanges - 1 - q) & 7]);
+      if (mx <= D.tol) { stop = 1; status = ST_OK; }
+    }
+    if (!stop) {
+      int allcap = 1;
+      for (int k = 1; k < d; ++k) allcap &= (st->r[k] >= D.cap);
+      if (allcap) { stop = 1; status = ST_RANK_CAP; }
+    }
+    if (!stop && s >= D.max_sweeps - 1) { stop = 1; status = ST_MAX_SWEEPS; }
+    if (stop) { st->pending_status = status; st->stop_pending = 1; }
+  }
+  st->prev = val;
+}
+
 __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
-  // per sweep: FP64 contraction for the stopping rule; final_dd: the
-  // double-double contraction of the final sets (after the run stopped)
   if (st->stop && !final_dd) return;
   if (final_dd && (!D.prec || st->nonfinite || st->singular)) return;
-  const int prec = final_dd;
+  const bool prec = final_dd != 0;
   extern __shared__ double sm[];
   __shared__ double xh[TTQ_MAXR], xl[TTQ_MAXR], th[TTQ_MAXR], tl[TTQ_MAXR];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
-  const int d = D.d, ld = D.cap;
+  __shared__ int is_last;
+  const int tid = threadIdx.x, nt = blockDim.x, d = D.d, m = (d + 1) / 2;
+  const bool left = blockIdx.x == 0;
   if (st->nonfinite || st->singular) {
-    if (tid == 0) {
+    if (tid == 0 && left) {
       st->pending_status = st->nonfinite ? ST_ERR_NONFINITE : ST_ERR_SINGULAR;
       st->stop_pending = 1;
     }
     return;
   }
-  double *Rs = sm;                               // r x r row-major
-  for (int b = tid; b < st->r[1]; b += nt) { xh[b] = D.V[1][b]; xl[b] = D.Vlo[1][b]; }
-  if (tid == 0) {
+  double *Rs = sm;
+  if (tid == 0 && left) {
     unsigned long long fl = 0;
     for (int k = 1; k <= d - 1; ++k) {
       unsigned long long r = st->r[k], rn = st->r[k + 1];
@@ -492,109 +653,247 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
     }
     atomicAdd(&st->flops[2], fl);
   }
-  for (int k = 1; k <= d - 1; ++k) {
-    const int r = st->r[k], rn = st->r[k + 1];
-    const double *Qc = D.Qc[k];
-    for (int e = tid; e < r * r; e += nt) {
-      int i = e / r, j = e % r;
-      Rs[i * r + j] = (j >= i) ? D.Rr[k][i * ld + j] : 0.0;
-    }
+  int len;                                       // length of this chain's vector
+  if (left) {
+    len = st->r[1];
+    for (int b = tid; b < len; b += nt) { xh[b] = D.V[1][b]; xl[b] = D.Vlo[1][b]; }
     __syncthreads();
-    // forward substitution R^T t = x (one warp, from shared memory)
-    if (warp == 0) {
-      if (!prec) {
-        for (int i = 0; i < r; ++i) {
-          double ti = xh[i] * D.rinv[k][i];
-          for (int j = i + 1 + lane; j < r; j += 32) xh[j] = fma(-Rs[i * r + j], ti, xh[j]);
-          if (lane == 0) th[i] = ti;
-          __syncwarp();
-        }
-      } else {
-        for (int i = 0; i < r; ++i) {
-          dd ti = dd_div_d({xh[i], xl[i]}, Rs[i * r + i]);
-          for (int j = i + 1 + lane; j < r; j += 32) {
-            dd v = dd_add({xh[j], xl[j]}, dd_mul_d(ti, -Rs[i * r + j]));
-            xh[j] = v.hi; xl[j] = v.lo;
+    for (int k = 1; k <= m - 1; ++k) {
+      const int r = st->r[k], rn = st->r[k + 1];
+      contract_left_solve(D, k, r, prec, Rs, xh, xl, th, tl);
+      for (int b = tid; b < rn; b += nt) {      // x <- x V_{k+1}
+        if (!prec) {
+          double acc = 0.0;
+          for (int a = 0; a < r; ++a) acc = fma(xh[a], D.V[k + 1][(size_t)a * D.capL[k + 1] + b], acc);
+          th[b] = acc;
+        } else {
+          dd acc = {0.0, 0.0};
+          for (int a = 0; a < r; ++a) {
+            const size_t vi = (size_t)a * D.capL[k + 1] + b;
+            acc = dd_add(acc, dd_mul({xh[a], xl[a]}, {D.V[k + 1][vi], D.Vlo[k + 1][vi]}));
           }
-          if (lane == 0) { th[i] = ti.hi; tl[i] = ti.lo; }
-          __syncwarp();
+          th[b] = acc.hi; tl[b] = acc.lo;
         }
       }
+      __syncthreads();
+      for (int b = tid; b < rn; b += nt) { xh[b] = th[b]; xl[b] = prec ? tl[b] : 0.0; }
+      __syncthreads();
+      len = rn;
     }
+  } else {
+    len = st->r[d - 1];
+    for (int a = tid; a < len; a += nt) { xh[a] = D.V[d][a]; xl[a] = D.Vlo[d][a]; }
     __syncthreads();
-    // x <- Q t
-    for (int i = tid; i < r; i += nt) {
-      if (!prec) {
-        double acc = 0.0;
-        for (int j = 0; j < r; ++j) acc = fma(Qc[i + j * ld], th[j], acc);
-        xh[i] = acc;
-      } else {
-        dd acc = {0.0, 0.0};
-        for (int j = 0; j < r; ++j) acc = dd_add(acc, dd_mul_d({th[j], tl[j]}, Qc[i + j * ld]));
-        xh[i] = acc.hi; xl[i] = acc.lo;
-      }
-    }
-    __syncthreads();
-    // x <- x V_{k+1}
-    for (int b = tid; b < rn; b += nt) {
-      if (!prec) {
-        double acc = 0.0;
-        for (int a = 0; a < r; ++a) acc = fma(xh[a], D.V[k + 1][(size_t)a * D.capL[k + 1] + b], acc);
-        th[b] = acc;
-      } else {
-        dd acc = {0.0, 0.0};
-        for (int a = 0; a < r; ++a) {
-          size_t vi = (size_t)a * D.capL[k + 1] + b;
-          acc = dd_add(acc, dd_mul({xh[a], xl[a]}, {D.V[k + 1][vi], D.Vlo[k + 1][vi]}));
+    for (int k = d - 1; k >= m; --k) {
+      const int r = st->r[k];
+      contract_right_solve(D, k, r, prec, Rs, xh, xl, th, tl);
+      if (k == m) break;
+      const int rl = st->r[k - 1];
+      for (int a = tid; a < rl; a += nt) {       // y <- V_k y
+        const size_t row = (size_t)a * D.capL[k];
+        if (!prec) {
+          double acc = 0.0;
+          for (int b = 0; b < r; ++b) acc = fma(D.V[k][row + b], xh[b], acc);
+          th[a] = acc;
+        } else {
+          dd acc = {0.0, 0.0};
+          for (int b = 0; b < r; ++b) acc = dd_add(acc, dd_mul({D.V[k][row + b], D.Vlo[k][row + b]}, {xh[b], xl[b]}));
+          th[a] = acc.hi; tl[a] = acc.lo;
         }
-        th[b] = acc.hi; tl[b] = acc.lo;
       }
+      __syncthreads();
+      for (int a = tid; a < rl; a += nt) { xh[a] = th[a]; xl[a] = prec ? tl[a] : 0.0; }
+      __syncthreads();
+      len = rl;
     }
-    __syncthreads();
-    for (int b = tid; b < rn; b += nt) { xh[b] = th[b]; xl[b] = tl[b]; }
-    __syncthreads();
   }
-  if (tid == 0 && final_dd) {
-    dd v = dd_mul_d({xh[0], xl[0]}, D.constant);
-    st->value = v.hi;
-    st->value_lo = v.lo;
-    return;
-  }
+  // publish this chain's vector; the CTA that arrives second forms x y
+  double *mine = D.cbuf + (left ? 0 : 2 * D.cap);
+  for (int a = tid; a < len; a += nt) { mine[a] = xh[a]; mine[D.cap + a] = xl[a]; }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&st->contract_arrive, 1u) == 1u);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
   if (tid == 0) {
-    dd v = prec ? dd_mul_d({xh[0], xl[0]}, D.constant) : dd{xh[0] * D.constant, 0.0};
-    const double val = v.hi;
-    st->value = val;
-    st->value_lo = v.lo;
-    for (int k = 0; k <= d; ++k) st->ro[k] = st->r[k];
-    const int s = st->sweep;
-    if (st->rules) {
-      if (s > 0) {
-        double c = (val != 0.0) ? fabs(val - st->prev) / fabs(val) : fabs(val - st->prev);
-        st->conv = c;
-        st->changes[st->nchanges & 7] = c;
-        st->nchanges++;
-      }
-      int stop = 0, status = ST_OK;
-      if (st->nchanges >= D.conv_window) {
-        double mx = 0.0;
-        for (int q = 0; q < D.conv_window; ++q) mx = fmax(mx, st->changes[(st->nchanges - 1 - q) & 7]);
-        if (mx <= D.tol) { stop = 1; status = ST_OK; }
-      }
-      if (!stop) {
-        int allcap = 1;
-        for (int k = 1; k < d; ++k) allcap &= (st->r[k] >= D.cap);
-        if (allcap) { stop = 1; status = ST_RANK_CAP; }
-      }
-      if (!stop && s >= D.max_sweeps - 1) { stop = 1; status = ST_MAX_SWEEPS; }
-      if (stop) { st->pending_status = status; st->stop_pending = 1; }
+    st->contract_arrive = 0;
+    const double *other = D.cbuf + (left ? 2 * D.cap : 0);
+    dd acc = {0.0, 0.0};
+    for (int a = 0; a < len; ++a) {
+      const dd o = {__ldcg(other + a), __ldcg(other + D.cap + a)};
+      const dd me = {xh[a], xl[a]};
+      // the same order in either CTA: x_a y_a summed over a
+      acc = prec ? dd_add(acc, dd_mul(left ? me : o, left ? o : me)) : dd{fma(me.hi, o.hi, acc.hi), 0.0};
     }
-    st->prev = val;
+    contract_finish(D, st, acc, final_dd);
   }
 }
 
-// The solve of the next rook step, one CTA per interface with R_k staged in
-// shared memory: mode 0 z = G^-1 y for the column step, y = R_{k+1}(:, gamma*);
-// mode 1 b = G^-T l for the row step, l = L_k(rho*, :)^T.  Result in zvec[k].
+// Pass 2 of the argmax of a search stage (whole CTA, interface k): the first
+// candidate index whose score lies in the tie window below the stage maximum,
+// -1 if the stage had no eligible candidate.  Clears the stage reduction.
+//   stage 0 (samples): a scan of the S sample scores.
+//   stage 1 (column step, rho = alpha N_k + i): work item w = alpha nch + ch holds
+//     the contiguous rows i in chunk ch, so the answer lies in the first item whose
+//     maximum reaches the window; one scan of its <= TTQ_CHUNK rows.
+//   stage 2 (row step, gamma = j r_{k+1} + beta): item w = beta nch + ch holds the
+//     nodes j of chunk ch; the answer has the smallest j, so it lies in the lowest
+//     chunk any qualifying item reaches; the items of that chunk are scanned.
+__device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
+  __shared__ int si[TTQ_WARPS];
+  __shared__ double smax_s;
+  __shared__ unsigned n_s;
+  __shared__ int best_s;
+  State *st = D.st;
+  IfaceState &I = st->it[k];
+  const int lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+    smax_s = __longlong_as_double((long long)I.smax_bits);
+    n_s = I.stage_count;
+    best_s = 0x7fffffff;
+  }
+  __syncthreads();
+  const double smax = smax_s;
+  const unsigned n = n_s;
+  if (threadIdx.x == 0) { I.smax_bits = 0ULL; I.stage_count = 0; }
+  if (n == 0) { *e_out = 0.0; return -1; }
+  const double scale = __longlong_as_double((long long)st->scale_bits);
+  const double thr = __dadd_rn(smax, -__dadd_rn(__dmul_rn(TTQ_TIE_REL, smax), __dmul_rn(TTQ_TIE_ABS, scale)));
+  auto block_min = [&](int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) si[warp] = v;
+    __syncthreads();
+    v = si[0];
+    for (int w = 1; w < nw; ++w) v = min(v, si[w]);
+    return v;
+  };
+  int first = 0x7fffffff;
+  if (stage == 0) {
+    for (int t = threadIdx.x; t < D.S[k]; t += blockDim.x) {
+      const double v = D.cs[k][t];
+      if (v >= 0.0 && v >= thr) first = min(first, t);
+    }
+    first = block_min(first);
+  } else {
+    const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
+    const int rm = stage == 1 ? st->r[k - 1] : st->r[k + 1];   // rows / columns of the outer rank
+    const int nch = (Nm + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    int wmin = 0x7fffffff;                       // first qualifying item (stage 1) / its chunk (stage 2)
+    for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
+      const double v = D.im[k][w];
+      if (v >= 0.0 && v >= thr) wmin = min(wmin, stage == 1 ? w : w % nch);
+    }
+    wmin = block_min(wmin);
+    if (stage == 1) {
+      if (warp == 0) {
+        const int alpha = wmin / nch, ch = wmin % nch;
+        const int i0 = ch * TTQ_CHUNK, i1 = min(Nm, i0 + TTQ_CHUNK);
+        int f = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
+          const int i = i0 + lane + 32 * q;
+          if (i < i1) {
+            const double v = D.cs[k][alpha * Nm + i];
+            if (v >= 0.0 && v >= thr) f = min(f, alpha * Nm + i);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(0xffffffffu, f, o));
+        if (lane == 0) best_s = f;
+      }
+    } else {
+      const int ch = wmin, j0 = ch * TTQ_CHUNK, j1 = min(Nm, j0 + TTQ_CHUNK);
+      for (int beta = warp; beta < rm; beta += nw) {
+        const double m = D.im[k][beta * nch + ch];
+        if (!(m >= 0.0 && m >= thr)) continue;
+        int f = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
+          const int j = j0 + lane + 32 * q;
+          if (j < j1) {
+            const double v = D.cs[k][j * rm + beta];
+            if (v >= 0.0 && v >= thr) f = min(f, j * rm + beta);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(0xffffffffu, f, o));
+        if (lane == 0) atomicMin(&best_s, f);
+      }
+    }
+    __syncthreads();
+    first = best_s;
+  }
+  *e_out = D.ce[k][first];
+  return first;
+}
+
+// z = G_k^{-1} y, y = R_{k+1}(:, gamma) = Y_{k+1}(:, j, beta): the solve of the
+// column step (whole CTA; Rs, Qs in shared memory; result in zvec[k])
+__device__ void cta_col_solve(const Dev &D, int k, int r, int gam, double *Rs, double *Qs,
+                              double *v, double *t, double *ri) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
+  const int rn = D.st->r[k + 1], j = gam / rn, beta = gam % rn;
+  // R column-major (R[i][c] at Rs[i + c r]), Q row-major (Q[c][i] at Qs[c r + i])
+  stage_compact(Rs, D.Rc[k], Qs, D.Qr[k], r, ld);
+  for (int b = tid; b < r; b += nt) { v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)]; ri[b] = D.rinv[k][b]; }
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) {            // t = Q^T y
+    double acc = 0.0;
+    if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], v[b], acc);
+    else for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], v[b], acc);
+    t[i] = acc;
+  }
+  __syncthreads();
+  if (warp == 0) {                               // back substitution R z = t
+    for (int jj = r - 1; jj >= 0; --jj) {
+      double zj = t[jj] * ri[jj];
+      for (int i = lane; i < jj; i += 32) t[i] = fma(-Rs[i + jj * r], zj, t[i]);
+      if (lane == 0) v[jj] = zj;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b];
+}
+
+// b = G_k^{-T} l, l = L_k(rho, :)^T = Y_k(alpha, i, :): the solve of the row step
+__device__ void cta_row_solve(const Dev &D, int k, int r, int rho, double *Rs, double *Qs,
+                              double *v, double *t, double *ri) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
+  const int Nk = D.N[k - 1], alpha = rho / Nk, i0 = rho % Nk;
+  // R row-major (R[i][c] at Rs[i r + c]), Q column-major (Q[i][c] at Qs[i + c r])
+  stage_compact(Rs, D.Rr[k], Qs, D.Qc[k], r, ld);
+  for (int b = tid; b < r; b += nt) { v[b] = D.Y[k][core_at(D, k, alpha, i0, b)]; ri[b] = D.rinv[k][b]; }
+  __syncthreads();
+  if (warp == 0) {                               // forward substitution R^T t = l
+    for (int i = 0; i < r; ++i) {
+      double ti = v[i] * ri[i];
+      for (int jj = i + 1 + lane; jj < r; jj += 32) v[jj] = fma(-Rs[i * r + jj], ti, v[jj]);
+      if (lane == 0) t[i] = ti;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) {            // b = Q t
+    double acc = 0.0;
+    if (Qs) for (int jj = 0; jj < r; ++jj) acc = fma(Qs[i + jj * r], t[jj], acc);
+    else for (int jj = 0; jj < r; ++jj) acc = fma(D.Qc[k][i + jj * ld], t[jj], acc);
+    D.zvec[k][i] = acc;
+    D.pvec[k][i] = t[i];                         // R^-T l: the QR update of this row reuses it
+  }
+  if (tid == 0) { D.st->it[k].prow = rho; D.st->it[k].prank = r; }
+}
+
+// Decisions of Alg. 2 between its search stages, one CTA per interface: the
+// argmax of the stage just run (pass 2), the interface's search state, and the
+// solve the next stage needs (R_k staged in shared memory).
+//   mode 0, after the random samples: (rho*, gamma*) of the best sample; column solve.
+//   mode 1, after a column step: rho* = argmax over E(:, gamma*); row solve.
+//   mode 2, after a row step: gamma_new = argmax over E(rho*, :); the rook test
+//           (Eq. 2) or the round limit ends the search, else the next column solve.
 __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
@@ -602,65 +901,44 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   if (k > D.d - 1) return;
   if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
-  if (!I.active || I.rook_done) return;
+  if (mode != 0 && (!I.active || I.rook_done)) return;
   extern __shared__ double sm[];
-  __shared__ double v[TTQ_MAXR], t[TTQ_MAXR];
-  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
+  __shared__ double v[TTQ_MAXR], t[TTQ_MAXR], ri[TTQ_MAXR];
   const int r = st->r[k];
   double *Rs = sm;                               // r x r, orientation of the substitution
   double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
+  double e;
   if (mode == 0) {
-    const int rn = st->r[k + 1], j = I.col / rn, beta = I.col % rn;
-    for (int e = tid; e < r * r; e += nt) {
-      int i = e % r, c = e / r;                  // column-major: R[i][c] at Rs[i + c r]
-      Rs[i + c * r] = D.Rc[k][i + c * ld];
-      if (Qs) Qs[c * r + i] = D.Qr[k][c * ld + i];   // row-major Q[c][i]
+    const int pick = stage_pick(D, k, 0, &e);
+    if (pick < 0) return;                        // nothing to search from
+    const int Nk = D.N[k - 1], Nk1 = D.N[k], rn = st->r[k + 1];
+    const unsigned long long sid = stream_id(st->sweep, k, 1);
+    const int row = draw_index(D.seed, sid, 2ULL * pick, (unsigned long long)st->r[k - 1] * Nk);
+    const int col = draw_index(D.seed, sid, 2ULL * pick + 1, (unsigned long long)Nk1 * rn);
+    if (threadIdx.x == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
+    cta_col_solve(D, k, r, col, Rs, Qs, v, t, ri);
+  } else if (mode == 1) {
+    const int pick = stage_pick(D, k, 1, &e);
+    if (pick < 0) {
+      if (threadIdx.x == 0) I.active = 0;
+      return;
     }
-    for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
-    __syncthreads();
-    for (int i = tid; i < r; i += nt) {          // t = Q^T y
-      double acc = 0.0;
-      if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], v[b], acc);
-      else for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], v[b], acc);
-      t[i] = acc;
-    }
-    __syncthreads();
-    if (warp == 0) {                             // back substitution R z = t
-      for (int jj = r - 1; jj >= 0; --jj) {
-        double zj = t[jj] * D.rinv[k][jj];
-        for (int i = lane; i < jj; i += 32) t[i] = fma(-Rs[i + jj * r], zj, t[i]);
-        if (lane == 0) v[jj] = zj;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b];
+    if (threadIdx.x == 0) I.row = pick;
+    cta_row_solve(D, k, r, pick, Rs, Qs, v, t, ri);
   } else {
-    const int Nk = D.N[k - 1], alpha = I.row / Nk, i0 = I.row % Nk;
-    for (int e = tid; e < r * r; e += nt) {
-      int i = e / r, c = e % r;                  // row-major: R[i][c] at Rs[i r + c]
-      Rs[i * r + c] = D.Rr[k][i * ld + c];
-      if (Qs) Qs[i + c * r] = D.Qc[k][i + c * ld];   // column-major Q[i][c]
+    const int pick = stage_pick(D, k, 2, &e);
+    if (pick < 0) {
+      if (threadIdx.x == 0) I.active = 0;
+      return;
     }
-    for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
-    __syncthreads();
-    if (warp == 0) {                             // forward substitution R^T t = l
-      for (int i = 0; i < r; ++i) {
-        double ti = v[i] * D.rinv[k][i];
-        for (int jj = i + 1 + lane; jj < r; jj += 32) v[jj] = fma(-Rs[i * r + jj], ti, v[jj]);
-        if (lane == 0) t[i] = ti;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < r; i += nt) {          // b = Q t
-      double acc = 0.0;
-      if (Qs) for (int jj = 0; jj < r; ++jj) acc = fma(Qs[i + jj * r], t[jj], acc);
-      else for (int jj = 0; jj < r; ++jj) acc = fma(D.Qc[k][i + jj * ld], t[jj], acc);
-      D.zvec[k][i] = acc;
-    }
+    const int rounds = I.rounds + 1;
+    const bool done = (pick == I.col) || rounds >= D.rook_max;
+    __syncthreads();                             // every thread has read I.col
+    if (threadIdx.x == 0) { I.rounds = rounds; I.col = pick; I.err = e; I.rook_done = done ? 1 : 0; }
+    if (done) return;
+    cta_col_solve(D, k, r, pick, Rs, Qs, v, t, ri);
   }
-  if (tid == 0) atomicAdd(&st->flops[3], (unsigned long long)(3 * r * r));
+  if (threadIdx.x == 0) atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r));
 }
 
 // shared per-warp scratch of the search kernels
@@ -670,7 +948,7 @@ struct SearchSmem {
   double buf[TTQ_WARPS][TTQ_MAXR];
   double tmp[TTQ_WARPS][TTQ_MAXR];
   int exc[TTQ_WARPS][TTQ_MAXR];
-  double z[TTQ_MAXR];
+  double ri[TTQ_MAXR];
 };
 
 // per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
@@ -678,8 +956,17 @@ struct RookSmem {
   int ms[TTQ_WARPS][TTQ_MAXD];
   double pl[TTQ_WARPS][TTQ_MAXPAIR];
   int exc[TTQ_WARPS][TTQ_MAXR];
-  double z[TTQ_MAXR];
+  double z[TTQ_WARPS][TTQ_MAXR];
 };
+
+// a stage's candidates of one warp feed the interface's maximum (pass 1 of the
+// argmax; IEEE bits of non-negative doubles order like the values)
+__device__ __forceinline__ void stage_publish(IfaceState &I, double best, unsigned nelig) {
+  if (nelig) {
+    atomicMax(&I.smax_bits, (unsigned long long)__double_as_longlong(best));
+    atomicAdd(&I.stage_count, nelig);
+  }
+}
 
 __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, int k) {
   if (k > D.d - 1) return false;            // instances with fewer interfaces (batches)
@@ -705,15 +992,12 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
   const int M = rl * Nk, Ncol = Nk1 * rn, S = D.S[k];
   double *Rs = fac;                                  // R column-major, ld rk
   double *Qs = D.q_in_smem ? fac + (size_t)rk * rk : nullptr;   // Q row-major, ld rk
-  for (int e = threadIdx.x; e < rk * rk; e += blockDim.x) {
-    int i = e % rk, c = e / rk;
-    Rs[i + c * rk] = D.Rc[k][i + c * D.cap];
-    if (Qs) Qs[c * rk + i] = D.Qr[k][c * D.cap + i];
-  }
+  stage_compact(Rs, D.Rc[k], Qs, D.Qr[k], rk, D.cap);
+  for (int b = threadIdx.x; b < rk; b += blockDim.x) sh.ri[b] = D.rinv[k][b];
   __syncthreads();
   const unsigned long long sid = stream_id(st->sweep, k, 1);
-  double best = -1.0;
-  long long evals = 0;
+  double best = 0.0;
+  long long evals = 0, nel = 0;
   unsigned long long fl = 0;
   for (int t = blockIdx.x * TTQ_WARPS + warp; t < S; t += gridDim.x * TTQ_WARPS) {
     const int rho = draw_index(D.seed, sid, 2ULL * t, (unsigned long long)M);
@@ -743,57 +1027,72 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
     double A = 0.0;
     if (lane == 0) A = fiber_value(D, k - 1, sh.ms[warp], u, sh.pl[warp], i);
     A = __shfl_sync(0xffffffffu, A, 0);
-    warp_col_solve_s(D, k, rk, Qs, Rs, sh.buf[warp], sh.tmp[warp]);
+    warp_col_solve_s(D, k, rk, Qs, Rs, sh.ri, sh.buf[warp], sh.tmp[warp]);
     double acc = 0.0;
     for (int b = lane; b < rk; b += 32) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], sh.buf[warp][b], acc);
     acc = warp_sum(acc);
     const double E = A - acc;
     const double sc = isfinite(E) ? fabs(E) : -1.0;
     if (lane == 0) { D.cs[k][t] = sc; D.ce[k][t] = E; }
-    best = fmax(best, sc);
+    if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
     ++evals;
     fl += (unsigned long long)(u.fl_uniform + u.fl_node) + 3ULL * rk * rk + 2ULL * rk + 1;
     __syncwarp();
   }
-  if (lane == 0 && evals) atomicAdd(&st->it[k].evals, (unsigned long long)evals);
-  if (lane == 0 && fl) atomicAdd(&st->flops[3], fl);
-  int pick;
-  double epick;
-  if (!cta_pick_last(best, D, k, S, &pick, &epick)) return;
-  if (pick < 0) return;                        // nothing to search from
-  if (threadIdx.x == 0) {
-    const int t = pick;
-    IfaceState &I = st->it[k];
-    I.row = draw_index(D.seed, sid, 2ULL * t, (unsigned long long)M);
-    I.col = draw_index(D.seed, sid, 2ULL * t + 1, (unsigned long long)Ncol);
-    I.err = epick;
-    I.active = 1;
+  if (lane == 0) {
+    if (evals) atomicAdd(&st->it[k].evals, (unsigned long long)evals);
+    if (fl) atomicAdd(&st->flops[3], fl);
+    stage_publish(st->it[k], best, (unsigned)nel);
   }
 }
 
-// Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i); argmax -> rho*.
+// Work list of a rook step over every interface of the instance: lane k-1
+// holds interface k's item count; prefix sums over the lanes.
+struct ItemMap {
+  int pre, cnt, total;
+};
+__device__ __forceinline__ ItemMap item_map(int cnt) {
+  const int lane = lane_id();
+  int pre = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, pre, o);
+    if (lane >= o) pre += v;
+  }
+  return {pre, cnt, __shfl_sync(0xffffffffu, pre, 31)};
+}
+
+// Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i) of every
+// searching interface; a load-balanced list of (interface, alpha, node chunk)
+// items; pass 1 of the argmax per interface (pass 2 in k_solve).
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
-  const int k = blockIdx.y + 1;
-  if (k > D.d - 1) return;
   if (st->stop || !st->search) return;
-  IfaceState &I = st->it[k];
-  if (!I.active || I.rook_done) return;
   __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
-  const int Nk = D.N[k - 1];
-  const int gam = I.col, j = gam / rn, beta = gam % rn;
-  for (int b = threadIdx.x; b < rk; b += blockDim.x) sh.z[b] = D.zvec[k][b];
-  __syncthreads();
-  const int nch = (Nk + TTQ_CHUNK - 1) / TTQ_CHUNK;
-  const int items = rl * nch;
-  double best = -1.0;
-  long long evals = 0;
+  int cnt = 0;
+  if (lane < d - 1) {
+    const IfaceState &I = st->it[lane + 1];
+    if (I.active && !I.rook_done) cnt = st->r[lane] * ((D.N[lane] + TTQ_CHUNK - 1) / TTQ_CHUNK);
+  }
+  const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
-  for (int w = blockIdx.x * TTQ_WARPS + warp; w < items; w += gridDim.x * TTQ_WARPS) {
-    const int alpha = w / nch, ch = w % nch;
+  int zk = 0;                                   // interface whose z sits in sh.z[warp]
+  for (int w = blockIdx.x * TTQ_WARPS + warp; w < im.total; w += gridDim.x * TTQ_WARPS) {
+    const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
+    const int k = __ffs(ball);                  // interface (1-based)
+    const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
+    IfaceState &I = st->it[k];
+    const int rk = st->r[k], rn = st->r[k + 1];
+    const int Nk = D.N[k - 1];
+    const int nch = (Nk + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    const int alpha = local / nch, ch = local % nch;
+    const int gam = I.col, j = gam / rn, beta = gam % rn;
+    if (k != zk) {
+      for (int b = lane; b < rk; b += 32) sh.z[warp][b] = D.zvec[k][b];
+      zk = k;
+    }
     if (lane < d) {
       int v = 0;
       if (lane < k - 1) v = D.lidx[k - 1][alpha * d + lane];
@@ -834,7 +1133,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
       const int c0 = min(iq[0], Nk - 1), c1 = min(iq[1], Nk - 1), c2 = min(iq[2], Nk - 1), c3 = min(iq[3], Nk - 1);
 #pragma unroll 4
       for (int b = 0; b < rk; ++b) {
-        const double zb = sh.z[b];
+        const double zb = sh.z[warp][b];
         const double *row = Yc + b * cst;
         acc[0] = fma(row[c0], zb, acc[0]);
         acc[1] = fma(row[c1], zb, acc[1]);
@@ -842,6 +1141,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
         acc[3] = fma(row[c3], zb, acc[3]);
       }
     }
+    double best = 0.0;
+    unsigned nel = 0, nev = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (iq[q] >= i1) continue;
@@ -851,48 +1152,55 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
       const double sc = isfinite(E) ? fabs(E) : -1.0;
       D.cs[k][rho] = sc;
       D.ce[k][rho] = E;
-      best = fmax(best, sc);
-      ++evals;
+      ++nev;
+      if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+      nel += __shfl_xor_sync(0xffffffffu, nel, o);
+      nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    }
+    if (lane == 0) {
+      if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
+      D.im[k][local] = nel ? best : -1.0;
+      stage_publish(I, best, nel);
     }
     __syncwarp();
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-  if (lane == 0 && evals) atomicAdd(&I.evals, (unsigned long long)evals);
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
-  int pick;
-  double epick;
-  if (!cta_pick_last(best, D, k, rl * Nk, &pick, &epick)) return;
-  if (threadIdx.x == 0) {
-    if (pick < 0) I.active = 0;
-    else I.row = pick;
-  }
 }
 
-// Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta); argmax -> gamma_new,
-// then the rook test (Eq. 2): gamma_new == gamma* ends the search.
+// Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
+// searching interface, items (interface, beta, node chunk); pass 1 of the argmax.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
-  const int k = blockIdx.y + 1;
-  if (k > D.d - 1) return;
   if (st->stop || !st->search) return;
-  IfaceState &I = st->it[k];
-  if (!I.active || I.rook_done) return;
   __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  const int rk = st->r[k], rn = st->r[k + 1];
-  const int Nk = D.N[k - 1], Nk1 = D.N[k];
-  const int rho = I.row, alpha = rho / Nk, i = rho % Nk;
-  for (int b = threadIdx.x; b < rk; b += blockDim.x) sh.z[b] = D.zvec[k][b];
-  __syncthreads();
-  const int nch = (Nk1 + TTQ_CHUNK - 1) / TTQ_CHUNK;
-  const int items = rn * nch;
-  double best = -1.0;
+  int cnt = 0;
+  if (lane < d - 1) {
+    const IfaceState &I = st->it[lane + 1];
+    if (I.active && !I.rook_done) cnt = st->r[lane + 2] * ((D.N[lane + 1] + TTQ_CHUNK - 1) / TTQ_CHUNK);
+  }
+  const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
-  long long evals = 0;
-  for (int w = blockIdx.x * TTQ_WARPS + warp; w < items; w += gridDim.x * TTQ_WARPS) {
-    const int beta = w / nch, ch = w % nch;
+  int zk = 0;
+  for (int w = blockIdx.x * TTQ_WARPS + warp; w < im.total; w += gridDim.x * TTQ_WARPS) {
+    const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
+    const int k = __ffs(ball);
+    const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
+    IfaceState &I = st->it[k];
+    const int rk = st->r[k], rn = st->r[k + 1];
+    const int Nk = D.N[k - 1], Nk1 = D.N[k];
+    const int nch = (Nk1 + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    const int beta = local / nch, ch = local % nch;
+    const int rho = I.row, alpha = rho / Nk, i = rho % Nk;
+    if (k != zk) {
+      for (int b = lane; b < rk; b += 32) sh.z[warp][b] = D.zvec[k][b];
+      zk = k;
+    }
     if (lane < d) {
       int v = 0;
       if (lane < k - 1) v = D.lidx[k - 1][alpha * d + lane];
@@ -929,7 +1237,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
       const int c0 = min(jq[0], Nk1 - 1), c1 = min(jq[1], Nk1 - 1), c2 = min(jq[2], Nk1 - 1), c3 = min(jq[3], Nk1 - 1);
 #pragma unroll 4
       for (int a = 0; a < rk; ++a) {
-        const double za = sh.z[a];
+        const double za = sh.z[warp][a];
         const double *row = Yr + (size_t)a * Nk1;
         acc[0] = fma(row[c0], za, acc[0]);
         acc[1] = fma(row[c1], za, acc[1]);
@@ -937,6 +1245,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
         acc[3] = fma(row[c3], za, acc[3]);
       }
     }
+    double best = 0.0;
+    unsigned nel = 0, nev = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (jq[q] >= j1) continue;
@@ -946,30 +1256,23 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
       const double sc = isfinite(E) ? fabs(E) : -1.0;
       D.cs[k][g] = sc;
       D.ce[k][g] = E;
-      best = fmax(best, sc);
-      ++evals;
+      ++nev;
+      if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+      nel += __shfl_xor_sync(0xffffffffu, nel, o);
+      nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    }
+    if (lane == 0) {
+      if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
+      D.im[k][local] = nel ? best : -1.0;
+      stage_publish(I, best, nel);
     }
     __syncwarp();
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-  if (lane == 0 && evals) atomicAdd(&I.evals, (unsigned long long)evals);
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
-  int pick;
-  double epick;
-  if (!cta_pick_last(best, D, k, Nk1 * rn, &pick, &epick)) return;
-  if (threadIdx.x == 0) {
-    if (pick < 0) {
-      I.active = 0;
-    } else {
-      const int rounds = I.rounds + 1;
-      const bool done = (pick == I.col) || rounds >= D.rook_max;
-      I.rounds = rounds;
-      I.col = pick;
-      I.err = epick;
-      I.rook_done = done ? 1 : 0;
-    }
-  }
 }
 
 // End of sweep (Alg. 6): append every accepted pivot, nested by construction.
@@ -978,11 +1281,10 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
 __global__ void k_update(Dev *const *Dps, cudaGraphConditionalHandle h, int use_cond) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
-  const int d = D.d;
-  const int k = threadIdx.x + 1;            // one thread per interface (d - 1 <= 31)
+  const int d = D.d, lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
   __shared__ int rold[TTQ_MAXD + 1];
   __shared__ int nacc;
-  __shared__ long long ev;
+  __shared__ unsigned long long ev;
   __shared__ int mode;                      // 0: nothing to do, 1: apply pending stop, 2: no search, 3: append
   if (threadIdx.x == 0) {
     nacc = 0; ev = 0;
@@ -998,31 +1300,34 @@ __global__ void k_update(Dev *const *Dps, cudaGraphConditionalHandle h, int use_
     for (int q = threadIdx.x; q <= d; q += blockDim.x) rold[q] = st->r[q];
     __syncthreads();
     const double scale = __longlong_as_double((long long)st->scale_bits);
-    if (k <= d - 1) {
+    // one warp per interface, lanes over the modes of the new index tuples
+    for (int k = warp + 1; k <= d - 1; k += nw) {
       IfaceState &I = st->it[k];
-      atomicAdd((unsigned long long *)&ev, (unsigned long long)I.evals);
-      if (I.active) {
-        const bool acc = fabs(I.err) > D.pivot_tol * scale && rold[k] < D.cap;
-        I.accepted = acc ? 1 : 0;
-        if (acc) {
-          atomicAdd(&nacc, 1);
-          const int Nk = D.N[k - 1], rn = rold[k + 1];
-          const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
-          const int a = rold[k];
-          int *L = D.lidx[k] + (size_t)a * d, *R = D.ridx[k] + (size_t)a * d;
-          for (int m = 0; m < d; ++m) {
-            L[m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
-            R[m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
-          }
-          D.lpar[k][a] = alpha; D.lnode[k][a] = i;
-          D.rpar[k][a] = beta; D.rnode[k][a] = j;
-        }
+      const bool acc = I.active && fabs(I.err) > D.pivot_tol * scale && rold[k] < D.cap;
+      if (lane == 0) {
+        atomicAdd(&ev, I.evals);
+        if (I.active) I.accepted = acc ? 1 : 0;
+        if (acc) atomicAdd(&nacc, 1);
+      }
+      if (!acc) continue;
+      const int Nk = D.N[k - 1], rn = rold[k + 1];
+      const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
+      const int a = rold[k];
+      if (lane < d) {
+        const int m = lane;
+        D.lidx[k][(size_t)a * d + m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
+        D.ridx[k][(size_t)a * d + m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
+      }
+      if (lane == 0) {
+        D.lpar[k][a] = alpha; D.lnode[k][a] = i;
+        D.rpar[k][a] = beta; D.rnode[k][a] = j;
       }
     }
     __syncthreads();
-    if (k <= d - 1 && st->it[k].accepted) st->r[k] = rold[k] + 1;
+    for (int k = threadIdx.x + 1; k <= d - 1; k += blockDim.x)
+      if (st->it[k].active && st->it[k].accepted) st->r[k] = rold[k] + 1;
     if (threadIdx.x == 0) {
-      st->search_evals += ev;
+      st->search_evals += (long long)ev;
       if (st->rules && nacc == 0) { st->stop = 1; st->status = ST_NO_PIVOT; }
       st->sweep++;
     }
