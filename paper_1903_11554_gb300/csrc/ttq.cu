@@ -6,6 +6,7 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -222,7 +223,7 @@ static void make_layout(const ttq_problem *p, Layout *L) {
   }
   const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;
   auto clampi = [](long v, long lo, long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
-  L->sblocks = clampi((maxS + TTQ_WARPS - 1) / TTQ_WARPS, 1, 64);
+  L->sblocks = clampi((maxS + TTQ_WARPS * TTQ_SPW - 1) / (TTQ_WARPS * TTQ_SPW), 1, 64);
   // the rook kernels spread every interface's work over one grid per instance
   L->cblocks = clampi(((long)(d - 1) * cap * nch + TTQ_WARPS - 1) / TTQ_WARPS, 1, 456);
   L->rblocks = L->cblocks;
@@ -348,13 +349,26 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     P->sblocks = Ls[q].sblocks > P->sblocks ? Ls[q].sblocks : P->sblocks;
     P->cblocks = Ls[q].cblocks > P->cblocks ? Ls[q].cblocks : P->cblocks;
   }
+  // rook kernels: the device's resident CTA slots (a multiple of the SM count, so
+  // the round-robin item deal spreads evenly over the SMs), shared by the instances
+  {
+    int dev = 0, sms = 152, occ = 3;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col, TTQ_WARPS * 32, 0) != cudaSuccess || occ < 1)
+      occ = 1;
+    const int slots = sms * occ;
+    if (count == 1) P->cblocks = slots;
+    else P->cblocks = std::min(P->cblocks, std::max(1, (slots + count - 1) / count));
+    cudaGetLastError();
+  }
   P->rblocks = P->cblocks;
   size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
   P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
   const size_t cap = P->max_cap;
   const int q_in = cap <= 96 ? 1 : 0;
   P->qr_smem = (int)((cap * (cap + 1) + 8 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+7r
-  P->samples_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
+  // R (and Q when it fits), then per warp TTQ_SPW groups of two vectors of cap + 1
+  P->samples_smem = (int)(((q_in ? 2 : 1) * cap * cap + (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap + 1)) * 8);
   P->contract_smem = (int)(cap * cap * 8);
   P->solve_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
 }

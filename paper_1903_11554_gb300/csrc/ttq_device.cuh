@@ -381,4 +381,84 @@ __device__ __forceinline__ double fiber_value(const Dev &D, int f, const int *m,
   return u.W * wi * g;
 }
 
+// ---------------------------------------------------------------------------
+// Single-point evaluation (one thread): A(m) = prod_v w_{m_v} g(x_{m_0}, .., x_{m_{d-1}})
+// for the node indices m_v = m[v * stride].  The same integrand as the fiber
+// routines above, for work where every thread holds its own point.
+
+__device__ __forceinline__ double point_value(const Dev &D, const int *m, int stride) {
+  const int d = D.d;
+  double W = 1.0;
+  for (int v = 0; v < d; ++v) W *= D.w[D.off[v] + m[v * stride]];
+  if (D.family == FAM_TEST) {
+    double S = 0.0;
+    for (int v = 0; v < d; ++v) S += D.x[D.off[v] + m[v * stride]];
+    const double e = exp(-S / (double)d);
+    double g = 0.0;
+    for (int t = 0; t < D.n; ++t) g = (g + 1.0) * e;
+    return W * g;
+  }
+  if (D.form == FORM_RN) {
+    double s = 0.0;
+    for (int v = 0; v < d; ++v) s += D.c[D.off[v] + m[v * stride]];
+    double g = 1.0 / (s * s);
+    if (D.family == FAM_D) {
+      double p = 1.0;
+      for (int a = 0; a < d; ++a) {
+        const int ma = m[a * stride];
+        for (int b = a + 1; b < d; ++b) {
+          const int mb = m[b * stride];
+          if (D.uniformT) {
+            const int dm = ma - mb;
+            p *= D.T[dm < 0 ? -dm : dm];
+          } else {
+            const double t = tanh((D.x[D.off[a] + ma] - D.x[D.off[b] + mb]) * 0.5);
+            p *= t * t;
+          }
+        }
+      }
+      g *= p;
+    }
+    return W * g;
+  }
+  // unit cube: variable x_v (v = 2..n) lives in mode v-2
+  const int n = D.n;
+#define XP(v) (D.x[D.off[(v) - 2] + m[((v) - 2) * stride]])
+  double g = 1.0;
+  if (D.family == FAM_D || D.family == FAM_E) {
+    // A_n: pairs 1 <= i < j <= n with p_ij = x_{i+1} ... x_j, q = (1 - p) / (1 + p)
+    double num = 1.0, den = 1.0;
+    for (int i = 1; i <= n - 1; ++i) {
+      double p = 1.0;
+      for (int j = i + 1; j <= n; ++j) {
+        p *= XP(j);
+        num *= 1.0 - p;
+        den *= 1.0 + p;
+      }
+    }
+    const double q = num / den;
+    g = q * q;
+  }
+  if (D.family == FAM_C || D.family == FAM_D) {
+    double left = 1.0, right = 1.0, p = 1.0;
+    for (int v = 2; v <= n; ++v) { p *= XP(v); left += p; }
+    p = 1.0;
+    for (int v = n; v >= 2; --v) { p *= XP(v); right += p; }
+    g = g / (left * right);
+  }
+#undef XP
+  return W * g;
+}
+
+// FP64 operations of one point_value (algorithmic count)
+__device__ __forceinline__ int point_flops(const Dev &D) {
+  const int d = D.d, n = D.n;
+  if (D.family == FAM_TEST) return 2 * (d - 1) + 2 * n + 3;
+  if (D.form == FORM_RN) return 2 * (d - 1) + 5 + (D.family == FAM_D ? d * (d - 1) / 2 * (D.uniformT ? 1 : 4) + 1 : 0);
+  int fl = d;
+  if (D.family == FAM_D || D.family == FAM_E) fl += 3 * n * (n - 1) / 2 + 2;
+  if (D.family == FAM_C || D.family == FAM_D) fl += 4 * n + 2;
+  return fl;
+}
+
 }  // namespace ttq

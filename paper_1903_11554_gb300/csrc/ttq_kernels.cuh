@@ -21,28 +21,6 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
 
 // ---------------------------------------------------------------------------
-// solves with the QR factors of G_k (one warp; buf/tmp: per-warp shared scratch)
-
-// buf <- G^{-1} buf with factors staged in shared memory: Qs row-major (ld r)
-// or, if Qs == nullptr, Q from global; Rs column-major (ld r); ri = 1 / R_jj
-__device__ void warp_col_solve_s(const Dev &D, int k, int r, const double *Qs, const double *Rs,
-                                 const double *ri, double *buf, double *tmp) {
-  const int lane = lane_id(), ld = D.cap;
-  for (int i = lane; i < r; i += 32) {
-    double acc = 0.0;
-    if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], buf[b], acc);
-    else for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], buf[b], acc);
-    tmp[i] = acc;
-  }
-  __syncwarp();
-  for (int j = r - 1; j >= 0; --j) {
-    double zj = tmp[j] * ri[j];
-    for (int i = lane; i < j; i += 32) tmp[i] = fma(-Rs[i + j * r], zj, tmp[i]);
-    if (lane == 0) buf[j] = zj;
-    __syncwarp();
-  }
-}
-
 // Stage r x r blocks of the QR factors in shared memory: for e = (row, col) in
 // [0, r)^2, a_dst[row * ldd + col] = a_src[row * ld + col], the same for b if
 // b_dst; whole CTA, with eight independent loads in flight per thread (the
@@ -941,16 +919,6 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   if (threadIdx.x == 0) atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r));
 }
 
-// shared per-warp scratch of the search kernels
-struct SearchSmem {
-  int ms[TTQ_WARPS][TTQ_MAXD];
-  double pl[TTQ_WARPS][TTQ_MAXPAIR];
-  double buf[TTQ_WARPS][TTQ_MAXR];
-  double tmp[TTQ_WARPS][TTQ_MAXR];
-  int exc[TTQ_WARPS][TTQ_MAXR];
-  double ri[TTQ_MAXR];
-};
-
 // per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
 struct RookSmem {
   int ms[TTQ_WARPS][TTQ_MAXD];
@@ -978,71 +946,120 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
   return true;
 }
 
-// Alg. 2, first step: residuals E = A - B_k R_{k+1} at seeded random positions.
+// Alg. 2, first step: residuals E = A - L_k G_k^-1 R_{k+1} at seeded random
+// positions (rho_t, gamma_t) of superblock k.  A warp takes TTQ_SPW samples at a
+// time: one lane each evaluates A at its point, then a group of TTQ_SG lanes per
+// sample forms z = G_k^-1 R_{k+1}(:, gamma_t) = R^-1 (Q^T y) (rows of Q^T y and
+// of the back substitution split over the group, so one warp instruction of the
+// sequential substitution serves TTQ_SPW samples) and E = A - L_k(rho_t, :) z.
+#define TTQ_SG 8
+#define TTQ_SPW (32 / TTQ_SG)
 __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   const int k = blockIdx.y + 1;
   if (!iface_searchable(D, st, k)) return;
-  __shared__ SearchSmem sh;
+  __shared__ int mx[TTQ_WARPS][TTQ_MAXD][TTQ_SPW];   // node indices of the warp's points
+  __shared__ int rset[TTQ_MAXR], gset[TTQ_MAXR];      // cross rows / columns (excluded)
+  __shared__ double ri[TTQ_MAXR];
   extern __shared__ double fac[];
   const int lane = lane_id(), warp = warp_id(), d = D.d;
+  const int g = lane / TTQ_SG, gl = lane % TTQ_SG;
   const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
   const int Nk = D.N[k - 1], Nk1 = D.N[k];
   const int M = rl * Nk, Ncol = Nk1 * rn, S = D.S[k];
   double *Rs = fac;                                  // R column-major, ld rk
-  double *Qs = D.q_in_smem ? fac + (size_t)rk * rk : nullptr;   // Q row-major, ld rk
+  double *Qs = D.q_in_smem ? fac + (size_t)D.cap * D.cap : nullptr;   // Q row-major, ld rk
+  const int vst = D.cap + 1;                         // padded group vector stride
+  double *yv = fac + (size_t)D.cap * D.cap * (D.q_in_smem ? 2 : 1) + (size_t)warp * TTQ_SPW * 2 * vst;
+  double *y = yv + g * 2 * vst, *t = y + vst;        // this group's y (then z) and Q^T y
   stage_compact(Rs, D.Rc[k], Qs, D.Qr[k], rk, D.cap);
-  for (int b = threadIdx.x; b < rk; b += blockDim.x) sh.ri[b] = D.rinv[k][b];
+  for (int a = threadIdx.x; a < rk; a += blockDim.x) {
+    ri[a] = D.rinv[k][a];
+    rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
+    gset[a] = D.rnode[k][a] * rn + D.rpar[k][a];
+  }
   __syncthreads();
   const unsigned long long sid = stream_id(st->sweep, k, 1);
+  const int flp = point_flops(D);
   double best = 0.0;
-  long long evals = 0, nel = 0;
+  unsigned nel = 0, nev = 0;
   unsigned long long fl = 0;
-  for (int t = blockIdx.x * TTQ_WARPS + warp; t < S; t += gridDim.x * TTQ_WARPS) {
-    const int rho = draw_index(D.seed, sid, 2ULL * t, (unsigned long long)M);
-    const int gam = draw_index(D.seed, sid, 2ULL * t + 1, (unsigned long long)Ncol);
-    bool ex = false;
-    for (int a = lane; a < rk; a += 32) {
-      if (D.lpar[k][a] * Nk + D.lnode[k][a] == rho) ex = true;
-      if (D.rnode[k][a] * rn + D.rpar[k][a] == gam) ex = true;
-    }
-    if (__any_sync(0xffffffffu, ex)) {
-      if (lane == 0) { D.cs[k][t] = -1.0; D.ce[k][t] = 0.0; }
-      continue;
-    }
-    const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
-    if (lane < d) {
-      int v;
-      if (lane < k - 1) v = D.lidx[k - 1][alpha * d + lane];
-      else if (lane == k - 1) v = i;
-      else if (lane == k) v = j;
-      else v = D.ridx[k + 1][beta * d + lane];
-      sh.ms[warp][lane] = v;
-    }
-    // y = R_{k+1}(:, gamma) = Y_{k+1}(:, j, beta)
-    for (int b = lane; b < rk; b += 32) sh.buf[warp][b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
-    __syncwarp();
-    FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
+  for (int base = (blockIdx.x * TTQ_WARPS + warp) * TTQ_SPW; base < S; base += gridDim.x * TTQ_WARPS * TTQ_SPW) {
+    // one lane per sample: draw, exclusion test, A at the point
+    int rho = 0, gam = 0, ok = 0;
     double A = 0.0;
-    if (lane == 0) A = fiber_value(D, k - 1, sh.ms[warp], u, sh.pl[warp], i);
-    A = __shfl_sync(0xffffffffu, A, 0);
-    warp_col_solve_s(D, k, rk, Qs, Rs, sh.ri, sh.buf[warp], sh.tmp[warp]);
-    double acc = 0.0;
-    for (int b = lane; b < rk; b += 32) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], sh.buf[warp][b], acc);
-    acc = warp_sum(acc);
-    const double E = A - acc;
-    const double sc = isfinite(E) ? fabs(E) : -1.0;
-    if (lane == 0) { D.cs[k][t] = sc; D.ce[k][t] = E; }
-    if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
-    ++evals;
-    fl += (unsigned long long)(u.fl_uniform + u.fl_node) + 3ULL * rk * rk + 2ULL * rk + 1;
+    if (lane < TTQ_SPW && base + lane < S) {
+      const int tt = base + lane;
+      rho = draw_index(D.seed, sid, 2ULL * tt, (unsigned long long)M);
+      gam = draw_index(D.seed, sid, 2ULL * tt + 1, (unsigned long long)Ncol);
+      bool ex = false;
+      for (int a = 0; a < rk; ++a) ex |= (rset[a] == rho) | (gset[a] == gam);
+      if (ex) {
+        D.cs[k][tt] = -1.0;
+        D.ce[k][tt] = 0.0;
+      } else {
+        ok = 1;
+        const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
+        for (int v = 0; v < d; ++v) {
+          int mv;
+          if (v < k - 1) mv = D.lidx[k - 1][alpha * d + v];
+          else if (v == k - 1) mv = i;
+          else if (v == k) mv = j;
+          else mv = D.ridx[k + 1][beta * d + v];
+          mx[warp][v][lane] = mv;
+        }
+        A = point_value(D, &mx[warp][0][lane], TTQ_SPW);
+      }
+    }
+    // group g takes sample base + g
+    rho = __shfl_sync(0xffffffffu, rho, g);
+    gam = __shfl_sync(0xffffffffu, gam, g);
+    ok = __shfl_sync(0xffffffffu, ok, g);
+    A = __shfl_sync(0xffffffffu, A, g);
+    const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
+    for (int b = gl; b < rk; b += TTQ_SG) y[b] = ok ? D.Y[k + 1][core_at(D, k + 1, b, j, beta)] : 0.0;
+    __syncwarp();
+    for (int r0 = gl; r0 < rk; r0 += TTQ_SG) {   // t = Q^T y
+      double acc = 0.0;
+      if (Qs) for (int b = 0; b < rk; ++b) acc = fma(Qs[b * rk + r0], y[b], acc);
+      else for (int b = 0; b < rk; ++b) acc = fma(D.Qr[k][b * D.cap + r0], y[b], acc);
+      t[r0] = acc;
+    }
+    __syncwarp();
+    for (int jj = rk - 1; jj >= 0; --jj) {        // back substitution R z = t (z into y)
+      const double zj = t[jj] * ri[jj];
+      for (int r0 = gl; r0 < jj; r0 += TTQ_SG) t[r0] = fma(-Rs[r0 + jj * rk], zj, t[r0]);
+      if (gl == (jj % TTQ_SG)) y[jj] = zj;
+      __syncwarp();
+    }
+    double acc = 0.0;                             // L_k(rho, :) z
+    if (ok) for (int b = gl; b < rk; b += TTQ_SG) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], y[b], acc);
+#pragma unroll
+    for (int o = TTQ_SG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (ok && gl == 0) {
+      const int tt = base + g;
+      const double E = A - acc;
+      const double sc = isfinite(E) ? fabs(E) : -1.0;
+      D.cs[k][tt] = sc;
+      D.ce[k][tt] = E;
+      ++nev;
+      if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
+      fl += (unsigned long long)flp + 3ULL * rk * rk + 2ULL * rk + 1;
+    }
     __syncwarp();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    nel += __shfl_xor_sync(0xffffffffu, nel, o);
+    nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    fl += __shfl_xor_sync(0xffffffffu, fl, o);
+  }
   if (lane == 0) {
-    if (evals) atomicAdd(&st->it[k].evals, (unsigned long long)evals);
+    if (nev) atomicAdd(&st->it[k].evals, (unsigned long long)nev);
     if (fl) atomicAdd(&st->flops[3], fl);
-    stage_publish(st->it[k], best, (unsigned)nel);
+    stage_publish(st->it[k], best, nel);
   }
 }
 
@@ -1079,7 +1096,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
   const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface whose z sits in sh.z[warp]
-  for (int w = blockIdx.x * TTQ_WARPS + warp; w < im.total; w += gridDim.x * TTQ_WARPS) {
+  // items dealt round-robin over the CTAs first, so every CTA (and SM) gets an even share
+  for (int w = warp * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
     const int k = __ffs(ball);                  // interface (1-based)
     const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
@@ -1187,7 +1205,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
   const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
   int zk = 0;
-  for (int w = blockIdx.x * TTQ_WARPS + warp; w < im.total; w += gridDim.x * TTQ_WARPS) {
+  // items dealt round-robin over the CTAs first, so every CTA (and SM) gets an even share
+  for (int w = warp * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
     const int k = __ffs(ball);
     const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
