@@ -164,7 +164,8 @@ struct Layout {
   size_t dev, st, x, w, c, T, cbuf;
   size_t lidx[TTQ_MAXD], ridx[TTQ_MAXD], lpar[TTQ_MAXD], lnode[TTQ_MAXD], rpar[TTQ_MAXD], rnode[TTQ_MAXD];
   size_t Y[TTQ_MAXD + 1], V[TTQ_MAXD + 1], Vlo[TTQ_MAXD + 1];
-  size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], rinv[TTQ_MAXD], zvec[TTQ_MAXD], pvec[TTQ_MAXD];
+  size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], Cc[TTQ_MAXD], Sr[TTQ_MAXD], rinv[TTQ_MAXD],
+      zvec[TTQ_MAXD], pvec[TTQ_MAXD];
   size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD];
   size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
@@ -208,6 +209,8 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     L->Qc[k] = b.take((size_t)cap * cap * 8);
     L->Rc[k] = b.take((size_t)cap * cap * 8);
     L->Rr[k] = b.take((size_t)cap * cap * 8);
+    L->Cc[k] = b.take((size_t)cap * cap * 8);
+    L->Sr[k] = b.take((size_t)cap * cap * 8);
     L->rinv[k] = b.take((size_t)cap * 8);
     L->zvec[k] = b.take((size_t)cap * 8);
     L->pvec[k] = b.take((size_t)cap * 8);
@@ -297,6 +300,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
     D.rpar[k] = (int *)(base + L.rpar[k]); D.rnode[k] = (int *)(base + L.rnode[k]);
     D.Qr[k] = (double *)(base + L.Qr[k]); D.Qc[k] = (double *)(base + L.Qc[k]);
     D.Rc[k] = (double *)(base + L.Rc[k]); D.Rr[k] = (double *)(base + L.Rr[k]);
+    D.Cc[k] = (double *)(base + L.Cc[k]); D.Sr[k] = (double *)(base + L.Sr[k]);
     D.rinv[k] = (double *)(base + L.rinv[k]); D.zvec[k] = (double *)(base + L.zvec[k]);
     D.pvec[k] = (double *)(base + L.pvec[k]);
     D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);

@@ -90,6 +90,7 @@ struct Dev {
   double *Y[TTQ_MAXD + 1];
   double *V[TTQ_MAXD + 1], *Vlo[TTQ_MAXD + 1];
   double *Qr[TTQ_MAXD], *Qc[TTQ_MAXD], *Rc[TTQ_MAXD], *Rr[TTQ_MAXD], *rinv[TTQ_MAXD];
+  double *Cc[TTQ_MAXD], *Sr[TTQ_MAXD];   // R D^-1 column-major, D^-1 R row-major (D = diag R)
   double *zvec[TTQ_MAXD];   // per interface: G^{-1} y or G^{-T} l of the next rook step
   double *pvec[TTQ_MAXD];   // per interface: R^{-T} l of the last row solve
   double *cbuf;             // the two contraction chains' vectors (hi, lo) x 2, cap each

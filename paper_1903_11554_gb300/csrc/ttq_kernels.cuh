@@ -55,6 +55,114 @@ __device__ __forceinline__ void stage_compact(double *a_dst, const double *a_src
   stage_block(a_dst, a_src, b_dst, b_src, r, ld, r);
 }
 
+// asynchronous global -> shared copies (cp.async, 8 bytes each)
+__device__ __forceinline__ void cp_async8(double *smem, const double *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// the same r x r copies as stage_compact, issued asynchronously
+__device__ __forceinline__ void stage_compact_async(double *a_dst, const double *a_src, double *b_dst,
+                                                    const double *b_src, int r, int ld) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int o = (e / r) * ld + e % r;
+    cp_async8(a_dst + e, a_src + o);
+    if (b_dst) cp_async8(b_dst + e, b_src + o);
+  }
+}
+
+// out[i] = sum_b M(i, b) x[b], i < r, with M(i, b) at Mp[i * si + b * sb]; the
+// sum over b split into parts over all threads, partial sums combined in order
+__device__ __forceinline__ void cta_gemv(const double *Mp, int si, int sb, const double *x, int r, double *part,
+                                        double *out) {
+  const int nt = blockDim.x, P = r <= 64 ? 4 : 2, rows = nt / P;
+  const int i = threadIdx.x % rows, pp = threadIdx.x / rows;
+  if (i < r && pp < P) {
+    const int b0 = pp * r / P, b1 = (pp + 1) * r / P;
+    double acc = 0.0;
+    for (int b = b0; b < b1; ++b) acc = fma(Mp[(size_t)i * si + (size_t)b * sb], x[b], acc);
+    part[pp * TTQ_MAXR + i] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < r) {
+    double acc = part[threadIdx.x];
+    for (int q = 1; q < P; ++q) acc += part[q * TTQ_MAXR + threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
+  __syncthreads();
+}
+
+// Substitutions with the scaled triangles, one warp, lane l holding entries
+// l + 32 q in registers.  Back: v <- t, then for j = r-1 .. 0: v_i -= C_ij v_j
+// (i < j), C = R D^-1 column-major; the result z = D^-1 v.  Forward: u <- l,
+// then for i = 0 .. r-1: u_m -= S_im u_i (m > i), S = D^-1 R row-major; the
+// result t = D^-1 u.  The steps are split into segments of 32 so that the
+// number of register blocks a step touches is a compile-time constant (an FP64
+// warp instruction costs its full time whether or not its lanes are active).
+template <int NQ>
+__device__ __forceinline__ void back_seg(const double *C, int ld, int jhi, int jlo, double *tq, double *vout) {
+  const int lane = lane_id();
+  for (int jj = jhi; jj >= jlo; --jj) {
+    const double vj = __shfl_sync(0xffffffffu, tq[NQ - 1], jj & 31);
+    if (lane == (jj & 31)) vout[jj] = vj;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if (q < NQ - 1 || lane + 32 * q < jj) tq[q] = fma(-C[lane + 32 * q + (size_t)jj * ld], vj, tq[q]);
+  }
+}
+// vout[j] = v_j after the back substitution (z = D^-1 vout); C column-major, leading dimension ld
+__device__ __forceinline__ void warp_back_subst(const double *C, const double *t, double *vout, int r, int ld) {
+  const int lane = lane_id(), nq = (r + 31) >> 5;
+  double tq[TTQ_MAXR / 32];
+#pragma unroll
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) tq[q] = (lane + 32 * q < r) ? t[lane + 32 * q] : 0.0;
+  for (int sg = nq; sg >= 1; --sg) {
+    const int jhi = min(r, 32 * sg) - 1, jlo = 32 * (sg - 1);
+    switch (sg) {
+      case 4: back_seg<4>(C, ld, jhi, jlo, tq, vout); break;
+      case 3: back_seg<3>(C, ld, jhi, jlo, tq, vout); break;
+      case 2: back_seg<2>(C, ld, jhi, jlo, tq, vout); break;
+      default: back_seg<1>(C, ld, jhi, jlo, tq, vout); break;
+    }
+  }
+}
+template <int QLO, int NQ>
+__device__ __forceinline__ void fwd_seg(const double *S, int r, int ld, int ilo, int ihi, double *vq, double *uout) {
+  const int lane = lane_id();
+  for (int i = ilo; i <= ihi; ++i) {
+    const double ui = __shfl_sync(0xffffffffu, vq[QLO], i & 31);
+    if (lane == (i & 31)) uout[i] = ui;
+#pragma unroll
+    for (int q = QLO; q < NQ; ++q) {
+      const int m = lane + 32 * q;
+      if ((q > QLO || m > i) && (q < NQ - 1 || m < r)) vq[q] = fma(-S[(size_t)i * ld + m], ui, vq[q]);
+    }
+  }
+}
+// uout[i] = u_i after the forward substitution (t = D^-1 uout); S row-major, leading dimension ld
+__device__ __forceinline__ void warp_fwd_subst(const double *S, const double *l, double *uout, int r, int ld) {
+  const int lane = lane_id(), nq = (r + 31) >> 5;
+  double vq[TTQ_MAXR / 32];
+#pragma unroll
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) vq[q] = (lane + 32 * q < r) ? l[lane + 32 * q] : 0.0;
+  for (int sg = 0; sg < nq; ++sg) {
+    const int ilo = 32 * sg, ihi = min(r, 32 * (sg + 1)) - 1;
+    switch (nq * 4 + sg) {
+      case 16: fwd_seg<0, 4>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 17: fwd_seg<1, 4>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 18: fwd_seg<2, 4>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 19: fwd_seg<3, 4>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 12: fwd_seg<0, 3>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 13: fwd_seg<1, 3>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 14: fwd_seg<2, 3>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 8: fwd_seg<0, 2>(S, r, ld, ilo, ihi, vq, uout); break;
+      case 9: fwd_seg<1, 2>(S, r, ld, ilo, ihi, vq, uout); break;
+      default: fwd_seg<0, 1>(S, r, ld, ilo, ihi, vq, uout); break;
+    }
+  }
+}
+
 // core entry Y_k(alpha, i, beta)
 __device__ __forceinline__ size_t core_at(const Dev &D, int k, int alpha, int i, int beta) {
   return ((size_t)beta * D.capL[k - 1] + alpha) * D.N[k - 1] + i;
@@ -230,20 +338,31 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
 // (O(r^3), LAPACK dgeqr2/dorg2r conventions) runs when no factors are stored
 // (first sweep, or index sets replaced from outside).
 // Stored: Q column-major (Qc) and row-major (Qr), R column- and row-major,
-// 1/R_jj; leading dimension cap.
+// 1/R_jj, and R with its diagonal divided out for the FP64 substitutions:
+// Cc = R D^-1 column-major (entries R_ij / R_jj, back substitution) and
+// Sr = D^-1 R row-major (entries R_ij / R_ii, forward substitution), D = diag R,
+// so each step of a substitution is one multiply-add on its dependency chain;
+// leading dimension cap.
 
 __device__ void qr_store_R(const Dev &D, int k, int r, const double *Rs, int lds, bool rowmajor) {
+  __shared__ double rinv_s[TTQ_MAXR];
   const int ld = D.cap;
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    double rjj = rowmajor ? Rs[j * lds + j] : Rs[j + j * lds];
+    if (!(fabs(rjj) > 0.0) || !isfinite(rjj)) D.st->singular = 1;
+    rinv_s[j] = 1.0 / rjj;
+    D.rinv[k][j] = rinv_s[j];
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     int i = e / r, j = e % r;
     double v = (i <= j) ? (rowmajor ? Rs[i * lds + j] : Rs[i + j * lds]) : 0.0;
     D.Rc[k][i + j * ld] = v;
     D.Rr[k][i * ld + j] = v;
-  }
-  for (int j = threadIdx.x; j < r; j += blockDim.x) {
-    double rjj = rowmajor ? Rs[j * lds + j] : Rs[j + j * lds];
-    if (!(fabs(rjj) > 0.0) || !isfinite(rjj)) D.st->singular = 1;
-    D.rinv[k][j] = 1.0 / rjj;
+    if (i < j) {
+      D.Cc[k][i + j * ld] = v * rinv_s[j];
+      D.Sr[k][i * ld + j] = rinv_s[i] * v;
+    }
   }
 }
 
@@ -351,16 +470,11 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
   for (int a = tid; a < r; a += nt) cn[a] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], n)];
   __syncthreads();
   if (warp == 0) {
-    if (!cached) {                         // forward substitution R^T p = h
-      for (int c = lane; c < n; c += 32) p[c] = h[c];
+    if (!cached) {                         // R^T p = h, the same scaled substitution as the row solve
+      warp_fwd_subst(D.Sr[k], h, p, n, ld);
       __syncwarp();
-      for (int i = 0; i < n; ++i) {
-        const double pi = p[i] * ri[i];
-        for (int j = i + 1 + lane; j < n; j += 32) p[j] = fma(-Rs[i * ls + j], pi, p[j]);
-        __syncwarp();
-        if (lane == 0) p[i] = pi;
-        __syncwarp();
-      }
+      for (int c = lane; c < n; c += 32) p[c] *= ri[c];
+      __syncwarp();
     }
     // t_j by an inclusive scan of p_j^2 over chunks of 32, then c_j and s_j
     double carry = 1.0;
@@ -488,17 +602,15 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
 __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *xh, double *xl,
                                     double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
-  stage_compact(Rs, D.Rr[k], nullptr, nullptr, r, ld);      // row-major R
+  // FP64: D^-1 R (row-major), the scaled forward substitution; double-double: R itself
+  stage_compact(Rs, prec ? D.Rr[k] : D.Sr[k], nullptr, nullptr, r, ld);
   __syncthreads();
-  if (warp == 0) {                               // forward substitution R^T t = x
-    if (!prec) {
-      for (int i = 0; i < r; ++i) {
-        const double ti = xh[i] * D.rinv[k][i];
-        for (int j = i + 1 + lane; j < r; j += 32) xh[j] = fma(-Rs[i * r + j], ti, xh[j]);
-        if (lane == 0) th[i] = ti;
-        __syncwarp();
-      }
-    } else {
+  if (!prec) {                                   // forward substitution R^T t = x
+    if (warp == 0) warp_fwd_subst(Rs, xh, th, r, r);
+    __syncthreads();
+    for (int i = tid; i < r; i += nt) th[i] *= D.rinv[k][i];
+  } else if (warp == 0) {
+    {
       for (int i = 0; i < r; ++i) {
         const dd ti = dd_div_d({xh[i], xl[i]}, Rs[i * r + i]);
         for (int j = i + 1 + lane; j < r; j += 32) {
@@ -530,7 +642,8 @@ __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, doubl
 __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *yh, double *yl,
                                      double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
-  stage_compact(Rs, D.Rc[k], nullptr, nullptr, r, ld);      // column-major R: R[i][j] at Rs[i + j r]
+  // column-major: FP64 R D^-1 (the scaled back substitution), double-double R itself
+  stage_compact(Rs, prec ? D.Rc[k] : D.Cc[k], nullptr, nullptr, r, ld);
   for (int i = tid; i < r; i += nt) {            // t = Q^T y
     if (!prec) {
       double acc = 0.0;
@@ -543,15 +656,12 @@ __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, doub
     }
   }
   __syncthreads();
-  if (warp == 0) {                               // back substitution R z = t
-    if (!prec) {
-      for (int j = r - 1; j >= 0; --j) {
-        const double zj = th[j] * D.rinv[k][j];
-        for (int i = lane; i < j; i += 32) th[i] = fma(-Rs[i + j * r], zj, th[i]);
-        if (lane == 0) yh[j] = zj;
-        __syncwarp();
-      }
-    } else {
+  if (!prec) {                                   // back substitution R z = t
+    if (warp == 0) warp_back_subst(Rs, th, yh, r, r);
+    __syncthreads();
+    for (int j = tid; j < r; j += nt) yh[j] *= D.rinv[k][j];
+  } else if (warp == 0) {
+    {
       for (int j = r - 1; j >= 0; --j) {
         const dd zj = dd_div_d({th[j], tl[j]}, Rs[j + j * r]);
         for (int i = lane; i < j; i += 32) {
@@ -808,70 +918,18 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   return first;
 }
 
-// z = G_k^{-1} y, y = R_{k+1}(:, gamma) = Y_{k+1}(:, j, beta): the solve of the
-// column step (whole CTA; Rs, Qs in shared memory; result in zvec[k])
-__device__ void cta_col_solve(const Dev &D, int k, int r, int gam, double *Rs, double *Qs,
-                              double *v, double *t, double *ri) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
-  const int rn = D.st->r[k + 1], j = gam / rn, beta = gam % rn;
-  // R column-major (R[i][c] at Rs[i + c r]), Q row-major (Q[c][i] at Qs[c r + i])
-  stage_compact(Rs, D.Rc[k], Qs, D.Qr[k], r, ld);
-  for (int b = tid; b < r; b += nt) { v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)]; ri[b] = D.rinv[k][b]; }
-  __syncthreads();
-  for (int i = tid; i < r; i += nt) {            // t = Q^T y
-    double acc = 0.0;
-    if (Qs) for (int b = 0; b < r; ++b) acc = fma(Qs[b * r + i], v[b], acc);
-    else for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][b * ld + i], v[b], acc);
-    t[i] = acc;
-  }
-  __syncthreads();
-  if (warp == 0) {                               // back substitution R z = t
-    for (int jj = r - 1; jj >= 0; --jj) {
-      double zj = t[jj] * ri[jj];
-      for (int i = lane; i < jj; i += 32) t[i] = fma(-Rs[i + jj * r], zj, t[i]);
-      if (lane == 0) v[jj] = zj;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b];
-}
-
-// b = G_k^{-T} l, l = L_k(rho, :)^T = Y_k(alpha, i, :): the solve of the row step
-__device__ void cta_row_solve(const Dev &D, int k, int r, int rho, double *Rs, double *Qs,
-                              double *v, double *t, double *ri) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
-  const int Nk = D.N[k - 1], alpha = rho / Nk, i0 = rho % Nk;
-  // R row-major (R[i][c] at Rs[i r + c]), Q column-major (Q[i][c] at Qs[i + c r])
-  stage_compact(Rs, D.Rr[k], Qs, D.Qc[k], r, ld);
-  for (int b = tid; b < r; b += nt) { v[b] = D.Y[k][core_at(D, k, alpha, i0, b)]; ri[b] = D.rinv[k][b]; }
-  __syncthreads();
-  if (warp == 0) {                               // forward substitution R^T t = l
-    for (int i = 0; i < r; ++i) {
-      double ti = v[i] * ri[i];
-      for (int jj = i + 1 + lane; jj < r; jj += 32) v[jj] = fma(-Rs[i * r + jj], ti, v[jj]);
-      if (lane == 0) t[i] = ti;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < r; i += nt) {            // b = Q t
-    double acc = 0.0;
-    if (Qs) for (int jj = 0; jj < r; ++jj) acc = fma(Qs[i + jj * r], t[jj], acc);
-    else for (int jj = 0; jj < r; ++jj) acc = fma(D.Qc[k][i + jj * ld], t[jj], acc);
-    D.zvec[k][i] = acc;
-    D.pvec[k][i] = t[i];                         // R^-T l: the QR update of this row reuses it
-  }
-  if (tid == 0) { D.st->it[k].prow = rho; D.st->it[k].prank = r; }
-}
-
 // Decisions of Alg. 2 between its search stages, one CTA per interface: the
 // argmax of the stage just run (pass 2), the interface's search state, and the
-// solve the next stage needs (R_k staged in shared memory).
-//   mode 0, after the random samples: (rho*, gamma*) of the best sample; column solve.
-//   mode 1, after a column step: rho* = argmax over E(:, gamma*); row solve.
+// solve the next stage needs.  R_k, Q_k and 1/R_jj are copied to shared memory
+// asynchronously from the start, under the argmax.
+//   mode 0, after the random samples: (rho*, gamma*) of the best sample; column
+//           solve z = G^-1 y, y = R_{k+1}(:, gamma*) = Y_{k+1}(:, j, beta).
+//   mode 1, after a column step: rho* = argmax over E(:, gamma*); row solve
+//           b = G^-T l, l = L_k(rho*, :)^T = Y_k(alpha, i, :).
 //   mode 2, after a row step: gamma_new = argmax over E(rho*, :); the rook test
 //           (Eq. 2) or the round limit ends the search, else the next column solve.
+// The solve's result goes to zvec[k]; the row solve also keeps R^-T l in pvec[k]
+// for the QR update of the pivot's row.
 __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
@@ -881,42 +939,72 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   IfaceState &I = st->it[k];
   if (mode != 0 && (!I.active || I.rook_done)) return;
   extern __shared__ double sm[];
-  __shared__ double v[TTQ_MAXR], t[TTQ_MAXR], ri[TTQ_MAXR];
-  const int r = st->r[k];
-  double *Rs = sm;                               // r x r, orientation of the substitution
+  __shared__ double v[TTQ_MAXR], t[TTQ_MAXR], ri[TTQ_MAXR], part[4 * TTQ_MAXR];
+  const int r = st->r[k], ld = D.cap, tid = threadIdx.x, nt = blockDim.x;
+  double *Rs = sm;
   double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
+  if (mode != 1) stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], r, ld);   // R D^-1 col-major, Q row-major
+  else stage_compact_async(Rs, D.Sr[k], Qs, D.Qc[k], r, ld);             // D^-1 R row-major, Q col-major
+  for (int b = tid; b < r; b += nt) cp_async8(ri + b, D.rinv[k] + b);
   double e;
+  int col = -1, row = -1;
   if (mode == 0) {
     const int pick = stage_pick(D, k, 0, &e);
-    if (pick < 0) return;                        // nothing to search from
-    const int Nk = D.N[k - 1], Nk1 = D.N[k], rn = st->r[k + 1];
-    const unsigned long long sid = stream_id(st->sweep, k, 1);
-    const int row = draw_index(D.seed, sid, 2ULL * pick, (unsigned long long)st->r[k - 1] * Nk);
-    const int col = draw_index(D.seed, sid, 2ULL * pick + 1, (unsigned long long)Nk1 * rn);
-    if (threadIdx.x == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
-    cta_col_solve(D, k, r, col, Rs, Qs, v, t, ri);
+    if (pick >= 0) {
+      const int Nk = D.N[k - 1], Nk1 = D.N[k], rn = st->r[k + 1];
+      const unsigned long long sid = stream_id(st->sweep, k, 1);
+      row = draw_index(D.seed, sid, 2ULL * pick, (unsigned long long)st->r[k - 1] * Nk);
+      col = draw_index(D.seed, sid, 2ULL * pick + 1, (unsigned long long)Nk1 * rn);
+      if (tid == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
+    }
   } else if (mode == 1) {
     const int pick = stage_pick(D, k, 1, &e);
-    if (pick < 0) {
-      if (threadIdx.x == 0) I.active = 0;
-      return;
+    if (tid == 0) {
+      if (pick < 0) I.active = 0;
+      else I.row = pick;
     }
-    if (threadIdx.x == 0) I.row = pick;
-    cta_row_solve(D, k, r, pick, Rs, Qs, v, t, ri);
+    row = pick;
   } else {
     const int pick = stage_pick(D, k, 2, &e);
     if (pick < 0) {
-      if (threadIdx.x == 0) I.active = 0;
-      return;
+      if (tid == 0) I.active = 0;
+    } else {
+      const int rounds = I.rounds + 1;
+      const bool done = (pick == I.col) || rounds >= D.rook_max;
+      __syncthreads();                           // every thread has read I.col
+      if (tid == 0) { I.rounds = rounds; I.col = pick; I.err = e; I.rook_done = done ? 1 : 0; }
+      if (!done) col = pick;
     }
-    const int rounds = I.rounds + 1;
-    const bool done = (pick == I.col) || rounds >= D.rook_max;
-    __syncthreads();                             // every thread has read I.col
-    if (threadIdx.x == 0) { I.rounds = rounds; I.col = pick; I.err = e; I.rook_done = done ? 1 : 0; }
-    if (done) return;
-    cta_col_solve(D, k, r, pick, Rs, Qs, v, t, ri);
   }
-  if (threadIdx.x == 0) atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r));
+  const bool colsolve = mode != 1 && col >= 0, rowsolve = mode == 1 && row >= 0;
+  if (colsolve) {
+    const int rn = st->r[k + 1], j = col / rn, beta = col % rn;
+    for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
+  } else if (rowsolve) {
+    const int Nk = D.N[k - 1], alpha = row / Nk, i0 = row % Nk;
+    for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (colsolve) {
+    // t = Q^T y (Q row-major: Q[b][i] at Qs[b r + i]), then R z = t
+    if (Qs) cta_gemv(Qs, 1, r, v, r, part, t);
+    else cta_gemv(D.Qr[k], 1, ld, v, r, part, t);
+    if (warp_id() == 0) warp_back_subst(Rs, t, v, r, r);
+    __syncthreads();
+    for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b] * ri[b];
+  } else if (rowsolve) {
+    // R^T t = l, then b = Q t (Q column-major: Q[i][c] at Qs[i + c r])
+    if (warp_id() == 0) warp_fwd_subst(Rs, v, t, r, r);
+    __syncthreads();
+    for (int b = tid; b < r; b += nt) t[b] *= ri[b];
+    __syncthreads();
+    if (Qs) cta_gemv(Qs, 1, r, t, r, part, v);
+    else cta_gemv(D.Qc[k], 1, ld, t, r, part, v);
+    for (int b = tid; b < r; b += nt) { D.zvec[k][b] = v[b]; D.pvec[k][b] = t[b]; }
+    if (tid == 0) { I.prow = row; I.prank = r; }
+  }
+  if ((colsolve || rowsolve) && tid == 0) atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r));
 }
 
 // per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
@@ -973,7 +1061,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
   const int vst = D.cap + 1;                         // padded group vector stride
   double *yv = fac + (size_t)D.cap * D.cap * (D.q_in_smem ? 2 : 1) + (size_t)warp * TTQ_SPW * 2 * vst;
   double *y = yv + g * 2 * vst, *t = y + vst;        // this group's y (then z) and Q^T y
-  stage_compact(Rs, D.Rc[k], Qs, D.Qr[k], rk, D.cap);
+  stage_compact(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);   // Rs holds R D^-1 (column-major)
   for (int a = threadIdx.x; a < rk; a += blockDim.x) {
     ri[a] = D.rinv[k][a];
     rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
@@ -1027,12 +1115,13 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
       t[r0] = acc;
     }
     __syncwarp();
-    for (int jj = rk - 1; jj >= 0; --jj) {        // back substitution R z = t (z into y)
-      const double zj = t[jj] * ri[jj];
-      for (int r0 = gl; r0 < jj; r0 += TTQ_SG) t[r0] = fma(-Rs[r0 + jj * rk], zj, t[r0]);
-      if (gl == (jj % TTQ_SG)) y[jj] = zj;
+    for (int jj = rk - 1; jj >= 0; --jj) {        // back substitution with R D^-1: t_i -= C_ij t_j
+      const double vj = t[jj];
+      for (int r0 = gl; r0 < jj; r0 += TTQ_SG) t[r0] = fma(-Rs[r0 + jj * rk], vj, t[r0]);
       __syncwarp();
     }
+    for (int b = gl; b < rk; b += TTQ_SG) y[b] = t[b] * ri[b];   // z = D^-1 t
+    __syncwarp();
     double acc = 0.0;                             // L_k(rho, :) z
     if (ok) for (int b = gl; b < rk; b += TTQ_SG) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], y[b], acc);
 #pragma unroll
