@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -90,6 +91,25 @@ static cudaEvent_t ev_get(ttq_plan *P) {
 }
 
 // launch helper: counts the launch and, when timing, records events around it
+// Kernel launch in the sweep chain: with programmatic serialization (the next
+// kernel launches while this one drains; its pdl_wait orders the data), except
+// while per-kernel timing is on.
+template <typename... KArgs, typename... Args>
+static void launch_k(ttq_plan *P, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s,
+                     Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = P->timing ? 0 : 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename F>
 static void timed_on(ttq_plan *P, cudaStream_t s, int kid, F &&launch) {
   if (P->timing) {
@@ -363,11 +383,16 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     const int slots = sms * occ;
     if (count == 1) P->cblocks = slots;
     else P->cblocks = std::min(P->cblocks, std::max(1, (slots + count - 1) / count));
+    // evaluation kernel: the same deal, its grid the resident slots when one instance runs
+    int occe = 3;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occe, k_eval_slabs, TTQ_WARPS * 32, 0) != cudaSuccess || occe < 1)
+      occe = 1;
+    size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
+    ge = ge < 1 ? 1 : ge;
+    P->grid_eval = count == 1 ? sms * occe : (int)std::min(ge, (size_t)std::max(1, (sms * occe + count - 1) / count));
     cudaGetLastError();
   }
   P->rblocks = P->cblocks;
-  size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
-  P->grid_eval = (int)(ge < 1 ? 1 : (ge > 1216 ? 1216 : ge));
   const size_t cap = P->max_cap;
   const int q_in = cap <= 96 ? 1 : 0;
   P->qr_smem = (int)((cap * (cap + 1) + 8 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+7r
@@ -532,8 +557,9 @@ static void enqueue_sweep(ttq_plan *P) {
   cudaStream_t s = P->stream;
   const int ni = P->max_ni, nb = P->count;
   Dev *const *dv = P->devs;
+  const dim3 W(TTQ_WARPS * 32), T(256);
   timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
-  timed(P, KT_QR, [&] { k_qr<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
+  timed(P, KT_QR, [&] { launch_k(P, k_qr, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
   if (P->s2) {
     cudaEventRecord(P->fork, s);
     cudaStreamWaitEvent(P->s2, P->fork, 0);
@@ -542,19 +568,19 @@ static void enqueue_sweep(ttq_plan *P) {
   } else {
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
-  timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), TTQ_WARPS * 32, P->samples_smem, s>>>(dv); });
-  timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 0); });
+  timed(P, KT_SAMPLES, [&] { launch_k(P, k_samples, dim3(P->sblocks, ni, nb), W, P->samples_smem, s, dv); });
+  timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 0); });
   for (int q = 0; q < P->rook_max; ++q) {
-    timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
-    timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 1); });
-    timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
-    timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), 256, P->solve_smem, s>>>(dv, 2); });
+    timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
+    timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 1); });
+    timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv); });
+    timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 2); });
   }
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
   const int single_cond = P->in_loop && nb == 1;
-  timed(P, KT_UPDATE, [&] { k_update<<<dim3(1, 1, nb), 256, 0, s>>>(dv, P->cond, single_cond); });
+  timed(P, KT_UPDATE, [&] { launch_k(P, k_update, dim3(1, 1, nb), T, 0, s, dv, P->cond, single_cond); });
   if (P->in_loop && nb > 1) {
-    k_batch_cond<<<1, 256, 0, s>>>(dv, nb, P->max_sweeps, P->guard, P->cond);
+    launch_k(P, k_batch_cond, dim3(1), T, 0, s, dv, nb, P->max_sweeps, P->guard, P->cond);
     P->launches++;
   }
 }

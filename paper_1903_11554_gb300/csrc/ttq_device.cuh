@@ -207,6 +207,13 @@ __device__ __forceinline__ int draw_index(unsigned long long seed, unsigned long
   return (int)__umul64hi(v, M);
 }
 
+// Programmatic dependent launch: pdl_wait blocks until the preceding kernel of
+// the stream has completed and its writes are visible; pdl_release lets the
+// next kernel begin launching.  Both are no-ops for a kernel launched without
+// the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" :::); }
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }

@@ -256,6 +256,8 @@ __global__ void k_init(Dev *const *Dps) {
 // lanes over the N_k nodes; writes Y_k and the node sums V_k(alpha, beta).
 __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   if (st->stop) return;
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
@@ -274,7 +276,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
     if (lane >= o) pre += v;
   }
   const int total = __shfl_sync(0xffffffffu, pre, 31);
-  const long long gw = (long long)blockIdx.x * TTQ_WARPS + warp;
+  // fibers dealt round-robin over the CTAs first (an even share per CTA and SM)
+  const long long gw = (long long)warp * gridDim.x + blockIdx.x;
   const long long nw = (long long)gridDim.x * TTQ_WARPS;
   double vmax = 0.0;
   int bad = 0;
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
 // (r_k x r_k), one CTA per interface.  G_k only grows by bordering: the pivot
 // interface k accepted in the previous sweep appends the last row (its new
 // element of I<=k) and the last column (its new element of I>k), and nothing
-// else changes.  The stored factors are then updated in O(r^2): r - 1 Givens
+// else changes.  The stored factors are then updated in O(r^2): r - 1 plane
 // rotations fold the new row into R (Q gains a row and a column), and the new
 // column of R is Q'^T times the new column of G.  A full Householder QR
 // (O(r^3), LAPACK dgeqr2/dorg2r conventions) runs when no factors are stored
@@ -559,6 +562,8 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
 
 __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   if (st->stop) return;
   extern __shared__ double sm[];
@@ -716,6 +721,8 @@ __device__ void contract_finish(const Dev &D, State *st, dd v, int final_dd) {
 
 __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   if (st->stop && !final_dd) return;
   if (final_dd && (!D.prec || st->nonfinite || st->singular)) return;
@@ -932,6 +939,8 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
 // for the QR update of the pivot's row.
 __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   const int k = blockIdx.x + 1;
   if (k > D.d - 1) return;
@@ -1044,6 +1053,8 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
 #define TTQ_SPW (32 / TTQ_SG)
 __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   const int k = blockIdx.y + 1;
   if (!iface_searchable(D, st, k)) return;
@@ -1173,6 +1184,8 @@ __device__ __forceinline__ ItemMap item_map(int cnt) {
 // items; pass 1 of the argmax per interface (pass 2 in k_solve).
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   if (st->stop || !st->search) return;
   __shared__ RookSmem sh;
@@ -1282,6 +1295,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
 // searching interface, items (interface, beta, node chunk); pass 1 of the argmax.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   if (st->stop || !st->search) return;
   __shared__ RookSmem sh;
@@ -1388,6 +1403,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
 // the run is not over, never past max_sweeps (every path reaches the end).
 __global__ void k_update(Dev *const *Dps, cudaGraphConditionalHandle h, int use_cond) {
   const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
   State *st = D.st;
   const int d = D.d, lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
   __shared__ int rold[TTQ_MAXD + 1];
@@ -1461,6 +1478,8 @@ __global__ void k_begin(Dev *const *Dps, int sweep, int rules, int search) {
 // instance of the batch is still running (bounded by the largest max_sweeps).
 __global__ void k_batch_cond(Dev *const *Dps, int count, int max_sweeps, unsigned *guard,
                              cudaGraphConditionalHandle h) {
+  pdl_wait();
+  pdl_release();
   int running = 0;
   for (int q = threadIdx.x; q < count; q += blockDim.x) running |= !Dps[q]->st->stop;
   running = __syncthreads_or(running);
