@@ -163,6 +163,24 @@ __device__ __forceinline__ void warp_fwd_subst(const double *S, const double *l,
   }
 }
 
+// Node chunks of a mode for the rook steps: the ceil(N/32) rows of 32 nodes split
+// as evenly as possible into nch = ceil(rows/4) chunks of at most 4 rows, so no
+// chunk is a nearly empty one that still costs full warp instructions.
+struct NodeChunks {
+  int nch, base, extra;
+};
+__device__ __forceinline__ NodeChunks node_chunks(int N) {
+  const int rows = (N + 31) >> 5, nch = (rows + 3) >> 2;
+  return {nch, rows / nch, rows % nch};
+}
+// nodes [i0, i1) of chunk ch, in nq rows of 32
+__device__ __forceinline__ void chunk_span(const NodeChunks &c, int ch, int N, int &i0, int &i1, int &nq) {
+  const int q0 = ch * c.base + min(ch, c.extra);
+  nq = c.base + (ch < c.extra ? 1 : 0);
+  i0 = 32 * q0;
+  i1 = min(N, 32 * (q0 + nq));
+}
+
 // core entry Y_k(alpha, i, beta)
 __device__ __forceinline__ size_t core_at(const Dev &D, int k, int alpha, int i, int beta) {
   return ((size_t)beta * D.capL[k - 1] + alpha) * D.N[k - 1] + i;
@@ -829,9 +847,9 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 // candidate index whose score lies in the tie window below the stage maximum,
 // -1 if the stage had no eligible candidate.  Clears the stage reduction.
 //   stage 0 (samples): a scan of the S sample scores.
-//   stage 1 (column step, rho = alpha N_k + i): work item w = alpha nch + ch holds
-//     the contiguous rows i in chunk ch, so the answer lies in the first item whose
-//     maximum reaches the window; one scan of its <= TTQ_CHUNK rows.
+//   stage 1 (column step, rho = alpha N_k + i): the item at slot w = alpha nch + ch
+//     holds the contiguous rows i in chunk ch, so the answer lies in the first slot
+//     whose maximum reaches the window; one scan of its <= 128 rows.
 //   stage 2 (row step, gamma = j r_{k+1} + beta): item w = beta nch + ch holds the
 //     nodes j of chunk ch; the answer has the smallest j, so it lies in the lowest
 //     chunk any qualifying item reaches; the items of that chunk are scanned.
@@ -875,7 +893,8 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   } else {
     const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
     const int rm = stage == 1 ? st->r[k - 1] : st->r[k + 1];   // rows / columns of the outer rank
-    const int nch = (Nm + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    const NodeChunks nc = node_chunks(Nm);
+    const int nch = nc.nch;
     int wmin = 0x7fffffff;                       // first qualifying item (stage 1) / its chunk (stage 2)
     for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
       const double v = D.im[k][w];
@@ -885,7 +904,8 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
     if (stage == 1) {
       if (warp == 0) {
         const int alpha = wmin / nch, ch = wmin % nch;
-        const int i0 = ch * TTQ_CHUNK, i1 = min(Nm, i0 + TTQ_CHUNK);
+        int i0, i1, nq;
+        chunk_span(nc, ch, Nm, i0, i1, nq);
         int f = 0x7fffffff;
 #pragma unroll
         for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
@@ -900,7 +920,9 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
         if (lane == 0) best_s = f;
       }
     } else {
-      const int ch = wmin, j0 = ch * TTQ_CHUNK, j1 = min(Nm, j0 + TTQ_CHUNK);
+      const int ch = wmin;
+      int j0, j1, nq;
+      chunk_span(nc, ch, Nm, j0, j1, nq);
       for (int beta = warp; beta < rm; beta += nw) {
         const double m = D.im[k][beta * nch + ch];
         if (!(m >= 0.0 && m >= thr)) continue;
@@ -1179,9 +1201,136 @@ __device__ __forceinline__ ItemMap item_map(int cnt) {
   return {pre, cnt, __shfl_sync(0xffffffffu, pre, 31)};
 }
 
+// Score of a residual for the argmax, as IEEE bits: |E| for finite E (non-negative
+// doubles order like their bit patterns), else none.  Integer operations only.
+__device__ __forceinline__ bool score_bits(double E, unsigned long long &bits) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(E) & 0x7fffffffffffffffULL;
+  bits = b;
+  return b < 0x7ff0000000000000ULL;             // finite
+}
+
+// One work item of the column step: rows rho = (alpha, i), i in [i0, i1) with
+// NQ rows of 32 nodes per lane.  E = A(rho, gamma*) - L_k(rho, :) z.
+template <int NQ>
+__device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0, int i1, int rk, const int *ms,
+                                         const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
+                                         unsigned long long &best, unsigned &nel, unsigned &nev) {
+  const int lane = lane_id(), Nk = D.N[k - 1];
+  int iq[NQ];
+  bool ok[NQ];
+  double A[NQ], acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    iq[q] = i0 + lane + 32 * q;
+    bool ex = false;
+    for (int e = 0; e < nex; ++e) ex |= (exc[e] == iq[q]);
+    ok[q] = iq[q] < i1 && !ex;
+    A[q] = ok[q] ? fiber_value(D, k - 1, ms, u, pl, iq[q]) : 0.0;
+    acc[q] = 0.0;
+  }
+  {
+    const double *Yc = D.Y[k] + core_at(D, k, alpha, 0, 0);
+    const size_t cst = (size_t)D.capL[k - 1] * Nk;
+    int c[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) c[q] = min(iq[q], Nk - 1);
+#pragma unroll 4
+    for (int b = 0; b < rk; ++b) {
+      const double zb = z[b];
+      const double *row = Yc + b * cst;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(row[c[q]], zb, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (iq[q] >= i1) continue;
+    const int rho = alpha * Nk + iq[q];
+    if (!ok[q]) { D.cs[k][rho] = -1.0; D.ce[k][rho] = 0.0; continue; }
+    const double E = A[q] - acc[q];
+    unsigned long long sb;
+    const bool fin = score_bits(E, sb);
+    D.cs[k][rho] = fin ? __longlong_as_double((long long)sb) : -1.0;
+    D.ce[k][rho] = E;
+    ++nev;
+    if (fin) { best = sb > best ? sb : best; ++nel; }
+  }
+}
+
+// One work item of the row step: columns gamma = (j, beta), j in [j0, j1).
+// E = A(rho*, gamma) - l^T R_{k+1}(:, gamma) with z = G^-T l.
+template <int NQ>
+__device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, int j1, int rk, int rn, const int *ms,
+                                         const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
+                                         unsigned long long &best, unsigned &nel, unsigned &nev) {
+  const int lane = lane_id(), Nk1 = D.N[k];
+  int jq[NQ];
+  bool ok[NQ];
+  double A[NQ], acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    jq[q] = j0 + lane + 32 * q;
+    bool ex = false;
+    for (int e = 0; e < nex; ++e) ex |= (exc[e] == jq[q]);
+    ok[q] = jq[q] < j1 && !ex;
+    A[q] = ok[q] ? fiber_value(D, k, ms, u, pl, jq[q]) : 0.0;
+    acc[q] = 0.0;
+  }
+  {
+    const double *Yr = D.Y[k + 1] + core_at(D, k + 1, 0, 0, beta);
+    int c[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) c[q] = min(jq[q], Nk1 - 1);
+#pragma unroll 4
+    for (int a = 0; a < rk; ++a) {
+      const double za = z[a];
+      const double *row = Yr + (size_t)a * Nk1;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(row[c[q]], za, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    if (jq[q] >= j1) continue;
+    const int g = jq[q] * rn + beta;
+    if (!ok[q]) { D.cs[k][g] = -1.0; D.ce[k][g] = 0.0; continue; }
+    const double E = A[q] - acc[q];
+    unsigned long long sb;
+    const bool fin = score_bits(E, sb);
+    D.cs[k][g] = fin ? __longlong_as_double((long long)sb) : -1.0;
+    D.ce[k][g] = E;
+    ++nev;
+    if (fin) { best = sb > best ? sb : best; ++nel; }
+  }
+}
+
+// warp totals of an item: evaluations, the item's maximum (stored at its slot
+// outer * nch + chunk, the order of the candidate indices) and the stage reduction
+__device__ __forceinline__ void item_publish(const Dev &D, IfaceState &I, int k, int slot, unsigned long long best,
+                                             unsigned nel, unsigned nev) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    best = ob > best ? ob : best;
+    nel += __shfl_xor_sync(0xffffffffu, nel, o);
+    nev += __shfl_xor_sync(0xffffffffu, nev, o);
+  }
+  if (lane_id() == 0) {
+    if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
+    D.im[k][slot] = nel ? __longlong_as_double((long long)best) : -1.0;
+    if (nel) {
+      atomicMax(&I.smax_bits, best);
+      atomicAdd(&I.stage_count, nel);
+    }
+  }
+}
+
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i) of every
-// searching interface; a load-balanced list of (interface, alpha, node chunk)
-// items; pass 1 of the argmax per interface (pass 2 in k_solve).
+// searching interface; a load-balanced list of (interface, node chunk, alpha)
+// items; pass 1 of the argmax per interface (pass 2 in k_solve).  Items are
+// dealt round-robin over the CTAs first, so every CTA (and SM) gets an even
+// share, and walked chunk-major, so that the first chunks of the fibers
+// (possibly one row longer than the rest) do not recur with the deal's period.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   pdl_wait();
@@ -1193,21 +1342,22 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
   int cnt = 0;
   if (lane < d - 1) {
     const IfaceState &I = st->it[lane + 1];
-    if (I.active && !I.rook_done) cnt = st->r[lane] * ((D.N[lane] + TTQ_CHUNK - 1) / TTQ_CHUNK);
+    if (I.active && !I.rook_done) cnt = st->r[lane] * node_chunks(D.N[lane]).nch;
   }
   const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface whose z sits in sh.z[warp]
-  // items dealt round-robin over the CTAs first, so every CTA (and SM) gets an even share
   for (int w = warp * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
     const int k = __ffs(ball);                  // interface (1-based)
     const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
     IfaceState &I = st->it[k];
-    const int rk = st->r[k], rn = st->r[k + 1];
+    const int rk = st->r[k], rn = st->r[k + 1], rl = st->r[k - 1];
     const int Nk = D.N[k - 1];
-    const int nch = (Nk + TTQ_CHUNK - 1) / TTQ_CHUNK;
-    const int alpha = local / nch, ch = local % nch;
+    const NodeChunks nc = node_chunks(Nk);
+    const int ch = local / rl, alpha = local % rl, slot = alpha * nc.nch + ch;
+    int i0, i1, nq;
+    chunk_span(nc, ch, Nk, i0, i1, nq);
     const int gam = I.col, j = gam / rn, beta = gam % rn;
     if (k != zk) {
       for (int b = lane; b < rk; b += 32) sh.z[warp][b] = D.zvec[k][b];
@@ -1231,68 +1381,24 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
     }
     __syncwarp();
     FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
-    const int i0 = ch * TTQ_CHUNK, i1 = min(Nk, i0 + TTQ_CHUNK);
     fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + 2 * rk + 1);
-    // each lane takes 4 nodes of the chunk at once: 4 independent loads per step
-    // of the product L_k(rho, :) z over the core
-    int iq[4];
-    bool ok[4];
-    double A[4], acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      iq[q] = i0 + lane + 32 * q;
-      bool ex = false;
-      for (int e = 0; e < nex; ++e) ex |= (sh.exc[warp][e] == iq[q]);
-      ok[q] = iq[q] < i1 && !ex;
-      A[q] = ok[q] ? fiber_value(D, k - 1, sh.ms[warp], u, sh.pl[warp], iq[q]) : 0.0;
-      acc[q] = 0.0;
-    }
-    {
-      const double *Yc = D.Y[k] + core_at(D, k, alpha, 0, 0);
-      const size_t cst = (size_t)D.capL[k - 1] * Nk;
-      const int c0 = min(iq[0], Nk - 1), c1 = min(iq[1], Nk - 1), c2 = min(iq[2], Nk - 1), c3 = min(iq[3], Nk - 1);
-#pragma unroll 4
-      for (int b = 0; b < rk; ++b) {
-        const double zb = sh.z[warp][b];
-        const double *row = Yc + b * cst;
-        acc[0] = fma(row[c0], zb, acc[0]);
-        acc[1] = fma(row[c1], zb, acc[1]);
-        acc[2] = fma(row[c2], zb, acc[2]);
-        acc[3] = fma(row[c3], zb, acc[3]);
-      }
-    }
-    double best = 0.0;
+    unsigned long long best = 0;
     unsigned nel = 0, nev = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (iq[q] >= i1) continue;
-      const int rho = alpha * Nk + iq[q];
-      if (!ok[q]) { D.cs[k][rho] = -1.0; D.ce[k][rho] = 0.0; continue; }
-      const double E = A[q] - acc[q];
-      const double sc = isfinite(E) ? fabs(E) : -1.0;
-      D.cs[k][rho] = sc;
-      D.ce[k][rho] = E;
-      ++nev;
-      if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
+    switch (nq) {
+      case 4: col_item<4>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      case 3: col_item<3>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      case 2: col_item<2>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      default: col_item<1>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-      nel += __shfl_xor_sync(0xffffffffu, nel, o);
-      nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    }
-    if (lane == 0) {
-      if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
-      D.im[k][local] = nel ? best : -1.0;
-      stage_publish(I, best, nel);
-    }
+    item_publish(D, I, k, slot, best, nel, nev);
     __syncwarp();
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
 }
 
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
-// searching interface, items (interface, beta, node chunk); pass 1 of the argmax.
+// searching interface, items (interface, node chunk, beta), walked like the
+// column step's; pass 1 of the argmax.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   pdl_wait();
@@ -1304,12 +1410,11 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
   int cnt = 0;
   if (lane < d - 1) {
     const IfaceState &I = st->it[lane + 1];
-    if (I.active && !I.rook_done) cnt = st->r[lane + 2] * ((D.N[lane + 1] + TTQ_CHUNK - 1) / TTQ_CHUNK);
+    if (I.active && !I.rook_done) cnt = st->r[lane + 2] * node_chunks(D.N[lane + 1]).nch;
   }
   const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
   int zk = 0;
-  // items dealt round-robin over the CTAs first, so every CTA (and SM) gets an even share
   for (int w = warp * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
     const int k = __ffs(ball);
@@ -1317,8 +1422,10 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
     IfaceState &I = st->it[k];
     const int rk = st->r[k], rn = st->r[k + 1];
     const int Nk = D.N[k - 1], Nk1 = D.N[k];
-    const int nch = (Nk1 + TTQ_CHUNK - 1) / TTQ_CHUNK;
-    const int beta = local / nch, ch = local % nch;
+    const NodeChunks nc = node_chunks(Nk1);
+    const int ch = local / rn, beta = local % rn, slot = beta * nc.nch + ch;
+    int j0, j1, nq;
+    chunk_span(nc, ch, Nk1, j0, j1, nq);
     const int rho = I.row, alpha = rho / Nk, i = rho % Nk;
     if (k != zk) {
       for (int b = lane; b < rk; b += 32) sh.z[warp][b] = D.zvec[k][b];
@@ -1341,58 +1448,16 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
     }
     __syncwarp();
     FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
-    const int j0 = ch * TTQ_CHUNK, j1 = min(Nk1, j0 + TTQ_CHUNK);
     fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node + 2 * rk + 1);
-    int jq[4];
-    bool ok[4];
-    double A[4], acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      jq[q] = j0 + lane + 32 * q;
-      bool ex = false;
-      for (int e = 0; e < nex; ++e) ex |= (sh.exc[warp][e] == jq[q]);
-      ok[q] = jq[q] < j1 && !ex;
-      A[q] = ok[q] ? fiber_value(D, k, sh.ms[warp], u, sh.pl[warp], jq[q]) : 0.0;
-      acc[q] = 0.0;
-    }
-    {
-      const double *Yr = D.Y[k + 1] + core_at(D, k + 1, 0, 0, beta);
-      const int c0 = min(jq[0], Nk1 - 1), c1 = min(jq[1], Nk1 - 1), c2 = min(jq[2], Nk1 - 1), c3 = min(jq[3], Nk1 - 1);
-#pragma unroll 4
-      for (int a = 0; a < rk; ++a) {
-        const double za = sh.z[warp][a];
-        const double *row = Yr + (size_t)a * Nk1;
-        acc[0] = fma(row[c0], za, acc[0]);
-        acc[1] = fma(row[c1], za, acc[1]);
-        acc[2] = fma(row[c2], za, acc[2]);
-        acc[3] = fma(row[c3], za, acc[3]);
-      }
-    }
-    double best = 0.0;
+    unsigned long long best = 0;
     unsigned nel = 0, nev = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (jq[q] >= j1) continue;
-      const int g = jq[q] * rn + beta;
-      if (!ok[q]) { D.cs[k][g] = -1.0; D.ce[k][g] = 0.0; continue; }
-      const double E = A[q] - acc[q];
-      const double sc = isfinite(E) ? fabs(E) : -1.0;
-      D.cs[k][g] = sc;
-      D.ce[k][g] = E;
-      ++nev;
-      if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
+    switch (nq) {
+      case 4: row_item<4>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      case 3: row_item<3>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      case 2: row_item<2>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      default: row_item<1>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-      nel += __shfl_xor_sync(0xffffffffu, nel, o);
-      nev += __shfl_xor_sync(0xffffffffu, nev, o);
-    }
-    if (lane == 0) {
-      if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
-      D.im[k][local] = nel ? best : -1.0;
-      stage_publish(I, best, nel);
-    }
+    item_publish(D, I, k, slot, best, nel, nev);
     __syncwarp();
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
