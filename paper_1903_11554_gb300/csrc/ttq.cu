@@ -307,6 +307,14 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
   D.constant = family_constant(p);
   D.uniformT = uniform_pair_table(p, hx) ? 1 : 0;
   D.sblocks = L.sblocks; D.cblocks = L.cblocks; D.rblocks = L.rblocks;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      D.sms = sms;
+    else
+      D.sms = 0;
+    cudaGetLastError();
+  }
   D.q_in_smem = q_in_smem;
   int off = 0;
   for (int k = 0; k < d; ++k) { D.N[k] = p->nodes_per_mode[k]; D.off[k] = off; off += D.N[k]; }
@@ -568,8 +576,9 @@ static void enqueue_sweep(ttq_plan *P) {
   } else {
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
+  // the samples stage ends, per interface, in its last CTA (the best sample and
+  // the first column solve); each rook step is followed by the decisions kernel
   timed(P, KT_SAMPLES, [&] { launch_k(P, k_samples, dim3(P->sblocks, ni, nb), W, P->samples_smem, s, dv); });
-  timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 0); });
   for (int q = 0; q < P->rook_max; ++q) {
     timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
     timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 1); });

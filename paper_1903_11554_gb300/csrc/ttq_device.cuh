@@ -46,7 +46,7 @@ struct IfaceState {
   unsigned long long smax_bits;   // max score of the running stage's candidates (IEEE bits, >= 0)
   unsigned int stage_count;       // eligible candidates of the running stage
   int prow, prank;                // pvec holds R^-T L_k(prow, :)^T for the rank-prank factors (-1: none)
-  int pad;
+  unsigned items_done;            // work items of the running stage completed so far
 };
 
 struct State {
@@ -79,6 +79,7 @@ struct Dev {
   int d, family, form, n, cap, rook_max, init_samples, conv_window, max_sweeps, prec;
   int uniformT;             // 1: D in R^n on one shared uniform grid -> pair table T
   int sblocks, cblocks, rblocks;   // CTAs: per interface (samples), per instance (column / row)
+  int sms;                  // SMs of the device (placement of the item deals)
   int q_in_smem;            // the sample kernel stages Q_k in shared memory too (cap <= 96)
   double tol, pivot_tol, constant;
   unsigned long long seed;
@@ -205,6 +206,18 @@ __device__ __forceinline__ int draw_index(unsigned long long seed, unsigned long
   unsigned long long s2 = sm_out(s1, stream + 1);
   unsigned long long v = sm_out(s2, counter + 1);
   return (int)__umul64hi(v, M);
+}
+
+// Slot of a warp in a round-robin deal of work items over a grid that fills the
+// device's resident CTA slots (CTA c on SM c mod sms in the first wave).  Items
+// w = slot * gridDim.x + blockIdx.x; with `per` items per CTA the CTAs sharing an
+// SM rotate their slots by per each, so their items continue one deal over the
+// SM's four schedulers (FP64 issue is per scheduler) instead of all starting at
+// warp 0.
+__device__ __forceinline__ int deal_slot(int warp, int sms, long long total) {
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const int rot = (int)(((long long)(blockIdx.x / (sms > 0 ? sms : gridDim.x)) * per) & 7);
+  return (warp - rot) & 7;
 }
 
 // Programmatic dependent launch: pdl_wait blocks until the preceding kernel of

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
   }
   const int total = __shfl_sync(0xffffffffu, pre, 31);
   // fibers dealt round-robin over the CTAs first (an even share per CTA and SM)
-  const long long gw = (long long)warp * gridDim.x + blockIdx.x;
+  const long long gw = (long long)deal_slot(warp, D.sms, total) * gridDim.x + blockIdx.x;
   const long long nw = (long long)gridDim.x * TTQ_WARPS;
   double vmax = 0.0;
   int bad = 0;
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (threadIdx.x == 0) {
     IfaceState &I = st->it[k];
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
-    I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0;
+    I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0; I.items_done = 0;
   }
   if (have == r) {
     if (threadIdx.x == 0) st->it[k].prank = -1;
@@ -862,8 +862,8 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   IfaceState &I = st->it[k];
   const int lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
   if (threadIdx.x == 0) {
-    smax_s = __longlong_as_double((long long)I.smax_bits);
-    n_s = I.stage_count;
+    smax_s = __longlong_as_double((long long)__ldcg(&I.smax_bits));
+    n_s = __ldcg(&I.stage_count);
     best_s = 0x7fffffff;
   }
   __syncthreads();
@@ -886,7 +886,7 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   int first = 0x7fffffff;
   if (stage == 0) {
     for (int t = threadIdx.x; t < D.S[k]; t += blockDim.x) {
-      const double v = D.cs[k][t];
+      const double v = __ldcg(D.cs[k] + t);
       if (v >= 0.0 && v >= thr) first = min(first, t);
     }
     first = block_min(first);
@@ -897,7 +897,7 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
     const int nch = nc.nch;
     int wmin = 0x7fffffff;                       // first qualifying item (stage 1) / its chunk (stage 2)
     for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
-      const double v = D.im[k][w];
+      const double v = __ldcg(D.im[k] + w);
       if (v >= 0.0 && v >= thr) wmin = min(wmin, stage == 1 ? w : w % nch);
     }
     wmin = block_min(wmin);
@@ -911,7 +911,7 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
         for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
           const int i = i0 + lane + 32 * q;
           if (i < i1) {
-            const double v = D.cs[k][alpha * Nm + i];
+            const double v = __ldcg(D.cs[k] + alpha * Nm + i);
             if (v >= 0.0 && v >= thr) f = min(f, alpha * Nm + i);
           }
         }
@@ -924,14 +924,14 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
       int j0, j1, nq;
       chunk_span(nc, ch, Nm, j0, j1, nq);
       for (int beta = warp; beta < rm; beta += nw) {
-        const double m = D.im[k][beta * nch + ch];
+        const double m = __ldcg(D.im[k] + beta * nch + ch);
         if (!(m >= 0.0 && m >= thr)) continue;
         int f = 0x7fffffff;
 #pragma unroll
         for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
           const int j = j0 + lane + 32 * q;
           if (j < j1) {
-            const double v = D.cs[k][j * rm + beta];
+            const double v = __ldcg(D.cs[k] + j * rm + beta);
             if (v >= 0.0 && v >= thr) f = min(f, j * rm + beta);
           }
         }
@@ -943,14 +943,19 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
     __syncthreads();
     first = best_s;
   }
-  *e_out = D.ce[k][first];
+  *e_out = __ldcg(D.ce[k] + first);
   return first;
 }
 
-// Decisions of Alg. 2 between its search stages, one CTA per interface: the
-// argmax of the stage just run (pass 2), the interface's search state, and the
-// solve the next stage needs.  R_k, Q_k and 1/R_jj are copied to shared memory
-// asynchronously from the start, under the argmax.
+// Scratch of the decisions between search stages (one CTA)
+struct SolveSmem {
+  double v[TTQ_MAXR], t[TTQ_MAXR], ri[TTQ_MAXR], part[4 * TTQ_MAXR];
+  int is_last;
+};
+
+// Decisions of Alg. 2 after a search stage for interface k, by one CTA after the
+// stage's last work item of k: the argmax of the stage (pass 2),
+// the interface's search state, and the solve the next stage needs.
 //   mode 0, after the random samples: (rho*, gamma*) of the best sample; column
 //           solve z = G^-1 y, y = R_{k+1}(:, gamma*) = Y_{k+1}(:, j, beta).
 //   mode 1, after a column step: rho* = argmax over E(:, gamma*); row solve
@@ -958,25 +963,24 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
 //   mode 2, after a row step: gamma_new = argmax over E(rho*, :); the rook test
 //           (Eq. 2) or the round limit ends the search, else the next column solve.
 // The solve's result goes to zvec[k]; the row solve also keeps R^-T l in pvec[k]
-// for the QR update of the pivot's row.
-__global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
-  const Dev &D = *Dps[blockIdx.z];
-  pdl_wait();
-  pdl_release();
+// for the QR update of the pivot's row.  Fs: the scaled triangle the solve needs
+// (R D^-1 column-major for modes 0 and 2, D^-1 R row-major for mode 1) and Qs
+// (Q row-major / column-major), both compact with leading dimension r, when the
+// caller has them in shared memory; nullptr reads them from global memory.
+// ri: 1/R_jj in shared memory, or nullptr.
+__device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, const double *Qs, const double *ri_s,
+                             SolveSmem &sc, bool staging_in_flight = false) {
   State *st = D.st;
-  const int k = blockIdx.x + 1;
-  if (k > D.d - 1) return;
-  if (st->stop || !st->search) return;
   IfaceState &I = st->it[k];
-  if (mode != 0 && (!I.active || I.rook_done)) return;
-  extern __shared__ double sm[];
-  __shared__ double v[TTQ_MAXR], t[TTQ_MAXR], ri[TTQ_MAXR], part[4 * TTQ_MAXR];
   const int r = st->r[k], ld = D.cap, tid = threadIdx.x, nt = blockDim.x;
-  double *Rs = sm;
-  double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
-  if (mode != 1) stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], r, ld);   // R D^-1 col-major, Q row-major
-  else stage_compact_async(Rs, D.Sr[k], Qs, D.Qc[k], r, ld);             // D^-1 R row-major, Q col-major
-  for (int b = tid; b < r; b += nt) cp_async8(ri + b, D.rinv[k] + b);
+  double *v = sc.v, *t = sc.t;
+  const double *ri = ri_s;
+  if (!ri) {
+    for (int b = tid; b < r; b += nt) sc.ri[b] = D.rinv[k][b];
+    ri = sc.ri;
+  }
+  const double *F = Fs ? Fs : (mode == 1 ? D.Sr[k] : D.Cc[k]);
+  const int fld = Fs ? r : ld;
   double e;
   int col = -1, row = -1;
   if (mode == 0) {
@@ -1015,27 +1019,52 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
     const int Nk = D.N[k - 1], alpha = row / Nk, i0 = row % Nk;
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
   }
-  cp_async_wait_all();
+  if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
   if (colsolve) {
-    // t = Q^T y (Q row-major: Q[b][i] at Qs[b r + i]), then R z = t
-    if (Qs) cta_gemv(Qs, 1, r, v, r, part, t);
-    else cta_gemv(D.Qr[k], 1, ld, v, r, part, t);
-    if (warp_id() == 0) warp_back_subst(Rs, t, v, r, r);
+    // t = Q^T y (Q row-major: Q[b][i] at Q[b ld + i]), then R z = t
+    if (Qs) cta_gemv(Qs, 1, r, v, r, sc.part, t);
+    else cta_gemv(D.Qr[k], 1, ld, v, r, sc.part, t);
+    if (warp_id() == 0) warp_back_subst(F, t, v, r, fld);
     __syncthreads();
     for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b] * ri[b];
   } else if (rowsolve) {
-    // R^T t = l, then b = Q t (Q column-major: Q[i][c] at Qs[i + c r])
-    if (warp_id() == 0) warp_fwd_subst(Rs, v, t, r, r);
+    // R^T t = l, then b = Q t (Q column-major: Q[i][c] at Q[i + c ld])
+    if (warp_id() == 0) warp_fwd_subst(F, v, t, r, fld);
     __syncthreads();
     for (int b = tid; b < r; b += nt) t[b] *= ri[b];
     __syncthreads();
-    if (Qs) cta_gemv(Qs, 1, r, t, r, part, v);
-    else cta_gemv(D.Qc[k], 1, ld, t, r, part, v);
+    if (Qs) cta_gemv(Qs, 1, r, t, r, sc.part, v);
+    else cta_gemv(D.Qc[k], 1, ld, t, r, sc.part, v);
     for (int b = tid; b < r; b += nt) { D.zvec[k][b] = v[b]; D.pvec[k][b] = t[b]; }
     if (tid == 0) { I.prow = row; I.prank = r; }
   }
   if ((colsolve || rowsolve) && tid == 0) atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r));
+  __syncthreads();
+}
+
+// The decisions after a rook step (modes 1 and 2 of stage_finish), one CTA per
+// interface: the factors are copied to shared memory asynchronously from the
+// start, under the argmax.
+__global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
+  const Dev &D = *Dps[blockIdx.z];
+  pdl_wait();
+  pdl_release();
+  State *st = D.st;
+  const int k = blockIdx.x + 1;
+  if (k > D.d - 1) return;
+  if (st->stop || !st->search) return;
+  IfaceState &I = st->it[k];
+  if (!I.active || I.rook_done) return;
+  extern __shared__ double sm[];
+  __shared__ SolveSmem sc;
+  const int r = st->r[k], ld = D.cap;
+  double *Fs = sm;
+  double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
+  if (mode == 1) stage_compact_async(Fs, D.Sr[k], Qs, D.Qc[k], r, ld);   // D^-1 R row-major, Q col-major
+  else stage_compact_async(Fs, D.Cc[k], Qs, D.Qr[k], r, ld);             // R D^-1 col-major, Q row-major
+  for (int b = threadIdx.x; b < r; b += blockDim.x) cp_async8(sc.ri + b, D.rinv[k] + b);
+  stage_finish(D, k, mode, Fs, Qs, sc.ri, sc, true);
 }
 
 // per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
@@ -1083,6 +1112,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
   __shared__ int mx[TTQ_WARPS][TTQ_MAXD][TTQ_SPW];   // node indices of the warp's points
   __shared__ int rset[TTQ_MAXR], gset[TTQ_MAXR];      // cross rows / columns (excluded)
   __shared__ double ri[TTQ_MAXR];
+  __shared__ SolveSmem sc;
   extern __shared__ double fac[];
   const int lane = lane_id(), warp = warp_id(), d = D.d;
   const int g = lane / TTQ_SG, gl = lane % TTQ_SG;
@@ -1183,6 +1213,17 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
     if (fl) atomicAdd(&st->flops[3], fl);
     stage_publish(st->it[k], best, nel);
   }
+  // the last CTA of the interface takes the best sample and the first column solve
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sc.is_last = (atomicAdd(&st->it[k].items_done, 1u) == gridDim.x - 1) ? 1 : 0;
+    if (sc.is_last) st->it[k].items_done = 0;
+  }
+  __syncthreads();
+  if (!sc.is_last) return;
+  __threadfence();
+  stage_finish(D, k, 0, Rs, Qs, ri, sc);
 }
 
 // Work list of a rook step over every interface of the instance: lane k-1
@@ -1347,7 +1388,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
   const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface whose z sits in sh.z[warp]
-  for (int w = warp * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
+  for (int w = deal_slot(warp, D.sms, im.total) * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
     const int k = __ffs(ball);                  // interface (1-based)
     const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
@@ -1415,7 +1456,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps)
   const ItemMap im = item_map(cnt);
   unsigned long long fl = 0;
   int zk = 0;
-  for (int w = warp * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
+  for (int w = deal_slot(warp, D.sms, im.total) * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
     const int k = __ffs(ball);
     const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
