@@ -1242,6 +1242,17 @@ __device__ __forceinline__ ItemMap item_map(int cnt) {
   return {pre, cnt, __shfl_sync(0xffffffffu, pre, 31)};
 }
 
+// Rook kernels: resident CTAs per SM (registers for the loads in flight) and the
+// unroll of the product over the rank, which sets how many L_k rows a warp has
+// requested ahead of its multiply-adds
+#ifndef TTQ_ROOK_CTAS
+#define TTQ_ROOK_CTAS 2
+#endif
+#ifndef TTQ_ROOK_UNROLL
+#define TTQ_ROOK_UNROLL 8
+#endif
+constexpr int kRookUnroll = TTQ_ROOK_UNROLL;
+
 // Score of a residual for the argmax, as IEEE bits: |E| for finite E (non-negative
 // doubles order like their bit patterns), else none.  Integer operations only.
 __device__ __forceinline__ bool score_bits(double E, unsigned long long &bits) {
@@ -1275,7 +1286,7 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
     int c[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) c[q] = min(iq[q], Nk - 1);
-#pragma unroll 4
+#pragma unroll kRookUnroll
     for (int b = 0; b < rk; ++b) {
       const double zb = z[b];
       const double *row = Yc + b * cst;
@@ -1322,7 +1333,7 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, 
     int c[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) c[q] = min(jq[q], Nk1 - 1);
-#pragma unroll 4
+#pragma unroll kRookUnroll
     for (int a = 0; a < rk; ++a) {
       const double za = z[a];
       const double *row = Yr + (size_t)a * Nk1;
@@ -1372,7 +1383,7 @@ __device__ __forceinline__ void item_publish(const Dev &D, IfaceState &I, int k,
 // dealt round-robin over the CTAs first, so every CTA (and SM) gets an even
 // share, and walked chunk-major, so that the first chunks of the fibers
 // (possibly one row longer than the rest) do not recur with the deal's period.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   pdl_wait();
   pdl_release();
@@ -1440,7 +1451,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_col(Dev *const *Dps)
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
 // searching interface, items (interface, node chunk, beta), walked like the
 // column step's; pass 1 of the argmax.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 3) k_rook_row(Dev *const *Dps) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   pdl_wait();
   pdl_release();
