@@ -240,8 +240,9 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     nc = nc > nrow ? nc : nrow;
     L->cs[k] = b.take(nc * 8);
     L->ce[k] = b.take(nc * 8);
-    const size_t nchk = (p->nodes_per_mode[k - 1] + TTQ_CHUNK - 1) / TTQ_CHUNK;
-    const size_t nchk1 = (p->nodes_per_mode[k] + TTQ_CHUNK - 1) / TTQ_CHUNK;
+    // per-item maxima of a rook step: up to one item per row of 32 nodes
+    const size_t nchk = (p->nodes_per_mode[k - 1] + 31) / 32;
+    const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
     L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);
   }
   const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;

@@ -164,13 +164,14 @@ __device__ __forceinline__ void warp_fwd_subst(const double *S, const double *l,
 }
 
 // Node chunks of a mode for the rook steps: the ceil(N/32) rows of 32 nodes split
-// as evenly as possible into nch = ceil(rows/4) chunks of at most 4 rows, so no
-// chunk is a nearly empty one that still costs full warp instructions.
+// as evenly as possible into nch = ceil(rows / R) chunks of at most R rows (R in
+// 1, 2, 4), so no chunk is a nearly empty one that still costs full warp
+// instructions.
 struct NodeChunks {
   int nch, base, extra;
 };
-__device__ __forceinline__ NodeChunks node_chunks(int N) {
-  const int rows = (N + 31) >> 5, nch = (rows + 3) >> 2;
+__device__ __forceinline__ NodeChunks node_chunks(int N, int R) {
+  const int rows = (N + 31) >> 5, nch = (rows + R - 1) / R;
   return {nch, rows / nch, rows % nch};
 }
 // nodes [i0, i1) of chunk ch, in nq rows of 32
@@ -179,6 +180,24 @@ __device__ __forceinline__ void chunk_span(const NodeChunks &c, int ch, int N, i
   nq = c.base + (ch < c.extra ? 1 : 0);
   i0 = 32 * q0;
   i1 = min(N, 32 * (q0 + nq));
+}
+
+// Rows per work item of a rook step (the same in every CTA): the smallest of 1,
+// 2, 4 whose items all fit in one wave of the grid's warps.  An item's latency is
+// its FP64 instruction count (each takes its scheduler's FP64 unit for a fixed
+// time), so small items finish a low-rank step early, while full-rank steps use
+// 4-row items to spread the fibers' shared setup.  outer: lane k-1 holds
+// interface k's outer rank (0 when the interface does not search), Nl its nodes.
+__device__ __forceinline__ int rows_per_item(int outer, int Nl) {
+  const long long warps = (long long)gridDim.x * TTQ_WARPS;
+  int R = 1;
+  for (; R < 4; R *= 2) {
+    long long items = outer ? (long long)outer * node_chunks(Nl, R).nch : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) items += __shfl_xor_sync(0xffffffffu, items, o);
+    if (items <= warps) break;
+  }
+  return R;
 }
 
 // core entry Y_k(alpha, i, beta)
@@ -893,7 +912,7 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   } else {
     const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
     const int rm = stage == 1 ? st->r[k - 1] : st->r[k + 1];   // rows / columns of the outer rank
-    const NodeChunks nc = node_chunks(Nm);
+    const NodeChunks nc = node_chunks(Nm, st->stage_rows);
     const int nch = nc.nch;
     int wmin = 0x7fffffff;                       // first qualifying item (stage 1) / its chunk (stage 2)
     for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
@@ -1391,12 +1410,15 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   if (st->stop || !st->search) return;
   __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  int cnt = 0;
+  int outer = 0, Nl = 1;
   if (lane < d - 1) {
     const IfaceState &I = st->it[lane + 1];
-    if (I.active && !I.rook_done) cnt = st->r[lane] * node_chunks(D.N[lane]).nch;
+    if (I.active && !I.rook_done) outer = st->r[lane];
+    Nl = D.N[lane];
   }
-  const ItemMap im = item_map(cnt);
+  const int R = rows_per_item(outer, Nl);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->stage_rows = R;   // for the argmax that follows
+  const ItemMap im = item_map(outer ? outer * node_chunks(Nl, R).nch : 0);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface whose z sits in sh.z[warp]
   for (int w = deal_slot(warp, D.sms, im.total) * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
@@ -1406,7 +1428,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     IfaceState &I = st->it[k];
     const int rk = st->r[k], rn = st->r[k + 1], rl = st->r[k - 1];
     const int Nk = D.N[k - 1];
-    const NodeChunks nc = node_chunks(Nk);
+    const NodeChunks nc = node_chunks(Nk, R);
     const int ch = local / rl, alpha = local % rl, slot = alpha * nc.nch + ch;
     int i0, i1, nq;
     chunk_span(nc, ch, Nk, i0, i1, nq);
@@ -1459,12 +1481,15 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   if (st->stop || !st->search) return;
   __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  int cnt = 0;
+  int outer = 0, Nl = 1;
   if (lane < d - 1) {
     const IfaceState &I = st->it[lane + 1];
-    if (I.active && !I.rook_done) cnt = st->r[lane + 2] * node_chunks(D.N[lane + 1]).nch;
+    if (I.active && !I.rook_done) outer = st->r[lane + 2];
+    Nl = D.N[lane + 1];
   }
-  const ItemMap im = item_map(cnt);
+  const int R = rows_per_item(outer, Nl);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->stage_rows = R;
+  const ItemMap im = item_map(outer ? outer * node_chunks(Nl, R).nch : 0);
   unsigned long long fl = 0;
   int zk = 0;
   for (int w = deal_slot(warp, D.sms, im.total) * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
@@ -1474,7 +1499,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     IfaceState &I = st->it[k];
     const int rk = st->r[k], rn = st->r[k + 1];
     const int Nk = D.N[k - 1], Nk1 = D.N[k];
-    const NodeChunks nc = node_chunks(Nk1);
+    const NodeChunks nc = node_chunks(Nk1, R);
     const int ch = local / rn, beta = local % rn, slot = beta * nc.nch + ch;
     int j0, j1, nq;
     chunk_span(nc, ch, Nk1, j0, j1, nq);
