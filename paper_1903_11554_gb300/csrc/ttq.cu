@@ -184,6 +184,7 @@ struct Layout {
   size_t dev, st, x, w, c, T, cbuf;
   size_t lidx[TTQ_MAXD], ridx[TTQ_MAXD], lpar[TTQ_MAXD], lnode[TTQ_MAXD], rpar[TTQ_MAXD], rnode[TTQ_MAXD];
   size_t Y[TTQ_MAXD + 1], V[TTQ_MAXD + 1], Vlo[TTQ_MAXD + 1];
+  size_t vcnt[TTQ_MAXD + 1], vcnt_all, vcnt_bytes;   // fiber row counters: one region, zeroed at creation
   size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], Cc[TTQ_MAXD], Sr[TTQ_MAXD], rinv[TTQ_MAXD],
       zvec[TTQ_MAXD], pvec[TTQ_MAXD];
   size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD];
@@ -223,6 +224,17 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     L->Y[k] = b.take((size_t)capL[k - 1] * p->nodes_per_mode[k - 1] * capL[k] * 8);
     L->V[k] = b.take((size_t)capL[k - 1] * capL[k] * 8);
     L->Vlo[k] = b.take((size_t)capL[k - 1] * capL[k] * 8);
+  }
+  {
+    size_t tot = 0;
+    for (int k = 1; k <= d; ++k) tot += (size_t)capL[k - 1] * capL[k];
+    L->vcnt_bytes = tot * 4;
+    L->vcnt_all = b.take(L->vcnt_bytes);
+    size_t off = 0;
+    for (int k = 1; k <= d; ++k) {
+      L->vcnt[k] = L->vcnt_all + off * 4;
+      off += (size_t)capL[k - 1] * capL[k];
+    }
   }
   for (int k = 1; k < d; ++k) {
     L->Qr[k] = b.take((size_t)cap * cap * 8);
@@ -337,6 +349,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
   }
   for (int k = 1; k <= d; ++k) {
     D.Y[k] = (double *)(base + L.Y[k]); D.V[k] = (double *)(base + L.V[k]); D.Vlo[k] = (double *)(base + L.Vlo[k]);
+    D.vcnt[k] = (unsigned *)(base + L.vcnt[k]);
   }
   D.st = (State *)(base + L.st);
   D.cbuf = (double *)(base + L.cbuf);
@@ -486,6 +499,7 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
     if ((e = cudaMemcpyAsync(base + Ls[q].x, hx.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(base + Ls[q].w, hw.data(), sumN * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(P->hs[q].st, 0, sizeof(State), s)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(base + Ls[q].vcnt_all, 0, Ls[q].vcnt_bytes, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(devp[q], &P->hs[q], sizeof(Dev), cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     P->h2d += (long long)(2 * sumN * 8 + sizeof(Dev));
     if (p->inputs_on_device) P->d2h += (long long)(2 * sumN * 8);
@@ -1130,11 +1144,12 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
   Dev *devp = P.dev;
   cudaStream_t s = P.stream;
   // the scratch keeps the previous call's contents: everything read before it is
-  // written (node tables, descriptor, state, reduction partials) is set here
+  // written (node tables, descriptor, state, fiber row counters) is set here
   CK(set_smem_attributes(&P));
   CK(cudaMemcpyAsync(base + L.x, p->nodes, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(base + L.w, p->weights, sumN * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(P.h.st, 0, sizeof(State), s));
+  CK(cudaMemsetAsync(base + L.vcnt_all, 0, L.vcnt_bytes, s));
   CK(cudaMemcpyAsync(P.dev, &P.h, sizeof(Dev), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.devs, &devp, sizeof(Dev *), cudaMemcpyHostToDevice, s));
   k_setup<<<dim3((P.max_sum_n + 255) / 256, 1, 1), 256, 0, s>>>(P.devs);
@@ -1319,6 +1334,7 @@ static int server_admit(ttq_server *S) {
     CK(cudaMemcpyAsync(base + sl.L.x, sl.req.x.data(), sumN * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(base + sl.L.w, sl.req.w.data(), sumN * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(sl.h.st, 0, sizeof(State), s));
+    CK(cudaMemsetAsync(base + sl.L.vcnt_all, 0, sl.L.vcnt_bytes, s));
     S->active.push_back(std::move(sl));
     Slot &a = S->active.back();
     repoint(a.req);                         // vectors moved: pointers refreshed

@@ -91,6 +91,7 @@ struct Dev {
   int *lpar[TTQ_MAXD], *lnode[TTQ_MAXD], *rpar[TTQ_MAXD], *rnode[TTQ_MAXD];
   double *Y[TTQ_MAXD + 1];
   double *V[TTQ_MAXD + 1], *Vlo[TTQ_MAXD + 1];
+  unsigned *vcnt[TTQ_MAXD + 1];   // per fiber: rows evaluated in this sweep
   double *Qr[TTQ_MAXD], *Qc[TTQ_MAXD], *Rc[TTQ_MAXD], *Rr[TTQ_MAXD], *rinv[TTQ_MAXD];
   double *Cc[TTQ_MAXD], *Sr[TTQ_MAXD];   // R D^-1 column-major, D^-1 R row-major (D = diag R)
   double *zvec[TTQ_MAXD];   // per interface: G^{-1} y or G^{-T} l of the next rook step

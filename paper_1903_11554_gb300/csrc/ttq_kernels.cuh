@@ -182,16 +182,16 @@ __device__ __forceinline__ void chunk_span(const NodeChunks &c, int ch, int N, i
   i1 = min(N, 32 * (q0 + nq));
 }
 
-// Rows per work item of a rook step (the same in every CTA): the smallest of 1,
-// 2, 4 whose items all fit in one wave of the grid's warps.  An item's latency is
+// Rows per work item of a step (the same in every CTA): the smallest power of two
+// up to Rmax whose items all fit in one wave of the grid's warps.  An item's latency is
 // its FP64 instruction count (each takes its scheduler's FP64 unit for a fixed
 // time), so small items finish a low-rank step early, while full-rank steps use
 // 4-row items to spread the fibers' shared setup.  outer: lane k-1 holds
 // interface k's outer rank (0 when the interface does not search), Nl its nodes.
-__device__ __forceinline__ int rows_per_item(int outer, int Nl) {
+__device__ __forceinline__ int rows_per_item(int outer, int Nl, int Rmax = 4) {
   const long long warps = (long long)gridDim.x * TTQ_WARPS;
   int R = 1;
-  for (; R < 4; R *= 2) {
+  for (; R < Rmax; R *= 2) {
     long long items = outer ? (long long)outer * node_chunks(Nl, R).nch : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) items += __shfl_xor_sync(0xffffffffu, items, o);
@@ -289,8 +289,14 @@ __global__ void k_init(Dev *const *Dps) {
 }
 
 // Kernel (a): evaluate every core entry that is new since the previous sweep.
-// Fibers (k, alpha, beta) with alpha >= ro[k-1] or beta >= ro[k]; one warp per fiber,
-// lanes over the N_k nodes; writes Y_k and the node sums V_k(alpha, beta).
+// Fibers (k, alpha, beta) with alpha >= ro[k-1] or beta >= ro[k]; a work item is a
+// chunk of 1, 2, 4 .. rows of 32 nodes of a fiber, up to the whole fiber (one warp,
+// lanes over the nodes; the smallest rows per item whose items fit one wave of
+// the grid), so a low-rank sweep's few fibers still spread over many warps.
+// Writes Y_k; the warp that completes a fiber (an atomic count of its rows) forms
+// the node sum V_k(alpha, beta) from the written entries, lane l adding nodes
+// l, l + 32, .. and the lanes combined by the fixed butterfly -- the same order
+// whatever the chunking.
 __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   pdl_wait();
@@ -300,33 +306,38 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
   __shared__ double pl[TTQ_WARPS][TTQ_MAXPAIR];
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  // new-fiber counts per mode (lane k-1 <-> mode k), inclusive prefix over modes
-  int cnt = 0, rl = 0, rr = 0, ol = 0, orr = 0;
+  // new-fiber counts per mode (lane k-1 <-> mode k)
+  int cnt = 0, rl = 0, rr = 0, ol = 0, orr = 0, Nl = 1;
   if (lane < d) {
     rl = st->r[lane]; rr = st->r[lane + 1]; ol = st->ro[lane]; orr = st->ro[lane + 1];
     cnt = rl * rr - ol * orr;
+    Nl = D.N[lane];
   }
-  int pre = cnt;
+  const int R = rows_per_item(cnt, Nl, 32);
+  const int nchl = node_chunks(Nl, R).nch;
+  const int icnt = cnt * nchl;                   // items of mode lane+1
+  int pre = icnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     int v = __shfl_up_sync(0xffffffffu, pre, o);
     if (lane >= o) pre += v;
   }
   const int total = __shfl_sync(0xffffffffu, pre, 31);
-  // fibers dealt round-robin over the CTAs first (an even share per CTA and SM)
-  const long long gw = (long long)deal_slot(warp, D.sms, total) * gridDim.x + blockIdx.x;
   const long long nw = (long long)gridDim.x * TTQ_WARPS;
   double vmax = 0.0;
   int bad = 0;
   unsigned long long fl = 0;
-  for (long long g = gw; g < total; g += nw) {
+  for (long long g = (long long)deal_slot(warp, D.sms, total) * gridDim.x + blockIdx.x; g < total; g += nw) {
     unsigned ball = __ballot_sync(0xffffffffu, lane < d && pre > g);
     const int km1 = __ffs(ball) - 1;                 // mode k = km1 + 1
     const int k = km1 + 1;
-    const int before = __shfl_sync(0xffffffffu, pre - cnt, km1);
-    const int Rl = __shfl_sync(0xffffffffu, rl, km1), Rr = __shfl_sync(0xffffffffu, rr, km1);
+    const int before = __shfl_sync(0xffffffffu, pre - icnt, km1);
+    const int Cn = __shfl_sync(0xffffffffu, cnt, km1);
+    const int Rr = __shfl_sync(0xffffffffu, rr, km1);
     const int Ol = __shfl_sync(0xffffffffu, ol, km1), Or = __shfl_sync(0xffffffffu, orr, km1);
-    int t = (int)(g - before), alpha, beta;
+    const int local = (int)(g - before);
+    const int ch = local / Cn;                       // chunk-major walk
+    int t = local % Cn, alpha, beta;
     const int sizeA = Ol * (Rr - Or);
     if (t < sizeA) { alpha = t / (Rr - Or); beta = Or + t % (Rr - Or); }
     else { t -= sizeA; alpha = Ol + t / Rr; beta = t % Rr; }
@@ -338,26 +349,50 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
     }
     __syncwarp();
     FiberU u = fiber_setup(D, km1, ms[warp], pl[warp]);
-    const int Nk = D.N[km1];
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)Nk * (u.fl_node + (D.prec ? 20 : 1));
+    const int Nk = D.N[km1], nrows = (Nk + 31) >> 5;
+    const NodeChunks nc = node_chunks(Nk, R);
+    int i0, i1, nq;
+    chunk_span(nc, ch, Nk, i0, i1, nq);
+    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + (D.prec ? 20 : 1));
     double *Y = D.Y[k] + core_at(D, k, alpha, 0, beta);
-    double s = 0.0;
-    dd sd = {0.0, 0.0};
-    for (int i = lane; i < Nk; i += 32) {
-      double v = fiber_value(D, km1, ms[warp], u, pl[warp], i);
-      Y[i] = v;
-      if (!isfinite(v)) bad = 1;
-      vmax = fmax(vmax, fabs(v));
-      if (D.prec) sd = dd_add(sd, {v, 0.0});
-      else s += v;
+    const size_t fib = (size_t)alpha * D.capL[k] + beta;
+    for (int q = 0; q < nq; ++q) {
+      const int i = i0 + 32 * q + lane;
+      if (i < i1) {
+        const double v = fiber_value(D, km1, ms[warp], u, pl[warp], i);
+        Y[i] = v;
+        if (!isfinite(v)) bad = 1;
+        vmax = fmax(vmax, fabs(v));
+      }
     }
-    const size_t vi = (size_t)alpha * D.capL[k] + beta;
-    if (D.prec) {
-      sd = warp_sum_dd(sd);
-      if (lane == 0) { D.V[k][vi] = sd.hi; D.Vlo[k][vi] = sd.lo; }
+    // the warp that completes the fiber forms its node sum
+    int last = 0;
+    if (nq == nrows) {
+      last = 1;                                      // whole fiber in this item
     } else {
-      s = warp_sum(s);
-      if (lane == 0) { D.V[k][vi] = s; D.Vlo[k][vi] = 0.0; }
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned old = atomicAdd(D.vcnt[k] + fib, (unsigned)nq);
+        last = (old + nq == (unsigned)nrows) ? 1 : 0;
+        if (last) D.vcnt[k][fib] = 0;
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) __threadfence();
+    }
+    if (last) {
+      __syncwarp();
+      if (D.prec) {
+        dd sd = {0.0, 0.0};
+        for (int i = lane; i < Nk; i += 32) sd = dd_add(sd, {__ldcg(Y + i), 0.0});
+        sd = warp_sum_dd(sd);
+        if (lane == 0) { D.V[k][fib] = sd.hi; D.Vlo[k][fib] = sd.lo; }
+      } else {
+        double sr = 0.0;
+        for (int i = lane; i < Nk; i += 32) sr += __ldcg(Y + i);
+        sr = warp_sum(sr);
+        if (lane == 0) { D.V[k][fib] = sr; D.Vlo[k][fib] = 0.0; }
+      }
     }
     __syncwarp();
   }
