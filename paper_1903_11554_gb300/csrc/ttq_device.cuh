@@ -222,6 +222,20 @@ __device__ __forceinline__ int deal_slot(int warp, int sms, long long total) {
   return (warp - rot) & 7;
 }
 
+// The instance's descriptor copied to shared memory by the whole CTA (one
+// round of parallel loads) before anything else: it never changes during a
+// run, so the copy may overlap the previous kernel (it precedes pdl_wait), and
+// afterwards every descriptor field is a shared-memory read instead of the
+// first link of a chain of dependent global loads.
+__device__ __forceinline__ const Dev &stage_dev(Dev *const *Dps, Dev &sD) {
+  static_assert(sizeof(Dev) % 8 == 0, "descriptor copied in 8-byte words");
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(Dps[blockIdx.z]);
+  unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sD);
+  for (int i = threadIdx.x; i < (int)(sizeof(Dev) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return sD;
+}
+
 // Programmatic dependent launch: pdl_wait blocks until the preceding kernel of
 // the stream has completed and its writes are visible; pdl_release lets the
 // next kernel begin launching.  Both are no-ops for a kernel launched without
@@ -255,6 +269,13 @@ struct FiberU {
   int fl_uniform; // FP64 operations of the fiber's shared part
 };
 
+// q-th pair (a, b), a < b, of d modes in row order (integer work only)
+__device__ __forceinline__ void pair_of(int q, int d, int &a, int &b) {
+  a = 0;
+  while (q >= d - 1 - a) { q -= d - 1 - a; ++a; }
+  b = a + 1 + q;
+}
+
 // m: warp-uniform node indices (shared memory); plist: per-warp scratch of TTQ_MAXPAIR doubles
 __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m, double *plist) {
   const int lane = threadIdx.x & 31;
@@ -262,7 +283,30 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
   FiberU u;
   u.P = 1.0; u.S = 0.0; u.aL = u.bL = u.aR = u.bR = 0.0; u.npair = 0;
   double wj = 1.0;
-  if (lane < d && lane != f) wj = D.w[D.off[lane] + m[lane]];
+  const bool mine = lane < d && lane != f;
+  const int oj = mine ? D.off[lane] + m[lane] : 0;
+  if (mine) wj = D.w[oj];
+  // R^n: this lane's 2 cosh s and, for D on a uniform grid, its first pair
+  // factors are loaded with the weight, before the reductions, so the loads of
+  // the shared part overlap instead of following each other
+  double cj = 0.0, tp[3] = {1.0, 1.0, 1.0};
+  const bool rn_pairs = D.form == FORM_RN && D.family == FAM_D && D.uniformT;
+  if (D.form == FORM_RN && D.family != FAM_TEST && mine) cj = D.c[oj];
+  if (rn_pairs) {
+    const int np = d * (d - 1) / 2;
+#pragma unroll
+    for (int qq = 0; qq < 3; ++qq) {
+      const int q = lane + 32 * qq;
+      if (q < np) {
+        int a, b;
+        pair_of(q, d, a, b);
+        if (a != f && b != f) {
+          const int dm = m[a] - m[b];
+          tp[qq] = D.T[dm < 0 ? -dm : dm];
+        }
+      }
+    }
+  }
   u.W = warp_prod(wj);
   u.fl_uniform = d - 1;
   if (D.family == FAM_TEST) {
@@ -273,27 +317,34 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
     return u;
   }
   if (D.form == FORM_RN) {
-    double cj = (lane < d && lane != f) ? D.c[D.off[lane] + m[lane]] : 0.0;
     u.S = warp_sum(cj);
     u.fl_uniform += d - 1;
     u.fl_node = 5;
     if (D.family == FAM_D) {
       u.fl_node += d;
       u.fl_uniform += (d - 1) * (d - 2) / 2 * (D.uniformT ? 1 : 4);
+      // the pairs of other modes dealt over the lanes: one FP64 product per 32
+      // pairs on the warp's instruction stream instead of d - 1 on lane 0's
       double p = 1.0;
-      if (lane < d && lane != f) {
-        for (int b = lane + 1; b < d; ++b) {
-          if (b == f) continue;
-          double t2;
-          if (D.uniformT) {
-            int dm = m[lane] - m[b];
-            t2 = D.T[dm < 0 ? -dm : dm];
-          } else {
-            double t = tanh((D.x[D.off[lane] + m[lane]] - D.x[D.off[b] + m[b]]) * 0.5);
-            t2 = t * t;
-          }
-          p *= t2;
+      const int np = d * (d - 1) / 2;
+      int q0 = lane;
+      if (rn_pairs) {                         // the first three were loaded above
+        p = (tp[0] * tp[1]) * tp[2];
+        q0 = lane + 96;
+      }
+      for (int q = q0; q < np; q += 32) {
+        int a, b;
+        pair_of(q, d, a, b);
+        if (a == f || b == f) continue;
+        double t2;
+        if (D.uniformT) {
+          int dm = m[a] - m[b];
+          t2 = D.T[dm < 0 ? -dm : dm];
+        } else {
+          double t = tanh((D.x[D.off[a] + m[a]] - D.x[D.off[b] + m[b]]) * 0.5);
+          t2 = t * t;
         }
+        p *= t2;
       }
       u.P = warp_prod(p);
     }
@@ -470,6 +521,92 @@ __device__ __forceinline__ double point_value(const Dev &D, const int *m, int st
     g = g / (left * right);
   }
 #undef XP
+  return W * g;
+}
+
+// The same value, evaluated by a group of G lanes (lanes gl = 0..G-1 of an
+// aligned group, G a power of two <= 32): modes, pairs and rows of the
+// unit-cube pair product are dealt over the group and combined by butterflies
+// within it; every lane of the group returns A.  A lane's share of the FP64
+// instructions is ~1/G of a single lane's.
+template <int G>
+__device__ __forceinline__ double group_prod(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ double group_point_value(const Dev &D, const int *m, int stride, int gl) {
+  const int d = D.d;
+  double W = 1.0;
+  for (int v = gl; v < d; v += G) W *= D.w[D.off[v] + m[v * stride]];
+  W = group_prod<G>(W);
+  if (D.family == FAM_TEST) {
+    double S = 0.0;
+    for (int v = gl; v < d; v += G) S += D.x[D.off[v] + m[v * stride]];
+    S = group_sum<G>(S);
+    const double e = exp(-S / (double)d);
+    double g = 0.0;
+    for (int t = 0; t < D.n; ++t) g = (g + 1.0) * e;
+    return W * g;
+  }
+  if (D.form == FORM_RN) {
+    double s = 0.0;
+    for (int v = gl; v < d; v += G) s += D.c[D.off[v] + m[v * stride]];
+    s = group_sum<G>(s);
+    double g = 1.0 / (s * s);
+    if (D.family == FAM_D) {
+      double p = 1.0;
+      const int np = d * (d - 1) / 2;
+      for (int q = gl; q < np; q += G) {
+        int a, b;
+        pair_of(q, d, a, b);
+        const int ma = m[a * stride], mb = m[b * stride];
+        if (D.uniformT) {
+          const int dm = ma - mb;
+          p *= D.T[dm < 0 ? -dm : dm];
+        } else {
+          const double t = tanh((D.x[D.off[a] + ma] - D.x[D.off[b] + mb]) * 0.5);
+          p *= t * t;
+        }
+      }
+      g *= group_prod<G>(p);
+    }
+    return W * g;
+  }
+  const int n = D.n;
+#define XG(v) (D.x[D.off[(v) - 2] + m[((v) - 2) * stride]])
+  double g = 1.0;
+  if (D.family == FAM_D || D.family == FAM_E) {
+    // A_n: rows i of the pair product dealt over the group
+    double num = 1.0, den = 1.0;
+    for (int i = 1 + gl; i <= n - 1; i += G) {
+      double p = 1.0;
+      for (int j = i + 1; j <= n; ++j) {
+        p *= XG(j);
+        num *= 1.0 - p;
+        den *= 1.0 + p;
+      }
+    }
+    num = group_prod<G>(num);
+    den = group_prod<G>(den);
+    const double q = num / den;
+    g = q * q;
+  }
+  if (D.family == FAM_C || D.family == FAM_D) {
+    double left = 1.0, right = 1.0, p = 1.0;
+    for (int v = 2; v <= n; ++v) { p *= XG(v); left += p; }
+    p = 1.0;
+    for (int v = n; v >= 2; --v) { p *= XG(v); right += p; }
+    g = g / (left * right);
+  }
+#undef XG
   return W * g;
 }
 

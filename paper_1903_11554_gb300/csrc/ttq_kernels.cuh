@@ -298,7 +298,8 @@ __global__ void k_init(Dev *const *Dps) {
 // l, l + 32, .. and the lanes combined by the fixed butterfly -- the same order
 // whatever the chunking.
 __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -633,7 +634,8 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
 }
 
 __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -792,7 +794,8 @@ __device__ void contract_finish(const Dev &D, State *st, dd v, int final_dd) {
 }
 
 __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -1101,7 +1104,8 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
 // interface: the factors are copied to shared memory asynchronously from the
 // start, under the argmax.
 __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -1157,6 +1161,8 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
 #define TTQ_SG 8
 #define TTQ_SPW (32 / TTQ_SG)
 __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
+  // descriptor read in place: its shared-memory copy would cost the kernel its
+  // second resident CTA per SM (R, Q and the group vectors fill the rest)
   const Dev &D = *Dps[blockIdx.z];
   pdl_wait();
   pdl_release();
@@ -1191,9 +1197,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
   unsigned nel = 0, nev = 0;
   unsigned long long fl = 0;
   for (int base = (blockIdx.x * TTQ_WARPS + warp) * TTQ_SPW; base < S; base += gridDim.x * TTQ_WARPS * TTQ_SPW) {
-    // one lane per sample: draw, exclusion test, A at the point
+    // one lane per sample: draw and exclusion test
     int rho = 0, gam = 0, ok = 0;
-    double A = 0.0;
     if (lane < TTQ_SPW && base + lane < S) {
       const int tt = base + lane;
       rho = draw_index(D.seed, sid, 2ULL * tt, (unsigned long long)M);
@@ -1205,24 +1210,28 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
         D.ce[k][tt] = 0.0;
       } else {
         ok = 1;
-        const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
-        for (int v = 0; v < d; ++v) {
-          int mv;
-          if (v < k - 1) mv = D.lidx[k - 1][alpha * d + v];
-          else if (v == k - 1) mv = i;
-          else if (v == k) mv = j;
-          else mv = D.ridx[k + 1][beta * d + v];
-          mx[warp][v][lane] = mv;
-        }
-        A = point_value(D, &mx[warp][0][lane], TTQ_SPW);
       }
     }
-    // group g takes sample base + g
+    // group g takes sample base + g: its node indices, then A at the point
     rho = __shfl_sync(0xffffffffu, rho, g);
     gam = __shfl_sync(0xffffffffu, gam, g);
     ok = __shfl_sync(0xffffffffu, ok, g);
-    A = __shfl_sync(0xffffffffu, A, g);
     const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
+    // every group evaluates (full-warp shuffles inside); a group without a
+    // sample takes node 0 of every mode and its value is not used
+    for (int v = gl; v < d; v += TTQ_SG) {
+      int mv = 0;
+      if (ok) {
+        if (v < k - 1) mv = D.lidx[k - 1][alpha * d + v];
+        else if (v == k - 1) mv = i;
+        else if (v == k) mv = j;
+        else mv = D.ridx[k + 1][beta * d + v];
+      }
+      mx[warp][v][g] = mv;
+    }
+    __syncwarp();
+    double A = group_point_value<TTQ_SG>(D, &mx[warp][0][g], TTQ_SPW, gl);
+    if (!ok) A = 0.0;
     for (int b = gl; b < rk; b += TTQ_SG) y[b] = ok ? D.Y[k + 1][core_at(D, k + 1, b, j, beta)] : 0.0;
     __syncwarp();
     for (int r0 = gl; r0 < rk; r0 += TTQ_SG) {   // t = Q^T y
@@ -1438,7 +1447,8 @@ __device__ __forceinline__ void item_publish(const Dev &D, IfaceState &I, int k,
 // share, and walked chunk-major, so that the first chunks of the fibers
 // (possibly one row longer than the rest) do not recur with the deal's period.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -1467,25 +1477,36 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     const int ch = local / rl, alpha = local % rl, slot = alpha * nc.nch + ch;
     int i0, i1, nq;
     chunk_span(nc, ch, Nk, i0, i1, nq);
-    const int gam = I.col, j = gam / rn, beta = gam % rn;
-    if (k != zk) {
-      for (int b = lane; b < rk; b += 32) sh.z[warp][b] = D.zvec[k][b];
+    // the item's independent loads first (column, z, left indices, the cross's
+    // parent pointers), then what depends on the column
+    const int gam = I.col;
+    double zr[TTQ_MAXR / 32];
+    int lp[TTQ_MAXR / 32], ln[TTQ_MAXR / 32];
+    const bool newz = k != zk;
+#pragma unroll
+    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+      const int a = lane + 32 * q;
+      zr[q] = (newz && a < rk) ? D.zvec[k][a] : 0.0;
+      lp[q] = a < rk ? D.lpar[k][a] : -1;
+      ln[q] = a < rk ? D.lnode[k][a] : 0;
+    }
+    const int vl = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : 0;
+    const int j = gam / rn, beta = gam % rn;
+    const int vr = (lane > k && lane < d) ? D.ridx[k + 1][beta * d + lane] : 0;
+    if (newz) {
+#pragma unroll
+      for (int q = 0; q < TTQ_MAXR / 32; ++q)
+        if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
       zk = k;
     }
-    if (lane < d) {
-      int v = 0;
-      if (lane < k - 1) v = D.lidx[k - 1][alpha * d + lane];
-      else if (lane == k) v = j;
-      else if (lane > k) v = D.ridx[k + 1][beta * d + lane];
-      sh.ms[warp][lane] = v;
-    }
+    if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : (lane == k ? j : (lane > k ? vr : 0));
     // rows of the cross with this parent alpha: excluded nodes i
     int nex = 0;
-    for (int a0 = 0; a0 < rk; a0 += 32) {
-      int a = a0 + lane;
-      bool hit = a < rk && D.lpar[k][a] == alpha;
-      unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = D.lnode[k][a];
+#pragma unroll
+    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+      const bool hit = lp[q] == alpha;
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = ln[q];
       nex += __popc(bal);
     }
     __syncwarp();
@@ -1509,7 +1530,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
 // searching interface, items (interface, node chunk, beta), walked like the
 // column step's; pass 1 of the argmax.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -1538,24 +1560,33 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     const int ch = local / rn, beta = local % rn, slot = beta * nc.nch + ch;
     int j0, j1, nq;
     chunk_span(nc, ch, Nk1, j0, j1, nq);
-    const int rho = I.row, alpha = rho / Nk, i = rho % Nk;
-    if (k != zk) {
-      for (int b = lane; b < rk; b += 32) sh.z[warp][b] = D.zvec[k][b];
+    const int rho = I.row;
+    double zr[TTQ_MAXR / 32];
+    int rp[TTQ_MAXR / 32], rnd[TTQ_MAXR / 32];
+    const bool newz = k != zk;
+#pragma unroll
+    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+      const int b = lane + 32 * q;
+      zr[q] = (newz && b < rk) ? D.zvec[k][b] : 0.0;
+      rp[q] = b < rk ? D.rpar[k][b] : -1;
+      rnd[q] = b < rk ? D.rnode[k][b] : 0;
+    }
+    const int vr = (lane > k && lane < d) ? D.ridx[k + 1][beta * d + lane] : 0;
+    const int alpha = rho / Nk, i = rho % Nk;
+    const int vl = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : 0;
+    if (newz) {
+#pragma unroll
+      for (int q = 0; q < TTQ_MAXR / 32; ++q)
+        if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
       zk = k;
     }
-    if (lane < d) {
-      int v = 0;
-      if (lane < k - 1) v = D.lidx[k - 1][alpha * d + lane];
-      else if (lane == k - 1) v = i;
-      else if (lane > k) v = D.ridx[k + 1][beta * d + lane];
-      sh.ms[warp][lane] = v;
-    }
+    if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : (lane == k - 1 ? i : (lane > k ? vr : 0));
     int nex = 0;
-    for (int b0 = 0; b0 < rk; b0 += 32) {
-      int b = b0 + lane;
-      bool hit = b < rk && D.rpar[k][b] == beta;
-      unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = D.rnode[k][b];
+#pragma unroll
+    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+      const bool hit = rp[q] == beta;
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = rnd[q];
       nex += __popc(bal);
     }
     __syncwarp();
@@ -1579,7 +1610,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
 // Inside the whole-run graph it also sets the WHILE condition: continue while
 // the run is not over, never past max_sweeps (every path reaches the end).
 __global__ void k_update(Dev *const *Dps, cudaGraphConditionalHandle h, int use_cond) {
-  const Dev &D = *Dps[blockIdx.z];
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
   pdl_release();
   State *st = D.st;
