@@ -127,17 +127,21 @@ __device__ __forceinline__ void warp_back_subst(const double *C, const double *t
     }
   }
 }
-template <int QLO, int NQ>
-__device__ __forceinline__ void fwd_seg(const double *S, int r, int ld, int ilo, int ihi, double *vq, double *uout) {
+// Forward substitution in reversed row order: lane l, block q holds row
+// m = r - 1 - (l + 32 q), so the rows a step still updates (m > i) fill the
+// low blocks and a step touches ceil((r - 1 - i) / 32) register blocks, as in
+// the back substitution, instead of every block from i's on.
+template <int NQ>
+__device__ __forceinline__ void fwd_seg(const double *S, int r, int ld, int jhi, int jlo, double *vq, double *uout) {
   const int lane = lane_id();
-  for (int i = ilo; i <= ihi; ++i) {
-    const double ui = __shfl_sync(0xffffffffu, vq[QLO], i & 31);
-    if (lane == (i & 31)) uout[i] = ui;
+  for (int jj = jhi; jj >= jlo; --jj) {         // jj = r - 1 - i, i ascending
+    const double ui = __shfl_sync(0xffffffffu, vq[NQ - 1], jj & 31);
+    const int i = r - 1 - jj;
+    if (lane == (jj & 31)) uout[i] = ui;
+    const double *Si = S + (size_t)i * ld + (r - 1);
 #pragma unroll
-    for (int q = QLO; q < NQ; ++q) {
-      const int m = lane + 32 * q;
-      if ((q > QLO || m > i) && (q < NQ - 1 || m < r)) vq[q] = fma(-S[(size_t)i * ld + m], ui, vq[q]);
-    }
+    for (int q = 0; q < NQ; ++q)
+      if (q < NQ - 1 || lane + 32 * q < jj) vq[q] = fma(-Si[-(lane + 32 * q)], ui, vq[q]);
   }
 }
 // uout[i] = u_i after the forward substitution (t = D^-1 uout); S row-major, leading dimension ld
@@ -145,20 +149,14 @@ __device__ __forceinline__ void warp_fwd_subst(const double *S, const double *l,
   const int lane = lane_id(), nq = (r + 31) >> 5;
   double vq[TTQ_MAXR / 32];
 #pragma unroll
-  for (int q = 0; q < TTQ_MAXR / 32; ++q) vq[q] = (lane + 32 * q < r) ? l[lane + 32 * q] : 0.0;
-  for (int sg = 0; sg < nq; ++sg) {
-    const int ilo = 32 * sg, ihi = min(r, 32 * (sg + 1)) - 1;
-    switch (nq * 4 + sg) {
-      case 16: fwd_seg<0, 4>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 17: fwd_seg<1, 4>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 18: fwd_seg<2, 4>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 19: fwd_seg<3, 4>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 12: fwd_seg<0, 3>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 13: fwd_seg<1, 3>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 14: fwd_seg<2, 3>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 8: fwd_seg<0, 2>(S, r, ld, ilo, ihi, vq, uout); break;
-      case 9: fwd_seg<1, 2>(S, r, ld, ilo, ihi, vq, uout); break;
-      default: fwd_seg<0, 1>(S, r, ld, ilo, ihi, vq, uout); break;
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) vq[q] = (lane + 32 * q < r) ? l[r - 1 - (lane + 32 * q)] : 0.0;
+  for (int sg = nq; sg >= 1; --sg) {
+    const int jhi = min(r, 32 * sg) - 1, jlo = 32 * (sg - 1);
+    switch (sg) {
+      case 4: fwd_seg<4>(S, r, ld, jhi, jlo, vq, uout); break;
+      case 3: fwd_seg<3>(S, r, ld, jhi, jlo, vq, uout); break;
+      case 2: fwd_seg<2>(S, r, ld, jhi, jlo, vq, uout); break;
+      default: fwd_seg<1>(S, r, ld, jhi, jlo, vq, uout); break;
     }
   }
 }
@@ -912,95 +910,129 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 //     chunk any qualifying item reaches; the items of that chunk are scanned.
 __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   __shared__ int si[TTQ_WARPS];
-  __shared__ double smax_s;
-  __shared__ unsigned n_s;
+  __shared__ double se[TTQ_WARPS];
   __shared__ int best_s;
+  __shared__ double beste_s;
   State *st = D.st;
   IfaceState &I = st->it[k];
   const int lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) {
-    smax_s = __longlong_as_double((long long)__ldcg(&I.smax_bits));
-    n_s = __ldcg(&I.stage_count);
-    best_s = 0x7fffffff;
-  }
-  __syncthreads();
-  const double smax = smax_s;
-  const unsigned n = n_s;
+  // every thread reads the stage's maximum and count (one address each)
+  const unsigned long long mbits = __ldcg(&I.smax_bits);
+  const unsigned n = __ldcg(&I.stage_count);
+  const double scale = __longlong_as_double((long long)__ldcg(&st->scale_bits));
+  if (threadIdx.x == 0) best_s = 0x7fffffff;
+  __syncthreads();                               // all have read the reduction before it is cleared
   if (threadIdx.x == 0) { I.smax_bits = 0ULL; I.stage_count = 0; }
   if (n == 0) { *e_out = 0.0; return -1; }
-  const double scale = __longlong_as_double((long long)st->scale_bits);
+  const double smax = __longlong_as_double((long long)mbits);
   const double thr = __dadd_rn(smax, -__dadd_rn(__dmul_rn(TTQ_TIE_REL, smax), __dmul_rn(TTQ_TIE_ABS, scale)));
-  auto block_min = [&](int v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if (lane == 0) si[warp] = v;
-    __syncthreads();
-    v = si[0];
-    for (int w = 1; w < nw; ++w) v = min(v, si[w]);
-    return v;
-  };
+  // a score qualifies if it is eligible (>= 0) and within the window (>= thr):
+  // scores are non-negative doubles or -1, so this is one signed comparison of
+  // bit patterns (integer pipe, not the FP64 unit)
+  const long long thrb = thr > 0.0 ? __double_as_longlong(thr) : 0LL;
+  const long long *csb = reinterpret_cast<const long long *>(D.cs[k]);
+  const double *ce = D.ce[k];
   int first = 0x7fffffff;
+  double efirst = 0.0;
   if (stage == 0) {
-    for (int t = threadIdx.x; t < D.S[k]; t += blockDim.x) {
-      const double v = __ldcg(D.cs[k] + t);
-      if (v >= 0.0 && v >= thr) first = min(first, t);
-    }
-    first = block_min(first);
-  } else {
-    const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
-    const int rm = stage == 1 ? st->r[k - 1] : st->r[k + 1];   // rows / columns of the outer rank
-    const NodeChunks nc = node_chunks(Nm, st->stage_rows);
-    const int nch = nc.nch;
-    int wmin = 0x7fffffff;                       // first qualifying item (stage 1) / its chunk (stage 2)
-    for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
-      const double v = __ldcg(D.im[k] + w);
-      if (v >= 0.0 && v >= thr) wmin = min(wmin, stage == 1 ? w : w % nch);
-    }
-    wmin = block_min(wmin);
-    if (stage == 1) {
-      if (warp == 0) {
-        const int alpha = wmin / nch, ch = wmin % nch;
-        int i0, i1, nq;
-        chunk_span(nc, ch, Nm, i0, i1, nq);
-        int f = 0x7fffffff;
+    // the residuals are loaded with the scores, so the chosen one is at hand
+    const int Sk = D.S[k];
+    for (int t0 = threadIdx.x; t0 < Sk; t0 += 4 * blockDim.x) {
+      long long vb[4];
+      double e[4];
 #pragma unroll
-        for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
-          const int i = i0 + lane + 32 * q;
-          if (i < i1) {
-            const double v = __ldcg(D.cs[k] + alpha * Nm + i);
-            if (v >= 0.0 && v >= thr) f = min(f, alpha * Nm + i);
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(0xffffffffu, f, o));
-        if (lane == 0) best_s = f;
+      for (int u = 0; u < 4; ++u) {           // four candidates' loads in flight
+        const int t = t0 + u * blockDim.x;
+        vb[u] = t < Sk ? __ldcg(csb + t) : -1LL;
+        e[u] = t < Sk ? __ldcg(ce + t) : 0.0;
       }
-    } else {
-      const int ch = wmin;
-      int j0, j1, nq;
-      chunk_span(nc, ch, Nm, j0, j1, nq);
-      for (int beta = warp; beta < rm; beta += nw) {
-        const double m = __ldcg(D.im[k] + beta * nch + ch);
-        if (!(m >= 0.0 && m >= thr)) continue;
-        int f = 0x7fffffff;
 #pragma unroll
-        for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
-          const int j = j0 + lane + 32 * q;
-          if (j < j1) {
-            const double v = __ldcg(D.cs[k] + j * rm + beta);
-            if (v >= 0.0 && v >= thr) f = min(f, j * rm + beta);
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(0xffffffffu, f, o));
-        if (lane == 0) atomicMin(&best_s, f);
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (vb[u] >= thrb && t < first) { first = t; efirst = e[u]; }
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int ov = __shfl_xor_sync(0xffffffffu, first, o);
+      const double oe = __shfl_xor_sync(0xffffffffu, efirst, o);
+      if (ov < first) { first = ov; efirst = oe; }
+    }
+    if (lane == 0) { si[warp] = first; se[warp] = efirst; }
     __syncthreads();
-    first = best_s;
+    first = si[0];
+    efirst = se[0];
+    for (int w = 1; w < nw; ++w)
+      if (si[w] < first) { first = si[w]; efirst = se[w]; }
+    *e_out = efirst;
+    return first;                                // n > 0: some score reaches the window
   }
-  *e_out = __ldcg(D.ce[k] + first);
+  const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
+  const int rm = stage == 1 ? st->r[k - 1] : st->r[k + 1];   // rows / columns of the outer rank
+  const NodeChunks nc = node_chunks(Nm, st->stage_rows);
+  const int nch = nc.nch;
+  const long long *imb = reinterpret_cast<const long long *>(D.im[k]);
+  int wmin = 0x7fffffff;                       // first qualifying slot (stage 1) / its chunk (stage 2)
+  for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
+    const long long vb = __ldcg(imb + w);
+    if (vb >= thrb) wmin = min(wmin, stage == 1 ? w : w % nch);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+  if (lane == 0) si[warp] = wmin;
+  __syncthreads();
+  wmin = si[0];
+  for (int w = 1; w < nw; ++w) wmin = min(wmin, si[w]);
+  if (stage == 1) {
+    if (warp == 0) {
+      const int alpha = wmin / nch, ch = wmin % nch;
+      int i0, i1, nq;
+      chunk_span(nc, ch, Nm, i0, i1, nq);
+      int f = 0x7fffffff;
+      double fe = 0.0;
+#pragma unroll
+      for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
+        const int i = i0 + lane + 32 * q;
+        if (i < i1) {
+          const int c = alpha * Nm + i;
+          const long long vb = __ldcg(csb + c);
+          const double e = __ldcg(ce + c);
+          if (vb >= thrb && c < f) { f = c; fe = e; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const int of = __shfl_xor_sync(0xffffffffu, f, o);
+        const double oe = __shfl_xor_sync(0xffffffffu, fe, o);
+        if (of < f) { f = of; fe = oe; }
+      }
+      if (lane == 0) { best_s = f; beste_s = fe; }
+    }
+  } else {
+    const int ch = wmin;
+    int j0, j1, nq;
+    chunk_span(nc, ch, Nm, j0, j1, nq);
+    for (int beta = warp; beta < rm; beta += nw) {
+      const long long mb = __ldcg(imb + beta * nch + ch);
+      if (mb < thrb) continue;
+      int f = 0x7fffffff;
+#pragma unroll
+      for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
+        const int j = j0 + lane + 32 * q;
+        if (j < j1) {
+          const int c = j * rm + beta;
+          const long long vb = __ldcg(csb + c);
+          if (vb >= thrb && c < f) f = c;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(0xffffffffu, f, o));
+      if (lane == 0) atomicMin(&best_s, f);
+    }
+  }
+  __syncthreads();
+  first = best_s;
+  *e_out = (stage == 1) ? beste_s : __ldcg(ce + first);   // stage 2: several warps compete
   return first;
 }
 
