@@ -174,6 +174,33 @@ def cpu_baseline(wl, ranks_traj, budget):
 
 # --------------------------------------------------------------------------
 
+def measure_eval_full(plan, p, flush, reps=3):
+    """Kernel (a) on every entry of the final cores: the run's final index sets
+    are set back on the plan (so every fiber counts as new) and one sweep runs
+    without pivot search; CUDA events around the evaluation launch and its
+    device FP64 counter give its achieved rate.  Best of `reps`."""
+    st = plan.get_state()
+    ranks = st["ranks"]
+    entries = sum(ranks[k - 1] * p.N[k - 1] * ranks[k] for k in range(1, p.d + 1))
+    best = None
+    for _ in range(reps):
+        plan.set_state(ranks, st["lpar"], st["lnode"], st["rpar"], st["rnode"])
+        flush.zero_()
+        plan.set_timing(True)
+        plan.kernel_times(reset=True)
+        plan.sweep(0, search=False)
+        kt = plan.kernel_times()["eval_slabs"]
+        plan.set_timing(False)
+        tf = kt["flops"] / (kt["ms"] / 1000.0) / 1e12 if kt["ms"] > 0 else 0.0
+        if best is None or kt["ms"] < best["ms"]:
+            best = {"ms": kt["ms"], "tflops": tf}
+    return {"kernel": "k_eval_slabs", "entries": entries, "ms": best["ms"],
+            "entries_per_s": entries / (best["ms"] / 1000.0), "achieved_tflops": best["tflops"],
+            "peak_tflops": FP64_PEAK_TFLOPS, "frac": best["tflops"] / FP64_PEAK_TFLOPS,
+            "note": "one launch evaluating every entry of the final D_12 cores (ranks %s), best of %d" % (
+                max(ranks), reps)}
+
+
 def measure_batched(binding, inputs, torch, count=256):
     """The 256-instance mixed batch (families C/D/E cyclic, n in 4..24, N in
     {65,129,257,513}, rank caps in {8..128}): autotuned, one warm-up run, one
@@ -406,6 +433,10 @@ def main():
                             "tflops": (v["flops"] / (v["ms"] / 1000.0) / 1e12) if v["ms"] > 0 else 0.0}
                         for k, v in kt.items() if v["launches"]}}
 
+    # ---- kernel (a) on whole cores: the final index sets set back on the plan
+    # (every fiber new), one sweep without search; the evaluation kernel alone
+    eval_full = measure_eval_full(plan, p, flush)
+
     # ---- end to end through the C ABI with host buffers
     h2d0, d2h0 = 0, 0
     torch.cuda.synchronize()
@@ -459,7 +490,8 @@ def main():
         "result": {"value": results[-1]["value"], "value_lo": results[-1]["value_lo"], "sweeps": results[-1]["sweeps"],
                    "max_rank": results[-1]["max_rank"], "status": results[-1]["status_name"],
                    "n_eval": results[-1]["n_eval"], "internal_conv": results[-1]["internal_conv"], **check},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        "roofline": roof, "eval_full_cores": eval_full, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
         **systems,
     }
     print(json.dumps(line), flush=True)

@@ -188,6 +188,20 @@ __device__ __forceinline__ dd warp_sum_dd(dd v) {
 }
 
 // ---------------------------------------------------------------------------
+// 1/x for the R^n integrands' (sum 2 cosh s)^-2, x >= 2: the hardware's
+// approximate reciprocal (PTX rcp.approx.ftz.f64) refined by two Newton-Raphson
+// steps y <- y + y (1 - x y), each of which squares the relative error, so the
+// result is within an ulp of 1/x in four multiply-adds instead of a full IEEE
+// division (FP64 instructions are the kernels' scarce resource here).
+__device__ __forceinline__ double recip_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // SplitMix64 (Steele, Lea & Flood 2014): m-th output from state s is mix(s + m*GAMMA)
 
 __device__ __forceinline__ unsigned long long sm_mix(unsigned long long z) {
@@ -261,6 +275,7 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
 
 struct FiberU {
   double W;       // prod of weights of the other modes
+  double WP;      // R^n: W times P
   double S;       // R^n: sum 2cosh s of other modes; TEST: sum of x
   double P;       // product of the pair factors among the other modes
   double aL, bL, aR, bR;   // unit-cube B_n: left/right sums as a + b * x_F
@@ -308,6 +323,7 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
     }
   }
   u.W = warp_prod(wj);
+  u.WP = u.W;
   u.fl_uniform = d - 1;
   if (D.family == FAM_TEST) {
     double xj = (lane < d && lane != f) ? D.x[D.off[lane] + m[lane]] : 0.0;
@@ -319,9 +335,9 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
   if (D.form == FORM_RN) {
     u.S = warp_sum(cj);
     u.fl_uniform += d - 1;
-    u.fl_node = 5;
+    u.fl_node = 13;                             // add, reciprocal (1 + 8), square, 2 products
     if (D.family == FAM_D) {
-      u.fl_node += d;
+      u.fl_node += d - 1;                       // the pair factors with the free mode
       u.fl_uniform += (d - 1) * (d - 2) / 2 * (D.uniformT ? 1 : 4);
       // the pairs of other modes dealt over the lanes: one FP64 product per 32
       // pairs on the warp's instruction stream instead of d - 1 on lane 0's
@@ -347,6 +363,7 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
         p *= t2;
       }
       u.P = warp_prod(p);
+      u.WP = u.W * u.P;
     }
     return u;
   }
@@ -414,10 +431,11 @@ __device__ __forceinline__ double fiber_value(const Dev &D, int f, const int *m,
     return u.W * wi * g;
   }
   if (D.form == FORM_RN) {
-    double s = u.S + D.c[o];
-    double g = 1.0 / (s * s);
+    // W P w_i prod_j T(i, m_j) / s^2 with W P the fiber's shared product
+    const double s = u.S + D.c[o];
+    const double rs = recip_nr(s);
+    double p = u.WP * wi;
     if (D.family == FAM_D) {
-      double p = u.P;
       const int d = D.d;
       if (D.uniformT) {
         for (int j = 0; j < d; ++j) {
@@ -433,9 +451,8 @@ __device__ __forceinline__ double fiber_value(const Dev &D, int f, const int *m,
           p *= t * t;
         }
       }
-      g *= p;
     }
-    return u.W * wi * g;
+    return p * (rs * rs);
   }
   const double xf = D.x[o];
   double g = 1.0;
@@ -475,7 +492,8 @@ __device__ __forceinline__ double point_value(const Dev &D, const int *m, int st
   if (D.form == FORM_RN) {
     double s = 0.0;
     for (int v = 0; v < d; ++v) s += D.c[D.off[v] + m[v * stride]];
-    double g = 1.0 / (s * s);
+    const double rs = recip_nr(s);
+    double g = rs * rs;
     if (D.family == FAM_D) {
       double p = 1.0;
       for (int a = 0; a < d; ++a) {
@@ -560,7 +578,8 @@ __device__ __forceinline__ double group_point_value(const Dev &D, const int *m, 
     double s = 0.0;
     for (int v = gl; v < d; v += G) s += D.c[D.off[v] + m[v * stride]];
     s = group_sum<G>(s);
-    double g = 1.0 / (s * s);
+    const double rs = recip_nr(s);
+    double g = rs * rs;
     if (D.family == FAM_D) {
       double p = 1.0;
       const int np = d * (d - 1) / 2;
@@ -614,7 +633,7 @@ __device__ __forceinline__ double group_point_value(const Dev &D, const int *m, 
 __device__ __forceinline__ int point_flops(const Dev &D) {
   const int d = D.d, n = D.n;
   if (D.family == FAM_TEST) return 2 * (d - 1) + 2 * n + 3;
-  if (D.form == FORM_RN) return 2 * (d - 1) + 5 + (D.family == FAM_D ? d * (d - 1) / 2 * (D.uniformT ? 1 : 4) + 1 : 0);
+  if (D.form == FORM_RN) return 2 * (d - 1) + 13 + (D.family == FAM_D ? d * (d - 1) / 2 * (D.uniformT ? 1 : 4) + 1 : 0);
   int fl = d;
   if (D.family == FAM_D || D.family == FAM_E) fl += 3 * n * (n - 1) / 2 + 2;
   if (D.family == FAM_C || D.family == FAM_D) fl += 4 * n + 2;
