@@ -427,6 +427,8 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
 static cudaError_t set_smem_attributes(ttq_plan *P) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_qr_row, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
@@ -581,7 +583,17 @@ static void enqueue_sweep(ttq_plan *P) {
   const int ni = P->max_ni, nb = P->count;
   Dev *const *dv = P->devs;
   const dim3 W(TTQ_WARPS * 32), T(256);
+  // the QR row append (old entries only) beside the evaluation of the new slabs
+  if (P->s2) {
+    cudaEventRecord(P->fork, s);
+    cudaStreamWaitEvent(P->s2, P->fork, 0);
+    timed_on(P, P->s2, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, P->s2>>>(dv); });
+    cudaEventRecord(P->join, P->s2);
+  } else {
+    timed(P, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
+  }
   timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+  if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
   timed(P, KT_QR, [&] { launch_k(P, k_qr, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
   if (P->s2) {
     cudaEventRecord(P->fork, s);

@@ -266,7 +266,7 @@ __global__ void k_init(Dev *const *Dps) {
     st->sweep = 0; st->status = ST_OK; st->stop = 0; st->nonfinite = 0; st->singular = 0;
     st->nchanges = 0; st->scale_bits = 0ULL; st->value = st->value_lo = st->prev = 0.0;
     st->stop_pending = 0; st->pending_status = 0;
-    for (int k = 0; k < TTQ_MAXD; ++k) st->qr_rank[k] = 0;
+    for (int k = 0; k < TTQ_MAXD; ++k) { st->qr_rank[k] = 0; st->qr_row[k] = 0; }
     st->conv = __longlong_as_double(0x7ff0000000000000LL);
     st->search_evals = 0; st->init_evals = D.init_samples;
     if (!(c.score > 0.0)) { st->status = ST_ERR_NONFINITE; st->stop = 1; }
@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
   if (lane == 0 && fl) atomicAdd(&st->flops[0], fl);
 }
 
-// Kernel (b): QR factors G_k = Q R of every cross matrix G_k = A(I<=k, I>k)
-// (r_k x r_k), one CTA per interface.  G_k only grows by bordering: the pivot
+// Kernel (b), second half: QR factors G_k = Q R of every cross matrix
+// G_k = A(I<=k, I>k) (r_k x r_k), one CTA per interface.  G_k only grows by bordering: the pivot
 // interface k accepted in the previous sweep appends the last row (its new
 // element of I<=k) and the last column (its new element of I>k), and nothing
 // else changes.  The stored factors are then updated in O(r^2): r - 1 plane
@@ -519,19 +519,21 @@ __device__ void qr_full(const Dev &D, int k, int r, double *sm) {
 // R_jj p_j / t_{j-1} (Gill, Golub, Murray & Saunders 1974, method C1, for the
 // update R^T R + h h^T).  p comes from the row solve of the search that found
 // the pivot when it is still at hand, else from a forward substitution.  The
-// rotations then run down every column of R and every row of Q independently;
-// the new column of R is Q'^T G(:, n) = J [Q^T G(0:n-1, n); G(n, n)].
-__device__ void qr_border(const Dev &D, int k, int r, double *sm) {
+// rotations then run down every column of R and every row of Q independently.
+// The row append needs only entries evaluated in earlier sweeps (the new row's
+// parent alpha* belongs to the old left set), so it runs beside kernel (a) on
+// the second stream: qr_border_row leaves the rotated n x n block of R in Rr and
+// Q' = [[Q, 0], [0, 1]] J_0^T .. J_{n-1}^T in Qc / Qr.  qr_border_col then
+// adds the new column of R, Q'^T G(:, n), from the new slab of the core.
+__device__ void qr_border_row(const Dev &D, int k, int r, double *sm) {
   IfaceState &I = D.st->it[k];
   const int n = r - 1, ls = r, ld = D.cap;
   double *Rs = sm;                       // r x r row-major (ld ls)
   double *h = Rs + (size_t)r * ls;       // new row of G over the old columns
-  double *cn = h + r;                    // new column of G (length r)
-  double *gc = cn + r;                   // rotation cosines
+  double *gc = h + r;                    // rotation cosines
   double *gs = gc + r;                   // rotation sines
   double *p = gs + r;                    // R^-T h
-  double *v = p + r;                     // Q^T G(0:n-1, n), then the new column of R
-  double *ri = v + r;                    // 1 / R_jj of the old factor
+  double *ri = p + r;                    // 1 / R_jj of the old factor
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
   const int anew = D.lpar[k][n], inew = D.lnode[k][n];
   const bool cached = I.prank == n && I.prow == anew * D.N[k - 1] + inew;
@@ -541,7 +543,6 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
     ri[c] = D.rinv[k][c];
     if (cached) p[c] = D.pvec[k][c];
   }
-  for (int a = tid; a < r; a += nt) cn[a] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], n)];
   __syncthreads();
   if (warp == 0) {
     if (!cached) {                         // R^T p = h, the same scaled substitution as the row solve
@@ -571,13 +572,6 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
       }
       carry += __shfl_sync(0xffffffffu, sc, 31);
     }
-  } else {
-    for (int a = tid - 32; a < n; a += nt - 32) {   // v = Q^T G(0:n-1, n), old Q
-      double acc = 0.0;
-#pragma unroll 8
-      for (int i = 0; i < n; ++i) acc = fma(D.Qr[k][i * ld + a], cn[i], acc);
-      v[a] = acc;
-    }
   }
   __syncthreads();
   if (tid < 128) {
@@ -590,18 +584,8 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
         hq = fma(-sn, rjq, c * hq);
       }
     }
-    if (tid == 0) {                        // new column of R: rotations of [v; G(n, n)]
-      double vl = cn[n];
-      for (int j = 0; j < n; ++j) {
-        const double c = gc[j], sn = gs[j], vj = v[j];
-        v[j] = fma(c, vj, sn * vl);
-        vl = fma(-sn, vj, c * vl);
-      }
-      v[n] = vl;
-    }
   } else {
-    // Q' = [[Q, 0], [0, 1]] J_0^T ... J_{n-1}^T, one row per thread, old Q read
-    // sixteen columns at a time
+    // Q' one row per thread, old Q read sixteen columns at a time
     for (int i = tid - 128; i < r; i += nt - 128) {
       double qlast = (i == n) ? 1.0 : 0.0;
       for (int j0 = 0; j0 < n; j0 += 16) {
@@ -625,10 +609,42 @@ __device__ void qr_border(const Dev &D, int k, int r, double *sm) {
     }
   }
   __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {  // the rotated block, for qr_border_col
+    const int i = e / n, j = e % n;
+    D.Rr[k][i * ld + j] = Rs[i * ls + j];
+  }
+}
+
+// second half of the bordering update: new column of R = Q'^T G(:, n)
+__device__ void qr_border_col(const Dev &D, int k, int r, double *sm, double *part) {
+  const int n = r - 1, ls = r, ld = D.cap, tid = threadIdx.x, nt = blockDim.x;
+  double *Rs = sm;                       // r x r row-major (ld ls)
+  double *cn = Rs + (size_t)r * ls;      // new column of G (length r)
+  double *v = cn + r;                    // Q'^T cn
+  stage_block(Rs, D.Rr[k], nullptr, nullptr, n, ld, ls);
+  for (int a = tid; a < r; a += nt) cn[a] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], n)];
+  __syncthreads();
+  cta_gemv(D.Qr[k], 1, ld, cn, r, part, v);   // v[a] = sum_i Q'[i][a] cn[i]
   for (int a = tid; a < r; a += nt) Rs[a * ls + n] = v[a];
   for (int j = tid; j < n; j += nt) Rs[n * ls + j] = 0.0;
   __syncthreads();
   qr_store_R(D, k, r, Rs, ls, true);
+}
+
+// Kernel (b), first half: the row append of every interface whose G_k grew by
+// one (second stream, beside kernel (a)).
+__global__ void __launch_bounds__(256) k_qr_row(Dev *const *Dps) {
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
+  State *st = D.st;
+  if (st->stop) return;
+  extern __shared__ double sm[];
+  const int k = blockIdx.x + 1;
+  if (k > D.d - 1) return;
+  const int r = st->r[k], have = st->qr_rank[k];
+  if (!(have >= 1 && have == r - 1)) return;
+  qr_border_row(D, k, r, sm);
+  if (threadIdx.x == 0) st->qr_row[k] = r;
 }
 
 __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
@@ -652,15 +668,16 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
     if (threadIdx.x == 0) st->it[k].prank = -1;
     return;
   }
-  if (have >= 1 && have == r - 1) {
-    qr_border(D, k, r, sm);
+  if (have >= 1 && have == r - 1 && st->qr_row[k] == r) {
+    __shared__ double part[4 * TTQ_MAXR];
+    qr_border_col(D, k, r, sm, part);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * r * (double)r));
   } else {
     qr_full(D, k, r, sm);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(8.0 / 3.0 * r * (double)r * r));
   }
   __syncthreads();
-  if (threadIdx.x == 0) { st->qr_rank[k] = r; st->it[k].prank = -1; }
+  if (threadIdx.x == 0) { st->qr_rank[k] = r; st->it[k].prank = -1; st->qr_row[k] = 0; }
 }
 
 // Kernel (c): contraction of the weighted cores with the inverse cross matrices
