@@ -412,6 +412,17 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
     ge = ge < 1 ? 1 : ge;
     P->grid_eval = count == 1 ? sms * occe : (int)std::min(ge, (size_t)std::max(1, (sms * occe + count - 1) / count));
+    // samples: at least enough CTAs per interface to fill the resident slots
+    // once (each CTA holds one interface's factors), so no SM runs twice the
+    // CTAs of another while others idle
+    int occs = 1;
+    const size_t cap0 = P->max_cap;
+    const size_t ssm = (((cap0 <= 96) ? 2 : 1) * cap0 * cap0 + (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap0 + 1)) * 8;
+    cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs, k_samples, TTQ_WARPS * 32, ssm) != cudaSuccess || occs < 1)
+      occs = 1;
+    const int per = (sms * occs) / std::max(1, P->max_ni * count);
+    P->sblocks = std::max(P->sblocks, per);
     cudaGetLastError();
   }
   P->rblocks = P->cblocks;

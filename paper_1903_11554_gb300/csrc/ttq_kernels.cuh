@@ -990,9 +990,19 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   const int nch = nc.nch;
   const long long *imb = reinterpret_cast<const long long *>(D.im[k]);
   int wmin = 0x7fffffff;                       // first qualifying slot (stage 1) / its chunk (stage 2)
-  for (int w = threadIdx.x; w < rm * nch; w += blockDim.x) {
-    const long long vb = __ldcg(imb + w);
-    if (vb >= thrb) wmin = min(wmin, stage == 1 ? w : w % nch);
+  const int nslot = rm * nch;
+  for (int w0 = threadIdx.x; w0 < nslot; w0 += 4 * blockDim.x) {
+    long long vb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {              // four slots' loads in flight
+      const int w = w0 + u * blockDim.x;
+      vb[u] = w < nslot ? __ldcg(imb + w) : -1LL;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (vb[u] >= thrb) wmin = min(wmin, stage == 1 ? w : w % nch);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wmin = min(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
