@@ -186,7 +186,7 @@ struct Layout {
   size_t Y[TTQ_MAXD + 1], V[TTQ_MAXD + 1], Vlo[TTQ_MAXD + 1];
   size_t vcnt[TTQ_MAXD + 1], vcnt_all, vcnt_bytes;   // fiber row counters: one region, zeroed at creation
   size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], Cc[TTQ_MAXD], Sr[TTQ_MAXD], rinv[TTQ_MAXD],
-      zvec[TTQ_MAXD], pvec[TTQ_MAXD];
+      zvec[TTQ_MAXD], pvec[TTQ_MAXD], ptab[TTQ_MAXD];
   size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD];
   size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
@@ -246,6 +246,7 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     L->rinv[k] = b.take((size_t)cap * 8);
     L->zvec[k] = b.take((size_t)cap * 8);
     L->pvec[k] = b.take((size_t)cap * 8);
+    L->ptab[k] = b.take((size_t)(p->nodes_per_mode[k - 1] > p->nodes_per_mode[k] ? p->nodes_per_mode[k - 1] : p->nodes_per_mode[k]) * 8);
     size_t nc = (size_t)samples_for(p, k);
     size_t ncol = (size_t)cap * p->nodes_per_mode[k - 1], nrow = (size_t)p->nodes_per_mode[k] * cap;
     nc = nc > ncol ? nc : ncol;
@@ -344,6 +345,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
     D.Cc[k] = (double *)(base + L.Cc[k]); D.Sr[k] = (double *)(base + L.Sr[k]);
     D.rinv[k] = (double *)(base + L.rinv[k]); D.zvec[k] = (double *)(base + L.zvec[k]);
     D.pvec[k] = (double *)(base + L.pvec[k]);
+    D.ptab[k] = (double *)(base + L.ptab[k]);
     D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
     D.im[k] = (double *)(base + L.im[k]);
   }

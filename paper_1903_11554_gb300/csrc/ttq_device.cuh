@@ -97,6 +97,7 @@ struct Dev {
   double *Cc[TTQ_MAXD], *Sr[TTQ_MAXD];   // R D^-1 column-major, D^-1 R row-major (D = diag R)
   double *zvec[TTQ_MAXD];   // per interface: G^{-1} y or G^{-T} l of the next rook step
   double *pvec[TTQ_MAXD];   // per interface: R^{-T} l of the last row solve
+  double *ptab[TTQ_MAXD];   // per interface: the next rook step's shared pair-factor product per node
   double *cbuf;             // the two contraction chains' vectors (hi, lo) x 2, cap each
   double *cs[TTQ_MAXD];     // per interface: scores |E| of the current candidates (-1: not eligible)
   double *ce[TTQ_MAXD];     // per interface: residuals E of the current candidates
@@ -418,6 +419,26 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
   }
 #undef XV
   return u;
+}
+
+// The same value for the R^n form of D on one uniform grid when the pair
+// factors of the free mode with the modes outside [jlo, jhi) are the same for
+// every fiber of the step and their product per node sits in tab (built once
+// per rook step): tab[i] * prod_{jlo <= j < jhi, j != f} T(i, m_j) replaces the
+// product over all d - 1 other modes.
+__device__ __forceinline__ double fiber_value_tab(const Dev &D, int f, const int *m, const FiberU &u,
+                                                  int i, const double *tab, int jlo, int jhi) {
+  const int o = D.off[f] + i;
+  const double wi = D.w[o];
+  const double s = u.S + D.c[o];
+  const double rs = recip_nr(s);
+  double p = u.WP * wi * tab[i];
+  for (int j = jlo; j < jhi; ++j) {
+    if (j == f) continue;
+    const int dm = i - m[j];
+    p *= D.T[dm < 0 ? -dm : dm];
+  }
+  return p * (rs * rs);
 }
 
 // value at node i of the free mode f (lane-local)

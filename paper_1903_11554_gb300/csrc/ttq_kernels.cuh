@@ -1069,6 +1069,37 @@ struct SolveSmem {
   int is_last;
 };
 
+// Whether interface k's rook steps take their shared pair factors from the
+// step's table: the R^n form of D on one uniform grid, from rank 24 on (below,
+// the solve's substitution is too short to hide building it and the rook items
+// are latency bound).  The solve and the rook kernels decide alike.
+__device__ __forceinline__ bool uses_ptab(const Dev &D, int rk) {
+  return D.family == FAM_D && D.form == FORM_RN && D.uniformT && rk >= 24;
+}
+
+// The next rook step's pair factors that every fiber of the step shares (R^n
+// form of D on one uniform grid): a column step (free mode k-1) shares the
+// modes k.. of gamma* = (j, beta), a row step (free mode k) the modes ..k-1 of
+// rho* = (alpha, i).  Built by warps 1.. of the CTA while warp 0 runs the
+// substitution; fm: the fixed node indices of those modes (shared memory).
+__device__ __forceinline__ void build_ptab(const Dev &D, int k, bool col, const int *fm, int nfm) {
+  // only warps on the other three schedulers (warp w runs on scheduler w % 4),
+  // so the FP64 unit of warp 0's substitution chain is not shared
+  const int w = warp_id(), nw = blockDim.x >> 5;
+  if ((w & 3) == 0) return;
+  const int slot = (w - 1 - w / 4) * 32 + lane_id();            // 0 .. (3/4 nw - 1) * 32 + 31
+  const int nslots = (nw - (nw + 3) / 4) * 32;
+  const int Nf = col ? D.N[k - 1] : D.N[k];
+  for (int i = slot; i < Nf; i += nslots) {
+    double p = 1.0;
+    for (int q = 0; q < nfm; ++q) {
+      const int dm = i - fm[q];
+      p *= D.T[dm < 0 ? -dm : dm];
+    }
+    D.ptab[k][i] = p;
+  }
+}
+
 // Decisions of Alg. 2 after a search stage for interface k, by one CTA after the
 // stage's last work item of k: the argmax of the stage (pass 2),
 // the interface's search state, and the solve the next stage needs.
@@ -1128,12 +1159,19 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     }
   }
   const bool colsolve = mode != 1 && col >= 0, rowsolve = mode == 1 && row >= 0;
+  const bool tab = uses_ptab(D, r) && (colsolve || rowsolve) && blockDim.x > 32;
+  __shared__ int fm[TTQ_MAXD];
+  int nfm = 0;
   if (colsolve) {
     const int rn = st->r[k + 1], j = col / rn, beta = col % rn;
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
+    nfm = D.d - k;                               // modes k .. d-1
+    if (tab && tid < nfm) fm[tid] = tid == 0 ? j : D.ridx[k + 1][beta * D.d + k + tid];
   } else if (rowsolve) {
     const int Nk = D.N[k - 1], alpha = row / Nk, i0 = row % Nk;
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
+    nfm = k;                                     // modes 0 .. k-1
+    if (tab && tid < nfm) fm[tid] = tid == k - 1 ? i0 : D.lidx[k - 1][alpha * D.d + tid];
   }
   if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
@@ -1142,11 +1180,13 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     if (Qs) cta_gemv(Qs, 1, r, v, r, sc.part, t);
     else cta_gemv(D.Qr[k], 1, ld, v, r, sc.part, t);
     if (warp_id() == 0) warp_back_subst(F, t, v, r, fld);
+    else if (tab) build_ptab(D, k, true, fm, nfm);
     __syncthreads();
     for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b] * ri[b];
   } else if (rowsolve) {
     // R^T t = l, then b = Q t (Q column-major: Q[i][c] at Q[i + c ld])
     if (warp_id() == 0) warp_fwd_subst(F, v, t, r, fld);
+    else if (tab) build_ptab(D, k, false, fm, nfm);
     __syncthreads();
     for (int b = tid; b < r; b += nt) t[b] *= ri[b];
     __syncthreads();
@@ -1155,7 +1195,9 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     for (int b = tid; b < r; b += nt) { D.zvec[k][b] = v[b]; D.pvec[k][b] = t[b]; }
     if (tid == 0) { I.prow = row; I.prank = r; }
   }
-  if ((colsolve || rowsolve) && tid == 0) atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r));
+  if ((colsolve || rowsolve) && tid == 0)
+    atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r) +
+                                 (tab ? (unsigned long long)(colsolve ? D.N[k - 1] : D.N[k]) * nfm : 0ULL));
   __syncthreads();
 }
 
@@ -1389,6 +1431,7 @@ template <int NQ>
 __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0, int i1, int rk, const int *ms,
                                          const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
                                          unsigned long long &best, unsigned &nel, unsigned &nev) {
+  const double *tab = uses_ptab(D, rk) ? D.ptab[k] : nullptr;
   const int lane = lane_id(), Nk = D.N[k - 1];
   int iq[NQ];
   bool ok[NQ];
@@ -1399,7 +1442,8 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
     bool ex = false;
     for (int e = 0; e < nex; ++e) ex |= (exc[e] == iq[q]);
     ok[q] = iq[q] < i1 && !ex;
-    A[q] = ok[q] ? fiber_value(D, k - 1, ms, u, pl, iq[q]) : 0.0;
+    A[q] = !ok[q] ? 0.0
+           : (tab ? fiber_value_tab(D, k - 1, ms, u, iq[q], tab, 0, k - 1) : fiber_value(D, k - 1, ms, u, pl, iq[q]));
     acc[q] = 0.0;
   }
   {
@@ -1437,6 +1481,7 @@ template <int NQ>
 __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, int j1, int rk, int rn, const int *ms,
                                          const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
                                          unsigned long long &best, unsigned &nel, unsigned &nev) {
+  const double *tab = uses_ptab(D, rk) ? D.ptab[k] : nullptr;
   const int lane = lane_id(), Nk1 = D.N[k];
   int jq[NQ];
   bool ok[NQ];
@@ -1447,7 +1492,7 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, 
     bool ex = false;
     for (int e = 0; e < nex; ++e) ex |= (exc[e] == jq[q]);
     ok[q] = jq[q] < j1 && !ex;
-    A[q] = ok[q] ? fiber_value(D, k, ms, u, pl, jq[q]) : 0.0;
+    A[q] = !ok[q] ? 0.0 : (tab ? fiber_value_tab(D, k, ms, u, jq[q], tab, k + 1, D.d) : fiber_value(D, k, ms, u, pl, jq[q]));
     acc[q] = 0.0;
   }
   {
@@ -1570,7 +1615,9 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     }
     __syncwarp();
     FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + 2 * rk + 1);
+    // per node: the entry (the shared right-mode factors come from the step's table), the product, the residual
+    const int tabbed = uses_ptab(D, rk) ? (d - k) - 1 : 0;
+    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node - tabbed + 2 * rk + 1);
     unsigned long long best = 0;
     unsigned nel = 0, nev = 0;
     switch (nq) {
@@ -1650,7 +1697,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     }
     __syncwarp();
     FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node + 2 * rk + 1);
+    const int tabbed = uses_ptab(D, rk) ? k - 1 : 0;
+    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node - tabbed + 2 * rk + 1);
     unsigned long long best = 0;
     unsigned nel = 0, nev = 0;
     switch (nq) {
