@@ -286,11 +286,15 @@ struct FiberU {
   int fl_uniform; // FP64 operations of the fiber's shared part
 };
 
-// q-th pair (a, b), a < b, of d modes in row order (integer work only)
+// q-th pair (a, b), a < b, of d modes in row order: the row from the
+// triangular-number inverse a = d - 2 - floor((sqrt(4 d (d-1) - 7 - 8 q) - 1) / 2)
+// (an FP32 square root of an integer below 4000, exact for every q of every
+// d <= 32), the column from the row's first index; a loop over the rows would
+// cost up to d - 1 dependent steps per pair
 __device__ __forceinline__ void pair_of(int q, int d, int &a, int &b) {
-  a = 0;
-  while (q >= d - 1 - a) { q -= d - 1 - a; ++a; }
-  b = a + 1 + q;
+  const float sq = sqrtf((float)(4 * d * (d - 1) - 7 - 8 * q));
+  a = d - 2 - (int)floorf((sq - 1.0f) * 0.5f);
+  b = q + a + 1 - d * (d - 1) / 2 + (d - a) * (d - a - 1) / 2;
 }
 
 // m: warp-uniform node indices (shared memory); plist: per-warp scratch of TTQ_MAXPAIR doubles
