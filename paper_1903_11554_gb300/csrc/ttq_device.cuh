@@ -588,8 +588,21 @@ __device__ __forceinline__ double group_sum(double v) {
 template <int G>
 __device__ __forceinline__ double group_point_value(const Dev &D, const int *m, int stride, int gl) {
   const int d = D.d;
+  // a lane's modes (at most 32 / G of them): their weights and, for R^n, 2 cosh s
+  // loaded together before any product, so the loads overlap
+  constexpr int MV = (TTQ_MAXD + G - 1) / G;
+  double wv[MV], cv[MV];
+  const bool rn = D.form == FORM_RN && D.family != FAM_TEST;
+#pragma unroll
+  for (int u = 0; u < MV; ++u) {
+    const int v = gl + u * G;
+    const int o = v < d ? D.off[v] + m[v * stride] : 0;
+    wv[u] = v < d ? D.w[o] : 1.0;
+    cv[u] = (v < d && rn) ? D.c[o] : 0.0;
+  }
   double W = 1.0;
-  for (int v = gl; v < d; v += G) W *= D.w[D.off[v] + m[v * stride]];
+#pragma unroll
+  for (int u = 0; u < MV; ++u) W *= wv[u];
   W = group_prod<G>(W);
   if (D.family == FAM_TEST) {
     double S = 0.0;
@@ -602,21 +615,35 @@ __device__ __forceinline__ double group_point_value(const Dev &D, const int *m, 
   }
   if (D.form == FORM_RN) {
     double s = 0.0;
-    for (int v = gl; v < d; v += G) s += D.c[D.off[v] + m[v * stride]];
+#pragma unroll
+    for (int u = 0; u < MV; ++u) s += cv[u];
     s = group_sum<G>(s);
     const double rs = recip_nr(s);
     double g = rs * rs;
     if (D.family == FAM_D) {
       double p = 1.0;
       const int np = d * (d - 1) / 2;
-      for (int q = gl; q < np; q += G) {
-        int a, b;
-        pair_of(q, d, a, b);
-        const int ma = m[a * stride], mb = m[b * stride];
-        if (D.uniformT) {
-          const int dm = ma - mb;
-          p *= D.T[dm < 0 ? -dm : dm];
-        } else {
+      if (D.uniformT) {
+        for (int q0 = gl; q0 < np; q0 += 4 * G) {   // four pair factors' loads in flight
+          double t4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * G;
+            t4[u] = 1.0;
+            if (q < np) {
+              int a, b;
+              pair_of(q, d, a, b);
+              const int dm = m[a * stride] - m[b * stride];
+              t4[u] = D.T[dm < 0 ? -dm : dm];
+            }
+          }
+          p *= (t4[0] * t4[1]) * (t4[2] * t4[3]);
+        }
+      } else {
+        for (int q = gl; q < np; q += G) {
+          int a, b;
+          pair_of(q, d, a, b);
+          const int ma = m[a * stride], mb = m[b * stride];
           const double t = tanh((D.x[D.off[a] + ma] - D.x[D.off[b] + mb]) * 0.5);
           p *= t * t;
         }

@@ -1261,7 +1261,7 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
 // sequential substitution serves TTQ_SPW samples) and E = A - L_k(rho_t, :) z.
 #define TTQ_SG 8
 #define TTQ_SPW (32 / TTQ_SG)
-__global__ void __launch_bounds__(TTQ_WARPS * 32) k_samples(Dev *const *Dps) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) {
   // descriptor read in place: its shared-memory copy would cost the kernel its
   // second resident CTA per SM (R, Q and the group vectors fill the rest)
   const Dev &D = *Dps[blockIdx.z];
