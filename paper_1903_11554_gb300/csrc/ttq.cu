@@ -407,13 +407,17 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     const int slots = sms * occ;
     if (count == 1) P->cblocks = slots;
     else P->cblocks = std::min(P->cblocks, std::max(1, (slots + count - 1) / count));
-    // evaluation kernel: the same deal, its grid the resident slots when one instance runs
+    // evaluation kernel: the same deal, its grid the resident slots when one
+    // instance runs less one slot per interface, so that the QR row appends
+    // (one CTA per interface, on the second stream) find room beside it at once
+    // instead of waiting for its CTAs to retire
     int occe = 3;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occe, k_eval_slabs, TTQ_WARPS * 32, 0) != cudaSuccess || occe < 1)
       occe = 1;
     size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
     ge = ge < 1 ? 1 : ge;
-    P->grid_eval = count == 1 ? sms * occe : (int)std::min(ge, (size_t)std::max(1, (sms * occe + count - 1) / count));
+    P->grid_eval = count == 1 ? std::max(sms, sms * occe - P->max_ni)
+                              : (int)std::min(ge, (size_t)std::max(1, (sms * occe + count - 1) / count));
     // samples: at least enough CTAs per interface to fill the resident slots
     // once (each CTA holds one interface's factors), so no SM runs twice the
     // CTAs of another while others idle

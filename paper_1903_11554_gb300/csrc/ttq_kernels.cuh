@@ -62,13 +62,18 @@ __device__ __forceinline__ void cp_async8(double *smem, const double *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// the same r x r copies as stage_compact, issued asynchronously
+// the same r x r copies as stage_compact, issued asynchronously: a warp per
+// row, lanes over its columns (no index division on the issuing path)
 __device__ __forceinline__ void stage_compact_async(double *a_dst, const double *a_src, double *b_dst,
                                                     const double *b_src, int r, int ld) {
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int o = (e / r) * ld + e % r;
-    cp_async8(a_dst + e, a_src + o);
-    if (b_dst) cp_async8(b_dst + e, b_src + o);
+  const int lane = lane_id(), nw = blockDim.x >> 5;
+  for (int row = warp_id(); row < r; row += nw) {
+    const size_t so = (size_t)row * ld;
+    const int dof = row * r;
+    for (int c = lane; c < r; c += 32) {
+      cp_async8(a_dst + dof + c, a_src + so + c);
+      if (b_dst) cp_async8(b_dst + dof + c, b_src + so + c);
+    }
   }
 }
 
@@ -101,14 +106,41 @@ __device__ __forceinline__ void cta_gemv(const double *Mp, int si, int sb, const
 // number of register blocks a step touches is a compile-time constant (an FP64
 // warp instruction costs its full time whether or not its lanes are active).
 template <int NQ>
-__device__ __forceinline__ void back_seg(const double *C, int ld, int jhi, int jlo, double *tq, double *vout) {
+__device__ __forceinline__ void back_step(int j, const double (&c)[NQ], double *tq, double *vout) {
   const int lane = lane_id();
-  for (int jj = jhi; jj >= jlo; --jj) {
-    const double vj = __shfl_sync(0xffffffffu, tq[NQ - 1], jj & 31);
-    if (lane == (jj & 31)) vout[jj] = vj;
+  const double vj = __shfl_sync(0xffffffffu, tq[NQ - 1], j & 31);
+  if (lane == (j & 31)) vout[j] = vj;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
-      if (q < NQ - 1 || lane + 32 * q < jj) tq[q] = fma(-C[lane + 32 * q + (size_t)jj * ld], vj, tq[q]);
+  for (int q = NQ - 1; q >= 0; --q)               // the block the next step reads first
+    if (q < NQ - 1 || lane + 32 * q < j) tq[q] = fma(-c[q], vj, tq[q]);
+}
+// the entries of column j the step uses (the others are never read)
+template <int NQ>
+__device__ __forceinline__ void back_load(const double *C, int ld, int j, double (&c)[NQ]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) c[q] = (q < NQ - 1 || lane + 32 * q < j) ? C[lane + 32 * q + (size_t)j * ld] : 0.0;
+}
+// four steps at a time with their triangle entries loaded first, so that no
+// load sits on the chain of multiply-adds and shuffles
+template <int NQ>
+__device__ __forceinline__ void back_seg(const double *C, int ld, int jhi, int jlo, double *tq, double *vout) {
+  int jj = jhi;
+  for (; jj - 3 >= jlo; jj -= 4) {
+    double c0[NQ], c1[NQ], c2[NQ], c3[NQ];
+    back_load<NQ>(C, ld, jj, c0);
+    back_load<NQ>(C, ld, jj - 1, c1);
+    back_load<NQ>(C, ld, jj - 2, c2);
+    back_load<NQ>(C, ld, jj - 3, c3);
+    back_step<NQ>(jj, c0, tq, vout);
+    back_step<NQ>(jj - 1, c1, tq, vout);
+    back_step<NQ>(jj - 2, c2, tq, vout);
+    back_step<NQ>(jj - 3, c3, tq, vout);
+  }
+  for (; jj >= jlo; --jj) {
+    double c0[NQ];
+    back_load<NQ>(C, ld, jj, c0);
+    back_step<NQ>(jj, c0, tq, vout);
   }
 }
 // vout[j] = v_j after the back substitution (z = D^-1 vout); C column-major, leading dimension ld
@@ -132,16 +164,39 @@ __device__ __forceinline__ void warp_back_subst(const double *C, const double *t
 // low blocks and a step touches ceil((r - 1 - i) / 32) register blocks, as in
 // the back substitution, instead of every block from i's on.
 template <int NQ>
-__device__ __forceinline__ void fwd_seg(const double *S, int r, int ld, int jhi, int jlo, double *vq, double *uout) {
+__device__ __forceinline__ void fwd_load(const double *S, int r, int ld, int jj, double (&c)[NQ]) {
   const int lane = lane_id();
-  for (int jj = jhi; jj >= jlo; --jj) {         // jj = r - 1 - i, i ascending
-    const double ui = __shfl_sync(0xffffffffu, vq[NQ - 1], jj & 31);
-    const int i = r - 1 - jj;
-    if (lane == (jj & 31)) uout[i] = ui;
-    const double *Si = S + (size_t)i * ld + (r - 1);
+  const double *Si = S + (size_t)(r - 1 - jj) * ld + (r - 1);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
-      if (q < NQ - 1 || lane + 32 * q < jj) vq[q] = fma(-Si[-(lane + 32 * q)], ui, vq[q]);
+  for (int q = 0; q < NQ; ++q) c[q] = (q < NQ - 1 || lane + 32 * q < jj) ? Si[-(lane + 32 * q)] : 0.0;
+}
+template <int NQ>
+__device__ __forceinline__ void fwd_step(int r, int jj, const double (&c)[NQ], double *vq, double *uout) {
+  const int lane = lane_id();
+  const double ui = __shfl_sync(0xffffffffu, vq[NQ - 1], jj & 31);
+  if (lane == (jj & 31)) uout[r - 1 - jj] = ui;
+#pragma unroll
+  for (int q = NQ - 1; q >= 0; --q)
+    if (q < NQ - 1 || lane + 32 * q < jj) vq[q] = fma(-c[q], ui, vq[q]);
+}
+template <int NQ>
+__device__ __forceinline__ void fwd_seg(const double *S, int r, int ld, int jhi, int jlo, double *vq, double *uout) {
+  int jj = jhi;                                  // jj = r - 1 - i, i ascending
+  for (; jj - 3 >= jlo; jj -= 4) {
+    double c0[NQ], c1[NQ], c2[NQ], c3[NQ];
+    fwd_load<NQ>(S, r, ld, jj, c0);
+    fwd_load<NQ>(S, r, ld, jj - 1, c1);
+    fwd_load<NQ>(S, r, ld, jj - 2, c2);
+    fwd_load<NQ>(S, r, ld, jj - 3, c3);
+    fwd_step<NQ>(r, jj, c0, vq, uout);
+    fwd_step<NQ>(r, jj - 1, c1, vq, uout);
+    fwd_step<NQ>(r, jj - 2, c2, vq, uout);
+    fwd_step<NQ>(r, jj - 3, c3, vq, uout);
+  }
+  for (; jj >= jlo; --jj) {
+    double c0[NQ];
+    fwd_load<NQ>(S, r, ld, jj, c0);
+    fwd_step<NQ>(r, jj, c0, vq, uout);
   }
 }
 // uout[i] = u_i after the forward substitution (t = D^-1 uout); S row-major, leading dimension ld
@@ -924,22 +979,41 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 //     whose maximum reaches the window; one scan of its <= 128 rows.
 //   stage 2 (row step, gamma = j r_{k+1} + beta): item w = beta nch + ch holds the
 //     nodes j of chunk ch; the answer has the smallest j, so it lies in the lowest
-//     chunk any qualifying item reaches; the items of that chunk are scanned.
-__device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
+//     chunk any qualifying item reaches; the qualifying items of that chunk are scanned.
+// The first loads (the stage maximum and count, the scale, the outer rank, the
+// item rows and the first 4 blockDim candidates, read up to the arrays'
+// capacity before their counts are known) form one round, so a pick costs two
+// dependent rounds of global reads.  qbits: blockDim.x words of shared scratch
+// (stage 2 marks the qualifying items there, TTQ_MAXR * TTQ_MAX_NODES / 32 bits
+// at most).
+__device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigned *qbits) {
   __shared__ int si[TTQ_WARPS];
   __shared__ double se[TTQ_WARPS];
-  __shared__ int best_s;
-  __shared__ double beste_s;
   State *st = D.st;
   IfaceState &I = st->it[k];
-  const int lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
-  // every thread reads the stage's maximum and count (one address each)
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), nw = nt >> 5;
+  const long long *csb = reinterpret_cast<const long long *>(D.cs[k]);
+  const double *ce = D.ce[k];
+  const long long *imb = reinterpret_cast<const long long *>(D.im[k]);
+  const long long *src = stage == 0 ? csb : imb;
+  const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
+  const int lim = stage == 0 ? D.S[k] : D.cap * ((Nm + 31) >> 5);
   const unsigned long long mbits = __ldcg(&I.smax_bits);
   const unsigned n = __ldcg(&I.stage_count);
   const double scale = __longlong_as_double((long long)__ldcg(&st->scale_bits));
-  if (threadIdx.x == 0) best_s = 0x7fffffff;
+  const int rm = stage == 0 ? 0 : __ldcg(stage == 1 ? &st->r[k - 1] : &st->r[k + 1]);
+  const int srows = stage == 0 ? 1 : __ldcg(&st->stage_rows);
+  long long vb[4];
+  double ev[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int t = tid + u * nt;
+    vb[u] = t < lim ? __ldcg(src + t) : -1LL;
+    ev[u] = (stage == 0 && t < lim) ? __ldcg(ce + t) : 0.0;
+  }
+  if (stage == 2) qbits[tid] = 0u;
   __syncthreads();                               // all have read the reduction before it is cleared
-  if (threadIdx.x == 0) { I.smax_bits = 0ULL; I.stage_count = 0; }
+  if (tid == 0) { I.smax_bits = 0ULL; I.stage_count = 0; }
   if (n == 0) { *e_out = 0.0; return -1; }
   const double smax = __longlong_as_double((long long)mbits);
   const double thr = __dadd_rn(smax, -__dadd_rn(__dmul_rn(TTQ_TIE_REL, smax), __dmul_rn(TTQ_TIE_ABS, scale)));
@@ -947,26 +1021,26 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   // scores are non-negative doubles or -1, so this is one signed comparison of
   // bit patterns (integer pipe, not the FP64 unit)
   const long long thrb = thr > 0.0 ? __double_as_longlong(thr) : 0LL;
-  const long long *csb = reinterpret_cast<const long long *>(D.cs[k]);
-  const double *ce = D.ce[k];
-  int first = 0x7fffffff;
-  double efirst = 0.0;
   if (stage == 0) {
-    // the residuals are loaded with the scores, so the chosen one is at hand
-    const int Sk = D.S[k];
-    for (int t0 = threadIdx.x; t0 < Sk; t0 += 4 * blockDim.x) {
-      long long vb[4];
-      double e[4];
+    const int Sk = lim;
+    int first = 0x7fffffff;
+    double efirst = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = tid + u * nt;
+      if (t < Sk && vb[u] >= thrb && t < first) { first = t; efirst = ev[u]; }
+    }
+    for (int t0 = tid + 4 * nt; t0 < Sk; t0 += 4 * nt) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {           // four candidates' loads in flight
-        const int t = t0 + u * blockDim.x;
+        const int t = t0 + u * nt;
         vb[u] = t < Sk ? __ldcg(csb + t) : -1LL;
-        e[u] = t < Sk ? __ldcg(ce + t) : 0.0;
+        ev[u] = t < Sk ? __ldcg(ce + t) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int t = t0 + u * blockDim.x;
-        if (vb[u] >= thrb && t < first) { first = t; efirst = e[u]; }
+        const int t = t0 + u * nt;
+        if (vb[u] >= thrb && t < first) { first = t; efirst = ev[u]; }
       }
     }
 #pragma unroll
@@ -984,24 +1058,25 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
     *e_out = efirst;
     return first;                                // n > 0: some score reaches the window
   }
-  const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
-  const int rm = stage == 1 ? st->r[k - 1] : st->r[k + 1];   // rows / columns of the outer rank
-  const NodeChunks nc = node_chunks(Nm, st->stage_rows);
+  const NodeChunks nc = node_chunks(Nm, srows);
   const int nch = nc.nch;
-  const long long *imb = reinterpret_cast<const long long *>(D.im[k]);
   int wmin = 0x7fffffff;                       // first qualifying slot (stage 1) / its chunk (stage 2)
   const int nslot = rm * nch;
-  for (int w0 = threadIdx.x; w0 < nslot; w0 += 4 * blockDim.x) {
-    long long vb[4];
+  for (int w0 = tid; w0 < nslot; w0 += 4 * nt) {
+    if (w0 != tid) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {              // four slots' loads in flight
-      const int w = w0 + u * blockDim.x;
-      vb[u] = w < nslot ? __ldcg(imb + w) : -1LL;
+      for (int u = 0; u < 4; ++u) {            // four slots' loads in flight
+        const int w = w0 + u * nt;
+        vb[u] = w < nslot ? __ldcg(imb + w) : -1LL;
+      }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int w = w0 + u * blockDim.x;
-      if (vb[u] >= thrb) wmin = min(wmin, stage == 1 ? w : w % nch);
+      const int w = w0 + u * nt;
+      if (w < nslot && vb[u] >= thrb) {
+        wmin = min(wmin, stage == 1 ? w : w % nch);
+        if (stage == 2) atomicOr(qbits + (w >> 5), 1u << (w & 31));
+      }
     }
   }
 #pragma unroll
@@ -1010,57 +1085,59 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out) {
   __syncthreads();
   wmin = si[0];
   for (int w = 1; w < nw; ++w) wmin = min(wmin, si[w]);
+  __syncthreads();                               // si is reused below
+  int f = 0x7fffffff;
+  double fe = 0.0;
   if (stage == 1) {
     if (warp == 0) {
       const int alpha = wmin / nch, ch = wmin % nch;
       int i0, i1, nq;
       chunk_span(nc, ch, Nm, i0, i1, nq);
-      int f = 0x7fffffff;
-      double fe = 0.0;
 #pragma unroll
       for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
         const int i = i0 + lane + 32 * q;
         if (i < i1) {
           const int c = alpha * Nm + i;
-          const long long vb = __ldcg(csb + c);
+          const long long v = __ldcg(csb + c);
           const double e = __ldcg(ce + c);
-          if (vb >= thrb && c < f) { f = c; fe = e; }
+          if (v >= thrb && c < f) { f = c; fe = e; }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const int of = __shfl_xor_sync(0xffffffffu, f, o);
-        const double oe = __shfl_xor_sync(0xffffffffu, fe, o);
-        if (of < f) { f = of; fe = oe; }
-      }
-      if (lane == 0) { best_s = f; beste_s = fe; }
     }
   } else {
+    // the qualifying items of chunk ch, a warp each (their marks are in shared memory)
     const int ch = wmin;
     int j0, j1, nq;
     chunk_span(nc, ch, Nm, j0, j1, nq);
     for (int beta = warp; beta < rm; beta += nw) {
-      const long long mb = __ldcg(imb + beta * nch + ch);
-      if (mb < thrb) continue;
-      int f = 0x7fffffff;
+      const int w = beta * nch + ch;
+      if (!((qbits[w >> 5] >> (w & 31)) & 1u)) continue;
 #pragma unroll
       for (int q = 0; q < TTQ_CHUNK / 32; ++q) {
         const int j = j0 + lane + 32 * q;
         if (j < j1) {
           const int c = j * rm + beta;
-          const long long vb = __ldcg(csb + c);
-          if (vb >= thrb && c < f) f = c;
+          const long long v = __ldcg(csb + c);
+          const double e = __ldcg(ce + c);
+          if (v >= thrb && c < f) { f = c; fe = e; }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(0xffffffffu, f, o));
-      if (lane == 0) atomicMin(&best_s, f);
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int of = __shfl_xor_sync(0xffffffffu, f, o);
+    const double oe = __shfl_xor_sync(0xffffffffu, fe, o);
+    if (of < f) { f = of; fe = oe; }
+  }
+  if (lane == 0) { si[warp] = f; se[warp] = fe; }
   __syncthreads();
-  first = best_s;
-  *e_out = (stage == 1) ? beste_s : __ldcg(ce + first);   // stage 2: several warps compete
-  return first;
+  f = si[0];
+  fe = se[0];
+  for (int w = 1; w < nw; ++w)
+    if (si[w] < f) { f = si[w]; fe = se[w]; }
+  *e_out = fe;
+  return f;
 }
 
 // Scratch of the decisions between search stages (one CTA)
@@ -1128,10 +1205,11 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   }
   const double *F = Fs ? Fs : (mode == 1 ? D.Sr[k] : D.Cc[k]);
   const int fld = Fs ? r : ld;
+  unsigned *qb = reinterpret_cast<unsigned *>(sc.part);   // free until the solve's products
   double e;
   int col = -1, row = -1;
   if (mode == 0) {
-    const int pick = stage_pick(D, k, 0, &e);
+    const int pick = stage_pick(D, k, 0, &e, qb);
     if (pick >= 0) {
       const int Nk = D.N[k - 1], Nk1 = D.N[k], rn = st->r[k + 1];
       const unsigned long long sid = stream_id(st->sweep, k, 1);
@@ -1140,14 +1218,14 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
       if (tid == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
     }
   } else if (mode == 1) {
-    const int pick = stage_pick(D, k, 1, &e);
+    const int pick = stage_pick(D, k, 1, &e, qb);
     if (tid == 0) {
       if (pick < 0) I.active = 0;
       else I.row = pick;
     }
     row = pick;
   } else {
-    const int pick = stage_pick(D, k, 2, &e);
+    const int pick = stage_pick(D, k, 2, &e, qb);
     if (pick < 0) {
       if (tid == 0) I.active = 0;
     } else {
@@ -1202,27 +1280,32 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
 }
 
 // The decisions after a rook step (modes 1 and 2 of stage_finish), one CTA per
-// interface: the factors are copied to shared memory asynchronously from the
-// start, under the argmax.
+// interface.  The rank and the factors are fixed from kernel (b) to the end of
+// the search, so their copies to shared memory are issued before the wait for
+// the preceding rook step: they overlap its tail (the rook step streams the
+// cores through L2, so the factors come from DRAM) instead of delaying the argmax.
 __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
-  pdl_wait();
-  pdl_release();
   State *st = D.st;
   const int k = blockIdx.x + 1;
-  if (k > D.d - 1) return;
-  if (st->stop || !st->search) return;
-  IfaceState &I = st->it[k];
-  if (!I.active || I.rook_done) return;
+  const bool mine = k <= D.d - 1;
   extern __shared__ double sm[];
   __shared__ SolveSmem sc;
-  const int r = st->r[k], ld = D.cap;
+  const int r = mine ? st->r[k] : 0, ld = D.cap;
   double *Fs = sm;
   double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
-  if (mode == 1) stage_compact_async(Fs, D.Sr[k], Qs, D.Qc[k], r, ld);   // D^-1 R row-major, Q col-major
-  else stage_compact_async(Fs, D.Cc[k], Qs, D.Qr[k], r, ld);             // R D^-1 col-major, Q row-major
-  for (int b = threadIdx.x; b < r; b += blockDim.x) cp_async8(sc.ri + b, D.rinv[k] + b);
+  if (r > 0) {
+    if (mode == 1) stage_compact_async(Fs, D.Sr[k], Qs, D.Qc[k], r, ld);   // D^-1 R row-major, Q col-major
+    else stage_compact_async(Fs, D.Cc[k], Qs, D.Qr[k], r, ld);             // R D^-1 col-major, Q row-major
+    for (int b = threadIdx.x; b < r; b += blockDim.x) cp_async8(sc.ri + b, D.rinv[k] + b);
+  }
+  pdl_wait();
+  pdl_release();
+  if (!mine || st->stop || !st->search || !st->it[k].active || st->it[k].rook_done) {
+    cp_async_wait_all();                         // no copy outlives the CTA
+    return;
+  }
   stage_finish(D, k, mode, Fs, Qs, sc.ri, sc, true);
 }
 
@@ -1285,12 +1368,14 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
   const int vst = D.cap + 1;                         // padded group vector stride
   double *yv = fac + (size_t)D.cap * D.cap * (D.q_in_smem ? 2 : 1) + (size_t)warp * TTQ_SPW * 2 * vst;
   double *y = yv + g * 2 * vst, *t = y + vst;        // this group's y (then z) and Q^T y
-  stage_compact(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);   // Rs holds R D^-1 (column-major)
+  // R D^-1 (column-major) and Q copied asynchronously beside the loads of the cross
+  stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);
   for (int a = threadIdx.x; a < rk; a += blockDim.x) {
     ri[a] = D.rinv[k][a];
     rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
     gset[a] = D.rnode[k][a] * rn + D.rpar[k][a];
   }
+  cp_async_wait_all();
   __syncthreads();
   const unsigned long long sid = stream_id(st->sweep, k, 1);
   const int flp = point_flops(D);
