@@ -1382,7 +1382,10 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
   double best = 0.0;
   unsigned nel = 0, nev = 0;
   unsigned long long fl = 0;
-  for (int base = (blockIdx.x * TTQ_WARPS + warp) * TTQ_SPW; base < S; base += gridDim.x * TTQ_WARPS * TTQ_SPW) {
+  // tasks of TTQ_SPW samples dealt CTA-first, so the interface's CTAs (and the
+  // SMs they share) carry counts that differ by one task at most
+  for (int task = warp * gridDim.x + blockIdx.x; task * TTQ_SPW < S; task += gridDim.x * TTQ_WARPS) {
+    const int base = task * TTQ_SPW;
     // one lane per sample: draw and exclusion test
     int rho = 0, gam = 0, ok = 0;
     if (lane < TTQ_SPW && base + lane < S) {
@@ -1499,6 +1502,10 @@ __device__ __forceinline__ ItemMap item_map(int cnt) {
 #endif
 #ifndef TTQ_ROOK_UNROLL
 #define TTQ_ROOK_UNROLL 8
+#endif
+// largest item of a rook step, in rows of 32 nodes (1, 2 or 4)
+#ifndef TTQ_ROOK_RMAX
+#define TTQ_ROOK_RMAX 4
 #endif
 constexpr int kRookUnroll = TTQ_ROOK_UNROLL;
 
@@ -1650,7 +1657,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     if (I.active && !I.rook_done) outer = st->r[lane];
     Nl = D.N[lane];
   }
-  const int R = rows_per_item(outer, Nl);
+  const int R = rows_per_item(outer, Nl, TTQ_ROOK_RMAX);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->stage_rows = R;   // for the argmax that follows
   const ItemMap im = item_map(outer ? outer * node_chunks(Nl, R).nch : 0);
   unsigned long long fl = 0;
@@ -1735,7 +1742,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     if (I.active && !I.rook_done) outer = st->r[lane + 2];
     Nl = D.N[lane + 1];
   }
-  const int R = rows_per_item(outer, Nl);
+  const int R = rows_per_item(outer, Nl, TTQ_ROOK_RMAX);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->stage_rows = R;
   const ItemMap im = item_map(outer ? outer * node_chunks(Nl, R).nch : 0);
   unsigned long long fl = 0;
