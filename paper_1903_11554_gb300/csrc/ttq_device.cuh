@@ -65,7 +65,6 @@ struct State {
   unsigned batch_guard;     // sweeps run by a batch's loop (used in instance 0 of a batch)
   int pending_status;
   unsigned contract_arrive;  // CTAs of the two contraction chains that have finished
-  int stage_rows;           // rows of 32 nodes per work item of the last rook step
   int qr_rank[TTQ_MAXD];    // size of the stored QR factors of G_k (0: none)
   int qr_row[TTQ_MAXD];     // rank whose row append is done (k_qr_row), 0: none pending
   unsigned long long scale_bits;   // max |core entry| as IEEE bits (non-negative)

@@ -974,12 +974,13 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 // candidate index whose score lies in the tie window below the stage maximum,
 // -1 if the stage had no eligible candidate.  Clears the stage reduction.
 //   stage 0 (samples): a scan of the S sample scores.
-//   stage 1 (column step, rho = alpha N_k + i): the item at slot w = alpha nch + ch
-//     holds the contiguous rows i in chunk ch, so the answer lies in the first slot
-//     whose maximum reaches the window; one scan of its <= 128 rows.
-//   stage 2 (row step, gamma = j r_{k+1} + beta): item w = beta nch + ch holds the
-//     nodes j of chunk ch; the answer has the smallest j, so it lies in the lowest
-//     chunk any qualifying item reaches; the qualifying items of that chunk are scanned.
+//   stage 1 (column step, rho = alpha N_k + i): slot w = alpha rows + q holds the
+//     maximum over the 32 nodes i of row q, so the answer lies in the first slot
+//     whose maximum reaches the window; one scan of its 32 candidates.
+//   stage 2 (row step, gamma = j r_{k+1} + beta): slot w = beta rows + q holds the
+//     maximum over the nodes j of row q of fiber beta; the answer has the smallest
+//     j, so it lies in the lowest row any qualifying slot reaches; the qualifying
+//     slots of that row are scanned.
 // The first loads (the stage maximum and count, the scale, the outer rank, the
 // item rows and the first 4 blockDim candidates, read up to the arrays'
 // capacity before their counts are known) form one round, so a pick costs two
@@ -1002,7 +1003,6 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigne
   const unsigned n = __ldcg(&I.stage_count);
   const double scale = __longlong_as_double((long long)__ldcg(&st->scale_bits));
   const int rm = stage == 0 ? 0 : __ldcg(stage == 1 ? &st->r[k - 1] : &st->r[k + 1]);
-  const int srows = stage == 0 ? 1 : __ldcg(&st->stage_rows);
   long long vb[4];
   double ev[4];
 #pragma unroll
@@ -1058,7 +1058,7 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigne
     *e_out = efirst;
     return first;                                // n > 0: some score reaches the window
   }
-  const NodeChunks nc = node_chunks(Nm, srows);
+  const NodeChunks nc = node_chunks(Nm, 1);      // a slot per row of 32 nodes
   const int nch = nc.nch;
   int wmin = 0x7fffffff;                       // first qualifying slot (stage 1) / its chunk (stage 2)
   const int nslot = rm * nch;
@@ -1503,10 +1503,6 @@ __device__ __forceinline__ ItemMap item_map(int cnt) {
 #ifndef TTQ_ROOK_UNROLL
 #define TTQ_ROOK_UNROLL 8
 #endif
-// largest item of a rook step, in rows of 32 nodes (1, 2 or 4)
-#ifndef TTQ_ROOK_RMAX
-#define TTQ_ROOK_RMAX 4
-#endif
 constexpr int kRookUnroll = TTQ_ROOK_UNROLL;
 
 // Score of a residual for the argmax, as IEEE bits: |E| for finite E (non-negative
@@ -1522,7 +1518,7 @@ __device__ __forceinline__ bool score_bits(double E, unsigned long long &bits) {
 template <int NQ>
 __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0, int i1, int rk, const int *ms,
                                          const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
-                                         unsigned long long &best, unsigned &nel, unsigned &nev) {
+                                         unsigned long long (&bq)[NQ], unsigned &nel, unsigned &nev) {
   const double *tab = uses_ptab(D, rk) ? D.ptab[k] : nullptr;
   const int lane = lane_id(), Nk = D.N[k - 1];
   int iq[NQ];
@@ -1554,6 +1550,7 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
   }
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
+    bq[q] = 0ULL;                                  // score bits + 1 of the row's eligible candidate, 0: none
     if (iq[q] >= i1) continue;
     const int rho = alpha * Nk + iq[q];
     if (!ok[q]) { D.cs[k][rho] = -1.0; D.ce[k][rho] = 0.0; continue; }
@@ -1563,7 +1560,7 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
     D.cs[k][rho] = fin ? __longlong_as_double((long long)sb) : -1.0;
     D.ce[k][rho] = E;
     ++nev;
-    if (fin) { best = sb > best ? sb : best; ++nel; }
+    if (fin) { bq[q] = sb + 1ULL; ++nel; }
   }
 }
 
@@ -1572,7 +1569,7 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
 template <int NQ>
 __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, int j1, int rk, int rn, const int *ms,
                                          const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
-                                         unsigned long long &best, unsigned &nel, unsigned &nev) {
+                                         unsigned long long (&bq)[NQ], unsigned &nel, unsigned &nev) {
   const double *tab = uses_ptab(D, rk) ? D.ptab[k] : nullptr;
   const int lane = lane_id(), Nk1 = D.N[k];
   int jq[NQ];
@@ -1602,6 +1599,7 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, 
   }
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
+    bq[q] = 0ULL;
     if (jq[q] >= j1) continue;
     const int g = jq[q] * rn + beta;
     if (!ok[q]) { D.cs[k][g] = -1.0; D.ce[k][g] = 0.0; continue; }
@@ -1611,37 +1609,98 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, 
     D.cs[k][g] = fin ? __longlong_as_double((long long)sb) : -1.0;
     D.ce[k][g] = E;
     ++nev;
-    if (fin) { best = sb > best ? sb : best; ++nel; }
+    if (fin) { bq[q] = sb + 1ULL; ++nel; }
   }
 }
 
-// warp totals of an item: evaluations, the item's maximum (stored at its slot
-// outer * nch + chunk, the order of the candidate indices) and the stage reduction
-__device__ __forceinline__ void item_publish(const Dev &D, IfaceState &I, int k, int slot, unsigned long long best,
-                                             unsigned nel, unsigned nev) {
+// warp totals of a stretch of NQ rows: evaluations, each row's maximum (stored
+// at its slot outer * rows + row, the order of the candidate indices, -1 when
+// the row has no eligible candidate) and the stage reduction (pass 1 of the argmax)
+template <int NQ>
+__device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k, int slot0,
+                                             unsigned long long (&bq)[NQ], unsigned nel, unsigned nev) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-    best = ob > best ? ob : best;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bq[q], o);
+      bq[q] = ob > bq[q] ? ob : bq[q];
+    }
     nel += __shfl_xor_sync(0xffffffffu, nel, o);
     nev += __shfl_xor_sync(0xffffffffu, nev, o);
   }
   if (lane_id() == 0) {
+    unsigned long long best = 0ULL;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      D.im[k][slot0 + q] = bq[q] ? __longlong_as_double((long long)(bq[q] - 1ULL)) : -1.0;
+      best = bq[q] > best ? bq[q] : best;
+    }
     if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
-    D.im[k][slot] = nel ? __longlong_as_double((long long)best) : -1.0;
     if (nel) {
-      atomicMax(&I.smax_bits, best);
+      atomicMax(&I.smax_bits, best - 1ULL);
       atomicAdd(&I.stage_count, nel);
     }
   }
 }
 
+// Work of a rook step.  Its unit is a row: 32 candidates of one fiber (one
+// outer index) of one searching interface, in the order of the candidate
+// indices.  Two deals, decided alike by every CTA:
+//  - items: fibers split into chunks of R rows (R in 1, 2, 4, the smallest whose
+//    items fit in one wave of the grid's warps), one item per warp at most,
+//    walked chunk-major; when the items fit, every warp meets one chain of
+//    dependent loads and setup (the latency of low-rank steps);
+//  - stretches, when even 4-row items overflow one wave: every warp takes a
+//    contiguous stretch of rows of near-equal length (they differ by one row at
+//    most), processed in pieces of at most four rows that stop at fiber ends,
+//    so every scheduler of every SM gets the same share of the FP64 work and
+//    no sparse second wave of items trails the first.
+// Lane k-1 of the warp holds interface k's outer rank and nodes; pieces come
+// out as (interface, outer index, first row, rows).
+struct RookDeal {
+  ItemMap im;
+  int R, pos, end;
+  bool items;
+};
+__device__ __forceinline__ RookDeal rook_deal(const Dev &D, int outer, int Nl) {
+  const long long W = (long long)gridDim.x * TTQ_WARPS;
+  RookDeal q;
+  q.R = rows_per_item(outer, Nl);
+  q.im = item_map(outer ? outer * node_chunks(Nl, q.R).nch : 0);
+  q.items = q.im.total <= W;
+  if (!q.items) q.im = item_map(outer ? outer * ((Nl + 31) >> 5) : 0);
+  const long long g = (long long)deal_slot(warp_id(), D.sms, q.im.total) * gridDim.x + blockIdx.x;
+  if (q.items) {
+    q.pos = (int)g;
+    q.end = g < q.im.total ? (int)g + 1 : (int)g;
+  } else {
+    q.pos = (int)(g * q.im.total / W);
+    q.end = (int)((g + 1) * q.im.total / W);
+  }
+  return q;
+}
+// the next piece: interface k, outer index o (of outer rank ok), rows [q0, q0 + nq) of N nodes
+__device__ __forceinline__ void rook_piece(RookDeal &q, int k, int ok, int N, int &o, int &q0, int &nq) {
+  const int local = q.pos - __shfl_sync(0xffffffffu, q.im.pre - q.im.cnt, k - 1);
+  if (q.items) {
+    const NodeChunks nc = node_chunks(N, q.R);
+    const int ch = local / ok;
+    o = local % ok;
+    q0 = ch * nc.base + min(ch, nc.extra);
+    nq = nc.base + (ch < nc.extra ? 1 : 0);
+    q.pos += 1;
+  } else {
+    const int rows = (N + 31) >> 5;
+    o = local / rows;
+    q0 = local % rows;
+    nq = min(min(4, rows - q0), q.end - q.pos);
+    q.pos += nq;
+  }
+}
+
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i) of every
-// searching interface; a load-balanced list of (interface, node chunk, alpha)
-// items; pass 1 of the argmax per interface (pass 2 in k_solve).  Items are
-// dealt round-robin over the CTAs first, so every CTA (and SM) gets an even
-// share, and walked chunk-major, so that the first chunks of the fibers
-// (possibly one row longer than the rest) do not recur with the deal's period.
+// searching interface; pass 1 of the argmax per interface (pass 2 in k_solve).
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
@@ -1657,23 +1716,19 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     if (I.active && !I.rook_done) outer = st->r[lane];
     Nl = D.N[lane];
   }
-  const int R = rows_per_item(outer, Nl, TTQ_ROOK_RMAX);
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->stage_rows = R;   // for the argmax that follows
-  const ItemMap im = item_map(outer ? outer * node_chunks(Nl, R).nch : 0);
+  RookDeal dl = rook_deal(D, outer, Nl);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface whose z sits in sh.z[warp]
-  for (int w = deal_slot(warp, D.sms, im.total) * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
-    const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
+  while (dl.pos < dl.end) {
+    const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);                  // interface (1-based)
-    const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
     IfaceState &I = st->it[k];
     const int rk = st->r[k], rn = st->r[k + 1], rl = st->r[k - 1];
-    const int Nk = D.N[k - 1];
-    const NodeChunks nc = node_chunks(Nk, R);
-    const int ch = local / rl, alpha = local % rl, slot = alpha * nc.nch + ch;
-    int i0, i1, nq;
-    chunk_span(nc, ch, Nk, i0, i1, nq);
-    // the item's independent loads first (column, z, left indices, the cross's
+    const int Nk = D.N[k - 1], rows = (Nk + 31) >> 5;
+    int alpha, q0, nq;
+    rook_piece(dl, k, rl, Nk, alpha, q0, nq);
+    const int i0 = 32 * q0, i1 = min(Nk, 32 * (q0 + nq)), slot0 = alpha * rows + q0;
+    // the piece's independent loads first (column, z, left indices, the cross's
     // parent pointers), then what depends on the column
     const int gam = I.col;
     double zr[TTQ_MAXR / 32];
@@ -1710,22 +1765,28 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     // per node: the entry (the shared right-mode factors come from the step's table), the product, the residual
     const int tabbed = uses_ptab(D, rk) ? (d - k) - 1 : 0;
     fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node - tabbed + 2 * rk + 1);
-    unsigned long long best = 0;
     unsigned nel = 0, nev = 0;
+#define TTQ_COL_PIECE(Q)                                                                                      \
+  {                                                                                                           \
+    unsigned long long bq[Q];                                                                                 \
+    col_item<Q>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
+                nev);                                                                                         \
+    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                            \
+  }
     switch (nq) {
-      case 4: col_item<4>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
-      case 3: col_item<3>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
-      case 2: col_item<2>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
-      default: col_item<1>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      case 4: TTQ_COL_PIECE(4) break;
+      case 3: TTQ_COL_PIECE(3) break;
+      case 2: TTQ_COL_PIECE(2) break;
+      default: TTQ_COL_PIECE(1) break;
     }
-    item_publish(D, I, k, slot, best, nel, nev);
+#undef TTQ_COL_PIECE
     __syncwarp();
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
 }
 
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
-// searching interface, items (interface, node chunk, beta), walked like the
+// searching interface, rows of 32 nodes j of the fibers beta, dealt like the
 // column step's; pass 1 of the argmax.
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps) {
   __shared__ Dev sD;
@@ -1742,22 +1803,18 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     if (I.active && !I.rook_done) outer = st->r[lane + 2];
     Nl = D.N[lane + 1];
   }
-  const int R = rows_per_item(outer, Nl, TTQ_ROOK_RMAX);
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->stage_rows = R;
-  const ItemMap im = item_map(outer ? outer * node_chunks(Nl, R).nch : 0);
+  RookDeal dl = rook_deal(D, outer, Nl);
   unsigned long long fl = 0;
   int zk = 0;
-  for (int w = deal_slot(warp, D.sms, im.total) * gridDim.x + blockIdx.x; w < im.total; w += gridDim.x * TTQ_WARPS) {
-    const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && im.pre > w);
+  while (dl.pos < dl.end) {
+    const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);
-    const int local = w - __shfl_sync(0xffffffffu, im.pre - im.cnt, k - 1);
     IfaceState &I = st->it[k];
     const int rk = st->r[k], rn = st->r[k + 1];
-    const int Nk = D.N[k - 1], Nk1 = D.N[k];
-    const NodeChunks nc = node_chunks(Nk1, R);
-    const int ch = local / rn, beta = local % rn, slot = beta * nc.nch + ch;
-    int j0, j1, nq;
-    chunk_span(nc, ch, Nk1, j0, j1, nq);
+    const int Nk = D.N[k - 1], Nk1 = D.N[k], rows = (Nk1 + 31) >> 5;
+    int beta, q0, nq;
+    rook_piece(dl, k, rn, Nk1, beta, q0, nq);
+    const int j0 = 32 * q0, j1 = min(Nk1, 32 * (q0 + nq)), slot0 = beta * rows + q0;
     const int rho = I.row;
     double zr[TTQ_MAXR / 32];
     int rp[TTQ_MAXR / 32], rnd[TTQ_MAXR / 32];
@@ -1791,15 +1848,21 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
     const int tabbed = uses_ptab(D, rk) ? k - 1 : 0;
     fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node - tabbed + 2 * rk + 1);
-    unsigned long long best = 0;
     unsigned nel = 0, nev = 0;
+#define TTQ_ROW_PIECE(Q)                                                                                           \
+  {                                                                                                                \
+    unsigned long long bq[Q];                                                                                      \
+    row_item<Q>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
+                nev);                                                                                              \
+    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                                 \
+  }
     switch (nq) {
-      case 4: row_item<4>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
-      case 3: row_item<3>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
-      case 2: row_item<2>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
-      default: row_item<1>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], best, nel, nev); break;
+      case 4: TTQ_ROW_PIECE(4) break;
+      case 3: TTQ_ROW_PIECE(3) break;
+      case 2: TTQ_ROW_PIECE(2) break;
+      default: TTQ_ROW_PIECE(1) break;
     }
-    item_publish(D, I, k, slot, best, nel, nev);
+#undef TTQ_ROW_PIECE
     __syncwarp();
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
