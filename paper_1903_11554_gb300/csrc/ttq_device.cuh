@@ -47,6 +47,8 @@ struct IfaceState {
   unsigned int stage_count;       // eligible candidates of the running stage
   int prow, prank;                // pvec holds R^-T L_k(prow, :)^T for the rank-prank factors (-1: none)
   unsigned items_done;            // work items of the running stage completed so far
+  int fix[TTQ_MAXD];              // node indices the next rook step fixes: modes k.. of gamma
+                                  // (column step), modes ..k-1 of rho (row step)
 };
 
 struct State {

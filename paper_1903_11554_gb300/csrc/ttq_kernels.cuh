@@ -1240,16 +1240,24 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   const bool tab = uses_ptab(D, r) && (colsolve || rowsolve) && blockDim.x > 32;
   __shared__ int fm[TTQ_MAXD];
   int nfm = 0;
+  // the node indices the next rook step fixes go to I.fix, so that its work
+  // items read them in their first round of loads
   if (colsolve) {
     const int rn = st->r[k + 1], j = col / rn, beta = col % rn;
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
     nfm = D.d - k;                               // modes k .. d-1
-    if (tab && tid < nfm) fm[tid] = tid == 0 ? j : D.ridx[k + 1][beta * D.d + k + tid];
+    if (tid < nfm) {
+      fm[tid] = tid == 0 ? j : D.ridx[k + 1][beta * D.d + k + tid];
+      I.fix[k + tid] = fm[tid];
+    }
   } else if (rowsolve) {
     const int Nk = D.N[k - 1], alpha = row / Nk, i0 = row % Nk;
     for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
     nfm = k;                                     // modes 0 .. k-1
-    if (tab && tid < nfm) fm[tid] = tid == k - 1 ? i0 : D.lidx[k - 1][alpha * D.d + tid];
+    if (tid < nfm) {
+      fm[tid] = tid == k - 1 ? i0 : D.lidx[k - 1][alpha * D.d + tid];
+      I.fix[tid] = fm[tid];
+    }
   }
   if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
@@ -1707,15 +1715,21 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   pdl_wait();
   pdl_release();
   State *st = D.st;
-  if (st->stop || !st->search) return;
   __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  int outer = 0, Nl = 1;
+  // one round of loads: the run's flags and, lane k-1, interface k's search
+  // state and the ranks around it
+  const int stop = st->stop, search = st->search;
+  int act = 0, r0 = 0, r1 = 0, Nl = 1;
   if (lane < d - 1) {
     const IfaceState &I = st->it[lane + 1];
-    if (I.active && !I.rook_done) outer = st->r[lane];
+    act = I.active && !I.rook_done;
+    r0 = st->r[lane];
+    r1 = st->r[lane + 1];
     Nl = D.N[lane];
   }
+  if (stop || !search) return;
+  const int outer = act ? r0 : 0;
   RookDeal dl = rook_deal(D, outer, Nl);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface whose z sits in sh.z[warp]
@@ -1723,14 +1737,12 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);                  // interface (1-based)
     IfaceState &I = st->it[k];
-    const int rk = st->r[k], rn = st->r[k + 1], rl = st->r[k - 1];
+    const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rl = __shfl_sync(0xffffffffu, r0, k - 1);
     const int Nk = D.N[k - 1], rows = (Nk + 31) >> 5;
     int alpha, q0, nq;
     rook_piece(dl, k, rl, Nk, alpha, q0, nq);
     const int i0 = 32 * q0, i1 = min(Nk, 32 * (q0 + nq)), slot0 = alpha * rows + q0;
-    // the piece's independent loads first (column, z, left indices, the cross's
-    // parent pointers), then what depends on the column
-    const int gam = I.col;
+    // the piece's loads in one round: z, left indices, the fixed right indices, the cross's parent pointers
     double zr[TTQ_MAXR / 32];
     int lp[TTQ_MAXR / 32], ln[TTQ_MAXR / 32];
     const bool newz = k != zk;
@@ -1742,15 +1754,14 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
       ln[q] = a < rk ? D.lnode[k][a] : 0;
     }
     const int vl = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : 0;
-    const int j = gam / rn, beta = gam % rn;
-    const int vr = (lane > k && lane < d) ? D.ridx[k + 1][beta * d + lane] : 0;
+    const int vr = (lane >= k && lane < d) ? I.fix[lane] : 0;
     if (newz) {
 #pragma unroll
       for (int q = 0; q < TTQ_MAXR / 32; ++q)
         if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
       zk = k;
     }
-    if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : (lane == k ? j : (lane > k ? vr : 0));
+    if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : vr;
     // rows of the cross with this parent alpha: excluded nodes i
     int nex = 0;
 #pragma unroll
@@ -1794,15 +1805,19 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   pdl_wait();
   pdl_release();
   State *st = D.st;
-  if (st->stop || !st->search) return;
   __shared__ RookSmem sh;
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  int outer = 0, Nl = 1;
+  const int stop = st->stop, search = st->search;
+  int act = 0, r1 = 0, r2 = 0, Nl = 1;
   if (lane < d - 1) {
     const IfaceState &I = st->it[lane + 1];
-    if (I.active && !I.rook_done) outer = st->r[lane + 2];
+    act = I.active && !I.rook_done;
+    r1 = st->r[lane + 1];
+    r2 = st->r[lane + 2];
     Nl = D.N[lane + 1];
   }
+  if (stop || !search) return;
+  const int outer = act ? r2 : 0;
   RookDeal dl = rook_deal(D, outer, Nl);
   unsigned long long fl = 0;
   int zk = 0;
@@ -1810,12 +1825,11 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);
     IfaceState &I = st->it[k];
-    const int rk = st->r[k], rn = st->r[k + 1];
-    const int Nk = D.N[k - 1], Nk1 = D.N[k], rows = (Nk1 + 31) >> 5;
+    const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rn = __shfl_sync(0xffffffffu, r2, k - 1);
+    const int Nk1 = D.N[k], rows = (Nk1 + 31) >> 5;
     int beta, q0, nq;
     rook_piece(dl, k, rn, Nk1, beta, q0, nq);
     const int j0 = 32 * q0, j1 = min(Nk1, 32 * (q0 + nq)), slot0 = beta * rows + q0;
-    const int rho = I.row;
     double zr[TTQ_MAXR / 32];
     int rp[TTQ_MAXR / 32], rnd[TTQ_MAXR / 32];
     const bool newz = k != zk;
@@ -1827,15 +1841,14 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
       rnd[q] = b < rk ? D.rnode[k][b] : 0;
     }
     const int vr = (lane > k && lane < d) ? D.ridx[k + 1][beta * d + lane] : 0;
-    const int alpha = rho / Nk, i = rho % Nk;
-    const int vl = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : 0;
+    const int vl = (lane < k) ? I.fix[lane] : 0;
     if (newz) {
 #pragma unroll
       for (int q = 0; q < TTQ_MAXR / 32; ++q)
         if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
       zk = k;
     }
-    if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : (lane == k - 1 ? i : (lane > k ? vr : 0));
+    if (lane < d) sh.ms[warp][lane] = (lane < k) ? vl : vr;
     int nex = 0;
 #pragma unroll
     for (int q = 0; q < TTQ_MAXR / 32; ++q) {
