@@ -595,7 +595,7 @@ extern "C" int ttq_batch_create(const ttq_problem *probs, int count, void *works
 // One sweep for every instance: eval -> qr -> { contract (side stream) |
 // samples -> rook rounds } -> update.  Every launch covers all instances
 // (grid z); CTAs of instances or interfaces with no work exit at once.
-static void enqueue_sweep(ttq_plan *P) {
+static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
   cudaStream_t s = P->stream;
   const int ni = P->max_ni, nb = P->count;
   Dev *const *dv = P->devs;
@@ -609,7 +609,7 @@ static void enqueue_sweep(ttq_plan *P) {
   } else {
     timed(P, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
   }
-  timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), TTQ_WARPS * 32, 0, s>>>(dv); });
+  timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, 0, s, dv); });
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
   timed(P, KT_QR, [&] { launch_k(P, k_qr, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
   if (P->s2) {
@@ -630,15 +630,15 @@ static void enqueue_sweep(ttq_plan *P) {
     timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 2); });
   }
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
-  const int single_cond = P->in_loop && nb == 1;
+  const int single_cond = P->in_loop && loop_end && nb == 1;
   timed(P, KT_UPDATE, [&] { launch_k(P, k_update, dim3(1, 1, nb), T, 0, s, dv, P->cond, single_cond); });
-  if (P->in_loop && nb > 1) {
+  if (P->in_loop && loop_end && nb > 1) {
     launch_k(P, k_batch_cond, dim3(1), T, 0, s, dv, nb, P->max_sweeps, P->guard, P->cond);
     P->launches++;
   }
 }
 
-// Whole run as one graph: a conditional WHILE node whose body is one sweep;
+// Whole run as one graph: a conditional WHILE node whose body is two sweeps;
 // the condition is set on the device (k_update for one instance, k_batch_cond
 // for a batch), so a run needs no host round trip per sweep.
 static int build_run_graph(ttq_plan *P) {
@@ -663,9 +663,13 @@ static int build_run_graph(ttq_plan *P) {
   memcpy(n0, P->kt_n, sizeof(n0));
   P->cond = h;
   P->in_loop = 1;
+  // two sweeps per iteration: the condition is evaluated (and the body
+  // relaunched) half as often; a sweep that follows the stop finds it set and
+  // its kernels return at once
   e = cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    enqueue_sweep(P);
+    enqueue_sweep(P, false);
+    enqueue_sweep(P, true);
     e = cudaStreamEndCapture(P->stream, &body);
   }
   P->in_loop = 0;
