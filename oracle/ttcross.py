@@ -309,17 +309,24 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
         return None
     row, col = int(srows[t]), int(scols[t])
 
-    # rook pivoting: alternate column and row searches, Eq. (2)
+    # rook pivoting: alternate column and row searches until the rook condition,
+    # Eq. (2), holds.  It is tested after each search: a column search that
+    # returns the row searched in the previous round ends the search, since that
+    # row search returned the current column (the pivot already dominates its
+    # row and its column, and a repeated row search would return the same pivot).
     rows_all = np.arange(M)
     cols_all = np.arange(Ncol)
     err = 0.0
     rounds = 0
+    prev_row = -1
     for _ in range(max(1, problem.rook_max)):
         rounds += 1
         cscore = np.full(M, -1.0)
         cscore[row_ok] = np.abs(residual(rows_all[row_ok], np.full(int(row_ok.sum()), col)))
         evals += int(row_ok.sum())
         row = tie_argmax(cscore, scale)
+        if row == prev_row:
+            break
         rres = np.zeros(Ncol)
         rres[col_ok] = residual(np.full(int(col_ok.sum()), row), cols_all[col_ok])
         evals += int(col_ok.sum())
@@ -328,6 +335,7 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
         err = float(rres[new_col])
         if new_col == col:
             break
+        prev_row = row
         col = new_col
     accepted = abs(err) > problem.pivot_tol * scale and rk < problem.rank_cap
     return Pivot(k=k, row=row, col=col, err=err, accepted=bool(accepted), rounds=rounds, evals=evals)

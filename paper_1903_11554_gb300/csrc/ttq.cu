@@ -623,15 +623,19 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
   // the samples stage ends, per interface, in its last CTA (the best sample and
   // the first column solve); each rook step is followed by the decisions kernel
   timed(P, KT_SAMPLES, [&] { launch_k(P, k_samples, dim3(P->sblocks, ni, nb), W, P->samples_smem, s, dv); });
-  for (int q = 0; q < P->rook_max; ++q) {
-    timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
-    timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 1); });
-    timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv); });
-    timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 2); });
-  }
-  if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
+  // the last decisions kernel also ends the sweep (appends, ranks, stopping
+  // rules, the WHILE condition), after the contraction has joined
   const int single_cond = P->in_loop && loop_end && nb == 1;
-  timed(P, KT_UPDATE, [&] { launch_k(P, k_update, dim3(1, 1, nb), T, 0, s, dv, P->cond, single_cond); });
+  for (int q = 0; q < P->rook_max; ++q) {
+    const bool fin = q == P->rook_max - 1;
+    timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
+    timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 1, 0, P->cond, 0); });
+    timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv); });
+    if (fin && P->s2) cudaStreamWaitEvent(s, P->join, 0);
+    timed(P, fin ? KT_UPDATE : KT_SOLVE, [&] {
+      launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 2, fin ? 1 : 0, P->cond, fin ? single_cond : 0);
+    });
+  }
   if (P->in_loop && loop_end && nb > 1) {
     launch_k(P, k_batch_cond, dim3(1), T, 0, s, dv, nb, P->max_sweeps, P->guard, P->cond);
     P->launches++;
@@ -639,7 +643,7 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
 }
 
 // Whole run as one graph: a conditional WHILE node whose body is two sweeps;
-// the condition is set on the device (k_update for one instance, k_batch_cond
+// the condition is set on the device (the last decisions kernel of the sweep for one instance, k_batch_cond
 // for a batch), so a run needs no host round trip per sweep.
 static int build_run_graph(ttq_plan *P) {
   cudaGraph_t g = nullptr;

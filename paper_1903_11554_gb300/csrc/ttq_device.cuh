@@ -62,11 +62,12 @@ struct State {
   int nonfinite;
   int singular;
   int nchanges;
-  int stop_pending;         // a stopping rule fired in this sweep's contraction; applied by k_update
+  int stop_pending;         // a stopping rule fired in this sweep's contraction; applied at the end of the sweep
   int loop_guard;           // sweeps run by the device-side loop of this run (bounded by max_sweeps)
   unsigned batch_guard;     // sweeps run by a batch's loop (used in instance 0 of a batch)
   int pending_status;
   unsigned contract_arrive;  // CTAs of the two contraction chains that have finished
+  unsigned end_arrive;      // CTAs of the last decisions kernel through the end of the sweep
   int qr_rank[TTQ_MAXD];    // size of the stored QR factors of G_k (0: none)
   int qr_row[TTQ_MAXD];     // rank whose row append is done (k_qr_row), 0: none pending
   unsigned long long scale_bits;   // max |core entry| as IEEE bits (non-negative)

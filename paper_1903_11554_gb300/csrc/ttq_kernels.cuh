@@ -2,15 +2,18 @@
 //
 // Per sweep, in stream order:
 //   k_eval_slabs  evaluate the core entries that are new since the last sweep
-//                 (one warp per fiber; node sums V_k on the fly)          [kernel (a)]
-//   k_qr          Householder QR of every cross matrix G_k = A(I<=k, I>k),
-//                 one CTA per interface                                    [kernel (b)]
+//                 (fibers split into rows of 32 nodes; node sums V_k)     [kernel (a)]
+//   k_qr_row,     QR factors of every cross matrix G_k = A(I<=k, I>k), one CTA
+//   k_qr          per interface: bordering by the new row (beside kernel (a))
+//                 and the new column, full Householder when none stored [kernel (b)]
 //   k_contract    x <- V_1; x <- x G_k^-1; x <- x V_{k+1}: the product of
 //                 2d-1 matrices of Sec. 4.1, FP64 or double-double        [kernel (c)]
 //   k_samples     Alg. 2, first step: residuals at seeded random positions
 //   k_rook_col    Alg. 2, column step: residual on a whole column of the superblock
+//   k_solve       argmax pass 2, search state, the next step's solve
 //   k_rook_row    Alg. 2, row step: residual on a whole row (rook test, Eq. 2)
-//   k_update      append the accepted pivots to the nested sets (Alg. 6, end of sweep)
+//   k_solve       ... and, the last one, the end of the sweep: the accepted
+//                 pivots appended to the nested sets (Alg. 6), ranks, stopping rules
 // Every reduction (argmax, sums) runs in a fixed order, so two runs are bitwise equal.
 #pragma once
 #include "ttq_device.cuh"
@@ -1183,7 +1186,8 @@ __device__ __forceinline__ void build_ptab(const Dev &D, int k, bool col, const 
 //   mode 0, after the random samples: (rho*, gamma*) of the best sample; column
 //           solve z = G^-1 y, y = R_{k+1}(:, gamma*) = Y_{k+1}(:, j, beta).
 //   mode 1, after a column step: rho* = argmax over E(:, gamma*); row solve
-//           b = G^-T l, l = L_k(rho*, :)^T = Y_k(alpha, i, :).
+//           b = G^-T l, l = L_k(rho*, :)^T = Y_k(alpha, i, :), unless rho* is
+//           the previous round's row (the rook test, Eq. 2, then ends the search).
 //   mode 2, after a row step: gamma_new = argmax over E(rho*, :); the rook test
 //           (Eq. 2) or the round limit ends the search, else the next column solve.
 // The solve's result goes to zvec[k]; the row solve also keeps R^-T l in pvec[k]
@@ -1219,11 +1223,18 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     }
   } else if (mode == 1) {
     const int pick = stage_pick(D, k, 1, &e, qb);
+    const int prev = I.row, done_rounds = I.rounds;
+    __syncthreads();                             // every thread has read the previous row
+    // Eq. 2 already holds when the column search returns the row searched in the
+    // previous round: that search returned the current column, so the pivot
+    // dominates its row and its column and the search ends without a row search
+    const bool rook = pick >= 0 && done_rounds >= 1 && pick == prev;
     if (tid == 0) {
       if (pick < 0) I.active = 0;
+      else if (rook) { I.rounds = done_rounds + 1; I.rook_done = 1; }
       else I.row = pick;
     }
-    row = pick;
+    row = rook ? -1 : pick;
   } else {
     const int pick = stage_pick(D, k, 2, &e, qb);
     if (pick < 0) {
@@ -1287,12 +1298,90 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   __syncthreads();
 }
 
+// End of the sweep (Alg. 6), in the last decisions kernel of the search: every
+// CTA appends its interface's accepted pivot (new row alpha* + i* of I<=k, new
+// column j* + beta* of I>k, nested by construction; the neighbours' sets are
+// read below their current ranks, which no CTA changes before all have
+// arrived), then the last CTA of the instance to arrive applies the ranks, the
+// stopping rules and the sweep count and, inside the whole-run graph, sets the
+// WHILE condition: continue while the run is not over, never past max_sweeps.
+__device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHandle h, int use_cond) {
+  State *st = D.st;
+  const int d = D.d, tid = threadIdx.x, lane = lane_id();
+  __shared__ int last_s, nacc_s;
+  __shared__ unsigned long long ev_s;
+  const bool append = !st->stop && !st->stop_pending && st->search;   // changed below by the last CTA only
+  if (append && mine && warp_id() == 0) {
+    IfaceState &I = st->it[k];
+    const double scale = __longlong_as_double((long long)st->scale_bits);
+    const int a = st->r[k];
+    const bool acc = I.active && fabs(I.err) > D.pivot_tol * scale && a < D.cap;
+    if (lane == 0 && I.active) I.accepted = acc ? 1 : 0;
+    if (acc) {
+      const int Nk = D.N[k - 1], rn = st->r[k + 1];
+      const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
+      if (lane < d) {
+        const int m = lane;
+        D.lidx[k][(size_t)a * d + m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
+        D.ridx[k][(size_t)a * d + m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
+      }
+      if (lane == 0) {
+        D.lpar[k][a] = alpha; D.lnode[k][a] = i;
+        D.rpar[k][a] = beta; D.rnode[k][a] = j;
+      }
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    last_s = (atomicAdd(&st->end_arrive, 1u) == gridDim.x - 1) ? 1 : 0;
+    nacc_s = 0;
+    ev_s = 0ULL;
+  }
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  if (append) {
+    // a thread per interface: its rank, the sweep's evaluations, the accepted count
+    for (int q = tid + 1; q <= d - 1; q += blockDim.x) {
+      const IfaceState &I = st->it[q];
+      atomicAdd(&ev_s, I.evals);
+      if (I.active && I.accepted) {
+        st->r[q] += 1;
+        atomicAdd(&nacc_s, 1);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    st->end_arrive = 0;
+    if (st->stop) {
+    } else if (st->stop_pending) {
+      st->stop = 1;
+      st->status = st->pending_status;
+    } else if (!st->search) {
+      st->sweep++;
+    } else {
+      st->search_evals += (long long)ev_s;
+      if (st->rules && nacc_s == 0) { st->stop = 1; st->status = ST_NO_PIVOT; }
+      st->sweep++;
+    }
+    if (use_cond) {
+      const int guard = ++st->loop_guard;
+      const int cont = !st->stop && st->sweep < D.max_sweeps && guard < D.max_sweeps + 2;
+      cudaGraphSetConditional(h, cont ? 1u : 0u);
+    }
+  }
+}
+
 // The decisions after a rook step (modes 1 and 2 of stage_finish), one CTA per
 // interface.  The rank and the factors are fixed from kernel (b) to the end of
 // the search, so their copies to shared memory are issued before the wait for
 // the preceding rook step: they overlap its tail (the rook step streams the
 // cores through L2, so the factors come from DRAM) instead of delaying the argmax.
-__global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
+// fin: the search's last decisions kernel, which also ends the sweep (sweep_end).
+__global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fin, cudaGraphConditionalHandle h,
+                                               int use_cond) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
   State *st = D.st;
@@ -1310,11 +1399,11 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode) {
   }
   pdl_wait();
   pdl_release();
-  if (!mine || st->stop || !st->search || !st->it[k].active || st->it[k].rook_done) {
+  if (mine && !st->stop && st->search && st->it[k].active && !st->it[k].rook_done)
+    stage_finish(D, k, mode, Fs, Qs, sc.ri, sc, true);
+  else
     cp_async_wait_all();                         // no copy outlives the CTA
-    return;
-  }
-  stage_finish(D, k, mode, Fs, Qs, sc.ri, sc, true);
+  if (fin) sweep_end(D, k, mine, h, use_cond);
 }
 
 // per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
@@ -1879,73 +1968,6 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     __syncwarp();
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
-}
-
-// End of sweep (Alg. 6): append every accepted pivot, nested by construction.
-// Inside the whole-run graph it also sets the WHILE condition: continue while
-// the run is not over, never past max_sweeps (every path reaches the end).
-__global__ void k_update(Dev *const *Dps, cudaGraphConditionalHandle h, int use_cond) {
-  __shared__ Dev sD;
-  const Dev &D = stage_dev(Dps, sD);
-  pdl_wait();
-  pdl_release();
-  State *st = D.st;
-  const int d = D.d, lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5;
-  __shared__ int rold[TTQ_MAXD + 1];
-  __shared__ int nacc;
-  __shared__ unsigned long long ev;
-  __shared__ int mode;                      // 0: nothing to do, 1: apply pending stop, 2: no search, 3: append
-  if (threadIdx.x == 0) {
-    nacc = 0; ev = 0;
-    if (st->stop) mode = 0;
-    else if (st->stop_pending) mode = 1;
-    else if (!st->search) mode = 2;
-    else mode = 3;
-  }
-  __syncthreads();
-  if (mode == 1 && threadIdx.x == 0) { st->stop = 1; st->status = st->pending_status; }
-  if (mode == 2 && threadIdx.x == 0) st->sweep++;
-  if (mode == 3) {
-    for (int q = threadIdx.x; q <= d; q += blockDim.x) rold[q] = st->r[q];
-    __syncthreads();
-    const double scale = __longlong_as_double((long long)st->scale_bits);
-    // one warp per interface, lanes over the modes of the new index tuples
-    for (int k = warp + 1; k <= d - 1; k += nw) {
-      IfaceState &I = st->it[k];
-      const bool acc = I.active && fabs(I.err) > D.pivot_tol * scale && rold[k] < D.cap;
-      if (lane == 0) {
-        atomicAdd(&ev, I.evals);
-        if (I.active) I.accepted = acc ? 1 : 0;
-        if (acc) atomicAdd(&nacc, 1);
-      }
-      if (!acc) continue;
-      const int Nk = D.N[k - 1], rn = rold[k + 1];
-      const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
-      const int a = rold[k];
-      if (lane < d) {
-        const int m = lane;
-        D.lidx[k][(size_t)a * d + m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
-        D.ridx[k][(size_t)a * d + m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
-      }
-      if (lane == 0) {
-        D.lpar[k][a] = alpha; D.lnode[k][a] = i;
-        D.rpar[k][a] = beta; D.rnode[k][a] = j;
-      }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x + 1; k <= d - 1; k += blockDim.x)
-      if (st->it[k].active && st->it[k].accepted) st->r[k] = rold[k] + 1;
-    if (threadIdx.x == 0) {
-      st->search_evals += (long long)ev;
-      if (st->rules && nacc == 0) { st->stop = 1; st->status = ST_NO_PIVOT; }
-      st->sweep++;
-    }
-  }
-  if (use_cond && threadIdx.x == 0) {
-    const int guard = ++st->loop_guard;
-    const int cont = !st->stop && st->sweep < D.max_sweeps && guard < D.max_sweeps + 2;
-    cudaGraphSetConditional(h, cont ? 1u : 0u);
-  }
 }
 
 __global__ void k_begin(Dev *const *Dps, int sweep, int rules, int search) {
