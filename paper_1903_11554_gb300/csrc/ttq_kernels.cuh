@@ -1439,8 +1439,59 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
 // sample forms z = G_k^-1 R_{k+1}(:, gamma_t) = R^-1 (Q^T y) (rows of Q^T y and
 // of the back substitution split over the group, so one warp instruction of the
 // sequential substitution serves TTQ_SPW samples) and E = A - L_k(rho_t, :) z.
+#ifndef TTQ_SG
 #define TTQ_SG 8
+#endif
 #define TTQ_SPW (32 / TTQ_SG)
+// One sample's interpolant L_k(rho, :) G_k^-1 y by a group of TTQ_SG lanes, with
+// the group's vector in registers: lane gl holds rows gl + TTQ_SG m, m < NB
+// (NB = the row blocks of r_k <= TTQ_SG NB).  t = Q^T y is formed for all of a lane's rows in
+// one pass over y, the back substitution with R D^-1 takes its pivot value
+// from the lane that holds it (a shuffle within the group) and updates the
+// rows above it, and z = D^-1 t meets the row l = L_k(rho, :) in the lane's
+// partial dot product.  Every entry sees the same multiply-adds in the same
+// order as in the shared-memory form, so the results are the same bits.
+// Qs: Q row-major, Rs: R D^-1 column-major, both leading dimension rk; y: the
+// group's right-hand side (shared); lrow(b) = L_k(rho, b).
+template <int NB>
+__device__ __forceinline__ double group_interp(const double *Qs, const double *Rs, const double *ri,
+                                               const double *y, const double *lrow, size_t lst, int rk, bool ok) {
+  const int lane = lane_id(), gl = lane % TTQ_SG, gbase = lane & ~(TTQ_SG - 1);
+  double tq[NB];
+#pragma unroll
+  for (int m = 0; m < NB; ++m) tq[m] = 0.0;
+  for (int b = 0; b < rk; ++b) {                 // t = Q^T y
+    const double yb = y[b];
+    const double *Qb = Qs + b * rk + gl;
+#pragma unroll
+    for (int m = 0; m < NB; ++m)
+      if (m < NB - 1 || gl + TTQ_SG * m < rk) tq[m] = fma(Qb[TTQ_SG * m], yb, tq[m]);
+  }
+#pragma unroll
+  for (int m = NB - 1; m >= 0; --m) {            // back substitution: t_i -= C_ij t_j, j descending
+#pragma unroll
+    for (int sl = TTQ_SG - 1; sl >= 0; --sl) {
+      const int jj = TTQ_SG * m + sl;
+      if (jj >= rk) continue;
+      const double vj = __shfl_sync(0xffffffffu, tq[m], gbase + sl);
+      const double *Cj = Rs + (size_t)jj * rk + gl;
+#pragma unroll
+      for (int mm = 0; mm < m; ++mm) tq[mm] = fma(-Cj[TTQ_SG * mm], vj, tq[mm]);
+      if (gl < sl) tq[m] = fma(-Cj[TTQ_SG * m], vj, tq[m]);
+    }
+  }
+  double acc = 0.0;                              // L_k(rho, :) z, z = D^-1 t
+#pragma unroll
+  for (int m = 0; m < NB; ++m) {
+    const int b = gl + TTQ_SG * m;
+    if (m < NB - 1 || b < rk) {
+      const double zb = tq[m] * ri[b];
+      if (ok) acc = fma(lrow[(size_t)b * lst], zb, acc);
+    }
+  }
+  return acc;
+}
+
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) {
   // descriptor read in place: its shared-memory copy would cost the kernel its
   // second resident CTA per SM (R, Q and the group vectors fill the rest)
@@ -1481,7 +1532,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
   unsigned long long fl = 0;
   // tasks of TTQ_SPW samples dealt CTA-first, so the interface's CTAs (and the
   // SMs they share) carry counts that differ by one task at most
-  for (int task = warp * gridDim.x + blockIdx.x; task * TTQ_SPW < S; task += gridDim.x * TTQ_WARPS) {
+  const int ntask = (S + TTQ_SPW - 1) / TTQ_SPW;
+  for (int task = warp * gridDim.x + blockIdx.x; task < ntask; task += gridDim.x * TTQ_WARPS) {
     const int base = task * TTQ_SPW;
     // one lane per sample: draw and exclusion test
     int rho = 0, gam = 0, ok = 0;
@@ -1520,6 +1572,22 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
     if (!ok) A = 0.0;
     for (int b = gl; b < rk; b += TTQ_SG) y[b] = ok ? D.Y[k + 1][core_at(D, k + 1, b, j, beta)] : 0.0;
     __syncwarp();
+    const int nb = (rk + TTQ_SG - 1) / TTQ_SG;
+    double acc = 0.0;                             // L_k(rho, :) G_k^-1 y
+    if (Qs && nb <= 8) {                          // ranks up to 8 TTQ_SG in registers
+      const double *lrow = D.Y[k] + core_at(D, k, alpha, i, 0);
+      const size_t lst = (size_t)D.capL[k - 1] * Nk;
+      switch (nb) {
+        case 8: acc = group_interp<8>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 7: acc = group_interp<7>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 6: acc = group_interp<6>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 5: acc = group_interp<5>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 4: acc = group_interp<4>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 3: acc = group_interp<3>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 2: acc = group_interp<2>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        default: acc = group_interp<1>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+      }
+    } else {
     for (int r0 = gl; r0 < rk; r0 += TTQ_SG) {   // t = Q^T y
       double acc = 0.0;
       if (Qs) for (int b = 0; b < rk; ++b) acc = fma(Qs[b * rk + r0], y[b], acc);
@@ -1534,8 +1602,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
     }
     for (int b = gl; b < rk; b += TTQ_SG) y[b] = t[b] * ri[b];   // z = D^-1 t
     __syncwarp();
-    double acc = 0.0;                             // L_k(rho, :) z
     if (ok) for (int b = gl; b < rk; b += TTQ_SG) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], y[b], acc);
+    }
 #pragma unroll
     for (int o = TTQ_SG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (ok && gl == 0) {
