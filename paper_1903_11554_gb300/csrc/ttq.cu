@@ -90,6 +90,17 @@ static cudaEvent_t ev_get(ttq_plan *P) {
   return e;
 }
 
+// The second stream (QR row append, contraction) at the device's highest
+// priority, and graphs instantiated with their nodes' priorities: at the start
+// of a graph body the QR row kernel's CTAs are dispatched before kernel (a)'s,
+// instead of waiting behind them.
+static cudaError_t create_side_stream(cudaStream_t *s2) {
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e != cudaSuccess) return e;
+  return cudaStreamCreateWithPriority(s2, cudaStreamNonBlocking, hi);
+}
+
 // launch helper: counts the launch and, when timing, records events around it
 // Kernel launch in the sweep chain: with programmatic serialization (the next
 // kernel launches while this one drains; its pdl_wait orders the data), except
@@ -187,7 +198,7 @@ struct Layout {
   size_t vcnt[TTQ_MAXD + 1], vcnt_all, vcnt_bytes;   // fiber row counters: one region, zeroed at creation
   size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], Cc[TTQ_MAXD], Sr[TTQ_MAXD], rinv[TTQ_MAXD],
       zvec[TTQ_MAXD], pvec[TTQ_MAXD], ptab[TTQ_MAXD];
-  size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD];
+  size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD], zs[TTQ_MAXD];
   size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
   int sblocks, cblocks, rblocks;
@@ -253,6 +264,7 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     nc = nc > nrow ? nc : nrow;
     L->cs[k] = b.take(nc * 8);
     L->ce[k] = b.take(nc * 8);
+    L->zs[k] = b.take((size_t)samples_for(p, k) * cap * 8);
     // per-item maxima of a rook step: up to one item per row of 32 nodes
     const size_t nchk = (p->nodes_per_mode[k - 1] + 31) / 32;
     const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
@@ -347,6 +359,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
     D.pvec[k] = (double *)(base + L.pvec[k]);
     D.ptab[k] = (double *)(base + L.ptab[k]);
     D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
+    D.zs[k] = (double *)(base + L.zs[k]);
     D.im[k] = (double *)(base + L.im[k]);
   }
   for (int k = 1; k <= d; ++k) {
@@ -405,7 +418,9 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col, TTQ_WARPS * 32, 0) != cudaSuccess || occ < 1)
       occ = 1;
     const int slots = sms * occ;
-    if (count == 1) P->cblocks = slots;
+    // one instance: the resident slots less the two of the contraction chains,
+    // which may still run on the second stream when the first rook step starts
+    if (count == 1) P->cblocks = std::max(sms, slots - 2);
     else P->cblocks = std::min(P->cblocks, std::max(1, (slots + count - 1) / count));
     // evaluation kernel: the same deal, its grid the resident slots when one
     // instance runs less one slot per interface, so that the QR row appends
@@ -540,7 +555,7 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
     P->st = P->sts[0];
     P->guard = (unsigned *)((char *)P->sts[0] + offsetof(State, batch_guard));
     if ((e = set_smem_attributes(P)) == cudaSuccess &&
-        (e = cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = create_side_stream(&P->s2)) == cudaSuccess &&
         (e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming)) == cudaSuccess &&
         (e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming)) == cudaSuccess) {
       P->use_graph = s != nullptr ? 1 : 0;   // no capture on the legacy default stream
@@ -609,7 +624,13 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
   } else {
     timed(P, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
   }
-  timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, 0, s, dv); });
+  // kernel (a) overlaps its predecessor's tail (programmatic serialization)
+  // except as the first node of the run graph's body, where nothing precedes it
+  // and a plain launch lets the QR row kernel beside it start at once
+  if (P->in_loop && !loop_end)
+    timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, 0, s>>>(dv); });
+  else
+    timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, 0, s, dv); });
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
   timed(P, KT_QR, [&] { launch_k(P, k_qr, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
   if (P->s2) {
@@ -680,7 +701,7 @@ static int build_run_graph(ttq_plan *P) {
   P->sweep_kernels = (int)(P->launches - l0);
   P->launches = l0;
   memcpy(P->kt_n, n0, sizeof(n0));
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->run_exec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->run_exec, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) { g_last_error = std::string("run graph: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
   return TTQ_OK;
@@ -700,7 +721,7 @@ static int launch_sweep(ttq_plan *P) {
       const int nk = (int)(P->launches - l0);
       P->launches = l0;
       memcpy(P->kt_n, n0, sizeof(n0));
-      e = cudaGraphInstantiate(&P->sweep_exec, g, 0);
+      e = cudaGraphInstantiate(&P->sweep_exec, g, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) { g_last_error = std::string("sweep graph: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
       P->sweep_kernels = nk;
@@ -1296,7 +1317,7 @@ extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, v
   S->P.devs = S->devs;
   S->P.hst = S->hst;
   cudaError_t e;
-  if ((e = cudaStreamCreateWithFlags(&S->P.s2, cudaStreamNonBlocking)) != cudaSuccess ||
+  if ((e = create_side_stream(&S->P.s2)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&S->P.fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&S->P.join, cudaEventDisableTiming)) != cudaSuccess) {
     g_last_error = std::string("server setup: ") + cudaGetErrorString(e);

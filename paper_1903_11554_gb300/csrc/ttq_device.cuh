@@ -103,6 +103,7 @@ struct Dev {
   double *cbuf;             // the two contraction chains' vectors (hi, lo) x 2, cap each
   double *cs[TTQ_MAXD];     // per interface: scores |E| of the current candidates (-1: not eligible)
   double *ce[TTQ_MAXD];     // per interface: residuals E of the current candidates
+  double *zs[TTQ_MAXD];     // per interface: z = G^-1 y of every random sample, cap apart
   double *im[TTQ_MAXD];     // per interface: max score of each rook work item (-1: none eligible)
   State *st;
 };

@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
-  pdl_release();
+  // the successor (kernel b) is released at the end, not here: launched early
+  // its CTAs would take the resident slots left free for the QR row kernel
   State *st = D.st;
   if (st->stop) return;
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
@@ -458,6 +459,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
   if (lane == 0 && vmax > 0.0) atomic_max_nonneg(&st->scale_bits, vmax);
   if (__any_sync(0xffffffffu, bad) && lane == 0) st->nonfinite = 1;
   if (lane == 0 && fl) atomicAdd(&st->flops[0], fl);
+  pdl_release();
 }
 
 // Kernel (b), second half: QR factors G_k = Q R of every cross matrix
@@ -1211,9 +1213,10 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   const int fld = Fs ? r : ld;
   unsigned *qb = reinterpret_cast<unsigned *>(sc.part);   // free until the solve's products
   double e;
-  int col = -1, row = -1;
+  int col = -1, row = -1, spick = -1;
   if (mode == 0) {
     const int pick = stage_pick(D, k, 0, &e, qb);
+    spick = pick;
     if (pick >= 0) {
       const int Nk = D.N[k - 1], Nk1 = D.N[k], rn = st->r[k + 1];
       const unsigned long long sid = stream_id(st->sweep, k, 1);
@@ -1255,7 +1258,8 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   // items read them in their first round of loads
   if (colsolve) {
     const int rn = st->r[k + 1], j = col / rn, beta = col % rn;
-    for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
+    if (mode != 0)                               // after the samples the best sample's z is at hand
+      for (int b = tid; b < r; b += nt) v[b] = D.Y[k + 1][core_at(D, k + 1, b, j, beta)];
     nfm = D.d - k;                               // modes k .. d-1
     if (tid < nfm) {
       fm[tid] = tid == 0 ? j : D.ridx[k + 1][beta * D.d + k + tid];
@@ -1272,7 +1276,10 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   }
   if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
-  if (colsolve) {
+  if (colsolve && mode == 0) {
+    for (int b = tid; b < r; b += nt) D.zvec[k][b] = D.zs[k][(size_t)spick * D.cap + b];
+    if (tab) build_ptab(D, k, true, fm, nfm);
+  } else if (colsolve) {
     // t = Q^T y (Q row-major: Q[b][i] at Q[b ld + i]), then R z = t
     if (Qs) cta_gemv(Qs, 1, r, v, r, sc.part, t);
     else cta_gemv(D.Qr[k], 1, ld, v, r, sc.part, t);
@@ -1292,7 +1299,7 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     for (int b = tid; b < r; b += nt) { D.zvec[k][b] = v[b]; D.pvec[k][b] = t[b]; }
     if (tid == 0) { I.prow = row; I.prank = r; }
   }
-  if ((colsolve || rowsolve) && tid == 0)
+  if (((colsolve && mode != 0) || rowsolve) && tid == 0)
     atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r) +
                                  (tab ? (unsigned long long)(colsolve ? D.N[k - 1] : D.N[k]) * nfm : 0ULL));
   __syncthreads();
@@ -1455,7 +1462,8 @@ __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, 
 // group's right-hand side (shared); lrow(b) = L_k(rho, b).
 template <int NB>
 __device__ __forceinline__ double group_interp(const double *Qs, const double *Rs, const double *ri,
-                                               const double *y, const double *lrow, size_t lst, int rk, bool ok) {
+                                               const double *y, const double *lrow, size_t lst, int rk, bool ok,
+                                               double *zrow) {
   const int lane = lane_id(), gl = lane % TTQ_SG, gbase = lane & ~(TTQ_SG - 1);
   double tq[NB];
 #pragma unroll
@@ -1486,7 +1494,10 @@ __device__ __forceinline__ double group_interp(const double *Qs, const double *R
     const int b = gl + TTQ_SG * m;
     if (m < NB - 1 || b < rk) {
       const double zb = tq[m] * ri[b];
-      if (ok) acc = fma(lrow[(size_t)b * lst], zb, acc);
+      if (ok) {
+        acc = fma(lrow[(size_t)b * lst], zb, acc);
+        zrow[b] = zb;
+      }
     }
   }
   return acc;
@@ -1574,18 +1585,20 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
     __syncwarp();
     const int nb = (rk + TTQ_SG - 1) / TTQ_SG;
     double acc = 0.0;                             // L_k(rho, :) G_k^-1 y
+    // the sample's z = G^-1 y is kept: the best sample's is the first rook step's
+    double *zrow = D.zs[k] + (size_t)(base + g) * D.cap;
     if (Qs && nb <= 8) {                          // ranks up to 8 TTQ_SG in registers
       const double *lrow = D.Y[k] + core_at(D, k, alpha, i, 0);
       const size_t lst = (size_t)D.capL[k - 1] * Nk;
       switch (nb) {
-        case 8: acc = group_interp<8>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        case 7: acc = group_interp<7>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        case 6: acc = group_interp<6>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        case 5: acc = group_interp<5>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        case 4: acc = group_interp<4>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        case 3: acc = group_interp<3>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        case 2: acc = group_interp<2>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
-        default: acc = group_interp<1>(Qs, Rs, ri, y, lrow, lst, rk, ok); break;
+        case 8: acc = group_interp<8>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        case 7: acc = group_interp<7>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        case 6: acc = group_interp<6>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        case 5: acc = group_interp<5>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        case 4: acc = group_interp<4>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        case 3: acc = group_interp<3>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        case 2: acc = group_interp<2>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+        default: acc = group_interp<1>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
       }
     } else {
     for (int r0 = gl; r0 < rk; r0 += TTQ_SG) {   // t = Q^T y
@@ -1600,7 +1613,10 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
       for (int r0 = gl; r0 < jj; r0 += TTQ_SG) t[r0] = fma(-Rs[r0 + jj * rk], vj, t[r0]);
       __syncwarp();
     }
-    for (int b = gl; b < rk; b += TTQ_SG) y[b] = t[b] * ri[b];   // z = D^-1 t
+    for (int b = gl; b < rk; b += TTQ_SG) {       // z = D^-1 t
+      y[b] = t[b] * ri[b];
+      if (ok) zrow[b] = y[b];
+    }
     __syncwarp();
     if (ok) for (int b = gl; b < rk; b += TTQ_SG) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], y[b], acc);
     }
