@@ -1404,9 +1404,14 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fi
     else stage_compact_async(Fs, D.Cc[k], Qs, D.Qr[k], r, ld);             // R D^-1 col-major, Q row-major
     for (int b = threadIdx.x; b < r; b += blockDim.x) cp_async8(sc.ri + b, D.rinv[k] + b);
   }
+  // the run flags and the interface's search state were last written two or
+  // more launches back (the previous decisions kernel, the samples' finisher,
+  // the end of the previous sweep), which had completed before the preceding
+  // rook step passed its own wait: they are read before this kernel's wait
+  const bool work = mine && !st->stop && st->search && st->it[k].active && !st->it[k].rook_done;
   pdl_wait();
   pdl_release();
-  if (mine && !st->stop && st->search && st->it[k].active && !st->it[k].rook_done)
+  if (work)
     stage_finish(D, k, mode, Fs, Qs, sc.ri, sc, true);
   else
     cp_async_wait_all();                         // no copy outlives the CTA
@@ -1507,8 +1512,9 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
   // descriptor read in place: its shared-memory copy would cost the kernel its
   // second resident CTA per SM (R, Q and the group vectors fill the rest)
   const Dev &D = *Dps[blockIdx.z];
-  pdl_wait();
-  pdl_release();
+  // the run flags, the ranks and the cross's parent pointers were last written
+  // at the end of the previous sweep, which had completed before kernel (b)
+  // passed its own wait: they are read before this kernel's wait
   State *st = D.st;
   const int k = blockIdx.y + 1;
   if (!iface_searchable(D, st, k)) return;
@@ -1527,13 +1533,15 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
   const int vst = D.cap + 1;                         // padded group vector stride
   double *yv = fac + (size_t)D.cap * D.cap * (D.q_in_smem ? 2 : 1) + (size_t)warp * TTQ_SPW * 2 * vst;
   double *y = yv + g * 2 * vst, *t = y + vst;        // this group's y (then z) and Q^T y
-  // R D^-1 (column-major) and Q copied asynchronously beside the loads of the cross
-  stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);
   for (int a = threadIdx.x; a < rk; a += blockDim.x) {
-    ri[a] = D.rinv[k][a];
     rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
     gset[a] = D.rnode[k][a] * rn + D.rpar[k][a];
   }
+  pdl_wait();
+  pdl_release();
+  // R D^-1 (column-major), Q and 1/R_jj from kernel (b), copied asynchronously
+  stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);
+  for (int a = threadIdx.x; a < rk; a += blockDim.x) cp_async8(ri + a, D.rinv[k] + a);
   cp_async_wait_all();
   __syncthreads();
   const unsigned long long sid = stream_id(st->sweep, k, 1);
