@@ -90,11 +90,14 @@ static cudaEvent_t ev_get(ttq_plan *P) {
   return e;
 }
 
-// The second stream (QR row append, contraction) at the device's highest
-// priority, and graphs instantiated with their nodes' priorities: at the start
-// of a graph body the QR row kernel's CTAs are dispatched before kernel (a)'s,
-// instead of waiting behind them.
-static cudaError_t create_side_stream(cudaStream_t *s2) {
+// The second stream (QR row append, contraction).  For one instance it runs
+// at the device's highest priority and graphs are instantiated with their
+// nodes' priorities: at the start of a graph body the QR row kernel's 11-odd
+// CTAs are dispatched before kernel (a)'s instead of waiting behind them.  For
+// a batch (hundreds of CTAs on the second stream, off the critical path) it
+// keeps the default priority.
+static cudaError_t create_side_stream(cudaStream_t *s2, bool high) {
+  if (!high) return cudaStreamCreateWithFlags(s2, cudaStreamNonBlocking);
   int lo = 0, hi = 0;
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
   if (e != cudaSuccess) return e;
@@ -555,7 +558,7 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
     P->st = P->sts[0];
     P->guard = (unsigned *)((char *)P->sts[0] + offsetof(State, batch_guard));
     if ((e = set_smem_attributes(P)) == cudaSuccess &&
-        (e = create_side_stream(&P->s2)) == cudaSuccess &&
+        (e = create_side_stream(&P->s2, count == 1)) == cudaSuccess &&
         (e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming)) == cudaSuccess &&
         (e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming)) == cudaSuccess) {
       P->use_graph = s != nullptr ? 1 : 0;   // no capture on the legacy default stream
@@ -1317,7 +1320,7 @@ extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, v
   S->P.devs = S->devs;
   S->P.hst = S->hst;
   cudaError_t e;
-  if ((e = create_side_stream(&S->P.s2)) != cudaSuccess ||
+  if ((e = create_side_stream(&S->P.s2, false)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&S->P.fork, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&S->P.join, cudaEventDisableTiming)) != cudaSuccess) {
     g_last_error = std::string("server setup: ") + cudaGetErrorString(e);
