@@ -902,30 +902,31 @@ extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
               (P->kt_ms[KT_ROOK_COL] - before[KT_ROOK_COL]) + (P->kt_ms[KT_ROOK_ROW] - before[KT_ROOK_ROW]);
     return TTQ_OK;
   };
+  // Each dimension in turn: the largest candidate whose time is within 3% of
+  // the fastest.  The trial sweeps are the first of the run (low ranks, where
+  // the grid size hardly matters and timing noise would decide), while the
+  // later, higher-rank sweeps that dominate a run gain from the larger grids.
   int rc = TTQ_OK;
-  double best = 1e300, ms = 0;
-  int bc = P->cblocks, bs = P->sblocks, be = P->grid_eval;
-  for (int c : cand_c) {
-    P->cblocks = P->rblocks = c;
-    if ((rc = time_cfg(&ms))) break;
-    if (ms < best) { best = ms; bc = c; }
-  }
+  auto pick = [&](const int *cand, int n, int *target, int *target2) -> int {
+    double t[8];
+    double best = 1e300;
+    for (int q = 0; q < n; ++q) {
+      *target = cand[q];
+      if (target2) *target2 = cand[q];
+      if ((rc = time_cfg(&t[q]))) return cand[0];
+      best = t[q] < best ? t[q] : best;
+    }
+    int chosen = cand[0];
+    for (int q = 0; q < n; ++q)
+      if (t[q] <= 1.03 * best && cand[q] > chosen) chosen = cand[q];
+    return chosen;
+  };
+  const int bc = pick(cand_c, 7, &P->cblocks, &P->rblocks);
   P->cblocks = P->rblocks = bc;
-  best = 1e300;
-  for (int sb : cand_s) {
-    if (rc) break;
-    P->sblocks = sb;
-    if ((rc = time_cfg(&ms))) break;
-    if (ms < best) { best = ms; bs = sb; }
-  }
+  int bs = P->sblocks, be = P->grid_eval;
+  if (!rc) bs = pick(cand_s, 5, &P->sblocks, nullptr);
   P->sblocks = bs;
-  best = 1e300;
-  for (int ge : cand_e) {
-    if (rc) break;
-    P->grid_eval = ge;
-    if ((rc = time_cfg(&ms))) break;
-    if (ms < best) { best = ms; be = ge; }
-  }
+  if (!rc) be = pick(cand_e, 4, &P->grid_eval, nullptr);
   P->grid_eval = be;
   P->timing = save_timing;
   for (int k = 0; k < KT_N; ++k) { P->kt_ms[k] = 0.0; P->kt_n[k] = 0; }
