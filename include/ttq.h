@@ -250,8 +250,10 @@ int ttq_plan_transfer_bytes(const ttq_plan *plan, int64_t *h2d, int64_t *d2h);
 
 /* Per-kernel timing.  With timing enabled every launch of a sweep is
  * bracketed by CUDA events on the plan's stream; ttq_plan_kernel_times writes,
- * for each of the TTQ_NUM_KERNELS kernels (index order: eval_slabs, qr,
- * contract, samples, rook_col, rook_row, update, init, setup, solve), the summed
+ * for each of the TTQ_NUM_KERNELS kernel kinds (index order: eval_slabs, qr
+ * (both halves of the QR update), contract, samples, rook_col, rook_row,
+ * update (the search's last decisions launch, which also ends the sweep),
+ * init, setup, solve (the other decisions launches)), the summed
  * device time in ms and the launch count since the last reset, and the
  * algorithmic FP64 operations the kernel has done since the plan's state was
  * last set (cumulative; a division, exp or cosh counts as one operation, an
