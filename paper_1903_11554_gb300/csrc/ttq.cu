@@ -613,7 +613,7 @@ extern "C" int ttq_batch_create(const ttq_problem *probs, int count, void *works
 // One sweep for every instance: eval -> qr -> { contract (side stream) |
 // samples -> rook rounds } -> update.  Every launch covers all instances
 // (grid z); CTAs of instances or interfaces with no work exit at once.
-static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
+static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) {
   cudaStream_t s = P->stream;
   const int ni = P->max_ni, nb = P->count;
   Dev *const *dv = P->devs;
@@ -630,7 +630,7 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
   // kernel (a) overlaps its predecessor's tail (programmatic serialization)
   // except as the first node of the run graph's body, where nothing precedes it
   // and a plain launch lets the QR row kernel beside it start at once
-  if (P->in_loop && !loop_end)
+  if (P->in_loop && head)
     timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, 0, s>>>(dv); });
   else
     timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, 0, s, dv); });
@@ -666,7 +666,7 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true) {
   }
 }
 
-// Whole run as one graph: a conditional WHILE node whose body is two sweeps;
+// Whole run as one graph: a conditional WHILE node whose body is four sweeps;
 // the condition is set on the device (the last decisions kernel of the sweep for one instance, k_batch_cond
 // for a batch), so a run needs no host round trip per sweep.
 static int build_run_graph(ttq_plan *P) {
@@ -691,11 +691,13 @@ static int build_run_graph(ttq_plan *P) {
   memcpy(n0, P->kt_n, sizeof(n0));
   P->cond = h;
   P->in_loop = 1;
-  // two sweeps per iteration: the condition is evaluated (and the body
-  // relaunched) half as often; a sweep that follows the stop finds it set and
-  // its kernels return at once
+  // four sweeps per iteration: the condition is evaluated (and the body
+  // relaunched, ~5 us) a quarter as often; a sweep that follows the stop finds
+  // it set and its kernels return at once
   e = cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
+    enqueue_sweep(P, false, true);
+    enqueue_sweep(P, false);
     enqueue_sweep(P, false);
     enqueue_sweep(P, true);
     e = cudaStreamEndCapture(P->stream, &body);

@@ -710,15 +710,20 @@ __global__ void __launch_bounds__(256) k_qr_row(Dev *const *Dps) {
 __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
+  // the run flag, the rank and the factors' rank were written in earlier
+  // sweeps, the row append's mark by k_qr_row (a full dependency of this
+  // launch): read before the wait for kernel (a)
+  State *st = D.st;
+  const int k = blockIdx.x + 1;
+  const bool mine = k <= D.d - 1;           // instances with fewer interfaces (batches)
+  const int stop = st->stop;
+  const int r = mine ? st->r[k] : 0;
+  const int have = mine ? st->qr_rank[k] : 0;
+  const int rowdone = mine ? st->qr_row[k] : 0;
   pdl_wait();
   pdl_release();
-  State *st = D.st;
-  if (st->stop) return;
+  if (stop || !mine) return;
   extern __shared__ double sm[];
-  const int k = blockIdx.x + 1;
-  if (k > D.d - 1) return;                  // instances with fewer interfaces (batches)
-  const int r = st->r[k];
-  const int have = st->qr_rank[k];
   if (threadIdx.x == 0) {
     IfaceState &I = st->it[k];
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
@@ -728,7 +733,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
     if (threadIdx.x == 0) st->it[k].prank = -1;
     return;
   }
-  if (have >= 1 && have == r - 1 && st->qr_row[k] == r) {
+  if (have >= 1 && have == r - 1 && rowdone == r) {
     __shared__ double part[4 * TTQ_MAXR];
     qr_border_col(D, k, r, sm, part);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * r * (double)r));
@@ -991,8 +996,10 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 // capacity before their counts are known) form one round, so a pick costs two
 // dependent rounds of global reads.  qbits: blockDim.x words of shared scratch
 // (stage 2 marks the qualifying items there, TTQ_MAXR * TTQ_MAX_NODES / 32 bits
-// at most).
-__device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigned *qbits) {
+// at most).  vrow (stage 1, may be null): L_k(rho*, :) (r entries) is read into
+// it by the warp that finds rho*, before the block learns the result.
+__device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigned *qbits, double *vrow = nullptr,
+                          int r = 0) {
   __shared__ int si[TTQ_WARPS];
   __shared__ double se[TTQ_WARPS];
   State *st = D.st;
@@ -1106,6 +1113,18 @@ __device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigne
           const long long v = __ldcg(csb + c);
           const double e = __ldcg(ce + c);
           if (v >= thrb && c < f) { f = c; fe = e; }
+        }
+      }
+      if (vrow) {                                // stage 1's answer is this warp's
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const int of = __shfl_xor_sync(0xffffffffu, f, o);
+          const double oe = __shfl_xor_sync(0xffffffffu, fe, o);
+          if (of < f) { f = of; fe = oe; }
+        }
+        if (f != 0x7fffffff) {
+          const int ai = f / Nm, ii = f % Nm;
+          for (int b = lane; b < r; b += 32) vrow[b] = D.Y[k][core_at(D, k, ai, ii, b)];
         }
       }
     }
@@ -1225,7 +1244,7 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
       if (tid == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
     }
   } else if (mode == 1) {
-    const int pick = stage_pick(D, k, 1, &e, qb);
+    const int pick = stage_pick(D, k, 1, &e, qb, v, r);   // L_k(rho*, :) lands in v
     const int prev = I.row, done_rounds = I.rounds;
     __syncthreads();                             // every thread has read the previous row
     // Eq. 2 already holds when the column search returns the row searched in the
@@ -1267,7 +1286,6 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     }
   } else if (rowsolve) {
     const int Nk = D.N[k - 1], alpha = row / Nk, i0 = row % Nk;
-    for (int b = tid; b < r; b += nt) v[b] = D.Y[k][core_at(D, k, alpha, i0, b)];
     nfm = k;                                     // modes 0 .. k-1
     if (tid < nfm) {
       fm[tid] = tid == k - 1 ? i0 : D.lidx[k - 1][alpha * D.d + tid];
