@@ -289,6 +289,22 @@ def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120
             "served_equal_alone_on_8": bool(same)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of a per-rank quantity over the process group (the slowest
+    rank sets the job's time); x itself when there is one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units every rank processed over the job's time."""
+    return units_per_rank * world / (ms / 1000.0)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -393,13 +409,10 @@ def main():
     ms = e0.elapsed_time(e1)
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
     launches = plan.launches - l0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = args.steps * world / (ms / 1000.0)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(args.steps, world, ms)
     n_eval = sum(r["n_eval"] for r in results)
-    evals_per_s = n_eval * world / (ms / 1000.0)
+    evals_per_s = job_rate(n_eval, world, ms)
 
     # ---- per-kernel device time (CUDA events around every launch on its stream)
     # and algorithmic FP64 operations, over ROOF_STEPS more whole integrals
@@ -459,8 +472,8 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = max(f0.elapsed_time(f1), (time.time() - t_host) * 1000.0)
-    e2e = {"value": e2e_steps * world / (e2e_ms / 1000.0), "unit": "integrals/s",
+    e2e_ms = max_over_ranks(max(f0.elapsed_time(f1), (time.time() - t_host) * 1000.0), dist, "cuda")
+    e2e = {"value": job_rate(e2e_steps, world, e2e_ms), "unit": "integrals/s",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
 
     systems = {}
