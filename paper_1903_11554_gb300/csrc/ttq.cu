@@ -268,7 +268,7 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     L->cs[k] = b.take(nc * 8);
     L->ce[k] = b.take(nc * 8);
     L->zs[k] = b.take((size_t)samples_for(p, k) * cap * 8);
-    // per-item maxima of a rook step: up to one item per row of 32 nodes
+    // per-row maxima of a rook step: one slot per outer index and row of 32 nodes
     const size_t nchk = (p->nodes_per_mode[k - 1] + 31) / 32;
     const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
     L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);

@@ -21,7 +21,7 @@
 #define TTQ_MAXD 32
 #define TTQ_MAXR 128
 #define TTQ_WARPS 8                      // warps per CTA in the fiber kernels
-#define TTQ_CHUNK 128                    // at most this many nodes per work item of the rook kernels
+#define TTQ_CHUNK 128                    // at most this many nodes per piece of work of the rook kernels
 #define TTQ_TIE_REL 1e-10                // Alg. 2 argmax: |E| >= max - (REL*max + ABS*scale) is a tie
 #define TTQ_TIE_ABS 1e-14
 #define TTQ_MAXPAIR 288                  // varying pairs of one cube-form fiber, <= (n/2)^2 for n <= 33
@@ -104,7 +104,7 @@ struct Dev {
   double *cs[TTQ_MAXD];     // per interface: scores |E| of the current candidates (-1: not eligible)
   double *ce[TTQ_MAXD];     // per interface: residuals E of the current candidates
   double *zs[TTQ_MAXD];     // per interface: z = G^-1 y of every random sample, cap apart
-  double *im[TTQ_MAXD];     // per interface: max score of each rook work item (-1: none eligible)
+  double *im[TTQ_MAXD];     // per interface: max score of each row of 32 rook candidates (-1: none eligible)
   State *st;
 };
 
