@@ -669,26 +669,51 @@ __device__ void qr_border_row(const Dev &D, int k, int r, double *sm) {
     }
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {  // the rotated block, for qr_border_col
+  // the rotated n x n block of R in every stored layout (the column append
+  // leaves it as it is and only adds the last column): 1/R_jj first
+  for (int j = tid; j < n; j += nt) {
+    const double rjj = Rs[j * ls + j];
+    if (!(fabs(rjj) > 0.0) || !isfinite(rjj)) D.st->singular = 1;
+    ri[j] = 1.0 / rjj;
+    D.rinv[k][j] = ri[j];
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e % n;
-    D.Rr[k][i * ld + j] = Rs[i * ls + j];
+    const double v = (i <= j) ? Rs[i * ls + j] : 0.0;
+    D.Rc[k][i + j * ld] = v;
+    D.Rr[k][i * ld + j] = v;
+    if (i < j) {
+      D.Cc[k][i + j * ld] = v * ri[j];
+      D.Sr[k][i * ld + j] = ri[i] * v;
+    }
   }
 }
 
-// second half of the bordering update: new column of R = Q'^T G(:, n)
+// second half of the bordering update: new column of R = Q'^T G(:, n), written
+// into every stored layout beside the block the row append stored
 __device__ void qr_border_col(const Dev &D, int k, int r, double *sm, double *part) {
-  const int n = r - 1, ls = r, ld = D.cap, tid = threadIdx.x, nt = blockDim.x;
-  double *Rs = sm;                       // r x r row-major (ld ls)
-  double *cn = Rs + (size_t)r * ls;      // new column of G (length r)
+  const int n = r - 1, ld = D.cap, tid = threadIdx.x, nt = blockDim.x;
+  double *cn = sm;                       // new column of G (length r)
   double *v = cn + r;                    // Q'^T cn
-  stage_block(Rs, D.Rr[k], nullptr, nullptr, n, ld, ls);
   for (int a = tid; a < r; a += nt) cn[a] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], n)];
   __syncthreads();
   cta_gemv(D.Qr[k], 1, ld, cn, r, part, v);   // v[a] = sum_i Q'[i][a] cn[i]
-  for (int a = tid; a < r; a += nt) Rs[a * ls + n] = v[a];
-  for (int j = tid; j < n; j += nt) Rs[n * ls + j] = 0.0;
-  __syncthreads();
-  qr_store_R(D, k, r, Rs, ls, true);
+  const double rnn = v[n];
+  if (tid == 0 && (!(fabs(rnn) > 0.0) || !isfinite(rnn))) D.st->singular = 1;
+  const double rinn = 1.0 / rnn;
+  if (tid == 0) D.rinv[k][n] = rinn;
+  for (int a = tid; a <= n; a += nt) {
+    const double va = v[a];
+    D.Rc[k][a + n * ld] = va;
+    D.Rr[k][a * ld + n] = va;
+    if (a < n) {
+      D.Cc[k][a + n * ld] = va * rinn;
+      D.Sr[k][a * ld + n] = D.rinv[k][a] * va;
+      D.Rc[k][n + a * ld] = 0.0;             // below the diagonal
+      D.Rr[k][n * ld + a] = 0.0;
+    }
+  }
 }
 
 // Kernel (b), first half: the row append of every interface whose G_k grew by
