@@ -678,16 +678,21 @@ __device__ void qr_border_row(const Dev &D, int k, int r, double *sm) {
     D.rinv[k][j] = ri[j];
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e % n;
-    const double v = (i <= j) ? Rs[i * ls + j] : 0.0;
-    D.Rc[k][i + j * ld] = v;
-    D.Rr[k][i * ld + j] = v;
-    if (i < j) {
-      D.Cc[k][i + j * ld] = v * ri[j];
-      D.Sr[k][i * ld + j] = ri[i] * v;
+  // row-major layouts a warp per row, column-major ones a warp per column, so
+  // every store of a warp is contiguous
+  const int nw = nt >> 5;
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) {
+      const double v = (i <= j) ? Rs[i * ls + j] : 0.0;
+      D.Rr[k][i * ld + j] = v;
+      if (i < j) D.Sr[k][i * ld + j] = ri[i] * v;
     }
-  }
+  for (int j = warp; j < n; j += nw)
+    for (int i = lane; i < n; i += 32) {
+      const double v = (i <= j) ? Rs[i * ls + j] : 0.0;
+      D.Rc[k][i + j * ld] = v;
+      if (i < j) D.Cc[k][i + j * ld] = v * ri[j];
+    }
 }
 
 // second half of the bordering update: new column of R = Q'^T G(:, n), written
