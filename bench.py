@@ -114,62 +114,101 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------
-# CPU baseline: the oracle on a bounded sample of the workload
+# CPU baseline: the oracle, timed on a bounded sample of the workload
+#
+# A sample is a set of whole sweeps of the workload's stored oracle run
+# (tests/golden/oracle_full.json), spread evenly over its sweep range
+# (stratified: sweep s_q = floor((q + 1/2) S / K) of S, q = 0..K-1).  Each
+# sampled sweep starts from that run's own index sets at that sweep (the first
+# r_k(s) rows of its final nested sets: pivots are appended in order, so a
+# prefix is the state of an earlier sweep) and runs exactly as the oracle's
+# integrate() runs it: every core re-evaluated, the integral contracted, Alg. 2
+# on every interface, the pivots appended.  The K sweeps stand for K / S of an
+# integral, so integrals/s = (K / S) / (their summed wall time).  Every number
+# is a timed measurement; nothing is fitted or extrapolated.
 
-BASELINE_SNIPPET = r"""
-import json, sys, time
+SWEEP_SNIPPET = r"""
+import json, os, sys, time
 sys.path.insert(0, %(root)r)
 import numpy as np
 from oracle import ttcross
 from paper_1903_11554_gb300 import inputs
 p = {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16}[%(wl)r]()
-budget = %(budget)f
-st = ttcross.initial_state(p)
-rows = []
-t0 = time.time()
-for s in range(p.sweeps_limit()):
-    t = time.time()
-    value, cores, scale, piv = ttcross.sweep(p, st, s, search=True)
-    rows.append([s, max(st.ranks()), time.time() - t])
+g = json.load(open(os.path.join(%(root)r, "tests", "golden", "oracle_full.json")))[%(wl)r]
+ranks_at = g["history_ranks"]
+par = g["parents"]
+out = []
+for s in %(sweeps)r:
+    rk = ranks_at[s]
+    lp = [np.array(par["lpar"][k - 1][:rk[k]]) for k in range(1, p.d)]
+    ln = [np.array(par["lnode"][k - 1][:rk[k]]) for k in range(1, p.d)]
+    rp = [np.array(par["rpar"][k - 1][:rk[k]]) for k in range(1, p.d)]
+    rn = [np.array(par["rnode"][k - 1][:rk[k]]) for k in range(1, p.d)]
+    st = ttcross.from_parents(p, lp, ln, rp, rn)
+    assert st.ranks() == rk
+    t = time.perf_counter()
+    value, cores, scale, piv = ttcross.sweep(p, st, s, search=s < len(ranks_at) - 1)
     st = ttcross.apply_pivots(p, st, piv)
-    if time.time() - t0 > budget or all(x is None or not x.accepted for x in piv):
-        break
-print(json.dumps(rows))
+    dt = time.perf_counter() - t
+    out.append([s, max(rk), dt, repr(value) == g["history"][s]])
+    print(json.dumps(out[-1]), flush=True)
 """
 
 
-def cpu_baseline(wl, ranks_traj, budget):
-    """Time the oracle's first sweeps of the workload on one host core, fit
-    t(r) = a + b r^2 + c r^3 to the per-sweep times, and sum it over the rank
-    trajectory the GPU run took (the oracle re-evaluates its cores every sweep,
-    so its sweep cost grows with the rank)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    code = BASELINE_SNIPPET % {"root": ROOT, "wl": wl, "budget": budget}
-    t = time.time()
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=budget * 4 + 120)
-    wall = time.time() - t
-    rows = json.loads(out.stdout.strip().splitlines()[-1])
-    import numpy as np
-    r = np.array([row[1] for row in rows], dtype=float)
-    ts = np.array([row[2] for row in rows], dtype=float)
-    if len(rows) >= 3:
-        A = np.stack([np.ones_like(r), r ** 2, r ** 3], axis=1)
-        coef, *_ = np.linalg.lstsq(A, ts, rcond=None)
-        coef = np.maximum(coef, 0.0)
-        model = lambda x: coef[0] + coef[1] * x * x + coef[2] * x ** 3
-    else:
-        model = lambda x: ts.mean()
-    if len(ranks_traj) <= len(rows):
-        est = float(ts[:len(ranks_traj)].sum())
-    else:
-        est = float(ts.sum() + sum(model(x) for x in ranks_traj[len(rows):]))
-    return {"value": 1.0 / est, "unit": "integrals/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle sweeps 0..%d of the same workload (ranks 1..%d) timed in %.1f s on one host core; "
-                      "seconds per integral = measured sweeps + t(r) = a + b r^2 + c r^3 fitted to them, summed over "
-                      "the %d-sweep rank trajectory of the GPU run (%.0f s estimated)"
-                      % (len(rows) - 1, int(r.max()), float(ts.sum()), len(ranks_traj), est),
-            "seconds_sampled": round(wall, 1)}
+def stratified(total, k):
+    """Sweep indices of a stratified sample of k sweeps of a total-sweep run
+    (with repeats when k > total, so the sample still stands for k / total of it)."""
+    return [min(total - 1, int((q + 0.5) * total / k)) for q in range(k)]
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"host_cpus": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def oracle_sweeps(wl, sweeps, threads, timeout):
+    """Time the given sweeps of the workload's stored oracle run in a fresh
+    process (the oracle never shares a process with the GPU path); threads =
+    BLAS threads (the oracle's integrand evaluation is single-threaded numpy)."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    code = SWEEP_SNIPPET % {"root": ROOT, "wl": wl, "sweeps": list(sweeps)}
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+    rows = [json.loads(l) for l in out.stdout.splitlines() if l.startswith("[")]
+    if len(rows) != len(sweeps):
+        raise RuntimeError("oracle sweep timing failed: %s" % out.stderr[-2000:])
+    return rows
+
+
+def cpu_baseline(wl, k_sweeps=3):
+    """The oracle on one host core and on all of them (BLAS threads), each on
+    the same stratified sample of k_sweeps sweeps of the workload."""
+    g = golden(wl)
+    total = g["sweeps"]
+    sw = stratified(total, k_sweeps)
+    info = cpu_info()
+    res = {}
+    for label, th in (("one_core", 1), ("all_cores", info["host_cpus"] or 1)):
+        rows = oracle_sweeps(wl, sw, th, timeout=1800)
+        secs = sum(r[2] for r in rows)
+        res[label] = {"value": (len(rows) / total) / secs, "cores": th, "seconds": round(secs, 2),
+                      "sweeps_timed": [r[0] for r in rows], "ranks": [r[1] for r in rows],
+                      "values_equal_stored_run": all(r[3] for r in rows)}
+    one = res["one_core"]
+    return {"value": one["value"], "unit": "integrals/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle sweeps %s of the %d-sweep %s run (ranks %s), each from that run's own index sets at that "
+                      "sweep, timed on one host core in %.1f s; they stand for %d/%d of an integral (stratified "
+                      "sample, no fit)" % (one["sweeps_timed"], total, wl, one["ranks"], one["seconds"],
+                                           len(one["sweeps_timed"]), total),
+            "all_cores": res["all_cores"], **info}
 
 
 # --------------------------------------------------------------------------
@@ -199,6 +238,66 @@ def measure_eval_full(plan, p, flush, reps=3):
             "peak_tflops": FP64_PEAK_TFLOPS, "frac": best["tflops"] / FP64_PEAK_TFLOPS,
             "note": "one launch evaluating every entry of the final D_12 cores (ranks %s), best of %d" % (
                 max(ranks), reps)}
+
+
+def measure_workload(binding, torch, name, steps, flush):
+    """Another configured workload (C_4 or E_16), timed like the headline one:
+    warm-up runs, then `steps` whole integrals enqueued back to back on the
+    plan's stream with the L2 flushed between them, CUDA events around them;
+    its error against the stored oracle run, and the oracle's own time on the
+    host (C_4: whole integrals on one core; E_16: a stratified two-sweep sample)."""
+    p = workload(name)
+    plan = binding.Plan(p)
+    stream = plan.stream
+    for q in range(3):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        plan.launch(q)
+    for q in range(3):
+        plan.result(q)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for q in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        plan.launch(q % 64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res = [plan.result(q) for q in range(min(steps, 64))]
+    ms = e0.elapsed_time(e1)
+    plan.close()
+    out = {"workload": workload_config(p)["workload"], "integrals_per_s": steps / (ms / 1000.0),
+           "ms_per_integral": ms / steps, "fiber_evals_per_s": res[-1]["n_eval"] * steps / (ms / 1000.0),
+           "value": res[-1]["value"], "value_lo": res[-1]["value_lo"], "status": res[-1]["status_name"],
+           "sweeps": res[-1]["sweeps"], "max_rank": res[-1]["max_rank"], "n_eval": res[-1]["n_eval"],
+           "runs_identical": all(r == res[0] for r in res)}
+    g = golden(name)
+    if g is not None:
+        ref = float(g["value"])
+        out["rel_err_vs_oracle"] = abs(res[-1]["value"] - ref) / abs(ref)
+        out["same_trajectory_as_oracle"] = (res[-1]["sweeps"], res[-1]["n_eval"]) == (g["sweeps"], g["n_eval"])
+        if name == "c4":
+            env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+            code = ("import sys, time, json; sys.path.insert(0, %r)\n"
+                    "from oracle import ttcross\nfrom paper_1903_11554_gb300 import inputs\n"
+                    "p = inputs.config_c4(); ttcross.integrate(p)\n"
+                    "t = time.perf_counter(); n = 0\n"
+                    "while time.perf_counter() - t < 5.0:\n    ttcross.integrate(p); n += 1\n"
+                    "print(json.dumps([n, time.perf_counter() - t]))" % ROOT)
+            o = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+            n, secs = json.loads(o.stdout.strip().splitlines()[-1])
+            out["cpu_oracle"] = {"value": n / secs, "unit": "integrals/s", "cores": 1,
+                                 "sample": "%d whole C_4 oracle integrals in %.1f s on one host core" % (n, secs)}
+        elif "history_ranks" in g:
+            rows = oracle_sweeps(name, stratified(g["sweeps"], 2), 1, timeout=1800)
+            secs = sum(r[2] for r in rows)
+            out["cpu_oracle"] = {"value": (len(rows) / g["sweeps"]) / secs, "unit": "integrals/s", "cores": 1,
+                                 "sample": "oracle sweeps %s of the %d-sweep run on one host core, %.1f s; they stand "
+                                           "for %d/%d of an integral" % ([r[0] for r in rows], g["sweeps"], secs,
+                                                                         len(rows), g["sweeps"])}
+    return out
 
 
 def measure_batched(binding, inputs, torch, count=256):
@@ -306,24 +405,36 @@ def job_rate(units_per_rank, world, ms):
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, on the host's cores (BLAS
+    threads = all of them), on the same workload.  A step is one whole sweep of
+    the workload's stored oracle run; the W warm-up steps are its first W sweeps,
+    the K timed steps a stratified sample of K sweeps (see cpu_baseline), so the
+    timed steps stand for K / S of an integral."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     p = workload(args.workload)
     g = golden(args.workload)
-    traj = list(range(1, (g["sweeps"] if g else p.rank_cap) + 1))
-    traj = [min(x, p.rank_cap) for x in traj]
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(args.workload, traj, budget=max(5.0, 60.0 / max(1, args.steps + args.warmup))))
-    timed = vals[args.warmup:]
-    v = statistics.median(x["value"] for x in timed)
+    total = g["sweeps"]
+    info = cpu_info()
+    threads = info["host_cpus"] or 1
+    warm = list(range(min(args.warmup, total)))
+    timed_sweeps = stratified(total, args.steps)
+    rows = oracle_sweeps(args.workload, warm + timed_sweeps, threads, timeout=7200)
+    timed = rows[len(warm):]
+    secs = sum(r[2] for r in timed)
+    v = (len(timed) / total) / secs
+    sample = ("%d whole sweeps of the %d-sweep oracle run of the workload (stratified: sweeps %s, ranks up to %d), "
+              "each from that run's own index sets at that sweep, %.1f s in all on %d host threads (BLAS); they stand "
+              "for %d/%d of an integral; %d warm-up sweeps before them"
+              % (len(timed), total, [r[0] for r in timed], max(r[1] for r in timed), secs, threads, len(timed), total,
+                 len(warm)))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "integrals/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(p),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": timed[0]["sample"], "value": v,
-                             "unit": "integrals/s"},
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": v, "unit": "integrals/s",
+                             "values_equal_stored_run": all(r[3] for r in timed), **info},
             "e2e": {"value": v, "unit": "integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -336,7 +447,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="d12", choices=["d12", "c4", "e16"])
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-sweeps", type=int, default=2, help="oracle sweeps in the cpu_baseline sample")
     ap.add_argument("--no-systems", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--launch-mode", default="graph", choices=["graph", "plain"],
@@ -476,6 +587,10 @@ def main():
     e2e = {"value": job_rate(e2e_steps, world, e2e_ms), "unit": "integrals/s",
            "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
 
+    others = {}
+    if args.workload == "d12" and args.launch_mode == "graph":
+        for name in ("c4", "e16"):
+            others[name] = measure_workload(binding, torch, name, max(3, min(args.steps, 20)), flush)
     systems = {}
     if not args.no_systems and args.launch_mode == "graph":
         del plan
@@ -494,9 +609,9 @@ def main():
         ref = float(g["value"])
         check = {"oracle_value": ref, "rel_err_vs_oracle": abs(results[-1]["value"] - ref) / abs(ref),
                  "oracle_sweeps": g["sweeps"], "oracle_seconds": g.get("oracle_seconds")}
-    traj = list(range(1, results[-1]["sweeps"] + 1))
-    traj = [min(x, p.rank_cap) for x in traj]
-    cpu = cpu_baseline(args.workload, traj, args.cpu_budget)
+    g = golden(args.workload)
+    cpu = cpu_baseline(args.workload, args.cpu_sweeps) if (g and "history_ranks" in g and args.cpu_sweeps > 0) \
+        else None
     line = {
         "metric": METRIC, "value": value, "unit": "integrals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -509,6 +624,7 @@ def main():
                    "n_eval": results[-1]["n_eval"], "internal_conv": results[-1]["internal_conv"], **check},
         "roofline": roof, "eval_full_cores": eval_full, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
+        **others,
         **systems,
     }
     print(json.dumps(line), flush=True)

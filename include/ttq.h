@@ -71,6 +71,7 @@ typedef enum {
 #define TTQ_MAX_MODES 32      /* d <= 32 */
 #define TTQ_MAX_RANK 128      /* rank cap <= 128 */
 #define TTQ_MAX_NODES 2048    /* N_k <= 2048 */
+#define TTQ_MAX_INIT_SAMPLES 1024
 
 /* The problem statement (Sec. 4.1: integrand, per-mode nodes and weights;
  * Alg. 6 inputs: rank cap and stopping tolerance). */
@@ -91,8 +92,10 @@ typedef struct ttq_problem {
   uint64_t seed;              /* counter-based SplitMix64 key of the random samples */
   int32_t n_samples;          /* random samples per interface; 0 -> N_k + N_{k+1} */
   int32_t rook_max;           /* column/row rounds of rook pivoting, >= 1 */
-  int32_t init_samples;       /* random points scanned for the first pivot, >= 1 */
+  int32_t init_samples;       /* random points scanned for the initial multi-indices, 1..TTQ_MAX_INIT_SAMPLES */
   int32_t precision;          /* ttq_precision */
+  int32_t r0;                 /* initial multi-indices (the rank of every interface before the first sweep),
+                                 1..rank_cap and at most min(N_1, N_d, init_samples); 0 is taken as 1 */
 } ttq_problem;
 
 typedef struct ttq_result {
@@ -103,12 +106,13 @@ typedef struct ttq_result {
   int32_t sweeps;             /* sweeps run (each with its own integral value) */
   int32_t max_rank;
   int32_t status;             /* ttq_status of the run */
-  int32_t reserved;
+  int32_t d;                  /* number of modes */
+  int32_t ranks[TTQ_MAX_MODES + 1];   /* final TT ranks r_0 = 1, r_1 .. r_{d-1}, r_d = 1 (entries past d are 0) */
 } ttq_result;
 
 /* Per-interface outcome of one pivot search (Alg. 2 on superblock k).  The
  * argmax of every step treats candidates whose |E| lies within
- * 1e-10 * max + 1e-14 * max|core entry| of the maximum as tied and takes the
+ * 1e-12 * max + 1e-14 * max|core entry| of the maximum as tied and takes the
  * first in scan order (the paper does not define ties). */
 typedef struct ttq_pivot {
   int32_t k;                  /* interface 1..d-1 */
@@ -151,6 +155,29 @@ int ttq_plan_run(ttq_plan *plan, ttq_result *out);
  * ttq_plan_launch runs synchronously. */
 int ttq_plan_launch(ttq_plan *plan, int slot);
 int ttq_plan_result(ttq_plan *plan, int slot, ttq_result *out);
+
+/* --- the tensor train as a result ------------------------------------------
+ * Alg. 6 returns the TT cross itself: the cores Y_k = A(I<=k-1, i_k, I>k)
+ * (Eq. 3, weights folded, Sec. 4.1) and the nested index sets (Eq. 4) that
+ * define them.  ttq_tt_export copies one instance's tensor train, for the
+ * ranks of its last evaluated sweep, from the plan's workspace into a
+ * caller-owned device buffer (>= ttq_tt_bytes, 256-byte aligned) and returns a
+ * handle; it blocks until the copy is done, and the handle stays valid until
+ * ttq_tt_free, whatever the plan does afterwards (the buffer stays the
+ * caller's: free it after ttq_tt_free).  ttq_tt_get gives, for k = 1..d, the
+ * shape and device pointers of core k (row-major r_{k-1} x N_k x r_k
+ * doubles, family constant not included), of I<=k-1 (row-major
+ * r_{k-1} x (k-1) int32 node indices of modes 1..k-1; NULL for k = 1) and of
+ * I>k (row-major r_k x (d-k) node indices of modes k+1..d; NULL for k = d).
+ * The integral is the product of 2d-1 matrices built from these (Sec. 4.1).
+ * instance: 0 for a single plan, 0..count-1 for a batch. */
+typedef struct ttq_tt ttq_tt;
+int ttq_tt_bytes(ttq_plan *plan, int instance, size_t *bytes);
+int ttq_tt_export(ttq_plan *plan, int instance, void *buffer, size_t bytes, ttq_tt **out);
+int ttq_tt_get(const ttq_tt *tt, int k, int32_t *r_left, int32_t *n_k, int32_t *r_right, const double **core_dev,
+               const int32_t **left_idx_dev, const int32_t **right_idx_dev);
+int ttq_tt_ranks(const ttq_tt *tt, int32_t *d, int32_t *ranks /* [d+1] */);
+int ttq_tt_free(ttq_tt *tt);
 
 /* --- batches ---------------------------------------------------------------
  * Many integrals with uneven families, n, node counts and rank caps advance
@@ -273,8 +300,12 @@ int ttq_plan_kernel_times(ttq_plan *plan, double *ms, int64_t *launches, double 
  *    (ttq_workspace_bytes) is rejected with TTQ_ERR_WORKSPACE.
  *  - nodes/weights must be host arrays (inputs_on_device == 0).
  *  - The first call on a device looks up the scratch's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current, once per device for
+ *    the life of the process; make that first call before any stream capture
+ *    starts, and do not reset the device (cudaDeviceReset) between calls.
+ *  - The call waits for its stream and copies from host memory on its own
+ *    stack; on a stream that is capturing it returns TTQ_ERR_INVALID_ARG
+ *    before doing any CUDA work, so the caller's capture is left intact.
  *  - Every call on a device uses the same scratch, which keeps the previous
  *    call's contents (the call resets what it reads).  Calls that overlap on
  *    the GPU (other streams, other host threads) race on it: serialize them.

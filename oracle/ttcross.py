@@ -16,8 +16,14 @@ Follows the paper step by step:
     (sum_i A(i, I_>1)) G_1^-1 (sum_i A(I_<=1, i, I_>2)) ... (sum_i A(I_<=d-1, i)).
 
 Readings where the paper is silent:
-  * initial index set: one multi-index, the largest |A| among `init_samples`
-    seeded random points (first in draw order on ties);
+  * initial index sets (Alg. 6 needs nested sets to start from): r0 seeded
+    random multi-indices x^(1..r0), I_<=k = their prefixes of length k and
+    I_>k = their suffixes from mode k+1, in the order chosen (nested by
+    construction).  They are taken from `init_samples` seeded random points in
+    decreasing |A| (ties by draw order), skipping a point whose first or last
+    node index equals that of a point already taken (then all its prefixes and
+    suffixes are new, so every interface has rank r0) or whose value is not
+    finite and nonzero; r0 = 1 is the single largest |A|;
   * random samples: `samples_for(k)` draws per interface from the counter-based
     SplitMix64 of oracle/rng.py, keyed by (seed, sweep, k); samples that land
     in a row or column of the current cross are skipped (the error is zero
@@ -45,7 +51,7 @@ import numpy as np
 from . import rng
 from .integrands import family_constant, tensor_entries
 
-TIE_REL = 1e-10
+TIE_REL = 1e-12
 TIE_ABS = 1e-14
 
 STATUS_CONVERGED = 0
@@ -346,19 +352,34 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
 # ---------------------------------------------------------------------------
 
 def initial_state(problem) -> CrossState:
-    """One seeded multi-index: the largest |A| among init_samples random points."""
+    """r0 seeded multi-indices: the init_samples random points in decreasing
+    |A| (ties by draw order), each kept when its first and last node indices
+    differ from those of the points already kept, until r0 are kept; their
+    prefixes and suffixes are the initial nested sets (Eq. 4)."""
     d = problem.d
+    r0 = getattr(problem, "r0", 1)
     stream = rng.stream_id(0, 0, rng.PURPOSE_INIT)
     pts = np.array([[rng.draw_index(problem.seed, stream, p * d + k, problem.N[k]) for k in range(d)]
                     for p in range(problem.init_samples)], dtype=np.int64)
     vals = np.abs(eval_points(problem, pts))
     vals = np.where(np.isfinite(vals), vals, -1.0)
-    p = int(np.argmax(vals))
-    if not vals[p] > 0:
-        raise ValueError("no nonzero entry among the initial samples")
-    x = pts[p]
-    left = [x[:k].reshape(1, k).copy() for k in range(d)]
-    right = [np.zeros((0, d), dtype=np.int64)] + [x[k:].reshape(1, d - k).copy() for k in range(1, d + 1)]
+    order = sorted(range(len(pts)), key=lambda p: (-vals[p], p))
+    chosen: List[int] = []
+    for p in order:
+        if not vals[p] > 0:
+            break
+        if any(pts[p][0] == pts[q][0] or pts[p][d - 1] == pts[q][d - 1] for q in chosen):
+            continue
+        chosen.append(p)
+        if len(chosen) == r0:
+            break
+    if len(chosen) < r0:
+        raise ValueError("fewer than r0 usable initial points among the initial samples")
+    X = pts[chosen]                                       # (r0, d)
+    left = [X[:, :k].copy() for k in range(d)]
+    right = [np.zeros((0, d), dtype=np.int64)] + [X[:, k:].copy() for k in range(1, d + 1)]
+    left[0] = np.zeros((1, 0), dtype=np.int64)
+    right[d] = np.zeros((1, 0), dtype=np.int64)
     return CrossState(left, right)
 
 

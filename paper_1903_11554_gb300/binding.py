@@ -32,13 +32,13 @@ class TTQProblem(_c.Structure):
                 ("inputs_on_device", _c.c_int32), ("rank_cap", _c.c_int32), ("tol", _c.c_double),
                 ("pivot_tol", _c.c_double), ("conv_window", _c.c_int32), ("max_sweeps", _c.c_int32),
                 ("seed", _c.c_uint64), ("n_samples", _c.c_int32), ("rook_max", _c.c_int32),
-                ("init_samples", _c.c_int32), ("precision", _c.c_int32)]
+                ("init_samples", _c.c_int32), ("precision", _c.c_int32), ("r0", _c.c_int32)]
 
 
 class TTQResult(_c.Structure):
     _fields_ = [("value", _c.c_double), ("value_lo", _c.c_double), ("internal_conv", _c.c_double),
                 ("n_eval", _c.c_int64), ("sweeps", _c.c_int32), ("max_rank", _c.c_int32),
-                ("status", _c.c_int32), ("reserved", _c.c_int32)]
+                ("status", _c.c_int32), ("d", _c.c_int32), ("ranks", _c.c_int32 * 33)]
 
 
 class TTQPivot(_c.Structure):
@@ -82,6 +82,12 @@ SIGNATURES = {
     "ttq_server_drain": (_c.c_int, [_vp, _c.POINTER(_c.c_uint64), _c.POINTER(TTQResult), _c.c_int,
                                     _c.POINTER(_c.c_int)]),
     "ttq_server_stats": (_c.c_int, [_vp, _c.POINTER(_c.c_int64)]),
+    "ttq_tt_bytes": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ttq_tt_export": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _c.POINTER(_vp)]),
+    "ttq_tt_get": (_c.c_int, [_vp, _c.c_int, _i32p, _i32p, _i32p, _c.POINTER(_vp), _c.POINTER(_vp),
+                              _c.POINTER(_vp)]),
+    "ttq_tt_ranks": (_c.c_int, [_vp, _i32p, _i32p]),
+    "ttq_tt_free": (_c.c_int, [_vp]),
     "ttq_status_string": (_c.c_char_p, [_c.c_int]),
     "ttq_last_error": (_c.c_char_p, []),
 }
@@ -157,6 +163,7 @@ def make_struct(p: inputs.Problem, arrays: _Arrays) -> TTQProblem:
     s.n_samples = p.n_samples
     s.rook_max = p.rook_max
     s.init_samples = p.init_samples
+    s.r0 = p.r0
     s.precision = inputs.PREC_CODE[p.precision]
     return s
 
@@ -211,9 +218,7 @@ class Plan:
     def run(self) -> Dict:
         res = TTQResult()
         _check(self.lib.ttq_plan_run(self.h, _c.byref(res)), "ttq_plan_run")
-        return {"value": res.value, "value_lo": res.value_lo, "internal_conv": res.internal_conv,
-                "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
-                "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
+        return _result_dict(res)
 
     def launch(self, slot: int = 0):
         """Enqueue a whole run; its result lands in `slot` (read with result())."""
@@ -222,9 +227,7 @@ class Plan:
     def result(self, slot: int = 0) -> Dict:
         res = TTQResult()
         _check(self.lib.ttq_plan_result(self.h, slot, _c.byref(res)), "ttq_plan_result")
-        return {"value": res.value, "value_lo": res.value_lo, "internal_conv": res.internal_conv,
-                "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
-                "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
+        return _result_dict(res)
 
     # -- stages -----------------------------------------------------------
     def init(self):
@@ -281,6 +284,11 @@ class Plan:
         out.record_stream(self.stream)
         return out
 
+    def export_tt(self, instance: int = 0) -> "TensorTrain":
+        """The tensor train of the last evaluated sweep, copied into a fresh
+        device buffer (torch) owned by the returned object."""
+        return TensorTrain(self, instance)
+
     def transfer_bytes(self):
         a, b = _c.c_int64(0), _c.c_int64(0)
         _check(self.lib.ttq_plan_transfer_bytes(self.h, _c.byref(a), _c.byref(b)), "ttq_plan_transfer_bytes")
@@ -304,10 +312,64 @@ class Plan:
         return int(self.lib.ttq_plan_launches(self.h))
 
 
+class TensorTrain:
+    """A TT handle (ttq_tt): cores and nested index sets in a device buffer.
+    core(k) returns (core, I<=k-1, I>k) as torch tensors viewing that buffer
+    (no copy), shapes (r_{k-1}, N_k, r_k), (r_{k-1}, k-1), (r_k, d-k)."""
+
+    def __init__(self, plan, instance: int = 0):
+        import torch
+        self.lib = load()
+        nb = _c.c_size_t(0)
+        _check(self.lib.ttq_tt_bytes(plan.h, instance, _c.byref(nb)), "ttq_tt_bytes")
+        self.buffer = torch.empty(max(256, int(nb.value)), dtype=torch.uint8, device="cuda")
+        h = _vp()
+        _check(self.lib.ttq_tt_export(plan.h, instance, _vp(self.buffer.data_ptr()), int(nb.value), _c.byref(h)),
+               "ttq_tt_export")
+        self.h = h
+        d = _c.c_int32(0)
+        ranks = (_c.c_int32 * 33)()
+        _check(self.lib.ttq_tt_ranks(self.h, _c.byref(d), ranks), "ttq_tt_ranks")
+        self.d = int(d.value)
+        self.ranks = [int(x) for x in ranks[:self.d + 1]]
+
+    def _view(self, ptr, count, dtype):
+        import torch
+        if not ptr or count == 0:
+            return torch.empty(0, dtype=dtype, device="cuda")
+        off = ptr - self.buffer.data_ptr()
+        itemsize = 8 if dtype == torch.float64 else 4
+        return self.buffer[off:off + count * itemsize].view(dtype)
+
+    def core(self, k: int):
+        import torch
+        rl, n, rr = _c.c_int32(0), _c.c_int32(0), _c.c_int32(0)
+        cp, lp, rp = _vp(), _vp(), _vp()
+        _check(self.lib.ttq_tt_get(self.h, k, _c.byref(rl), _c.byref(n), _c.byref(rr), _c.byref(cp), _c.byref(lp),
+                                   _c.byref(rp)), "ttq_tt_get")
+        rl, n, rr = int(rl.value), int(n.value), int(rr.value)
+        core = self._view(cp.value, rl * n * rr, torch.float64).view(rl, n, rr)
+        left = self._view(lp.value, rl * (k - 1), torch.int32).view(rl, k - 1)
+        right = self._view(rp.value, rr * (self.d - k), torch.int32).view(rr, self.d - k)
+        return core, left, right
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ttq_tt_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _result_dict(res) -> Dict:
     return {"value": res.value, "value_lo": res.value_lo, "internal_conv": res.internal_conv,
             "n_eval": int(res.n_eval), "sweeps": res.sweeps, "max_rank": res.max_rank,
-            "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status))}
+            "status": res.status, "status_name": STATUS_NAMES.get(res.status, str(res.status)),
+            "ranks": [int(x) for x in res.ranks[:res.d + 1]]}
 
 
 class Batch:

@@ -10,6 +10,7 @@
 #include <utility>
 #include <string>
 #include <vector>
+#include <mutex>
 
 #include "../../include/ttq.h"
 #include "ttq_kernels.cuh"
@@ -179,7 +180,14 @@ static int validate(const ttq_problem *p) {
   if (p->conv_window < 1 || p->conv_window > 8) return set_err(TTQ_ERR_INVALID_ARG, "conv_window must be in 1..8");
   if (p->max_sweeps < 1) return set_err(TTQ_ERR_INVALID_ARG, "max_sweeps must be >= 1");
   if (p->rook_max < 1) return set_err(TTQ_ERR_INVALID_ARG, "rook_max must be >= 1");
-  if (p->init_samples < 1) return set_err(TTQ_ERR_INVALID_ARG, "init_samples must be >= 1");
+  if (p->init_samples < 1 || p->init_samples > TTQ_MAX_INIT_SAMPLES)
+    return set_err(TTQ_ERR_INVALID_ARG, "init_samples must be in 1..1024");
+  {
+    const int r0 = p->r0 < 1 ? 1 : p->r0;
+    if (p->r0 < 0 || r0 > p->rank_cap || r0 > p->init_samples || r0 > p->nodes_per_mode[0] ||
+        r0 > p->nodes_per_mode[p->d - 1])
+      return set_err(TTQ_ERR_INVALID_ARG, "r0 must be in 1..min(rank_cap, init_samples, N_1, N_d)");
+  }
   if (p->n_samples < 0 || p->n_samples > (1 << 20)) return set_err(TTQ_ERR_INVALID_ARG, "bad n_samples");
   if (p->precision < 0 || p->precision > 1) return set_err(TTQ_ERR_INVALID_ARG, "bad precision");
   return TTQ_OK;
@@ -202,6 +210,7 @@ struct Layout {
   size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], Cc[TTQ_MAXD], Sr[TTQ_MAXD], rinv[TTQ_MAXD],
       zvec[TTQ_MAXD], pvec[TTQ_MAXD], ptab[TTQ_MAXD];
   size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD], zs[TTQ_MAXD];
+  size_t luh[TTQ_MAXD], lul[TTQ_MAXD], lup[TTQ_MAXD];   // double-double LU of G_k (precision DD only)
   size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
   int sblocks, cblocks, rblocks;
@@ -272,6 +281,10 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     const size_t nchk = (p->nodes_per_mode[k - 1] + 31) / 32;
     const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
     L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);
+    const size_t dd = p->precision == TTQ_PREC_DD ? 1 : 0;
+    L->luh[k] = b.take(dd * cap * cap * 8);
+    L->lul[k] = b.take(dd * cap * cap * 8);
+    L->lup[k] = b.take(dd * cap * 4);
   }
   const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;
   auto clampi = [](long v, long lo, long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
@@ -331,6 +344,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
   memset(&D, 0, sizeof(D));
   D.d = d; D.family = p->family; D.form = p->form; D.n = p->n; D.cap = p->rank_cap;
   D.rook_max = p->rook_max; D.init_samples = p->init_samples; D.conv_window = p->conv_window;
+  D.r0 = p->r0 < 1 ? 1 : p->r0;
   D.max_sweeps = p->max_sweeps; D.prec = p->precision;
   D.tol = p->tol; D.pivot_tol = p->pivot_tol; D.seed = p->seed;
   D.constant = family_constant(p);
@@ -364,6 +378,8 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
     D.cs[k] = (double *)(base + L.cs[k]); D.ce[k] = (double *)(base + L.ce[k]);
     D.zs[k] = (double *)(base + L.zs[k]);
     D.im[k] = (double *)(base + L.im[k]);
+    D.luh[k] = (double *)(base + L.luh[k]); D.lul[k] = (double *)(base + L.lul[k]);
+    D.lup[k] = (int *)(base + L.lup[k]);
   }
   for (int k = 1; k <= d; ++k) {
     D.Y[k] = (double *)(base + L.Y[k]); D.V[k] = (double *)(base + L.V[k]); D.Vlo[k] = (double *)(base + L.Vlo[k]);
@@ -770,7 +786,8 @@ static void fill_result_from(const Dev &D, const State &S, ttq_result *out) {
   out->sweeps = S.nchanges + 1;
   out->max_rank = mr;
   out->status = S.status;
-  out->reserved = 0;
+  out->d = D.d;
+  for (int k = 0; k <= TTQ_MAX_MODES; ++k) out->ranks[k] = k <= D.d ? S.r[k] : 0;
 }
 
 static int any_prec(const ttq_plan *P) {
@@ -790,6 +807,7 @@ static int enqueue_run(ttq_plan *P) {
   if (!P->run_exec && (rc = build_run_graph(P))) return rc;
   CK(cudaGraphLaunch(P->run_exec, P->stream));
   if (any_prec(P)) {                        // double-double contraction of the final sets
+    timed(P, KT_CONTRACT, [&] { k_dd_factor<<<dim3(P->max_ni, 1, P->count), 256, 0, P->stream>>>(P->devs); });
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
@@ -825,6 +843,7 @@ static int run_all(ttq_plan *P) {
     if (all) break;
   }
   if (any_prec(P)) {
+    timed(P, KT_CONTRACT, [&] { k_dd_factor<<<dim3(P->max_ni, 1, P->count), 256, 0, P->stream>>>(P->devs); });
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, P->count), 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
@@ -961,6 +980,7 @@ extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *
   if (rc) return rc;
   if (P->h.prec && !search) {               // this sweep's sets, contracted in double-double
     if (P->s2) CK(cudaStreamSynchronize(P->s2));
+    timed(P, KT_CONTRACT, [&] { k_dd_factor<<<P->max_ni, 256, 0, P->stream>>>(P->devs); });
     timed(P, KT_CONTRACT, [&] { k_contract<<<2, 256, P->contract_smem, P->stream>>>(P->devs, 1); });
     CK(cudaGetLastError());
   }
@@ -1080,6 +1100,112 @@ extern "C" int ttq_plan_get_core(ttq_plan *P, int k, double *host_out) {
   return TTQ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The tensor train as a result (Alg. 6's output: cores and nested index sets)
+
+struct ttq_tt {
+  int d;
+  int N[TTQ_MAXD];
+  int r[TTQ_MAXD + 1];
+  const double *core[TTQ_MAXD + 1];
+  const int *left[TTQ_MAXD], *right[TTQ_MAXD];
+};
+
+// Dense layout of one instance's tensor train in a caller's buffer.  Its ranks
+// are those of the last evaluated sweep (State.ro): the cores hold every entry
+// for them, and the first ro[k] rows of each nested set are that sweep's sets
+// (rows are only ever appended).
+static size_t tt_layout(const Dev &D, const State &S, size_t *core_off, size_t *left_off, size_t *right_off) {
+  Bump b;
+  for (int k = 1; k <= D.d; ++k) core_off[k] = b.take((size_t)S.ro[k - 1] * D.N[k - 1] * S.ro[k] * 8);
+  for (int k = 1; k < D.d; ++k) {
+    left_off[k] = b.take((size_t)S.ro[k] * k * 4);
+    right_off[k] = b.take((size_t)S.ro[k] * (D.d - k) * 4);
+  }
+  return (b.off + 255) & ~(size_t)255;
+}
+
+extern "C" int ttq_tt_bytes(ttq_plan *P, int instance, size_t *bytes) {
+  if (!P || !bytes) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  if (instance < 0 || instance >= P->count) return set_err(TTQ_ERR_INVALID_ARG, "instance out of range");
+  int rc = read_states(P);
+  if (rc) return rc;
+  size_t co[TTQ_MAXD + 1], lo[TTQ_MAXD], ro[TTQ_MAXD];
+  *bytes = tt_layout(P->hs[instance], P->hst[instance], co, lo, ro);
+  return TTQ_OK;
+}
+
+extern "C" int ttq_tt_export(ttq_plan *P, int instance, void *buffer, size_t bytes, ttq_tt **out) {
+  if (!P || !out) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
+  if (instance < 0 || instance >= P->count) return set_err(TTQ_ERR_INVALID_ARG, "instance out of range");
+  int rc = read_states(P);
+  if (rc) return rc;
+  const Dev &D = P->hs[instance];
+  const State &S = P->hst[instance];
+  size_t co[TTQ_MAXD + 1], lo[TTQ_MAXD], ro[TTQ_MAXD];
+  const size_t need = tt_layout(D, S, co, lo, ro);
+  if (!buffer || bytes < need || ((uintptr_t)buffer & 255))
+    return set_err(TTQ_ERR_WORKSPACE, "tensor-train buffer too small or not 256-byte aligned (ttq_tt_bytes)");
+  char *base = (char *)buffer;
+  TTExport E;
+  memset(&E, 0, sizeof(E));
+  ttq_tt *T = new ttq_tt();
+  T->d = D.d;
+  int maxn = 0;
+  for (int k = 0; k <= D.d; ++k) { E.r[k] = S.ro[k]; T->r[k] = S.ro[k]; }
+  for (int k = 1; k <= D.d; ++k) {
+    E.core[k] = (double *)(base + co[k]);
+    T->core[k] = E.core[k];
+    T->N[k - 1] = D.N[k - 1];
+    const int nk = S.ro[k - 1] * D.N[k - 1] * S.ro[k];
+    maxn = nk > maxn ? nk : maxn;
+  }
+  for (int k = 1; k < D.d; ++k) {
+    E.left[k] = (int *)(base + lo[k]);
+    E.right[k] = (int *)(base + ro[k]);
+    T->left[k] = E.left[k];
+    T->right[k] = E.right[k];
+  }
+  const int gx = std::max(1, std::min(1024, (maxn + 255) / 256));
+  k_export_tt<<<dim3(gx, D.d), 256, 0, P->stream>>>(P->devs, instance, E);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) {
+    delete T;
+    g_last_error = std::string("tensor-train export: ") + cudaGetErrorString(e);
+    return TTQ_ERR_CUDA;
+  }
+  P->launches++;
+  *out = T;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_tt_get(const ttq_tt *T, int k, int32_t *r_left, int32_t *n_k, int32_t *r_right,
+                          const double **core_dev, const int32_t **left_idx_dev, const int32_t **right_idx_dev) {
+  if (!T) return set_err(TTQ_ERR_INVALID_ARG, "null tensor train");
+  if (k < 1 || k > T->d) return set_err(TTQ_ERR_INVALID_ARG, "k out of range");
+  if (r_left) *r_left = T->r[k - 1];
+  if (n_k) *n_k = T->N[k - 1];
+  if (r_right) *r_right = T->r[k];
+  if (core_dev) *core_dev = T->core[k];
+  if (left_idx_dev) *left_idx_dev = k >= 2 ? T->left[k - 1] : nullptr;
+  if (right_idx_dev) *right_idx_dev = k <= T->d - 1 ? T->right[k] : nullptr;
+  return TTQ_OK;
+}
+
+extern "C" int ttq_tt_ranks(const ttq_tt *T, int32_t *d, int32_t *ranks) {
+  if (!T) return set_err(TTQ_ERR_INVALID_ARG, "null tensor train");
+  if (d) *d = T->d;
+  if (ranks)
+    for (int k = 0; k <= T->d; ++k) ranks[k] = T->r[k];
+  return TTQ_OK;
+}
+
+extern "C" int ttq_tt_free(ttq_tt *T) {
+  delete T;
+  return TTQ_OK;
+}
+
 extern "C" int ttq_plan_eval_points(ttq_plan *P, const int32_t *idx, int64_t npts, double *out) {
   if (P && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "stage calls need a single-instance plan");
   if (!P || (!idx && npts) || (!out && npts) || npts < 0) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
@@ -1166,7 +1292,12 @@ extern "C" const char *ttq_last_error(void) { return g_last_error.c_str(); }
 // scratch is this array.
 // size: TTQ_NOALLOC_SCRATCH_BYTES (16 MiB), include/ttq.h
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TTQ_NOALLOC_SCRATCH_BYTES];
-static void *g_noalloc_ptr[256];           // device address of the scratch, per device id
+// Device address of the scratch, per device id, looked up once per device with
+// that device current (host code cannot use the symbol's own address: it names
+// a host-side stand-in).  The lookup is guarded so that host threads calling
+// for the first time at once take the same, finished value.
+static void *g_noalloc_ptr[256];
+static std::mutex g_noalloc_mu;
 
 extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_result *out) {
   int rc = validate(p);
@@ -1178,13 +1309,22 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
   if (L.total > TTQ_NOALLOC_SCRATCH_BYTES)
     return set_err(TTQ_ERR_WORKSPACE, "problem needs more device scratch than the 16 MiB the "
                                       "no-allocation entry point holds; use ttq_plan_create");
+  // the call waits for its stream and copies from this stack frame: on a
+  // capturing stream it is refused before any CUDA work, leaving the capture intact
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_err(TTQ_ERR_INVALID_ARG, "ttq_integrate_noalloc called on a capturing stream");
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return set_err(TTQ_ERR_INVALID_ARG, "device id out of range");
-  if (!g_noalloc_ptr[dev]) {                // first call on this device: look up the scratch address
-    void *ptr = nullptr;
-    CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = ptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {              // first call on this device: look up the scratch address
+      void *ptr = nullptr;
+      CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = ptr;
+    }
   }
   char *base = (char *)g_noalloc_ptr[dev];
   const int d = p->d;
@@ -1459,6 +1599,7 @@ static int server_retire(ttq_server *S) {
     }
     if (a.h.prec) {
       const int cs = (int)((size_t)a.h.cap * a.h.cap * 8);
+      k_dd_factor<<<a.h.d - 1, 256, 0, S->stream>>>(a.own);
       k_contract<<<2, 256, cs, S->stream>>>(a.own, 1);
       CK(cudaGetLastError());
     }

@@ -22,9 +22,10 @@
 #define TTQ_MAXR 128
 #define TTQ_WARPS 8                      // warps per CTA in the fiber kernels
 #define TTQ_CHUNK 128                    // at most this many nodes per piece of work of the rook kernels
-#define TTQ_TIE_REL 1e-10                // Alg. 2 argmax: |E| >= max - (REL*max + ABS*scale) is a tie
+#define TTQ_TIE_REL 1e-12                // Alg. 2 argmax: |E| >= max - (REL*max + ABS*scale) is a tie
 #define TTQ_TIE_ABS 1e-14
 #define TTQ_MAXPAIR 288                  // varying pairs of one cube-form fiber, <= (n/2)^2 for n <= 33
+#define TTQ_MAX_INIT 1024                // initial random points scanned (include/ttq.h TTQ_MAX_INIT_SAMPLES)
 
 namespace ttq {
 
@@ -81,6 +82,7 @@ struct State {
 
 struct Dev {
   int d, family, form, n, cap, rook_max, init_samples, conv_window, max_sweeps, prec;
+  int r0;                   // initial multi-indices (rank of every interface before the first sweep)
   int uniformT;             // 1: D in R^n on one shared uniform grid -> pair table T
   int sblocks, cblocks, rblocks;   // CTAs: per interface (samples), per instance (column / row)
   int sms;                  // SMs of the device (placement of the item deals)
@@ -105,6 +107,8 @@ struct Dev {
   double *ce[TTQ_MAXD];     // per interface: residuals E of the current candidates
   double *zs[TTQ_MAXD];     // per interface: z = G^-1 y of every random sample, cap apart
   double *im[TTQ_MAXD];     // per interface: max score of each row of 32 rook candidates (-1: none eligible)
+  double *luh[TTQ_MAXD], *lul[TTQ_MAXD];   // double-double mode: P G_k = L U, column-major (hi, lo parts)
+  int *lup[TTQ_MAXD];       // double-double mode: row i of P G_k is row lup[k][i] of G_k
   State *st;
 };
 
@@ -181,6 +185,18 @@ __device__ __forceinline__ dd dd_div_d(dd a, double b) {
   double q2 = r.hi / b;
   return fast_two_sum(q1, q2);
 }
+// a / b for double-double b: three quotient digits by the leading part of b,
+// each followed by the exact remainder (long division, Dekker 1971)
+__device__ __forceinline__ dd dd_div(dd a, dd b) {
+  const double q1 = a.hi / b.hi;
+  dd r = dd_add(a, dd_mul({-b.hi, -b.lo}, {q1, 0.0}));
+  const double q2 = r.hi / b.hi;
+  r = dd_add(r, dd_mul({-b.hi, -b.lo}, {q2, 0.0}));
+  const double q3 = r.hi / b.hi;
+  dd q = fast_two_sum(q1, q2);
+  return dd_add(q, {q3, 0.0});
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ dd warp_sum_dd(dd v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

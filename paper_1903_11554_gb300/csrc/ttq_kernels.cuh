@@ -291,56 +291,100 @@ __global__ void k_eval_points(Dev *const *Dps, const int *idx, long long npts, d
   }
 }
 
-// initial index set: the largest |A| among init_samples seeded points
+// Initial nested sets: r0 multi-indices taken from init_samples seeded random
+// points in decreasing |A| (ties by draw order), a point kept when its first
+// and last node indices differ from those of the points already kept (so all
+// its prefixes and suffixes are new and every interface gets rank r0); a point
+// whose value is not finite and nonzero ends the scan.  I<=k = the kept
+// points' prefixes of length k and I>k = their suffixes from mode k+1, in the
+// order kept: nested by construction (Eq. 4).  Fewer than r0 usable points:
+// status NONFINITE.
 __global__ void k_init(Dev *const *Dps) {
   const Dev &D = *Dps[blockIdx.z];
   State *st = D.st;
   __shared__ int ms[TTQ_WARPS][TTQ_MAXD];
   __shared__ double pl[TTQ_WARPS][TTQ_MAXPAIR];
-  __shared__ Best sb[TTQ_WARPS];
-  const int lane = lane_id(), warp = warp_id(), d = D.d;
+  __shared__ double score[TTQ_MAX_INIT];          // |A| of each point (-1: not finite), -2 once consumed
+  __shared__ int first[TTQ_MAX_INIT], lastc[TTQ_MAX_INIT];   // its first and last node index
+  __shared__ int chosen[TTQ_MAXR];
+  __shared__ int nchosen, pick;
+  __shared__ double rs[TTQ_WARPS];
+  __shared__ int ri[TTQ_WARPS];
+  const int lane = lane_id(), warp = warp_id(), d = D.d, ns = D.init_samples;
   const unsigned long long sid = stream_id(0, 0, 0);
-  Best best = {-1.0, 0x7fffffff, 0.0};
-  for (int p = warp; p < D.init_samples; p += TTQ_WARPS) {
+  for (int p = warp; p < ns; p += TTQ_WARPS) {
     if (lane < d) ms[warp][lane] = draw_index(D.seed, sid, (unsigned long long)p * d + lane, D.N[lane]);
     __syncwarp();
     FiberU u = fiber_setup(D, 0, ms[warp], pl[warp]);
     double v = 0.0;
     if (lane == 0) v = fiber_value(D, 0, ms[warp], u, pl[warp], ms[warp][0]);
     v = __shfl_sync(0xffffffffu, v, 0);
-    double s = isfinite(v) ? fabs(v) : -1.0;
-    if (better(s, p, best.score, best.idx)) { best.score = s; best.idx = p; best.val = v; }
+    if (lane == 0) {
+      score[p] = isfinite(v) ? fabs(v) : -1.0;
+      first[p] = ms[warp][0];
+      lastc[p] = ms[warp][d - 1];
+    }
     __syncwarp();
   }
-  best = warp_best(best);
-  if (lane == 0) sb[warp] = best;
+  if (threadIdx.x == 0) nchosen = 0;
   __syncthreads();
+  // greedy scan in decreasing |A|: one block-wide argmax (ties to the lowest
+  // draw) per point consumed
+  for (int it = 0; it < ns; ++it) {
+    double bv = -3.0;
+    int bi = 0x7fffffff;
+    for (int p = threadIdx.x; p < ns; p += blockDim.x)
+      if (score[p] > bv || (score[p] == bv && p < bi)) { bv = score[p]; bi = p; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { rs[warp] = bv; ri[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = rs[0];
+      int q = ri[0];
+      for (int w = 1; w < TTQ_WARPS; ++w)
+        if (rs[w] > v || (rs[w] == v && ri[w] < q)) { v = rs[w]; q = ri[w]; }
+      pick = (v > 0.0) ? q : -1;                    // no finite nonzero point left: stop
+      if (pick >= 0) {
+        bool fresh = true;
+        for (int c = 0; c < nchosen; ++c)
+          fresh &= first[chosen[c]] != first[pick] && lastc[chosen[c]] != lastc[pick];
+        if (fresh) chosen[nchosen++] = pick;
+        score[pick] = -2.0;
+      }
+    }
+    __syncthreads();
+    if (pick < 0 || nchosen >= D.r0) break;
+  }
+  const int r0 = nchosen;
   if (threadIdx.x == 0) {
-    Best c = sb[0];
-    for (int w = 1; w < TTQ_WARPS; ++w)
-      if (better(sb[w].score, sb[w].idx, c.score, c.idx)) c = sb[w];
-    sb[0] = c;
-    for (int k = 0; k <= d; ++k) { st->r[k] = 1; st->ro[k] = 0; }
+    const int rr = r0 >= 1 ? r0 : 1;
+    for (int k = 0; k <= d; ++k) { st->r[k] = (k == 0 || k == d) ? 1 : rr; st->ro[k] = 0; }
     st->sweep = 0; st->status = ST_OK; st->stop = 0; st->nonfinite = 0; st->singular = 0;
     st->nchanges = 0; st->scale_bits = 0ULL; st->value = st->value_lo = st->prev = 0.0;
     st->stop_pending = 0; st->pending_status = 0;
     for (int k = 0; k < TTQ_MAXD; ++k) { st->qr_rank[k] = 0; st->qr_row[k] = 0; }
     st->conv = __longlong_as_double(0x7ff0000000000000LL);
     st->search_evals = 0; st->init_evals = D.init_samples;
-    if (!(c.score > 0.0)) { st->status = ST_ERR_NONFINITE; st->stop = 1; }
+    if (r0 < D.r0) { st->status = ST_ERR_NONFINITE; st->stop = 1; }
   }
-  __syncthreads();
-  // the chosen point: redraw its coordinates
-  const int p = sb[0].idx;
-  if (threadIdx.x < 32 && lane < d) ms[0][lane] = draw_index(D.seed, sid, (unsigned long long)p * d + lane, D.N[lane]);
-  __syncthreads();
-  for (int k = 1 + threadIdx.x; k <= d - 1; k += blockDim.x) {
-    for (int m = 0; m < d; ++m) {
-      D.lidx[k][m] = (m < k) ? ms[0][m] : -1;
-      D.ridx[k][m] = (m >= k) ? ms[0][m] : -1;
+  if (r0 < 1) return;
+  // the kept points' node indices, redrawn: ms-like rows per point in chosen order
+  for (int e = threadIdx.x; e < r0 * d; e += blockDim.x) {
+    const int j = e / d, m = e % d;
+    const int x = draw_index(D.seed, sid, (unsigned long long)chosen[j] * d + m, D.N[m]);
+    for (int k = 1; k <= d - 1; ++k) {
+      D.lidx[k][j * d + m] = (m < k) ? x : -1;
+      D.ridx[k][j * d + m] = (m >= k) ? x : -1;
     }
-    D.lpar[k][0] = 0; D.lnode[k][0] = ms[0][k - 1];
-    D.rpar[k][0] = 0; D.rnode[k][0] = ms[0][k];
+    // I<=k[j] = (I<=k-1[j], x_j[k-1]) and I>k[j] = (x_j[k], I>k+1[j]); the empty
+    // sets I<=0 and I>d have the single row 0
+    if (m <= d - 2) { D.lnode[m + 1][j] = x; D.lpar[m + 1][j] = m == 0 ? 0 : j; }
+    if (m >= 1) { D.rnode[m][j] = x; D.rpar[m][j] = m == d - 1 ? 0 : j; }
   }
 }
 
@@ -775,6 +819,83 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (threadIdx.x == 0) { st->qr_rank[k] = r; st->it[k].prank = -1; st->qr_row[k] = 0; }
 }
 
+// The final double-double contraction applies G_k^-1 through a double-double
+// LU factorization of G_k itself, taken from its exact FP64 entries (the
+// FP64 QR factors of the search carry an error of order u cond(G_k), which
+// double-double arithmetic downstream cannot remove): P G_k = L U by Gaussian
+// elimination with partial pivoting (largest leading part, ties to the lowest
+// row), L unit lower triangular below the diagonal and U on and above it, in
+// one column-major array of hi and lo parts (leading dimension cap); lup[k][i]
+// is the row of G_k that row i of P G_k holds.  One CTA per interface.
+__global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
+  State *st = D.st;
+  const int k = blockIdx.x + 1;
+  if (k > D.d - 1 || !D.prec || st->nonfinite || st->singular) return;
+  __shared__ int piv_s;
+  const int r = st->r[k], ld = D.cap, tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
+  double *Ah = D.luh[k], *Al = D.lul[k];
+  int *perm = D.lup[k];
+  for (int e = tid; e < r * r; e += nt) {
+    const int a = e % r, b = e / r;
+    Ah[a + (size_t)b * ld] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], b)];
+    Al[a + (size_t)b * ld] = 0.0;
+  }
+  for (int i = tid; i < r; i += nt) perm[i] = i;
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    if (warp == 0) {                             // pivot row: largest |hi| in column j at or below the diagonal
+      double bv = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = j + lane; i < r; i += 32) {
+        const double v = fabs(Ah[i + (size_t)j * ld]);
+        if (v > bv) { bv = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        piv_s = bi;
+        if (!(bv > 0.0)) st->singular = 1;
+      }
+    }
+    __syncthreads();
+    const int pr = piv_s;
+    if (pr != j) {                               // swap rows j and pr
+      for (int c = tid; c < r; c += nt) {
+        const size_t oj = j + (size_t)c * ld, op = pr + (size_t)c * ld;
+        const double th = Ah[oj], tl = Al[oj];
+        Ah[oj] = Ah[op]; Al[oj] = Al[op];
+        Ah[op] = th; Al[op] = tl;
+      }
+      if (tid == 0) { const int t = perm[j]; perm[j] = perm[pr]; perm[pr] = t; }
+    }
+    __syncthreads();
+    const dd u = {Ah[j + (size_t)j * ld], Al[j + (size_t)j * ld]};
+    if (u.hi != 0.0)
+      for (int i = j + 1 + tid; i < r; i += nt) {
+        const size_t o = i + (size_t)j * ld;
+        const dd l = dd_div({Ah[o], Al[o]}, u);
+        Ah[o] = l.hi; Al[o] = l.lo;
+      }
+    __syncthreads();
+    const int m = r - j - 1;
+    if (u.hi != 0.0)
+      for (int e = tid; e < m * m; e += nt) {    // trailing block: a_ic -= l_ij u_jc
+        const int i = j + 1 + e % m, c = j + 1 + e / m;
+        const size_t oi = i + (size_t)j * ld, oj = j + (size_t)c * ld, o = i + (size_t)c * ld;
+        const dd v = dd_add({Ah[o], Al[o]}, dd_neg(dd_mul({Ah[oi], Al[oi]}, {Ah[oj], Al[oj]})));
+        Ah[o] = v.hi; Al[o] = v.lo;
+      }
+    __syncthreads();
+  }
+  if (tid == 0) atomicAdd(&st->flops[2], (unsigned long long)(20.0 / 3.0 * r * (double)r * r));
+}
+
 // Kernel (c): contraction of the weighted cores with the inverse cross matrices
 // (Sec. 4.1), V_1 G_1^-1 V_2 ... G_{d-1}^-1 V_d, as two chains that meet at
 // m = (d+1)/2: CTA 0 forms the row x = V_1 G_1^-1 V_2 ... V_m from the left
@@ -787,81 +908,113 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
 // that fires is recorded as pending and applied at the end of the sweep.
 // final_dd: the double-double contraction of the final sets (after the run).
 
-// x <- x G_k^-1 for the row x (hi/lo pairs used when prec)
+// x <- x G_k^-1 for the row x.  FP64: through the QR factors (R^T t = x,
+// x <- Q t).  Double-double (the final contraction, hi/lo pairs): through the
+// double-double LU, P G = L U, so x G^-1 = ((x U^-1) L^-1) P.
 __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *xh, double *xl,
                                     double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
-  // FP64: D^-1 R (row-major), the scaled forward substitution; double-double: R itself
-  stage_compact(Rs, prec ? D.Rr[k] : D.Sr[k], nullptr, nullptr, r, ld);
-  __syncthreads();
-  if (!prec) {                                   // forward substitution R^T t = x
-    if (warp == 0) warp_fwd_subst(Rs, xh, th, r, r);
-    __syncthreads();
-    for (int i = tid; i < r; i += nt) th[i] *= D.rinv[k][i];
-  } else if (warp == 0) {
-    {
-      for (int i = 0; i < r; ++i) {
-        const dd ti = dd_div_d({xh[i], xl[i]}, Rs[i * r + i]);
-        for (int j = i + 1 + lane; j < r; j += 32) {
-          const dd v = dd_add({xh[j], xl[j]}, dd_mul_d(ti, -Rs[i * r + j]));
-          xh[j] = v.hi; xl[j] = v.lo;
+  if (prec) {
+    const double *Uh = D.luh[k], *Ul = D.lul[k];
+    if (warp == 0) {
+      // t U = x: t_j = x_j / U_jj, then x_c -= t_j U_jc for c > j
+      for (int j = 0; j < r; ++j) {
+        const size_t dj = j + (size_t)j * ld;
+        const dd tj = dd_div({xh[j], xl[j]}, {Uh[dj], Ul[dj]});
+        for (int c = j + 1 + lane; c < r; c += 32) {
+          const size_t o = j + (size_t)c * ld;
+          const dd v = dd_add({xh[c], xl[c]}, dd_neg(dd_mul(tj, {Uh[o], Ul[o]})));
+          xh[c] = v.hi; xl[c] = v.lo;
         }
-        if (lane == 0) { th[i] = ti.hi; tl[i] = ti.lo; }
+        if (lane == 0) { th[j] = tj.hi; tl[j] = tj.lo; }
+        __syncwarp();
+      }
+      // w L = t (unit lower): w_j = t_j, then t_c -= w_j L_jc for c < j, j descending
+      for (int j = r - 1; j >= 0; --j) {
+        const dd wj = {th[j], tl[j]};
+        for (int c = lane; c < j; c += 32) {
+          const size_t o = j + (size_t)c * ld;
+          const dd v = dd_add({th[c], tl[c]}, dd_neg(dd_mul(wj, {Uh[o], Ul[o]})));
+          th[c] = v.hi; tl[c] = v.lo;
+        }
         __syncwarp();
       }
     }
+    __syncthreads();
+    for (int i = tid; i < r; i += nt) {          // x = w P: x[perm[i]] = w_i
+      const int c = D.lup[k][i];
+      xh[c] = th[i]; xl[c] = tl[i];
+    }
+    __syncthreads();
+    return;
   }
+  // FP64: D^-1 R (row-major), the scaled forward substitution R^T t = x
+  stage_compact(Rs, D.Sr[k], nullptr, nullptr, r, ld);
+  __syncthreads();
+  if (warp == 0) warp_fwd_subst(Rs, xh, th, r, r);
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) th[i] *= D.rinv[k][i];
   __syncthreads();
   for (int i = tid; i < r; i += nt) {            // x <- Q t
     const double *Qrow = D.Qr[k] + (size_t)i * ld;
-    if (!prec) {
-      double acc = 0.0;
-      for (int j = 0; j < r; ++j) acc = fma(Qrow[j], th[j], acc);
-      xh[i] = acc;
-    } else {
-      dd acc = {0.0, 0.0};
-      for (int j = 0; j < r; ++j) acc = dd_add(acc, dd_mul_d({th[j], tl[j]}, Qrow[j]));
-      xh[i] = acc.hi; xl[i] = acc.lo;
-    }
+    double acc = 0.0;
+    for (int j = 0; j < r; ++j) acc = fma(Qrow[j], th[j], acc);
+    xh[i] = acc;
   }
   __syncthreads();
 }
 
-// y <- G_k^-1 y for the column y
+// y <- G_k^-1 y for the column y.  FP64: through the QR factors (t = Q^T y,
+// R z = t).  Double-double (the final contraction): through the double-double
+// LU, G^-1 y = U^-1 (L^-1 (P y)).
 __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *yh, double *yl,
                                      double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
-  // column-major: FP64 R D^-1 (the scaled back substitution), double-double R itself
-  stage_compact(Rs, prec ? D.Rc[k] : D.Cc[k], nullptr, nullptr, r, ld);
-  for (int i = tid; i < r; i += nt) {            // t = Q^T y
-    if (!prec) {
-      double acc = 0.0;
-      for (int j = 0; j < r; ++j) acc = fma(D.Qr[k][(size_t)j * ld + i], yh[j], acc);
-      th[i] = acc;
-    } else {
-      dd acc = {0.0, 0.0};
-      for (int j = 0; j < r; ++j) acc = dd_add(acc, dd_mul_d({yh[j], yl[j]}, D.Qr[k][(size_t)j * ld + i]));
-      th[i] = acc.hi; tl[i] = acc.lo;
+  if (prec) {
+    const double *Uh = D.luh[k], *Ul = D.lul[k];
+    for (int i = tid; i < r; i += nt) {          // w = P y
+      const int c = D.lup[k][i];
+      th[i] = yh[c]; tl[i] = yl[c];
     }
-  }
-  __syncthreads();
-  if (!prec) {                                   // back substitution R z = t
-    if (warp == 0) warp_back_subst(Rs, th, yh, r, r);
     __syncthreads();
-    for (int j = tid; j < r; j += nt) yh[j] *= D.rinv[k][j];
-  } else if (warp == 0) {
-    {
+    if (warp == 0) {
+      // L v = w (unit lower): v_i = w_i, then w_m -= L_mi v_i for m > i
+      for (int i = 0; i < r; ++i) {
+        const dd vi = {th[i], tl[i]};
+        for (int m = i + 1 + lane; m < r; m += 32) {
+          const size_t o = m + (size_t)i * ld;
+          const dd v = dd_add({th[m], tl[m]}, dd_neg(dd_mul(vi, {Uh[o], Ul[o]})));
+          th[m] = v.hi; tl[m] = v.lo;
+        }
+        __syncwarp();
+      }
+      // U z = v: z_j = v_j / U_jj, then v_m -= U_mj z_j for m < j, j descending
       for (int j = r - 1; j >= 0; --j) {
-        const dd zj = dd_div_d({th[j], tl[j]}, Rs[j + j * r]);
-        for (int i = lane; i < j; i += 32) {
-          const dd v = dd_add({th[i], tl[i]}, dd_mul_d(zj, -Rs[i + j * r]));
-          th[i] = v.hi; tl[i] = v.lo;
+        const size_t dj = j + (size_t)j * ld;
+        const dd zj = dd_div({th[j], tl[j]}, {Uh[dj], Ul[dj]});
+        for (int m = lane; m < j; m += 32) {
+          const size_t o = m + (size_t)j * ld;
+          const dd v = dd_add({th[m], tl[m]}, dd_neg(dd_mul(zj, {Uh[o], Ul[o]})));
+          th[m] = v.hi; tl[m] = v.lo;
         }
         if (lane == 0) { yh[j] = zj.hi; yl[j] = zj.lo; }
         __syncwarp();
       }
     }
+    __syncthreads();
+    return;
   }
+  // FP64: R D^-1 (column-major), the scaled back substitution
+  stage_compact(Rs, D.Cc[k], nullptr, nullptr, r, ld);
+  for (int i = tid; i < r; i += nt) {            // t = Q^T y
+    double acc = 0.0;
+    for (int j = 0; j < r; ++j) acc = fma(D.Qr[k][(size_t)j * ld + i], yh[j], acc);
+    th[i] = acc;
+  }
+  __syncthreads();
+  if (warp == 0) warp_back_subst(Rs, th, yh, r, r);   // R z = t
+  __syncthreads();
+  for (int j = tid; j < r; j += nt) yh[j] *= D.rinv[k][j];
   __syncthreads();
 }
 
@@ -2108,6 +2261,39 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     __syncwarp();
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
+}
+
+// The tensor train of one instance copied out to a caller's buffer in the
+// usual dense layouts: core k (1..d) as row-major r_{k-1} x N_k x r_k doubles
+// (weights folded, no family constant), and for k = 1..d-1 the nested sets
+// I<=k (r_k x k) and I>k (r_k x (d-k)) as row-major int32 node indices.
+// Grid: x strides over the entries, y = k - 1.
+struct TTExport {
+  double *core[TTQ_MAXD + 1];
+  int *left[TTQ_MAXD], *right[TTQ_MAXD];
+  int r[TTQ_MAXD + 1];
+};
+__global__ void k_export_tt(Dev *const *Dps, int q, TTExport E) {
+  const Dev &D = *Dps[q];
+  const int k = blockIdx.y + 1, d = D.d;
+  if (k > d) return;
+  const int rl = E.r[k - 1], rr = E.r[k], N = D.N[k - 1];
+  const long long n = (long long)rl * N * rr;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  for (long long e = t0; e < n; e += nt) {
+    const int b = (int)(e % rr), i = (int)((e / rr) % N), a = (int)(e / ((long long)rr * N));
+    E.core[k][e] = D.Y[k][core_at(D, k, a, i, b)];
+  }
+  if (k <= d - 1) {
+    for (long long e = t0; e < (long long)rr * k; e += nt) {
+      const int a = (int)(e / k), m = (int)(e % k);
+      E.left[k][e] = D.lidx[k][a * d + m];
+    }
+    for (long long e = t0; e < (long long)rr * (d - k); e += nt) {
+      const int b = (int)(e / (d - k)), m = (int)(e % (d - k));
+      E.right[k][e] = D.ridx[k][b * d + k + m];
+    }
+  }
 }
 
 __global__ void k_begin(Dev *const *Dps, int sweep, int rules, int search) {

@@ -67,7 +67,8 @@ class Problem:
     seed: int = 1
     n_samples: int = 0          # random samples per interface; 0 -> N_k + N_{k+1}
     rook_max: int = 3           # column/row rounds of rook pivoting
-    init_samples: int = 64      # random points scanned for the first pivot
+    init_samples: int = 64      # random points scanned for the initial multi-indices
+    r0: int = 1                 # initial multi-indices (rank of every interface before the first sweep)
     precision: str = "fp64"     # "fp64" or "dd" (double-double final contraction)
     name: str = ""
 
@@ -129,8 +130,8 @@ def config_c4(**kw) -> Problem:
 
 def config_d12(**kw) -> Problem:
     """D_12 in R^12, trapezoid [-24,24] with 385 nodes/mode (h = 0.125), rank cap 64, tol 1e-12,
-    seeded random initial index set."""
-    args = dict(rank_cap=64, tol=1e-12, seed=12, name="D12_rn_N385_r64")
+    seeded random initial index sets: r0 = 4 multi-indices."""
+    args = dict(rank_cap=64, tol=1e-12, seed=12, r0=4, name="D12_rn_N385_r64")
     args.update(kw)
     return make_problem("D", "rn", 12, 385, L=24.0, **args)
 
@@ -141,6 +142,34 @@ def config_e16(**kw) -> Problem:
     args = dict(rank_cap=96, tol=1e-14, seed=16, precision="dd", name="E16_cube_N128_r96")
     args.update(kw)
     return make_problem("E", "cube", 16, 128, **args)
+
+
+def config_d_cube(n: int, **kw) -> Problem:
+    """D_n in the paper's unit-cube form (Eq. 10) with Gauss-Legendre 129 nodes per
+    mode, the rule of the printed D_8 and D_16 values (Sec. 5.5, Fig. 7): D_8 at
+    rank cap 64 (seed 8), D_16 at rank cap 80 (seed 16), tol 1e-12."""
+    caps = {8: 64, 16: 80}
+    args = dict(rank_cap=caps.get(n, 64), tol=1e-12, seed=n, name="D%d_cube_N129" % n)
+    args.update(kw)
+    return make_problem("D", "cube", n, 129, **args)
+
+
+def config_c_cube(n: int, **kw) -> Problem:
+    """C_n in the paper's unit-cube form (Eq. 9) with Gauss-Legendre 33 nodes per
+    mode (the rule of the paper's double-precision C_d runs, Sec. 5.3), rank cap
+    40, tol 1e-13, seed n."""
+    args = dict(rank_cap=40, tol=1e-13, seed=n, name="C%d_cube_N33" % n)
+    args.update(kw)
+    return make_problem("C", "cube", n, 33, **args)
+
+
+def config_c_rn_grid(n: int, **kw) -> Problem:
+    """C_n in R^n on the trapezoid rule over [-12, 12] with 65 nodes per mode
+    (h = 0.375), rank cap 64, tol 1e-13, seed n: a grid whose exact tensor-product
+    sum is known in closed form (the separable 1-D integral of the C integrand)."""
+    args = dict(rank_cap=64, tol=1e-13, seed=n, name="C%d_rn_N65_L12" % n)
+    args.update(kw)
+    return make_problem("C", "rn", n, 65, L=12.0, **args)
 
 
 def batched_mix(count: int = 256, seed: int = 256, *, n_lo: int = 4, n_hi: int = 24,

@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import shutil
+import subprocess
 
 import pytest
 
@@ -43,11 +44,29 @@ def test_binding_covers_the_header():
     assert set(binding.SIGNATURES) >= set(declared_functions()) - set()
 
 
-def test_struct_sizes_match_c_layout():
-    # natural alignment of the C structs in include/ttq.h
-    assert ctypes.sizeof(binding.TTQProblem) == 96
-    assert ctypes.sizeof(binding.TTQResult) == 48
-    assert ctypes.sizeof(binding.TTQPivot) == 40
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every field offset and struct size of the ctypes mirrors equals what a C
+    compiler makes of include/ttq.h."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"ttq_problem": binding.TTQProblem, "ttq_result": binding.TTQResult,
+               "ttq_pivot": binding.TTQPivot}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ttq.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
 
 def test_workspace_size_and_validation(lib):

@@ -144,6 +144,41 @@ def test_parent_pointer_roundtrip():
         assert np.array_equal(st.right[k], st2.right[k])
 
 
+@pytest.mark.parametrize("r0", [1, 4, 9])
+def test_initial_sets_by_brute_force(r0):
+    """The initial nested sets against a direct restatement of the reading: all
+    init_samples points, sorted by |A| (ties by draw order), kept greedily when
+    their first and last node indices are new; prefixes and suffixes nested,
+    every interface of rank r0, every cross matrix nonsingular."""
+    from oracle import rng
+    p = inputs.make_problem("D", "rn", 5, 23, L=6.0, rank_cap=12, r0=r0, init_samples=48)
+    st = ttcross.initial_state(p)
+    d = p.d
+    pts = []
+    for q in range(p.init_samples):
+        x = tuple(rng.draw_index(p.seed, rng.stream_id(0, 0, rng.PURPOSE_INIT), q * d + k, p.N[k])
+                  for k in range(d))
+        a = abs(float(integrands.tensor_entries(p, np.array([x]))[0]))
+        pts.append((-a, q, x))
+    kept = []
+    for _, q, x in sorted(pts):
+        if all(x[0] != y[0] and x[-1] != y[-1] for y in kept):
+            kept.append(x)
+        if len(kept) == r0:
+            break
+    assert st.ranks() == [1] + [r0] * (d - 1) + [1]
+    for k in range(1, d):
+        assert [tuple(r) for r in st.left[k]] == [x[:k] for x in kept]
+        assert [tuple(r) for r in st.right[k]] == [x[k:] for x in kept]
+    par = ttcross.to_parents(p, st)                     # nested: every row has its parent
+    for k in range(1, d):
+        assert list(par["lpar"][k - 1]) == (list(range(r0)) if k > 1 else [0] * r0)
+        G = ttcross.core(p, st, k).reshape(-1, r0)[ttcross.cross_rows(p, st, k), :]
+        assert np.linalg.matrix_rank(G) == r0
+    if r0 == 1:                                           # the single largest |A| of the samples
+        assert tuple(st.left[d - 1][0]) + (int(st.right[d - 1][0][-1]),) == sorted(pts)[0][2]
+
+
 def test_ranks_grow_by_at_most_one_per_sweep():
     p = inputs.make_problem("C", "cube", 6, 33, rank_cap=12)
     r = ttcross.integrate(p)
