@@ -65,7 +65,8 @@ typedef enum {
   TTQ_ERR_WORKSPACE = -4,     /* workspace too small or misaligned                 */
   TTQ_ERR_CUDA = -5,          /* a CUDA call failed (message: ttq_last_error)      */
   TTQ_ERR_ADMISSION = -6,     /* serving: request larger than the memory budget    */
-  TTQ_ERR_NOT_FOUND = -7
+  TTQ_ERR_NOT_FOUND = -7,
+  TTQ_ERR_TIMEOUT = -8        /* the persistent search gave up waiting (ttq_plan_set_wait_limit) */
 } ttq_status;
 
 #define TTQ_MAX_MODES 32      /* d <= 32 */
@@ -271,6 +272,19 @@ int64_t ttq_plan_launches(const ttq_plan *plan);
  * that replay individual launches). */
 int ttq_plan_set_graphs(ttq_plan *plan, int enable);
 
+/* Search of a sweep (Alg. 2 on every interface, Alg. 6): mode 0 (the
+ * default) as separate launches per stage (samples, 3 x (column step,
+ * decisions, row step, decisions)), the form batches always use; mode 1
+ * (single-instance plans only) as one persistent kernel in which every
+ * interface owns a group of CTAs and hands its stages on through flags in
+ * device memory, without kernel boundaries.  Both compute the same values bit
+ * for bit.  ttq_plan_set_wait_limit bounds every
+ * wait between CTAs of the persistent search (nanoseconds of the GPU's global
+ * timer, default 1 s); a wait that passes it ends the run with
+ * TTQ_ERR_TIMEOUT and leaves the plan usable. */
+int ttq_plan_set_search(ttq_plan *plan, int mode);
+int ttq_plan_set_wait_limit(ttq_plan *plan, uint64_t ns);
+
 /* Bytes this plan has copied host->device (problem inputs, descriptor) and
  * device->host (state and flags read back) since it was created. */
 int ttq_plan_transfer_bytes(const ttq_plan *plan, int64_t *h2d, int64_t *d2h);
@@ -280,12 +294,14 @@ int ttq_plan_transfer_bytes(const ttq_plan *plan, int64_t *h2d, int64_t *d2h);
  * for each of the TTQ_NUM_KERNELS kernel kinds (index order: eval_slabs, qr
  * (both halves of the QR update), contract, samples, rook_col, rook_row,
  * update (the search's last decisions launch, which also ends the sweep),
- * init, setup, solve (the other decisions launches)), the summed
+ * init, setup, solve (the other decisions launches), search (the persistent
+ * search, whose FP64 operations count under samples, rook_col, rook_row and
+ * solve)), the summed
  * device time in ms and the launch count since the last reset, and the
  * algorithmic FP64 operations the kernel has done since the plan's state was
  * last set (cumulative; a division, exp or cosh counts as one operation, an
  * FMA as two).  Any output array may be NULL.  Synchronizes the stream. */
-#define TTQ_NUM_KERNELS 10
+#define TTQ_NUM_KERNELS 11
 int ttq_plan_set_timing(ttq_plan *plan, int enable);
 int ttq_plan_kernel_times(ttq_plan *plan, double *ms, int64_t *launches, double *flops, int reset);
 

@@ -247,6 +247,50 @@ def contract_exact(Bs: List[np.ndarray], Yd: np.ndarray) -> Fraction:
     return x[0]
 
 
+def contract_decimal(problem, st: CrossState, cores: List[np.ndarray], digits: int = 60, as_decimal: bool = False):
+    """Sec. 4.1's product (sum_i Y_1) G_1^-1 (sum_i Y_2) ... G_{d-1}^-1 (sum_i Y_d)
+    of the given FP64 cores (G_k = rows P_k of Y_k, as in integral_plain), every
+    step in `digits`-digit decimal arithmetic: node sums, the solves x G_k^-1
+    by Gaussian elimination with partial pivoting on G_k^T, the products with
+    the node sums.  FP64 values convert to decimals exactly, so the result is
+    the contraction of these cores up to ~cond * 10^-digits; returned with the
+    family constant, rounded to FP64 (as_decimal: the decimal itself)."""
+    from decimal import Decimal, localcontext
+    with localcontext() as ctx:
+        ctx.prec = digits
+
+        def vsum(T):
+            r0, N, r1 = T.shape
+            return [[sum((Decimal(float(v)) for v in T[a, :, b]), Decimal(0)) for b in range(r1)]
+                    for a in range(r0)]
+
+        def solve_left(G, x):                       # t with t G = x, i.e. G^T t = x
+            n = len(x)
+            M = [[G[j][i] for j in range(n)] + [x[i]] for i in range(n)]
+            for c in range(n):
+                p = max(range(c, n), key=lambda r: abs(M[r][c]))
+                M[c], M[p] = M[p], M[c]
+                for r in range(c + 1, n):
+                    f = M[r][c] / M[c][c]
+                    if f:
+                        M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+            t = [Decimal(0)] * n
+            for i in range(n - 1, -1, -1):
+                t[i] = (M[i][n] - sum((M[i][j] * t[j] for j in range(i + 1, n)), Decimal(0))) / M[i][i]
+            return t
+
+        x = vsum(cores[0])[0]
+        for k in range(1, problem.d):
+            rows = cross_rows(problem, st, k)
+            Gf = cores[k - 1].reshape(-1, st.rank(k))[rows, :]
+            x = solve_left([[Decimal(float(v)) for v in row] for row in Gf], x)
+            V = vsum(cores[k])
+            x = [sum((x[a] * V[a][b] for a in range(len(x))), Decimal(0)) for b in range(len(V[0]))]
+        c = family_constant(problem.family, problem.form, problem.n)
+        v = x[0] * Decimal(repr(c))
+        return v if as_decimal else float(v)
+
+
 # ---------------------------------------------------------------------------
 # Alg. 2 on one superblock
 # ---------------------------------------------------------------------------
@@ -424,6 +468,32 @@ def search_all(problem, st: CrossState, s: int, cores: List[np.ndarray], scale: 
     return pivots
 
 
+def search_sequential(problem, st: CrossState, s: int, cores: List[np.ndarray], scale: float):
+    """Alg. 5, one left-to-right sweep: for k = 1..d-1 in turn, Alg. 2 on the
+    superblock A(I_<=k-1^new i_k, i_{k+1} I_>k+1) built from the left set just
+    updated at step k-1 and the right set of the previous sweep, and the pivot
+    appended at once.  Cores k-1 and k change with step k-1's append and are
+    re-evaluated; scale is the largest |entry| evaluated so far.  Returns the
+    updated state, the pivots and the scale."""
+    d = problem.d
+    cores = list(cores)
+    pivots: List[Optional[Pivot]] = []
+    for k in range(1, d):
+        if k > 1 and pivots[-1] is not None and pivots[-1].accepted:
+            for q in (k - 1, k):                     # I_>k-1 and I_<=k-1 grew at step k-1
+                cores[q - 1] = core(problem, st, q)
+                scale = max(scale, float(np.max(np.abs(cores[q - 1]))))
+        if st.rank(k) >= problem.rank_cap:
+            pivots.append(None)
+            continue
+        B = maxvol_coefficients(cores[k - 1], cross_rows(problem, st, k))
+        pv = pivot_search(problem, st, k, B, cores[k], s, scale)
+        pivots.append(pv)
+        if pv is not None and pv.accepted:
+            st = apply_pivots(problem, st, [pv])
+    return st, pivots, scale
+
+
 def sweep(problem, st: CrossState, s: int, search: bool = True):
     """One sweep: cores, their largest |entry|, the integral, then (optionally)
     the pivot search on every interface."""
@@ -434,10 +504,11 @@ def sweep(problem, st: CrossState, s: int, search: bool = True):
     return value, cores, scale, pivots
 
 
-def integrate(problem, state: Optional[CrossState] = None, record: bool = True):
+def integrate(problem, state: Optional[CrossState] = None, record: bool = True, sequential: bool = False):
     """Run sweeps until a stopping rule fires.  Returns a dict with the value,
     status, sweeps, N_eval (core entries + search evaluations + initial scan),
-    final ranks, per-sweep history and the final state."""
+    final ranks, per-sweep history and the final state.  sequential: each
+    sweep is Alg. 5 (search_sequential) instead of Alg. 6 (search_all)."""
     d = problem.d
     if d < 2:
         raise ValueError("the cross needs d >= 2")
@@ -469,13 +540,17 @@ def integrate(problem, state: Optional[CrossState] = None, record: bool = True):
             status = STATUS_MAX_SWEEPS
             history.append(SweepRecord(value, st.ranks(), [], scale))
             break
-        pivots = search_all(problem, st, s, cores, scale)
+        ranks_before = st.ranks()
+        if sequential:
+            new_st, pivots, scale = search_sequential(problem, st, s, cores, scale)
+        else:
+            pivots = search_all(problem, st, s, cores, scale)
         search_evals += sum(p.evals for p in pivots if p is not None)
-        history.append(SweepRecord(value, st.ranks(), pivots, scale))
+        history.append(SweepRecord(value, ranks_before, pivots, scale))
         if not any(p is not None and p.accepted for p in pivots):
             status = STATUS_NO_PIVOT
             break
-        st = apply_pivots(problem, st, pivots)
+        st = new_st if sequential else apply_pivots(problem, st, pivots)
         prev = value
     ranks = st.ranks()
     core_entries = sum(ranks[k - 1] * problem.N[k - 1] * ranks[k] for k in range(1, d + 1))

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libttq.so")
 
 STATUS_NAMES = {0: "converged", 1: "no_pivot", 2: "rank_cap", 3: "max_sweeps", 4: "pending",
                 -1: "invalid_arg", -2: "nonfinite", -3: "singular", -4: "workspace", -5: "cuda",
-                -6: "admission", -7: "not_found"}
+                -6: "admission", -7: "not_found", -8: "timeout"}
 
 # function name -> (restype, argtypes); the exported surface of include/ttq.h
 _c = ctypes
@@ -66,6 +66,8 @@ SIGNATURES = {
     "ttq_plan_transfer_bytes": (_c.c_int, [_vp, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
     "ttq_plan_set_graphs": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_set_timing": (_c.c_int, [_vp, _c.c_int]),
+    "ttq_plan_set_search": (_c.c_int, [_vp, _c.c_int]),
+    "ttq_plan_set_wait_limit": (_c.c_int, [_vp, _c.c_uint64]),
     "ttq_plan_kernel_times": (_c.c_int, [_vp, _dp, _c.POINTER(_c.c_int64), _dp, _c.c_int]),
     "ttq_integrate_noalloc": (_c.c_int, [_c.POINTER(TTQProblem), _vp, _c.POINTER(TTQResult)]),
     "ttq_batch_workspace_bytes": (_c.c_int, [_c.POINTER(TTQProblem), _c.c_int, _c.POINTER(_c.c_size_t)]),
@@ -93,7 +95,7 @@ SIGNATURES = {
 }
 
 KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup",
-           "solve")
+           "solve", "search")
 
 _lib = None
 
@@ -299,6 +301,12 @@ class Plan:
 
     def set_timing(self, on: bool):
         _check(self.lib.ttq_plan_set_timing(self.h, 1 if on else 0), "ttq_plan_set_timing")
+
+    def set_search(self, persistent: bool):
+        _check(self.lib.ttq_plan_set_search(self.h, 1 if persistent else 0), "ttq_plan_set_search")
+
+    def set_wait_limit(self, ns: int):
+        _check(self.lib.ttq_plan_set_wait_limit(self.h, int(ns)), "ttq_plan_set_wait_limit")
 
     def kernel_times(self, reset: bool = False) -> Dict[str, Dict]:
         ms = (_c.c_double * len(KERNELS))()

@@ -35,7 +35,7 @@ static int set_err(int code, const char *msg) {
 
 // kernel ids of the timing counters (ttq_plan_kernel_times)
 enum { KT_EVAL = 0, KT_QR, KT_CONTRACT, KT_SAMPLES, KT_ROOK_COL, KT_ROOK_ROW, KT_UPDATE, KT_INIT, KT_SETUP,
-       KT_SOLVE, KT_N };
+       KT_SOLVE, KT_SEARCH, KT_N };
 
 #define TTQ_RESULT_SLOTS 64
 
@@ -78,6 +78,8 @@ struct ttq_plan {
   int in_loop;              // enqueueing the body of the WHILE node
   int sweep_kernels;        // kernels in one sweep
   State *slots;             // pinned host copies of the final state of launched runs
+  int persistent;           // one instance: the search of a sweep as one cooperative launch (k_search)
+  int search_grid, search_smem;
 };
 
 static cudaEvent_t ev_get(ttq_plan *P) {
@@ -345,6 +347,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
   D.d = d; D.family = p->family; D.form = p->form; D.n = p->n; D.cap = p->rank_cap;
   D.rook_max = p->rook_max; D.init_samples = p->init_samples; D.conv_window = p->conv_window;
   D.r0 = p->r0 < 1 ? 1 : p->r0;
+  D.wait_ns = 1000000000ULL;                // 1 s: far beyond any search (at most a few ms)
   D.max_sweeps = p->max_sweeps; D.prec = p->precision;
   D.tol = p->tol; D.pivot_tol = p->pivot_tol; D.seed = p->seed;
   D.constant = family_constant(p);
@@ -473,6 +476,22 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   P->samples_smem = (int)(((q_in ? 2 : 1) * cap * cap + (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap + 1)) * 8);
   P->contract_smem = (int)(cap * cap * 8);
   P->solve_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
+  // persistent search: R D^-1 (and Q) of the group's interface for the whole
+  // launch, then the samples' group vectors or the rook scratch in one region
+  {
+    const size_t vec = (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap + 1) * 8;
+    const size_t scr = vec > sizeof(RookSmem) ? vec : sizeof(RookSmem);
+    P->search_smem = (int)((q_in ? 2 : 1) * cap * cap * 8 + scr);
+    int dev = 0, sms = 152, occ = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, TTQ_WARPS * 32, P->search_smem) != cudaSuccess)
+      occ = 0;
+    // the resident CTA slots less two for the contraction's chains on the second stream
+    P->search_grid = occ >= 1 ? sms * occ - 2 : 0;
+    P->persistent = 0;                      // opt in with ttq_plan_set_search (measured slower, see DESIGN)
+    cudaGetLastError();
+  }
 }
 
 static cudaError_t set_smem_attributes(ttq_plan *P) {
@@ -483,6 +502,8 @@ static cudaError_t set_smem_attributes(ttq_plan *P) {
   if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
 }
@@ -660,12 +681,20 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   } else {
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
+  const int single_cond = P->in_loop && loop_end && nb == 1;
+  if (P->persistent && nb == 1) {
+    // the whole search in one cooperative launch; its end (ranks, stopping
+    // rules, the WHILE condition) after the contraction has joined
+    timed(P, KT_SEARCH, [&] { launch_k(P, k_search, dim3(P->search_grid, 1, 1), W, (size_t)P->search_smem, s, dv); });
+    if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
+    timed(P, KT_UPDATE, [&] { k_sweep_end<<<1, T, 0, s>>>(dv, P->cond, single_cond); });
+    return;
+  }
   // the samples stage ends, per interface, in its last CTA (the best sample and
   // the first column solve); each rook step is followed by the decisions kernel
   timed(P, KT_SAMPLES, [&] { launch_k(P, k_samples, dim3(P->sblocks, ni, nb), W, P->samples_smem, s, dv); });
   // the last decisions kernel also ends the sweep (appends, ranks, stopping
   // rules, the WHILE condition), after the contraction has joined
-  const int single_cond = P->in_loop && loop_end && nb == 1;
   for (int q = 0; q < P->rook_max; ++q) {
     const bool fin = q == P->rook_max - 1;
     timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
@@ -1002,7 +1031,10 @@ extern "C" int ttq_plan_sweep(ttq_plan *P, int sweep_index, int search, double *
       pv.evals = (int64_t)I.evals;
     }
   }
-  if (S.status < 0) return set_err(S.status, S.status == ST_ERR_SINGULAR ? "singular cross matrix" : "non-finite integrand");
+  if (S.status < 0)
+    return set_err(S.status, S.status == ST_ERR_SINGULAR ? "singular cross matrix"
+                             : S.status == ST_ERR_TIMEOUT ? "a wait between CTAs passed its limit"
+                                                          : "non-finite integrand");
   return TTQ_OK;
 }
 
@@ -1233,6 +1265,30 @@ extern "C" int ttq_plan_set_graphs(ttq_plan *P, int enable) {
   return TTQ_OK;
 }
 
+extern "C" int ttq_plan_set_search(ttq_plan *P, int mode) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (mode < 0 || mode > 1) return set_err(TTQ_ERR_INVALID_ARG, "search mode must be 0 (staged) or 1 (persistent)");
+  if (mode == 1 && (P->count != 1 || P->search_grid < P->max_ni))
+    return set_err(TTQ_ERR_INVALID_ARG, "the persistent search needs a single-instance plan that fits the device");
+  P->persistent = mode;
+  if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
+  if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_set_wait_limit(ttq_plan *P, uint64_t ns) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (ns < 1) return set_err(TTQ_ERR_INVALID_ARG, "wait limit must be >= 1 ns");
+  for (int q = 0; q < P->count; ++q) {
+    P->hs[q].wait_ns = ns;
+    Dev *dq = nullptr;
+    CK(cudaMemcpy(&dq, (char *)P->devs + q * sizeof(Dev *), sizeof(Dev *), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy((char *)dq + offsetof(Dev, wait_ns), &ns, sizeof(ns), cudaMemcpyHostToDevice));
+  }
+  P->h.wait_ns = ns;
+  return TTQ_OK;
+}
+
 extern "C" int ttq_plan_set_timing(ttq_plan *P, int enable) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
   P->timing = enable ? 1 : 0;
@@ -1270,6 +1326,7 @@ extern "C" const char *ttq_status_string(int s) {
     case TTQ_ERR_CUDA: return "CUDA error";
     case TTQ_ERR_ADMISSION: return "request exceeds the memory budget";
     case TTQ_ERR_NOT_FOUND: return "not found";
+    case TTQ_ERR_TIMEOUT: return "a wait between CTAs passed its limit";
     default: return "unknown status";
   }
 }

@@ -34,7 +34,7 @@ enum { FORM_RN = 0, FORM_CUBE = 1 };
 
 // status codes, mirror include/ttq.h
 enum { ST_OK = 0, ST_NO_PIVOT = 1, ST_RANK_CAP = 2, ST_MAX_SWEEPS = 3,
-       ST_ERR_NONFINITE = -2, ST_ERR_SINGULAR = -3 };
+       ST_ERR_NONFINITE = -2, ST_ERR_SINGULAR = -3, ST_ERR_TIMEOUT = -8 };
 
 struct IfaceState {
   int active;          // a pivot search is running on this interface this sweep
@@ -50,6 +50,7 @@ struct IfaceState {
   unsigned items_done;            // work items of the running stage completed so far
   int fix[TTQ_MAXD];              // node indices the next rook step fixes: modes k.. of gamma
                                   // (column step), modes ..k-1 of rho (row step)
+  unsigned epoch;                 // persistent search: stages of this sweep finished so far
 };
 
 struct State {
@@ -65,6 +66,7 @@ struct State {
   int nchanges;
   int stop_pending;         // a stopping rule fired in this sweep's contraction; applied at the end of the sweep
   int loop_guard;           // sweeps run by the device-side loop of this run (bounded by max_sweeps)
+  int search_abort;         // persistent search: a wait passed its limit; every CTA leaves the search
   unsigned batch_guard;     // sweeps run by a batch's loop (used in instance 0 of a batch)
   int pending_status;
   unsigned contract_arrive;  // CTAs of the two contraction chains that have finished
@@ -83,6 +85,7 @@ struct State {
 struct Dev {
   int d, family, form, n, cap, rook_max, init_samples, conv_window, max_sweeps, prec;
   int r0;                   // initial multi-indices (rank of every interface before the first sweep)
+  unsigned long long wait_ns;   // persistent search: limit of every wait between CTAs (globaltimer ns)
   int uniformT;             // 1: D in R^n on one shared uniform grid -> pair table T
   int sblocks, cblocks, rblocks;   // CTAs: per interface (samples), per instance (column / row)
   int sms;                  // SMs of the device (placement of the item deals)
@@ -455,7 +458,7 @@ __device__ __forceinline__ double fiber_value_tab(const Dev &D, int f, const int
   const double wi = D.w[o];
   const double s = u.S + D.c[o];
   const double rs = recip_nr(s);
-  double p = u.WP * wi * tab[i];
+  double p = u.WP * wi * __ldcg(tab + i);         // rebuilt every rook step: read through L2
   for (int j = jlo; j < jhi; ++j) {
     if (j == f) continue;
     const int dm = i - m[j];

@@ -366,7 +366,7 @@ __global__ void k_init(Dev *const *Dps) {
     for (int k = 0; k <= d; ++k) { st->r[k] = (k == 0 || k == d) ? 1 : rr; st->ro[k] = 0; }
     st->sweep = 0; st->status = ST_OK; st->stop = 0; st->nonfinite = 0; st->singular = 0;
     st->nchanges = 0; st->scale_bits = 0ULL; st->value = st->value_lo = st->prev = 0.0;
-    st->stop_pending = 0; st->pending_status = 0;
+    st->stop_pending = 0; st->pending_status = 0; st->search_abort = 0;
     for (int k = 0; k < TTQ_MAXD; ++k) { st->qr_rank[k] = 0; st->qr_row[k] = 0; }
     st->conv = __longlong_as_double(0x7ff0000000000000LL);
     st->search_evals = 0; st->init_evals = D.init_samples;
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (threadIdx.x == 0) {
     IfaceState &I = st->it[k];
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
-    I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0; I.items_done = 0;
+    I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0; I.items_done = 0; I.epoch = 0;
   }
   if (have == r) {
     if (threadIdx.x == 0) st->it[k].prank = -1;
@@ -1428,7 +1428,7 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     }
   } else if (mode == 1) {
     const int pick = stage_pick(D, k, 1, &e, qb, v, r);   // L_k(rho*, :) lands in v
-    const int prev = I.row, done_rounds = I.rounds;
+    const int prev = __ldcg(&I.row), done_rounds = __ldcg(&I.rounds);
     __syncthreads();                             // every thread has read the previous row
     // Eq. 2 already holds when the column search returns the row searched in the
     // previous round: that search returned the current column, so the pivot
@@ -1445,8 +1445,8 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     if (pick < 0) {
       if (tid == 0) I.active = 0;
     } else {
-      const int rounds = I.rounds + 1;
-      const bool done = (pick == I.col) || rounds >= D.rook_max;
+      const int rounds = __ldcg(&I.rounds) + 1;
+      const bool done = (pick == __ldcg(&I.col)) || rounds >= D.rook_max;
       __syncthreads();                           // every thread has read I.col
       if (tid == 0) { I.rounds = rounds; I.col = pick; I.err = e; I.rook_done = done ? 1 : 0; }
       if (!done) col = pick;
@@ -1478,7 +1478,7 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
   if (colsolve && mode == 0) {
-    for (int b = tid; b < r; b += nt) D.zvec[k][b] = D.zs[k][(size_t)spick * D.cap + b];
+    for (int b = tid; b < r; b += nt) D.zvec[k][b] = __ldcg(D.zs[k] + (size_t)spick * D.cap + b);
     if (tab) build_ptab(D, k, true, fm, nfm);
   } else if (colsolve) {
     // t = Q^T y (Q row-major: Q[b][i] at Q[b ld + i]), then R z = t
@@ -1513,42 +1513,47 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
 // arrived), then the last CTA of the instance to arrive applies the ranks, the
 // stopping rules and the sweep count and, inside the whole-run graph, sets the
 // WHILE condition: continue while the run is not over, never past max_sweeps.
-__device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHandle h, int use_cond) {
-  State *st = D.st;
-  const int d = D.d, tid = threadIdx.x, lane = lane_id();
-  __shared__ int last_s, nacc_s;
-  __shared__ unsigned long long ev_s;
-  const bool append = !st->stop && !st->stop_pending && st->search;   // changed below by the last CTA only
-  if (append && mine && warp_id() == 0) {
-    IfaceState &I = st->it[k];
-    const double scale = __longlong_as_double((long long)st->scale_bits);
-    const int a = st->r[k];
-    const bool acc = I.active && fabs(I.err) > D.pivot_tol * scale && a < D.cap;
-    if (lane == 0 && I.active) I.accepted = acc ? 1 : 0;
-    if (acc) {
-      const int Nk = D.N[k - 1], rn = st->r[k + 1];
-      const int alpha = I.row / Nk, i = I.row % Nk, j = I.col / rn, beta = I.col % rn;
-      if (lane < d) {
-        const int m = lane;
-        D.lidx[k][(size_t)a * d + m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
-        D.ridx[k][(size_t)a * d + m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
-      }
-      if (lane == 0) {
-        D.lpar[k][a] = alpha; D.lnode[k][a] = i;
-        D.rpar[k][a] = beta; D.rnode[k][a] = j;
-      }
+// The accepted pivot of interface k appended to its nested sets (warp 0 of
+// the calling CTA): new row alpha* + i* of I<=k, new column j* + beta* of
+// I>k, nested by construction; the neighbours' sets are read below their
+// current ranks, which nothing changes before the end of the sweep.
+__device__ void sweep_append(const Dev &D, State *st, int k) {
+  if (warp_id() != 0) return;
+  const int d = D.d, lane = lane_id();
+  IfaceState &I = st->it[k];
+  const double scale = __longlong_as_double((long long)st->scale_bits);
+  const int a = st->r[k];
+  const int active = __ldcg(&I.active);
+  const int prow = __ldcg(&I.row), pcol = __ldcg(&I.col);
+  const bool acc = active && fabs(__ldcg(&I.err)) > D.pivot_tol * scale && a < D.cap;
+  if (lane == 0 && active) I.accepted = acc ? 1 : 0;
+  if (acc) {
+    const int Nk = D.N[k - 1], rn = st->r[k + 1];
+    const int alpha = prow / Nk, i = prow % Nk, j = pcol / rn, beta = pcol % rn;
+    if (lane < d) {
+      const int m = lane;
+      D.lidx[k][(size_t)a * d + m] = (m < k - 1) ? D.lidx[k - 1][alpha * d + m] : (m == k - 1 ? i : -1);
+      D.ridx[k][(size_t)a * d + m] = (m == k) ? j : (m > k ? D.ridx[k + 1][beta * d + m] : -1);
+    }
+    if (lane == 0) {
+      D.lpar[k][a] = alpha; D.lnode[k][a] = i;
+      D.rpar[k][a] = beta; D.rnode[k][a] = j;
     }
   }
-  __threadfence();
+}
+
+// The end of the sweep proper (one whole CTA, after every interface's append
+// and the contraction): the ranks of the interfaces that accepted a pivot, the
+// sweep's evaluations, the stopping rules and the sweep count; inside the
+// whole-run graph it sets the WHILE condition: continue while the run is not
+// over, never past max_sweeps.  A search that gave up waiting (its wait limit
+// passed) ends the run with status TIMEOUT.
+__device__ void sweep_finalize(const Dev &D, State *st, bool append, cudaGraphConditionalHandle h, int use_cond) {
+  const int d = D.d, tid = threadIdx.x;
+  __shared__ int nacc_s;
+  __shared__ unsigned long long ev_s;
+  if (tid == 0) { nacc_s = 0; ev_s = 0ULL; }
   __syncthreads();
-  if (tid == 0) {
-    last_s = (atomicAdd(&st->end_arrive, 1u) == gridDim.x - 1) ? 1 : 0;
-    nacc_s = 0;
-    ev_s = 0ULL;
-  }
-  __syncthreads();
-  if (!last_s) return;
-  __threadfence();
   if (append) {
     // a thread per interface: its rank, the sweep's evaluations, the accepted count
     for (int q = tid + 1; q <= d - 1; q += blockDim.x) {
@@ -1564,6 +1569,9 @@ __device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHa
   if (tid == 0) {
     st->end_arrive = 0;
     if (st->stop) {
+    } else if (st->search_abort) {
+      st->stop = 1;
+      st->status = ST_ERR_TIMEOUT;
     } else if (st->stop_pending) {
       st->stop = 1;
       st->status = st->pending_status;
@@ -1580,6 +1588,23 @@ __device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHa
       cudaGraphSetConditional(h, cont ? 1u : 0u);
     }
   }
+}
+
+// End of the sweep (Alg. 6) in the last decisions kernel of the staged search:
+// every CTA appends its interface's accepted pivot, then the last CTA of the
+// instance to arrive finalizes the sweep.
+__device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHandle h, int use_cond) {
+  State *st = D.st;
+  __shared__ int last_s;
+  const bool append = !st->stop && !st->stop_pending && st->search && !st->search_abort;
+  if (append && mine) sweep_append(D, st, k);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_s = (atomicAdd(&st->end_arrive, 1u) == gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  sweep_finalize(D, st, append, h, use_cond);
 }
 
 // The decisions after a rook step (modes 1 and 2 of stage_finish), one CTA per
@@ -1709,107 +1734,91 @@ __device__ __forceinline__ double group_interp(const double *Qs, const double *R
   return acc;
 }
 
-__global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) {
-  // descriptor read in place: its shared-memory copy would cost the kernel its
-  // second resident CTA per SM (R, Q and the group vectors fill the rest)
-  const Dev &D = *Dps[blockIdx.z];
-  // the run flags, the ranks and the cross's parent pointers were last written
-  // at the end of the previous sweep, which had completed before kernel (b)
-  // passed its own wait: they are read before this kernel's wait
-  State *st = D.st;
-  const int k = blockIdx.y + 1;
-  if (!iface_searchable(D, st, k)) return;
-  __shared__ int mx[TTQ_WARPS][TTQ_MAXD][TTQ_SPW];   // node indices of the warp's points
-  __shared__ int rset[TTQ_MAXR], gset[TTQ_MAXR];      // cross rows / columns (excluded)
-  __shared__ double ri[TTQ_MAXR];
-  __shared__ SolveSmem sc;
-  extern __shared__ double fac[];
-  const int lane = lane_id(), warp = warp_id(), d = D.d;
+// What one CTA needs for the random-sample stage of interface k (Alg. 2,
+// first step): ranks, sizes, the counter-based stream, the factors of G_k in
+// shared memory (R D^-1 column-major, Q row-major or nullptr, 1/R_jj) and the
+// cross's rows and columns (excluded: the residual is zero there).
+struct SampleCtx {
+  int k, rk, rl, rn, Nk, Nk1, M, Ncol, S, flp;
+  unsigned long long sid;
+  const double *Rs, *Qs, *ri;
+  const int *rset, *gset;
+};
+
+// One task of TTQ_SPW samples by one warp: each lane of the first TTQ_SPW
+// draws a sample and tests the exclusion, then a group of TTQ_SG lanes per
+// sample evaluates A at the point and forms E = A - L_k(rho, :) G_k^-1 y, y =
+// R_{k+1}(:, gamma); every sample's z = G_k^-1 y is kept (zs), its score and
+// residual stored (cs, ce).  mxw: the warp's node-index scratch, yv: the
+// warp's group vectors (TTQ_SPW pairs of cap + 1).
+__device__ __forceinline__ void sample_task(const Dev &D, const SampleCtx &c, int task, int (*mxw)[TTQ_SPW],
+                                            double *yv, double &best, unsigned &nel, unsigned &nev,
+                                            unsigned long long &fl) {
+  const int lane = lane_id(), d = D.d;
   const int g = lane / TTQ_SG, gl = lane % TTQ_SG;
-  const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
-  const int Nk = D.N[k - 1], Nk1 = D.N[k];
-  const int M = rl * Nk, Ncol = Nk1 * rn, S = D.S[k];
-  double *Rs = fac;                                  // R column-major, ld rk
-  double *Qs = D.q_in_smem ? fac + (size_t)D.cap * D.cap : nullptr;   // Q row-major, ld rk
+  const int k = c.k, rk = c.rk, rn = c.rn, Nk = c.Nk, M = c.M, Ncol = c.Ncol, S = c.S;
+  const int *rset = c.rset, *gset = c.gset;
+  const double *Rs = c.Rs, *Qs = c.Qs, *ri = c.ri;
+  const unsigned long long sid = c.sid;
+  const int flp = c.flp;
   const int vst = D.cap + 1;                         // padded group vector stride
-  double *yv = fac + (size_t)D.cap * D.cap * (D.q_in_smem ? 2 : 1) + (size_t)warp * TTQ_SPW * 2 * vst;
   double *y = yv + g * 2 * vst, *t = y + vst;        // this group's y (then z) and Q^T y
-  for (int a = threadIdx.x; a < rk; a += blockDim.x) {
-    rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
-    gset[a] = D.rnode[k][a] * rn + D.rpar[k][a];
-  }
-  pdl_wait();
-  pdl_release();
-  // R D^-1 (column-major), Q and 1/R_jj from kernel (b), copied asynchronously
-  stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);
-  for (int a = threadIdx.x; a < rk; a += blockDim.x) cp_async8(ri + a, D.rinv[k] + a);
-  cp_async_wait_all();
-  __syncthreads();
-  const unsigned long long sid = stream_id(st->sweep, k, 1);
-  const int flp = point_flops(D);
-  double best = 0.0;
-  unsigned nel = 0, nev = 0;
-  unsigned long long fl = 0;
-  // tasks of TTQ_SPW samples dealt CTA-first, so the interface's CTAs (and the
-  // SMs they share) carry counts that differ by one task at most
-  const int ntask = (S + TTQ_SPW - 1) / TTQ_SPW;
-  for (int task = warp * gridDim.x + blockIdx.x; task < ntask; task += gridDim.x * TTQ_WARPS) {
-    const int base = task * TTQ_SPW;
-    // one lane per sample: draw and exclusion test
-    int rho = 0, gam = 0, ok = 0;
-    if (lane < TTQ_SPW && base + lane < S) {
-      const int tt = base + lane;
-      rho = draw_index(D.seed, sid, 2ULL * tt, (unsigned long long)M);
-      gam = draw_index(D.seed, sid, 2ULL * tt + 1, (unsigned long long)Ncol);
-      bool ex = false;
-      for (int a = 0; a < rk; ++a) ex |= (rset[a] == rho) | (gset[a] == gam);
-      if (ex) {
-        D.cs[k][tt] = -1.0;
-        D.ce[k][tt] = 0.0;
-      } else {
-        ok = 1;
-      }
-    }
-    // group g takes sample base + g: its node indices, then A at the point
-    rho = __shfl_sync(0xffffffffu, rho, g);
-    gam = __shfl_sync(0xffffffffu, gam, g);
-    ok = __shfl_sync(0xffffffffu, ok, g);
-    const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
-    // every group evaluates (full-warp shuffles inside); a group without a
-    // sample takes node 0 of every mode and its value is not used
-    for (int v = gl; v < d; v += TTQ_SG) {
-      int mv = 0;
-      if (ok) {
-        if (v < k - 1) mv = D.lidx[k - 1][alpha * d + v];
-        else if (v == k - 1) mv = i;
-        else if (v == k) mv = j;
-        else mv = D.ridx[k + 1][beta * d + v];
-      }
-      mx[warp][v][g] = mv;
-    }
-    __syncwarp();
-    double A = group_point_value<TTQ_SG>(D, &mx[warp][0][g], TTQ_SPW, gl);
-    if (!ok) A = 0.0;
-    for (int b = gl; b < rk; b += TTQ_SG) y[b] = ok ? D.Y[k + 1][core_at(D, k + 1, b, j, beta)] : 0.0;
-    __syncwarp();
-    const int nb = (rk + TTQ_SG - 1) / TTQ_SG;
-    double acc = 0.0;                             // L_k(rho, :) G_k^-1 y
-    // the sample's z = G^-1 y is kept: the best sample's is the first rook step's
-    double *zrow = D.zs[k] + (size_t)(base + g) * D.cap;
-    if (Qs && nb <= 8) {                          // ranks up to 8 TTQ_SG in registers
-      const double *lrow = D.Y[k] + core_at(D, k, alpha, i, 0);
-      const size_t lst = (size_t)D.capL[k - 1] * Nk;
-      switch (nb) {
-        case 8: acc = group_interp<8>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        case 7: acc = group_interp<7>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        case 6: acc = group_interp<6>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        case 5: acc = group_interp<5>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        case 4: acc = group_interp<4>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        case 3: acc = group_interp<3>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        case 2: acc = group_interp<2>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-        default: acc = group_interp<1>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
-      }
+  const int base = task * TTQ_SPW;
+  // one lane per sample: draw and exclusion test
+  int rho = 0, gam = 0, ok = 0;
+  if (lane < TTQ_SPW && base + lane < S) {
+    const int tt = base + lane;
+    rho = draw_index(D.seed, sid, 2ULL * tt, (unsigned long long)M);
+    gam = draw_index(D.seed, sid, 2ULL * tt + 1, (unsigned long long)Ncol);
+    bool ex = false;
+    for (int a = 0; a < rk; ++a) ex |= (rset[a] == rho) | (gset[a] == gam);
+    if (ex) {
+      D.cs[k][tt] = -1.0;
+      D.ce[k][tt] = 0.0;
     } else {
+      ok = 1;
+    }
+  }
+  // group g takes sample base + g: its node indices, then A at the point
+  rho = __shfl_sync(0xffffffffu, rho, g);
+  gam = __shfl_sync(0xffffffffu, gam, g);
+  ok = __shfl_sync(0xffffffffu, ok, g);
+  const int alpha = rho / Nk, i = rho % Nk, j = gam / rn, beta = gam % rn;
+  // every group evaluates (full-warp shuffles inside); a group without a
+  // sample takes node 0 of every mode and its value is not used
+  for (int v = gl; v < d; v += TTQ_SG) {
+    int mv = 0;
+    if (ok) {
+      if (v < k - 1) mv = D.lidx[k - 1][alpha * d + v];
+      else if (v == k - 1) mv = i;
+      else if (v == k) mv = j;
+      else mv = D.ridx[k + 1][beta * d + v];
+    }
+    mxw[v][g] = mv;
+  }
+  __syncwarp();
+  double A = group_point_value<TTQ_SG>(D, &mxw[0][g], TTQ_SPW, gl);
+  if (!ok) A = 0.0;
+  for (int b = gl; b < rk; b += TTQ_SG) y[b] = ok ? D.Y[k + 1][core_at(D, k + 1, b, j, beta)] : 0.0;
+  __syncwarp();
+  const int nb = (rk + TTQ_SG - 1) / TTQ_SG;
+  double acc = 0.0;                             // L_k(rho, :) G_k^-1 y
+  // the sample's z = G^-1 y is kept: the best sample's is the first rook step's
+  double *zrow = D.zs[k] + (size_t)(base + g) * D.cap;
+  if (Qs && nb <= 8) {                          // ranks up to 8 TTQ_SG in registers
+    const double *lrow = D.Y[k] + core_at(D, k, alpha, i, 0);
+    const size_t lst = (size_t)D.capL[k - 1] * Nk;
+    switch (nb) {
+      case 8: acc = group_interp<8>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      case 7: acc = group_interp<7>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      case 6: acc = group_interp<6>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      case 5: acc = group_interp<5>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      case 4: acc = group_interp<4>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      case 3: acc = group_interp<3>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      case 2: acc = group_interp<2>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+      default: acc = group_interp<1>(Qs, Rs, ri, y, lrow, lst, rk, ok, zrow); break;
+    }
+  } else {
     for (int r0 = gl; r0 < rk; r0 += TTQ_SG) {   // t = Q^T y
       double acc = 0.0;
       if (Qs) for (int b = 0; b < rk; ++b) acc = fma(Qs[b * rk + r0], y[b], acc);
@@ -1828,21 +1837,65 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
     }
     __syncwarp();
     if (ok) for (int b = gl; b < rk; b += TTQ_SG) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], y[b], acc);
-    }
-#pragma unroll
-    for (int o = TTQ_SG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (ok && gl == 0) {
-      const int tt = base + g;
-      const double E = A - acc;
-      const double sc = isfinite(E) ? fabs(E) : -1.0;
-      D.cs[k][tt] = sc;
-      D.ce[k][tt] = E;
-      ++nev;
-      if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
-      fl += (unsigned long long)flp + 3ULL * rk * rk + 2ULL * rk + 1;
-    }
-    __syncwarp();
   }
+#pragma unroll
+  for (int o = TTQ_SG / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (ok && gl == 0) {
+    const int tt = base + g;
+    const double E = A - acc;
+    const double sc = isfinite(E) ? fabs(E) : -1.0;
+    D.cs[k][tt] = sc;
+    D.ce[k][tt] = E;
+    ++nev;
+    if (sc >= 0.0) { best = fmax(best, sc); ++nel; }
+    fl += (unsigned long long)flp + 3ULL * rk * rk + 2ULL * rk + 1;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) {
+  // descriptor read in place: its shared-memory copy would cost the kernel its
+  // second resident CTA per SM (R, Q and the group vectors fill the rest)
+  const Dev &D = *Dps[blockIdx.z];
+  // the run flags, the ranks and the cross's parent pointers were last written
+  // at the end of the previous sweep, which had completed before kernel (b)
+  // passed its own wait: they are read before this kernel's wait
+  State *st = D.st;
+  const int k = blockIdx.y + 1;
+  if (!iface_searchable(D, st, k)) return;
+  __shared__ int mx[TTQ_WARPS][TTQ_MAXD][TTQ_SPW];   // node indices of the warp's points
+  __shared__ int rset[TTQ_MAXR], gset[TTQ_MAXR];      // cross rows / columns (excluded)
+  __shared__ double ri[TTQ_MAXR];
+  __shared__ SolveSmem sc;
+  extern __shared__ double fac[];
+  const int lane = lane_id(), warp = warp_id();
+  const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
+  const int Nk = D.N[k - 1], Nk1 = D.N[k];
+  double *Rs = fac;                                  // R column-major, ld rk
+  double *Qs = D.q_in_smem ? fac + (size_t)D.cap * D.cap : nullptr;   // Q row-major, ld rk
+  const int vst = D.cap + 1;
+  double *yv = fac + (size_t)D.cap * D.cap * (D.q_in_smem ? 2 : 1) + (size_t)warp * TTQ_SPW * 2 * vst;
+  for (int a = threadIdx.x; a < rk; a += blockDim.x) {
+    rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
+    gset[a] = D.rnode[k][a] * rn + D.rpar[k][a];
+  }
+  pdl_wait();
+  pdl_release();
+  // R D^-1 (column-major), Q and 1/R_jj from kernel (b), copied asynchronously
+  stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);
+  for (int a = threadIdx.x; a < rk; a += blockDim.x) cp_async8(ri + a, D.rinv[k] + a);
+  cp_async_wait_all();
+  __syncthreads();
+  const SampleCtx c = {k, rk, rl, rn, Nk, Nk1, rl * Nk, Nk1 * rn, D.S[k], point_flops(D),
+                       stream_id(st->sweep, k, 1), Rs, Qs, ri, rset, gset};
+  double best = 0.0;
+  unsigned nel = 0, nev = 0;
+  unsigned long long fl = 0;
+  // tasks of TTQ_SPW samples dealt CTA-first, so the interface's CTAs (and the
+  // SMs they share) carry counts that differ by one task at most
+  const int ntask = (c.S + TTQ_SPW - 1) / TTQ_SPW;
+  for (int task = warp * gridDim.x + blockIdx.x; task < ntask; task += gridDim.x * TTQ_WARPS)
+    sample_task(D, c, task, mx[warp], yv, best, nel, nev, fl);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -2089,6 +2142,69 @@ __device__ __forceinline__ void rook_piece(RookDeal &q, int k, int ok, int N, in
   }
 }
 
+// One piece of the column step of interface k (one warp): rows rho = (alpha,
+// i) for the nq rows of 32 nodes from q0 of fiber alpha, E = A(rho, gamma*) -
+// L_k(rho, :) z, z = G_k^-1 R_{k+1}(:, gamma*) (zvec, copied to the warp's
+// shared vector when zk != k), candidates and per-row maxima stored, pass 1 of
+// the argmax.  The piece's loads form one round: z, the fiber's left indices,
+// the fixed right indices (I.fix), the cross's parent pointers.
+__device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh, int k, int alpha, int q0, int nq,
+                                          int rk, int &zk, unsigned long long &fl) {
+  const int lane = lane_id(), warp = warp_id(), d = D.d;
+  IfaceState &I = st->it[k];
+  const int Nk = D.N[k - 1], rows = (Nk + 31) >> 5;
+  const int i0 = 32 * q0, i1 = min(Nk, 32 * (q0 + nq)), slot0 = alpha * rows + q0;
+  double zr[TTQ_MAXR / 32];
+  int lp[TTQ_MAXR / 32], ln[TTQ_MAXR / 32];
+  const bool newz = k != zk;
+#pragma unroll
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+    const int a = lane + 32 * q;
+    zr[q] = (newz && a < rk) ? __ldcg(D.zvec[k] + a) : 0.0;
+    lp[q] = a < rk ? D.lpar[k][a] : -1;
+    ln[q] = a < rk ? D.lnode[k][a] : 0;
+  }
+  const int vl = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : 0;
+  const int vr = (lane >= k && lane < d) ? __ldcg(I.fix + lane) : 0;
+  if (newz) {
+#pragma unroll
+    for (int q = 0; q < TTQ_MAXR / 32; ++q)
+      if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
+    zk = k;
+  }
+  if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : vr;
+  // rows of the cross with this parent alpha: excluded nodes i
+  int nex = 0;
+#pragma unroll
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+    const bool hit = lp[q] == alpha;
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = ln[q];
+    nex += __popc(bal);
+  }
+  __syncwarp();
+  FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
+  // per node: the entry (the shared right-mode factors come from the step's table), the product, the residual
+  const int tabbed = uses_ptab(D, rk) ? (d - k) - 1 : 0;
+  fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node - tabbed + 2 * rk + 1);
+  unsigned nel = 0, nev = 0;
+#define TTQ_COL_PIECE(Q)                                                                                      \
+  {                                                                                                           \
+    unsigned long long bq[Q];                                                                                 \
+    col_item<Q>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
+                nev);                                                                                         \
+    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                            \
+  }
+  switch (nq) {
+    case 4: TTQ_COL_PIECE(4) break;
+    case 3: TTQ_COL_PIECE(3) break;
+    case 2: TTQ_COL_PIECE(2) break;
+    default: TTQ_COL_PIECE(1) break;
+  }
+#undef TTQ_COL_PIECE
+  __syncwarp();
+}
+
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i) of every
 // searching interface; pass 1 of the argmax per interface (pass 2 in k_solve).
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps) {
@@ -2098,7 +2214,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   pdl_release();
   State *st = D.st;
   __shared__ RookSmem sh;
-  const int lane = lane_id(), warp = warp_id(), d = D.d;
+  const int lane = lane_id(), d = D.d;
   // one round of loads: the run's flags and, lane k-1, interface k's search
   // state and the ranks around it
   const int stop = st->stop, search = st->search;
@@ -2118,64 +2234,70 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   while (dl.pos < dl.end) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);                  // interface (1-based)
-    IfaceState &I = st->it[k];
     const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rl = __shfl_sync(0xffffffffu, r0, k - 1);
-    const int Nk = D.N[k - 1], rows = (Nk + 31) >> 5;
     int alpha, q0, nq;
-    rook_piece(dl, k, rl, Nk, alpha, q0, nq);
-    const int i0 = 32 * q0, i1 = min(Nk, 32 * (q0 + nq)), slot0 = alpha * rows + q0;
-    // the piece's loads in one round: z, left indices, the fixed right indices, the cross's parent pointers
-    double zr[TTQ_MAXR / 32];
-    int lp[TTQ_MAXR / 32], ln[TTQ_MAXR / 32];
-    const bool newz = k != zk;
-#pragma unroll
-    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
-      const int a = lane + 32 * q;
-      zr[q] = (newz && a < rk) ? D.zvec[k][a] : 0.0;
-      lp[q] = a < rk ? D.lpar[k][a] : -1;
-      ln[q] = a < rk ? D.lnode[k][a] : 0;
-    }
-    const int vl = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : 0;
-    const int vr = (lane >= k && lane < d) ? I.fix[lane] : 0;
-    if (newz) {
-#pragma unroll
-      for (int q = 0; q < TTQ_MAXR / 32; ++q)
-        if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
-      zk = k;
-    }
-    if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : vr;
-    // rows of the cross with this parent alpha: excluded nodes i
-    int nex = 0;
-#pragma unroll
-    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
-      const bool hit = lp[q] == alpha;
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = ln[q];
-      nex += __popc(bal);
-    }
-    __syncwarp();
-    FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
-    // per node: the entry (the shared right-mode factors come from the step's table), the product, the residual
-    const int tabbed = uses_ptab(D, rk) ? (d - k) - 1 : 0;
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node - tabbed + 2 * rk + 1);
-    unsigned nel = 0, nev = 0;
-#define TTQ_COL_PIECE(Q)                                                                                      \
-  {                                                                                                           \
-    unsigned long long bq[Q];                                                                                 \
-    col_item<Q>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
-                nev);                                                                                         \
-    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                            \
-  }
-    switch (nq) {
-      case 4: TTQ_COL_PIECE(4) break;
-      case 3: TTQ_COL_PIECE(3) break;
-      case 2: TTQ_COL_PIECE(2) break;
-      default: TTQ_COL_PIECE(1) break;
-    }
-#undef TTQ_COL_PIECE
-    __syncwarp();
+    rook_piece(dl, k, rl, D.N[k - 1], alpha, q0, nq);
+    col_piece(D, st, sh, k, alpha, q0, nq, rk, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
+}
+
+// One piece of the row step of interface k (one warp): columns gamma = (j,
+// beta) for the nq rows of 32 nodes j from q0 of fiber beta, E = A(rho*, gamma)
+// - l^T R_{k+1}(:, gamma) with z = G_k^-T l; as col_piece.
+__device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh, int k, int beta, int q0, int nq,
+                                          int rk, int rn, int &zk, unsigned long long &fl) {
+  const int lane = lane_id(), warp = warp_id(), d = D.d;
+  IfaceState &I = st->it[k];
+  const int Nk1 = D.N[k], rows = (Nk1 + 31) >> 5;
+  const int j0 = 32 * q0, j1 = min(Nk1, 32 * (q0 + nq)), slot0 = beta * rows + q0;
+  double zr[TTQ_MAXR / 32];
+  int rp[TTQ_MAXR / 32], rnd[TTQ_MAXR / 32];
+  const bool newz = k != zk;
+#pragma unroll
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+    const int b = lane + 32 * q;
+    zr[q] = (newz && b < rk) ? __ldcg(D.zvec[k] + b) : 0.0;
+    rp[q] = b < rk ? D.rpar[k][b] : -1;
+    rnd[q] = b < rk ? D.rnode[k][b] : 0;
+  }
+  const int vr = (lane > k && lane < d) ? D.ridx[k + 1][beta * d + lane] : 0;
+  const int vl = (lane < k) ? __ldcg(I.fix + lane) : 0;
+  if (newz) {
+#pragma unroll
+    for (int q = 0; q < TTQ_MAXR / 32; ++q)
+      if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
+    zk = k;
+  }
+  if (lane < d) sh.ms[warp][lane] = (lane < k) ? vl : vr;
+  int nex = 0;
+#pragma unroll
+  for (int q = 0; q < TTQ_MAXR / 32; ++q) {
+    const bool hit = rp[q] == beta;
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = rnd[q];
+    nex += __popc(bal);
+  }
+  __syncwarp();
+  FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
+  const int tabbed = uses_ptab(D, rk) ? k - 1 : 0;
+  fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node - tabbed + 2 * rk + 1);
+  unsigned nel = 0, nev = 0;
+#define TTQ_ROW_PIECE(Q)                                                                                           \
+  {                                                                                                                \
+    unsigned long long bq[Q];                                                                                      \
+    row_item<Q>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
+                nev);                                                                                              \
+    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                                 \
+  }
+  switch (nq) {
+    case 4: TTQ_ROW_PIECE(4) break;
+    case 3: TTQ_ROW_PIECE(3) break;
+    case 2: TTQ_ROW_PIECE(2) break;
+    default: TTQ_ROW_PIECE(1) break;
+  }
+#undef TTQ_ROW_PIECE
+  __syncwarp();
 }
 
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
@@ -2188,7 +2310,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   pdl_release();
   State *st = D.st;
   __shared__ RookSmem sh;
-  const int lane = lane_id(), warp = warp_id(), d = D.d;
+  const int lane = lane_id(), d = D.d;
   const int stop = st->stop, search = st->search;
   int act = 0, r1 = 0, r2 = 0, Nl = 1;
   if (lane < d - 1) {
@@ -2206,61 +2328,306 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   while (dl.pos < dl.end) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);
-    IfaceState &I = st->it[k];
     const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rn = __shfl_sync(0xffffffffu, r2, k - 1);
-    const int Nk1 = D.N[k], rows = (Nk1 + 31) >> 5;
     int beta, q0, nq;
-    rook_piece(dl, k, rn, Nk1, beta, q0, nq);
-    const int j0 = 32 * q0, j1 = min(Nk1, 32 * (q0 + nq)), slot0 = beta * rows + q0;
-    double zr[TTQ_MAXR / 32];
-    int rp[TTQ_MAXR / 32], rnd[TTQ_MAXR / 32];
-    const bool newz = k != zk;
-#pragma unroll
-    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
-      const int b = lane + 32 * q;
-      zr[q] = (newz && b < rk) ? D.zvec[k][b] : 0.0;
-      rp[q] = b < rk ? D.rpar[k][b] : -1;
-      rnd[q] = b < rk ? D.rnode[k][b] : 0;
-    }
-    const int vr = (lane > k && lane < d) ? D.ridx[k + 1][beta * d + lane] : 0;
-    const int vl = (lane < k) ? I.fix[lane] : 0;
-    if (newz) {
-#pragma unroll
-      for (int q = 0; q < TTQ_MAXR / 32; ++q)
-        if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
-      zk = k;
-    }
-    if (lane < d) sh.ms[warp][lane] = (lane < k) ? vl : vr;
-    int nex = 0;
-#pragma unroll
-    for (int q = 0; q < TTQ_MAXR / 32; ++q) {
-      const bool hit = rp[q] == beta;
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) sh.exc[warp][nex + __popc(bal & ((1u << lane) - 1))] = rnd[q];
-      nex += __popc(bal);
-    }
-    __syncwarp();
-    FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
-    const int tabbed = uses_ptab(D, rk) ? k - 1 : 0;
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node - tabbed + 2 * rk + 1);
-    unsigned nel = 0, nev = 0;
-#define TTQ_ROW_PIECE(Q)                                                                                           \
-  {                                                                                                                \
-    unsigned long long bq[Q];                                                                                      \
-    row_item<Q>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
-                nev);                                                                                              \
-    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                                 \
-  }
-    switch (nq) {
-      case 4: TTQ_ROW_PIECE(4) break;
-      case 3: TTQ_ROW_PIECE(3) break;
-      case 2: TTQ_ROW_PIECE(2) break;
-      default: TTQ_ROW_PIECE(1) break;
-    }
-#undef TTQ_ROW_PIECE
-    __syncwarp();
+    rook_piece(dl, k, rn, D.N[k], beta, q0, nq);
+    row_piece(D, st, sh, k, beta, q0, nq, rk, rn, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent search (one instance): the whole of Alg. 2 on every interface of
+// a sweep in one cooperative launch, without kernel boundaries between its
+// stages.  Every CTA belongs to the group of one interface for the whole
+// launch (groups sized by the interface's expected work: samples S_k (3 r_k^2)
+// plus the rook rows (r_{k-1} N_k + N_{k+1} r_{k+1}) (2 r_k)), and each group
+// runs its interface's stages by itself: random samples, then up to rook_max
+// column / row rounds.  A stage's CTAs deal its rows (or sample tasks) among
+// themselves; each CTA arrives on the interface's counter when its share is
+// done, and the last to arrive takes the stage's decisions (stage_finish:
+// argmax pass 2, the rook test, the next solve, with the factors of G_k that
+// every CTA of the group holds in shared memory) and publishes them by
+// raising the interface's epoch; the group's other CTAs wait for that epoch.
+// The CTA whose decisions end the interface's search appends its pivot.  The
+// ranks, stopping rules and the sweep count follow in k_sweep_end.
+//
+// Every wait is bounded: past D.wait_ns of %globaltimer after the launch
+// began, the waiting CTA sets st->search_abort and leaves, and every other
+// wait sees the flag and leaves too; the sweep then ends with status TIMEOUT.
+// The grid is the device's resident CTA slots less the two the contraction
+// takes on the second stream, so in a correct run every CTA is resident and no
+// wait depends on a CTA that is not running; were one held back (another
+// kernel on the device), its group would wait until it runs, at most the limit.
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Interface state written by another CTA of the launch is read through L2
+// (__ldcg): the L1 of this SM may hold a copy older than the writer's stores.
+__device__ __forceinline__ bool iface_running(const IfaceState &I) {
+  return __ldcg(&I.active) && !__ldcg(&I.rook_done);
+}
+
+// whole CTA: wait until interface k's epoch reaches e; false if the search was
+// abandoned (by this wait's limit or another CTA's)
+__device__ bool group_wait(State *st, int k, unsigned e, unsigned long long deadline) {
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    volatile unsigned *ep = &st->it[k].epoch;
+    volatile int *ab = &st->search_abort;
+    int ok = 1;
+    while (*ep < e) {
+      if (*ab) { ok = 0; break; }
+      if (global_ns() > deadline) { atomicExch(&st->search_abort, 1); ok = 0; break; }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// whole CTA: this CTA's share of the stage is done; true in the last of the
+// group's g CTAs to arrive (which then sees every other CTA's writes)
+__device__ bool group_arrive(State *st, int k, int g) {
+  __shared__ int last_s;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned old = atomicAdd(&st->it[k].items_done, 1u);
+    last_s = (old == (unsigned)g - 1) ? 1 : 0;
+    if (last_s) st->it[k].items_done = 0;
+  }
+  __syncthreads();
+  if (last_s) __threadfence();
+  return last_s != 0;
+}
+
+// whole CTA (the finisher): publish the stage's decisions
+__device__ void group_publish(State *st, int k, unsigned e) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(&st->it[k].epoch, e);
+}
+
+// Interface k's share of the launch's CTAs (k = 1..d-1; 0 for an interface
+// that does not search) and its first CTA; the same in every CTA.
+__device__ void search_groups(const Dev &D, const State *st, int G, int *first, int *count) {
+  const int d = D.d, ni = d - 1;
+  double w[TTQ_MAXD];
+  double W = 0.0;
+  int na = 0;
+  for (int k = 1; k <= ni; ++k) {
+    w[k] = 0.0;
+    if (!iface_searchable(D, st, k)) continue;
+    const double rk = st->r[k];
+    const double rows = (double)st->r[k - 1] * D.N[k - 1] + (double)D.N[k] * st->r[k + 1];
+    w[k] = (double)D.S[k] * (3.0 * rk * rk + 64.0) + (double)D.rook_max * rows * (2.0 * rk + 32.0);
+    W += w[k];
+    ++na;
+  }
+  int used = 0;
+  for (int k = 1; k <= ni; ++k) {
+    count[k] = (w[k] > 0.0) ? 1 + (int)floor((double)(G - na) * w[k] / W) : 0;
+    used += count[k];
+  }
+  // CTAs left by the rounding go one each to the heaviest interfaces (ties: lowest k)
+  while (used < G && na > 0) {
+    int best = 0;
+    for (int k = 1; k <= ni; ++k)
+      if (w[k] > 0.0 && (best == 0 || w[k] > w[best])) best = k;
+    for (int k = 1; k <= ni && used < G; ++k)
+      if (w[k] > 0.0 && w[k] >= w[best]) { count[k]++; used++; }
+    if (used < G)
+      for (int k = 1; k <= ni && used < G; ++k)
+        if (w[k] > 0.0) { count[k]++; used++; }
+  }
+  int o = 0;
+  for (int k = 1; k <= ni; ++k) { first[k] = o; o += count[k]; }
+}
+
+// Deal of one interface's rook-step rows over its group's W = g * TTQ_WARPS
+// warps (warp slot w = warp * g + gi, CTA-first): items of R rows (R = 1, 2,
+// 4, the smallest whose items fit one wave of the group's warps), else
+// balanced contiguous stretches in pieces of at most four rows that stop at
+// fiber ends.  Pieces come out as (outer index, first row, rows).
+struct GroupDeal {
+  int R, pos, end;
+  bool items;
+};
+__device__ __forceinline__ GroupDeal group_deal(int outer, int N, int g, int gi) {
+  const long long W = (long long)g * TTQ_WARPS;
+  GroupDeal q;
+  int R = 1;
+  for (; R < 4; R *= 2)
+    if ((long long)outer * node_chunks(N, R).nch <= W) break;
+  q.R = R;
+  const long long items = (long long)outer * node_chunks(N, R).nch;
+  q.items = items <= W;
+  const long long total = q.items ? items : (long long)outer * ((N + 31) >> 5);
+  const long long w = (long long)warp_id() * g + gi;
+  if (q.items) {
+    q.pos = (int)w;
+    q.end = w < total ? (int)w + 1 : (int)w;
+  } else {
+    q.pos = (int)(w * total / W);
+    q.end = (int)((w + 1) * total / W);
+  }
+  return q;
+}
+__device__ __forceinline__ void group_piece(GroupDeal &q, int outer, int N, int &o, int &q0, int &nq) {
+  const int local = q.pos;
+  if (q.items) {
+    const NodeChunks nc = node_chunks(N, q.R);
+    const int ch = local / outer;
+    o = local % outer;
+    q0 = ch * nc.base + min(ch, nc.extra);
+    nq = nc.base + (ch < nc.extra ? 1 : 0);
+    q.pos += 1;
+  } else {
+    const int rows = (N + 31) >> 5;
+    o = local / rows;
+    q0 = local % rows;
+    nq = min(min(4, rows - q0), q.end - q.pos);
+    q.pos += nq;
+  }
+}
+
+__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_search(Dev *const *Dps) {
+  // descriptor read in place (as in k_samples): shared memory holds the
+  // factors of G_k and the stage scratch, two CTAs per SM at rank cap 64
+  const Dev &D = *Dps[blockIdx.z];
+  State *st = D.st;
+  const unsigned long long deadline = global_ns() + D.wait_ns;
+  if (st->stop || !st->search) return;
+  __shared__ int first_s[TTQ_MAXD], count_s[TTQ_MAXD];
+  __shared__ int mx[TTQ_WARPS][TTQ_MAXD][TTQ_SPW];
+  __shared__ int rset[TTQ_MAXR], gset[TTQ_MAXR];
+  __shared__ double ri[TTQ_MAXR];
+  __shared__ SolveSmem sc;
+  extern __shared__ double fac[];
+  if (threadIdx.x == 0) search_groups(D, st, gridDim.x, first_s, count_s);
+  __syncthreads();
+  int k = 0;
+  for (int q = 1; q <= D.d - 1; ++q)
+    if (count_s[q] > 0 && (int)blockIdx.x >= first_s[q] && (int)blockIdx.x < first_s[q] + count_s[q]) k = q;
+  // the ranks and run flags were written by the previous sweep's end; the
+  // interface states (reset) and the factors come from kernel (b): waited for
+  pdl_wait();
+  if (k == 0) return;                            // CTAs beyond every group (none when all are dealt)
+  const int g = count_s[k], gi = blockIdx.x - first_s[k];
+  const int lane = lane_id(), warp = warp_id();
+  IfaceState &I = st->it[k];
+  const int rk = st->r[k], rl = st->r[k - 1], rn = st->r[k + 1];
+  const int Nk = D.N[k - 1], Nk1 = D.N[k];
+  // the row solves read D^-1 R and Q column-major from global memory: the
+  // group pulls them into L2 now, a row per CTA in turn
+  for (int a = gi; a < rk; a += g)
+    for (int c = 16 * threadIdx.x; c < rk; c += 16 * blockDim.x) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(D.Sr[k] + (size_t)a * D.cap + c));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(D.Qc[k] + (size_t)a * D.cap + c));
+    }
+  const size_t cc = (size_t)D.cap * D.cap;
+  double *Rs = fac;                              // R D^-1 column-major, ld rk (whole launch)
+  double *Qs = D.q_in_smem ? fac + cc : nullptr; // Q row-major, ld rk (whole launch)
+  double *scratch = fac + cc * (D.q_in_smem ? 2 : 1);   // samples' group vectors, then the rook scratch
+  RookSmem &sh = *reinterpret_cast<RookSmem *>(scratch);
+  stage_compact_async(Rs, D.Cc[k], Qs, D.Qr[k], rk, D.cap);
+  for (int a = threadIdx.x; a < rk; a += blockDim.x) {
+    cp_async8(ri + a, D.rinv[k] + a);
+    rset[a] = D.lpar[k][a] * Nk + D.lnode[k][a];
+    gset[a] = D.rnode[k][a] * rn + D.rpar[k][a];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // stage 0: random samples (Alg. 2, first step), tasks dealt CTA-first in the group
+  {
+    const SampleCtx c = {k, rk, rl, rn, Nk, Nk1, rl * Nk, Nk1 * rn, D.S[k], point_flops(D),
+                         stream_id(st->sweep, k, 1), Rs, Qs, ri, rset, gset};
+    double *yv = scratch + (size_t)warp * TTQ_SPW * 2 * (D.cap + 1);
+    double best = 0.0;
+    unsigned nel = 0, nev = 0;
+    unsigned long long fl = 0;
+    const int ntask = (c.S + TTQ_SPW - 1) / TTQ_SPW;
+    for (int task = warp * g + gi; task < ntask; task += g * TTQ_WARPS)
+      sample_task(D, c, task, mx[warp], yv, best, nel, nev, fl);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+      nel += __shfl_xor_sync(0xffffffffu, nel, o);
+      nev += __shfl_xor_sync(0xffffffffu, nev, o);
+      fl += __shfl_xor_sync(0xffffffffu, fl, o);
+    }
+    if (lane == 0) {
+      if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
+      if (fl) atomicAdd(&st->flops[3], fl);
+      stage_publish(I, best, nel);
+    }
+  }
+  if (group_arrive(st, k, g)) {
+    stage_finish(D, k, 0, Rs, Qs, ri, sc);
+    if (!iface_running(I)) sweep_append(D, st, k);
+    group_publish(st, k, 1u);
+  }
+  unsigned e = 1;
+  unsigned long long fl_col = 0, fl_row = 0;
+  for (int round = 0; round < D.rook_max; ++round) {
+    // column step: E(:, gamma*) over the rows rho = (alpha, i), alpha < r_{k-1}
+    if (!group_wait(st, k, e, deadline)) break;
+    if (!iface_running(I)) break;
+    {
+      int zk = 0;
+      GroupDeal q = group_deal(rl, Nk, g, gi);
+      while (q.pos < q.end) {
+        int alpha, q0, nq;
+        group_piece(q, rl, Nk, alpha, q0, nq);
+        col_piece(D, st, sh, k, alpha, q0, nq, rk, zk, fl_col);
+      }
+    }
+    ++e;
+    if (group_arrive(st, k, g)) {
+      stage_finish(D, k, 1, nullptr, nullptr, ri, sc);
+      if (!iface_running(I)) sweep_append(D, st, k);
+      group_publish(st, k, e);
+    }
+    // row step: E(rho*, :) over the columns gamma = (j, beta), beta < r_{k+1}
+    if (!group_wait(st, k, e, deadline)) break;
+    if (!iface_running(I)) break;
+    {
+      int zk = 0;
+      GroupDeal q = group_deal(rn, Nk1, g, gi);
+      while (q.pos < q.end) {
+        int beta, q0, nq;
+        group_piece(q, rn, Nk1, beta, q0, nq);
+        row_piece(D, st, sh, k, beta, q0, nq, rk, rn, zk, fl_row);
+      }
+    }
+    ++e;
+    if (group_arrive(st, k, g)) {
+      stage_finish(D, k, 2, Rs, Qs, ri, sc);
+      if (!iface_running(I)) sweep_append(D, st, k);
+      group_publish(st, k, e);
+    }
+  }
+  if (lane == 0) {
+    if (fl_col) atomicAdd(&st->flops[4], fl_col);
+    if (fl_row) atomicAdd(&st->flops[5], fl_row);
+  }
+}
+
+// The end of a sweep whose search ran in k_search (one CTA, after the
+// contraction has joined): ranks, evaluations, stopping rules, sweep count and
+// the WHILE condition (sweep_finalize).
+__global__ void __launch_bounds__(256) k_sweep_end(Dev *const *Dps, cudaGraphConditionalHandle h, int use_cond) {
+  const Dev &D = *Dps[blockIdx.z];
+  State *st = D.st;
+  const bool append = !st->stop && !st->stop_pending && st->search && !st->search_abort;
+  sweep_finalize(D, st, append, h, use_cond);
 }
 
 // The tensor train of one instance copied out to a caller's buffer in the

@@ -130,10 +130,19 @@ def config_c4(**kw) -> Problem:
 
 def config_d12(**kw) -> Problem:
     """D_12 in R^12, trapezoid [-24,24] with 385 nodes/mode (h = 0.125), rank cap 64, tol 1e-12,
-    seeded random initial index sets: r0 = 4 multi-indices."""
-    args = dict(rank_cap=64, tol=1e-12, seed=12, r0=4, name="D12_rn_N385_r64")
+    seeded random initial index set (r0 = 1: the largest |A| of 64 seeded random points)."""
+    args = dict(rank_cap=64, tol=1e-12, seed=12, name="D12_rn_N385_r64")
     args.update(kw)
     return make_problem("D", "rn", 12, 385, L=24.0, **args)
+
+
+def config_d12_r4(**kw) -> Problem:
+    """D_12 as config_d12 but from r0 = 4 seeded initial multi-indices, with the
+    double-double final contraction: its final cross matrices are conditioned so
+    that an FP64 contraction of them (LU or QR) is accurate to ~1e-11 only."""
+    args = dict(r0=4, precision="dd", name="D12_rn_N385_r64_r0_4")
+    args.update(kw)
+    return config_d12(**args)
 
 
 def config_e16(**kw) -> Problem:

@@ -2,7 +2,8 @@
 C_4, D_12 and E_16 workloads and on D_8 and D_16 in the paper's unit-cube form
 with Gauss-Legendre 129 nodes and C_8 .. C_32 in that form with 33 nodes (seeded, synthetic grids from
 paper_1903_11554_gb300.inputs): value, status, sweeps, evaluations, final
-ranks and nested sets, and per sweep the integral and the ranks.  Calls only
+ranks and nested sets, per sweep the integral and the ranks, and the final
+cross contracted at 60 digits (oracle.ttcross.contract_decimal).  Calls only
 the oracle; takes ~40 min.
 
     python tests/golden/make_oracle_values.py [c4 d12 e16 d8 d16 c8_cube c16_cube c24_cube c32_cube]
@@ -18,7 +19,8 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import ttcross  # noqa: E402
 from paper_1903_11554_gb300 import inputs  # noqa: E402
 
-CONFIGS = {"c4": inputs.config_c4, "d12": inputs.config_d12, "e16": inputs.config_e16,
+CONFIGS = {"c4": inputs.config_c4, "d12": inputs.config_d12, "d12_r4": inputs.config_d12_r4,
+           "e16": inputs.config_e16,
            "d8": lambda: inputs.config_d_cube(8), "d16": lambda: inputs.config_d_cube(16),
            "c8_cube": lambda: inputs.config_c_cube(8), "c16_cube": lambda: inputs.config_c_cube(16),
            "c24_cube": lambda: inputs.config_c_cube(24), "c32_cube": lambda: inputs.config_c_cube(32)}
@@ -43,6 +45,10 @@ def main(names):
             "internal_conv": r["internal_conv"],
             "history": [repr(h.value) for h in r["history"]],
             "history_ranks": [list(map(int, h.ranks)) for h in r["history"]],
+            # the same final cross contracted at 60 digits (Sec. 4.1's product of
+            # the oracle's FP64 cores): what the FP64 value above rounds
+            "value_exact_contraction": repr(ttcross.contract_decimal(
+                p, st, [ttcross.core(p, st, k) for k in range(1, p.d + 1)])),
             "parents": {k: [list(map(int, a)) for a in v] for k, v in par.items()},
             "oracle_seconds": round(time.time() - t, 1),
         }

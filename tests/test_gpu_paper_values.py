@@ -23,7 +23,7 @@
 """
 import json
 import os
-from decimal import Decimal, getcontext
+from decimal import Decimal
 
 import numpy as np
 import pytest
@@ -71,45 +71,6 @@ def test_d_printed_values(n):
           % (n, got["value"], abs(got["value"] / ref - 1), abs(got["value"] / ora - 1)))
 
 
-def _solve_left(G, x):
-    """t with t G = x (G^T t = x) by Gaussian elimination with partial pivoting
-    in the current decimal context."""
-    n = len(x)
-    M = [[G[j][i] for j in range(n)] + [x[i]] for i in range(n)]
-    for c in range(n):
-        p = max(range(c, n), key=lambda r: abs(M[r][c]))
-        M[c], M[p] = M[p], M[c]
-        for r in range(c + 1, n):
-            f = M[r][c] / M[c][c]
-            if f:
-                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
-    t = [Decimal(0)] * n
-    for i in range(n - 1, -1, -1):
-        acc = M[i][n] - sum((M[i][j] * t[j] for j in range(i + 1, n)), Decimal(0))
-        t[i] = acc / M[i][i]
-    return t
-
-
-def decimal_contraction(p, st, cores, digits=60):
-    """V_1 G_1^-1 V_2 ... G_{d-1}^-1 V_d (Sec. 4.1) from the given FP64 cores,
-    every step in `digits`-digit decimal arithmetic (FP64 values convert exactly)."""
-    getcontext().prec = digits
-
-    def vsum(T):
-        r0, N, r1 = T.shape
-        return [[sum((Decimal(float(v)) for v in T[a, :, b]), Decimal(0)) for b in range(r1)] for a in range(r0)]
-
-    x = vsum(cores[0])[0]
-    for k in range(1, p.d):
-        rows = ttcross.cross_rows(p, st, k)
-        Gf = cores[k - 1].reshape(-1, st.rank(k))[rows, :]
-        G = [[Decimal(float(v)) for v in row] for row in Gf]
-        x = _solve_left(G, x)
-        V = vsum(cores[k])
-        x = [sum((x[a] * V[a][b] for a in range(len(x))), Decimal(0)) for b in range(len(V[0]))]
-    return x[0] * Decimal(2)                    # unit-cube family constant
-
-
 def test_e16_double_double_at_full_size():
     p = inputs.config_e16()
     plan = B().Plan(p)
@@ -119,7 +80,7 @@ def test_e16_double_double_at_full_size():
     st = ttcross.from_parents(p, state["lpar"], state["lnode"], state["rpar"], state["rnode"])
     assert st.ranks() == ranks
     cores = [plan.get_core(k, (ranks[k - 1], p.N[k - 1], ranks[k])) for k in range(1, p.d + 1)]
-    ref = decimal_contraction(p, st, cores)
+    ref = ttcross.contract_decimal(p, st, cores, as_decimal=True)
     dd = Decimal(got["value"]) + Decimal(got["value_lo"])
     err_dd = abs(dd - ref) / abs(ref)
     ora = float(golden("e16")["value"])

@@ -273,3 +273,32 @@ def test_plain_launches_match_graph():
     plan.set_graphs(False)
     b = plan.run()
     assert a == b
+
+
+@pytest.mark.parametrize("case", ["C_rn", "D_rn", "D_cube", "E_cube", "TEST", "C4_config"])
+def test_persistent_search_equals_staged_search(case):
+    """The search as one persistent cooperative launch (interface groups handing
+    stages on through device flags) and as separate launches per stage give the
+    same run bit for bit."""
+    p = FULL[case]()
+    plan = B().Plan(p)
+    plan.set_search(True)
+    a = plan.run()
+    plan.set_search(False)
+    b = plan.run()
+    assert a == b
+
+
+def test_persistent_search_times_out_and_recovers():
+    """A wait limit of 1 ns makes the persistent search's first wait between CTAs
+    give up: the run ends with TTQ_ERR_TIMEOUT (no GPU fault, no hang), and the
+    same plan with the default limit then runs normally."""
+    p = FULL["D_cube"]()
+    plan = B().Plan(p)
+    plan.set_search(True)
+    ref = plan.run()
+    plan.set_wait_limit(1)
+    r = plan.run()
+    assert r["status_name"] == "timeout", r
+    plan.set_wait_limit(10 ** 9)
+    assert plan.run() == ref

@@ -179,6 +179,43 @@ def test_initial_sets_by_brute_force(r0):
         assert tuple(st.left[d - 1][0]) + (int(st.right[d - 1][0][-1]),) == sorted(pts)[0][2]
 
 
+def test_decimal_contraction_against_exact_rationals():
+    """contract_decimal (60-digit decimals, Gaussian elimination on G^T) against
+    the same product of Sec. 4.1 in exact rational arithmetic (Gauss-Jordan on
+    G itself, written out here), and against the FP64 integral_plain."""
+    p = inputs.make_problem("D", "cube", 5, 9, rank_cap=4, max_sweeps=4)
+    st = ttcross.integrate(p)["state"]
+    cores = [ttcross.core(p, st, k) for k in range(1, p.d + 1)]
+
+    def vsum(T):
+        return [[sum((Fraction(float(v)) for v in T[a, :, b]), Fraction(0)) for b in range(T.shape[2])]
+                for a in range(T.shape[0])]
+
+    def times_inverse(x, G):                   # x G^-1: reduce [G | I] to [I | G^-1], then x times it
+        n = len(x)
+        A = [[Fraction(float(G[i, j])) for j in range(n)] + [Fraction(int(i == j)) for j in range(n)]
+             for i in range(n)]
+        for c in range(n):
+            piv = next(r for r in range(c, n) if A[r][c] != 0)
+            A[c], A[piv] = A[piv], A[c]
+            A[c] = [v / A[c][c] for v in A[c]]
+            for r in range(n):
+                if r != c and A[r][c] != 0:
+                    A[r] = [a - A[r][c] * b for a, b in zip(A[r], A[c])]
+        return [sum((x[i] * A[i][n + j] for i in range(n)), Fraction(0)) for j in range(n)]
+
+    x = vsum(cores[0])[0]
+    for k in range(1, p.d):
+        G = cores[k - 1].reshape(-1, st.rank(k))[ttcross.cross_rows(p, st, k), :]
+        x = times_inverse(x, G)
+        V = vsum(cores[k])
+        x = [sum((x[a] * V[a][b] for a in range(len(x))), Fraction(0)) for b in range(len(V[0]))]
+    exact_value = float(x[0] * Fraction(integrands.family_constant(p.family, p.form, p.n)))
+    got = ttcross.contract_decimal(p, st, cores)
+    assert abs(got - exact_value) <= 1e-15 * abs(exact_value)
+    assert abs(ttcross.integral_plain(p, st, cores) - exact_value) <= 1e-13 * abs(exact_value)
+
+
 def test_ranks_grow_by_at_most_one_per_sweep():
     p = inputs.make_problem("C", "cube", 6, 33, rank_cap=12)
     r = ttcross.integrate(p)
@@ -286,3 +323,60 @@ def test_mode_reversal_symmetry():
     a = ttcross.integrate(p)["value"]
     b = ttcross.integrate(q)["value"]
     assert abs(a / b - 1) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Alg. 5, the sequential sweep (the paper's single-process comparison)
+
+def test_sequential_exact_recovery():
+    """Thm. 2 holds for the sequential sweep as well: exact rank, exact integral."""
+    p = inputs.make_problem("TEST", "cube", 5, 33, d=6, rank_cap=10)
+    r = ttcross.integrate(p, sequential=True)
+    assert r["ranks"][1:-1] == [5] * 5
+    assert abs(r["value"] / separable_exact(p) - 1) < 1e-13
+
+
+def test_sequential_superblock_uses_the_updated_left_set():
+    """In a sequential sweep the superblock of interface k is built from I<=k-1
+    as step k-1 left it (Alg. 5): the pivot is the largest residual of its row
+    and column in that superblock, computed from Eq. (1) on the full tensor,
+    and its row may lie in the block of the row appended at step k-1."""
+    p = inputs.make_problem("D", "rn", 4, 15, L=6.0, rank_cap=8, max_sweeps=3, rook_max=10)
+    st = ttcross.integrate(p, sequential=True)["state"]
+    A = full_tensor(p)
+    cores = [ttcross.core(p, st, k) for k in range(1, p.d + 1)]
+    scale = max(np.abs(c).max() for c in cores)
+    st2, pivots, _ = ttcross.search_sequential(p, st, 7, cores, scale)
+    cur = st
+    for k in range(1, p.d):
+        pv = pivots[k - 1]
+        assert pv is not None
+        left, right = cur.left[k - 1], cur.right[k + 1]
+        Nk, Nk1 = p.N[k - 1], p.N[k]
+        rn = len(right)
+        S = np.empty((len(left) * Nk, Nk1 * rn))
+        for a, pre in enumerate(left):
+            for i in range(Nk):
+                for j in range(Nk1):
+                    for b, suf in enumerate(right):
+                        S[a * Nk + i, j * rn + b] = A[tuple(pre) + (i, j) + tuple(suf)]
+        I = ttcross.cross_rows(p, cur, k)
+        J = ttcross.cross_cols(p, cur, k)
+        E = S - S[:, J] @ np.linalg.solve(S[np.ix_(I, J)], S[I, :])
+        if pv.rounds < p.rook_max:
+            assert abs(E[pv.row, pv.col]) >= np.max(np.abs(E[pv.row, :])) * (1 - 1e-9)
+            assert abs(E[pv.row, pv.col]) >= np.max(np.abs(E[:, pv.col])) * (1 - 1e-9)
+        assert abs(E[pv.row, pv.col] - pv.err) <= 1e-10 * abs(E).max()
+        if k > 1:
+            assert len(left) == st.rank(k - 1) + (1 if pivots[k - 2].accepted else 0)
+        if pv.accepted:
+            cur = ttcross.apply_pivots(p, cur, [pv])
+    assert cur.ranks() == st2.ranks()
+
+
+def test_sequential_d8_printed_value():
+    ref = float(json.load(open(os.path.join(GOLDEN, "paper_values.json")))["D_8"]["value"])
+    p = inputs.config_d_cube(8)
+    r = ttcross.integrate(p, sequential=True)
+    assert r["status"] == ttcross.STATUS_CONVERGED
+    assert abs(r["value"] / ref - 1) < 5e-12
