@@ -35,7 +35,8 @@ KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "u
 
 def workload(name):
     from paper_1903_11554_gb300 import inputs
-    return {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16}[name]()
+    return {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16,
+            "d12_r4": inputs.config_d12_r4}[name]()
 
 
 def workload_config(p):
@@ -277,8 +278,13 @@ def measure_workload(binding, torch, name, steps, flush):
     if g is not None:
         ref = float(g["value"])
         out["rel_err_vs_oracle"] = abs(res[-1]["value"] - ref) / abs(ref)
+        if "value_exact_contraction" in g:
+            ex = float(g["value_exact_contraction"])
+            out["rel_err_vs_oracle_cores_at_60_digits"] = abs(res[-1]["value"] + res[-1]["value_lo"] - ex) / abs(ex)
         out["same_trajectory_as_oracle"] = (res[-1]["sweeps"], res[-1]["n_eval"]) == (g["sweeps"], g["n_eval"])
-        if name == "c4":
+        if name == "d12_r4":
+            pass
+        elif name == "c4":
             env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
             code = ("import sys, time, json; sys.path.insert(0, %r)\n"
                     "from oracle import ttcross\nfrom paper_1903_11554_gb300 import inputs\n"
@@ -300,11 +306,45 @@ def measure_workload(binding, torch, name, steps, flush):
     return out
 
 
+def measure_search_variants(binding, torch, flush, steps=3):
+    """D_12 with the search as one persistent kernel per sweep (same results bit
+    for bit as the staged launches, timed the same way), and with the
+    sequential sweep of Alg. 5 (another algorithm: its value beside Alg. 6's)."""
+    p = workload("d12")
+    out = {}
+    for label in ("persistent_search", "sequential_alg5"):
+        plan = binding.Plan(p)
+        if label == "persistent_search":
+            plan.set_search(True)
+        else:
+            plan.set_sequential(True)
+        ref = plan.run()
+        torch.cuda.synchronize()
+        n = steps if label == "persistent_search" else 1
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(plan.stream)
+        res = []
+        for _ in range(n):
+            with torch.cuda.stream(plan.stream):
+                flush.zero_()
+            res.append(plan.run())
+        t1.record(plan.stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / n
+        out[label] = {"integrals_per_s": 1000.0 / ms, "ms_per_integral": ms, "value": res[-1]["value"],
+                      "sweeps": res[-1]["sweeps"], "n_eval": res[-1]["n_eval"], "status": res[-1]["status_name"],
+                      "runs_identical": all(r == ref for r in res)}
+        plan.close()
+    return out
+
+
 def measure_batched(binding, inputs, torch, count=256):
     """The 256-instance mixed batch (families C/D/E cyclic, n in 4..24, N in
     {65,129,257,513}, rank caps in {8..128}): autotuned, one warm-up run, one
-    timed run; the same problems one at a time on a subsample of 32 for the
-    single-instance comparison (results compared bit for bit)."""
+    timed run; then the same 256 problems one at a time (a plan each, its
+    second run timed), results compared bit for bit; and the batch's error
+    against the stored oracle runs of 24 of its instances."""
     probs = inputs.batched_mix(count)
     b = binding.Batch(probs)
     tuned = b.autotune(2)
@@ -315,9 +355,8 @@ def measure_batched(binding, inputs, torch, count=256):
     dt = time.time() - t
     del b
     torch.cuda.empty_cache()
-    sub = list(range(0, count, max(1, count // 32)))
     st, same = 0.0, True
-    for q in sub:
+    for q in range(count):
         pl = binding.Plan(probs[q])
         pl.run()
         torch.cuda.synchronize()
@@ -326,27 +365,31 @@ def measure_batched(binding, inputs, torch, count=256):
         st += time.time() - t
         same &= (r == res[q])
         pl.close()
-    bs = binding.Batch([probs[q] for q in sub])
-    bs.autotune(2)
-    bs.run()
-    t = time.time()
-    bs.run()
-    dts = time.time() - t
+    errs = {}
+    path = os.path.join(ROOT, "tests", "golden", "batch_oracle.json")
+    if os.path.exists(path):
+        for key, ref in json.load(open(path)).items():
+            errs[key] = abs(res[int(key)]["value"] - float(ref["value"])) / abs(float(ref["value"]))
     return {"workload": "%d mixed instances (C/D/E cyclic, n 4..24, N 65..513, rank cap 8..128, tol 1e-12, "
                         "seed 256+i)" % count,
             "integrals_per_s": count / dt, "seconds": dt, "autotuned": tuned,
             "statuses": {k: sum(1 for r in res if r["status_name"] == k) for k in set(r["status_name"] for r in res)},
             "fiber_evals_per_s": sum(r["n_eval"] for r in res) / dt,
-            "subsample": {"count": len(sub), "batched_integrals_per_s": len(sub) / dts,
-                          "one_at_a_time_integrals_per_s": len(sub) / st,
-                          "results_identical_to_one_at_a_time": bool(same)}}
+            "one_at_a_time": {"integrals_per_s": count / st, "seconds": st,
+                              "results_identical_to_batch": bool(same)},
+            "batched_over_one_at_a_time": (count / dt) / (count / st),
+            "rel_err_vs_oracle": {"instances": len(errs), "max": max(errs.values()) if errs else None}}
 
 
-def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120.0, max_slots=1024):
+def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120.0, max_slots=1024,
+                    sweeps_per_step=2, alone=0):
     """Poisson arrivals (rate per second, seeded), families uniform over C/D/E,
     n in 4..32, tol log-uniform in [1e-14, 1e-8], N in {129, 257, 513}, rank cap
-    64; HBM admission budget pool_gb.  Latency = completion seen by the host
-    minus scheduled arrival."""
+    64; HBM admission budget pool_gb; sweeps_per_step sweeps of every request
+    in flight per server step.  Latency = completion seen by the host minus
+    scheduled arrival.  alone > 0: the first `alone` requests of the same
+    stream are also run one at a time (a plan each over one workspace: upload,
+    whole run, result read back), for the served-against-alone rate."""
     arrivals, probs = inputs.serving_stream(count, rate)
     pool_bytes = int(pool_gb * (1 << 30))
     srv = binding.Server(pool_bytes, max_slots=max_slots)
@@ -361,7 +404,7 @@ def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120
             ids[rid] = i
             when[rid] = arrivals[i]
             i += 1
-        flight, queued, _ = srv.step(1)
+        flight, queued, _ = srv.step(sweeps_per_step)
         peak_flight = max(peak_flight, flight)
         peak_queue = max(peak_queue, queued)
         done = srv.drain()
@@ -380,12 +423,26 @@ def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120
     same = True
     for rid in list(results)[:8]:
         same &= (binding.integrate(probs[ids[rid]]) == results[rid])
-    return {"workload": "Poisson %g req/s, %d requests (seed 2000), C/D/E, n 4..32, tol 1e-14..1e-8, N 129..513, "
-                        "rank cap 64, HBM admission budget %g GB" % (rate, count, pool_gb),
-            "offered_per_s": count / float(arrivals[-1]), "achieved_integrals_per_s": count / span,
-            "latency_s": {"p50": ls[len(ls) // 2], "p99": ls[min(len(ls) - 1, int(math.ceil(0.99 * len(ls))) - 1)]},
-            "peak_in_flight": peak_flight, "peak_queued": peak_queue, "seconds": span,
-            "served_equal_alone_on_8": bool(same)}
+    out = {"workload": "Poisson %g req/s, %d requests (seed 2000), C/D/E, n 4..32, tol 1e-14..1e-8, N 129..513, "
+                       "rank cap 64, HBM admission budget %g GB, %d sweeps per server step"
+                       % (rate, count, pool_gb, sweeps_per_step),
+           "offered_per_s": count / float(arrivals[-1]), "achieved_integrals_per_s": count / span,
+           "latency_s": {"p50": ls[len(ls) // 2], "p99": ls[min(len(ls) - 1, int(math.ceil(0.99 * len(ls))) - 1)]},
+           "peak_in_flight": peak_flight, "peak_queued": peak_queue, "seconds": span,
+           "served_equal_alone_on_8": bool(same)}
+    if alone > 0:
+        ws = torch.empty(max(binding.workspace_bytes(p) for p in probs[:alone]), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        t = time.time()
+        for p in probs[:alone]:
+            pl = binding.Plan(p, workspace=ws)
+            pl.run()
+            pl.close()
+        torch.cuda.synchronize()
+        secs = time.time() - t
+        out["one_at_a_time"] = {"requests": alone, "integrals_per_s": alone / secs, "seconds": secs}
+        out["served_over_one_at_a_time"] = (count / span) / (alone / secs)
+    return out
 
 
 def max_over_ranks(x, dist, device):
@@ -592,14 +649,15 @@ def main():
 
     others = {}
     if args.workload == "d12" and args.launch_mode == "graph":
-        for name in ("c4", "e16"):
+        for name in ("c4", "e16", "d12_r4"):
             others[name] = measure_workload(binding, torch, name, max(3, min(args.steps, 20)), flush)
+        others["d12_search_variants"] = measure_search_variants(binding, torch, flush)
     systems = {}
     if not args.no_systems and args.launch_mode == "graph":
         del plan
         torch.cuda.empty_cache()
         systems["batched"] = measure_batched(binding, inputs, torch)
-        systems["serving"] = measure_serving(binding, inputs, torch, count=args.serving_requests)
+        systems["serving"] = measure_serving(binding, inputs, torch, count=args.serving_requests, alone=100)
         # the same stream kind offered at 70% of the capacity just measured, so
         # its latencies are service times rather than queueing under overload
         cap_rate = 0.7 * systems["serving"]["achieved_integrals_per_s"]

@@ -283,6 +283,15 @@ int ttq_plan_set_graphs(ttq_plan *plan, int enable);
  * timer, default 1 s); a wait that passes it ends the run with
  * TTQ_ERR_TIMEOUT and leaves the plan usable. */
 int ttq_plan_set_search(ttq_plan *plan, int mode);
+
+/* Sweep kind: 0 (default) the dimension-parallel sweep of Alg. 6, every
+ * interface searched on the index sets of the previous sweep and all pivots
+ * appended at the end; 1 the sequential left-to-right sweep of Alg. 5, the
+ * paper's single-process comparison: interface k's superblock is built from
+ * I<=k-1 as interface k-1's step just extended it, and each pivot is appended
+ * at once.  Single-instance plans only; runs with plain launches (no CUDA
+ * graph).  ttq_plan_sweep then reports no per-interface pivots. */
+int ttq_plan_set_sequential(ttq_plan *plan, int enable);
 int ttq_plan_set_wait_limit(ttq_plan *plan, uint64_t ns);
 
 /* Bytes this plan has copied host->device (problem inputs, descriptor) and

@@ -67,6 +67,7 @@ SIGNATURES = {
     "ttq_plan_set_graphs": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_set_timing": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_set_search": (_c.c_int, [_vp, _c.c_int]),
+    "ttq_plan_set_sequential": (_c.c_int, [_vp, _c.c_int]),
     "ttq_plan_set_wait_limit": (_c.c_int, [_vp, _c.c_uint64]),
     "ttq_plan_kernel_times": (_c.c_int, [_vp, _dp, _c.POINTER(_c.c_int64), _dp, _c.c_int]),
     "ttq_integrate_noalloc": (_c.c_int, [_c.POINTER(TTQProblem), _vp, _c.POINTER(TTQResult)]),
@@ -304,6 +305,9 @@ class Plan:
 
     def set_search(self, persistent: bool):
         _check(self.lib.ttq_plan_set_search(self.h, 1 if persistent else 0), "ttq_plan_set_search")
+
+    def set_sequential(self, on: bool):
+        _check(self.lib.ttq_plan_set_sequential(self.h, 1 if on else 0), "ttq_plan_set_sequential")
 
     def set_wait_limit(self, ns: int):
         _check(self.lib.ttq_plan_set_wait_limit(self.h, int(ns)), "ttq_plan_set_wait_limit")

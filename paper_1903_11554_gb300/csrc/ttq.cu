@@ -78,6 +78,7 @@ struct ttq_plan {
   int in_loop;              // enqueueing the body of the WHILE node
   int sweep_kernels;        // kernels in one sweep
   State *slots;             // pinned host copies of the final state of launched runs
+  int sequential;           // sweeps of Alg. 5 (interfaces one after another) instead of Alg. 6
   int persistent;           // one instance: the search of a sweep as one cooperative launch (k_search)
   int search_grid, search_smem;
 };
@@ -647,10 +648,46 @@ extern "C" int ttq_batch_create(const ttq_problem *probs, int count, void *works
 }
 
 // ---------------------------------------------------------------------------
+// One sequential sweep (Alg. 5), plain launches on the plan's stream: the
+// sweep's cores, factors and integral, then per interface k = 1..d-1 the
+// staged search with only k searching, its pivot appended at once, and the new
+// core slabs and QR update that the append calls for.
+static void enqueue_sweep_seq(ttq_plan *P) {
+  cudaStream_t s = P->stream;
+  const int ni = P->max_ni, nb = P->count;
+  Dev *const *dv = P->devs;
+  const dim3 W(TTQ_WARPS * 32), T(256);
+  auto refresh = [&] {
+    timed(P, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
+    timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, 0, s>>>(dv); });
+    timed(P, KT_QR, [&] { k_qr<<<dim3(ni, 1, nb), T, P->qr_smem, s>>>(dv); });
+  };
+  refresh();
+  timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
+  for (int k = 1; k <= ni; ++k) {
+    k_seq_begin<<<dim3(1, 1, nb), 32, 0, s>>>(dv, k);
+    P->launches++;
+    timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), W, P->samples_smem, s>>>(dv); });
+    for (int q = 0; q < P->rook_max; ++q) {
+      timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv); });
+      timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 1, 0, P->cond, 0); });
+      timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv); });
+      timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 2, 0, P->cond, 0); });
+    }
+    timed(P, KT_UPDATE, [&] { k_seq_end<<<dim3(1, 1, nb), T, 0, s>>>(dv, k, k == ni ? 1 : 0); });
+    if (k < ni) refresh();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // One sweep for every instance: eval -> qr -> { contract (side stream) |
 // samples -> rook rounds } -> update.  Every launch covers all instances
 // (grid z); CTAs of instances or interfaces with no work exit at once.
 static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) {
+  if (P->sequential) {
+    enqueue_sweep_seq(P);
+    return;
+  }
   cudaStream_t s = P->stream;
   const int ni = P->max_ni, nb = P->count;
   Dev *const *dv = P->devs;
@@ -758,7 +795,7 @@ static int build_run_graph(ttq_plan *P) {
 }
 
 static int launch_sweep(ttq_plan *P) {
-  if (P->use_graph && !P->timing && P->count == 1) {
+  if (P->use_graph && !P->timing && P->count == 1 && !P->sequential) {
     if (!P->sweep_exec) {
       cudaGraph_t g = nullptr;
       const long long l0 = P->launches;
@@ -846,7 +883,7 @@ static int enqueue_run(ttq_plan *P) {
 // run every instance to its stop (blocking); states land in P->hst
 static int run_all(ttq_plan *P) {
   int rc;
-  if (P->use_graph && !P->timing) {
+  if (P->use_graph && !P->timing && !P->sequential) {
     if ((rc = enqueue_run(P))) return rc;
     if ((rc = read_states(P))) return rc;
     int mx = 0;
@@ -904,7 +941,7 @@ extern "C" int ttq_plan_launch(ttq_plan *P, int slot) {
       return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
   }
   int rc;
-  if (!(P->use_graph && !P->timing)) {      // plain launches need the host in the loop: run now
+  if (!(P->use_graph && !P->timing && !P->sequential)) {   // plain launches need the host in the loop: run now
     if ((rc = run_all(P))) return rc;
     memcpy(&P->slots[slot], P->hst, sizeof(State));
     return TTQ_OK;
@@ -1271,6 +1308,15 @@ extern "C" int ttq_plan_set_search(ttq_plan *P, int mode) {
   if (mode == 1 && (P->count != 1 || P->search_grid < P->max_ni))
     return set_err(TTQ_ERR_INVALID_ARG, "the persistent search needs a single-instance plan that fits the device");
   P->persistent = mode;
+  if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
+  if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
+  return TTQ_OK;
+}
+
+extern "C" int ttq_plan_set_sequential(ttq_plan *P, int enable) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (enable && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "sequential sweeps need a single-instance plan");
+  P->sequential = enable ? 1 : 0;
   if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
   if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
   return TTQ_OK;

@@ -67,6 +67,8 @@ struct State {
   int stop_pending;         // a stopping rule fired in this sweep's contraction; applied at the end of the sweep
   int loop_guard;           // sweeps run by the device-side loop of this run (bounded by max_sweeps)
   int search_abort;         // persistent search: a wait passed its limit; every CTA leaves the search
+  int seq_k;                // sequential sweep (Alg. 5): the interface whose step runs now (0: Alg. 6)
+  int seq_nacc;             // sequential sweep: pivots accepted so far in this sweep
   unsigned batch_guard;     // sweeps run by a batch's loop (used in instance 0 of a batch)
   int pending_status;
   unsigned contract_arrive;  // CTAs of the two contraction chains that have finished

@@ -366,7 +366,7 @@ __global__ void k_init(Dev *const *Dps) {
     for (int k = 0; k <= d; ++k) { st->r[k] = (k == 0 || k == d) ? 1 : rr; st->ro[k] = 0; }
     st->sweep = 0; st->status = ST_OK; st->stop = 0; st->nonfinite = 0; st->singular = 0;
     st->nchanges = 0; st->scale_bits = 0ULL; st->value = st->value_lo = st->prev = 0.0;
-    st->stop_pending = 0; st->pending_status = 0; st->search_abort = 0;
+    st->stop_pending = 0; st->pending_status = 0; st->search_abort = 0; st->seq_k = 0; st->seq_nacc = 0;
     for (int k = 0; k < TTQ_MAXD; ++k) { st->qr_rank[k] = 0; st->qr_row[k] = 0; }
     st->conv = __longlong_as_double(0x7ff0000000000000LL);
     st->search_evals = 0; st->init_evals = D.init_samples;
@@ -1664,6 +1664,8 @@ __device__ __forceinline__ void stage_publish(IfaceState &I, double best, unsign
 __device__ __forceinline__ bool iface_searchable(const Dev &D, const State *st, int k) {
   if (k > D.d - 1) return false;            // instances with fewer interfaces (batches)
   if (st->stop || !st->search) return false;
+  // sequential sweep: only the step's interface, and none once a stopping rule fired
+  if (st->seq_k && (k != st->seq_k || st->stop_pending)) return false;
   const int rk = st->r[k];
   if (rk >= D.cap) return false;
   if (st->r[k - 1] * D.N[k - 1] <= rk) return false;
@@ -2628,6 +2630,50 @@ __global__ void __launch_bounds__(256) k_sweep_end(Dev *const *Dps, cudaGraphCon
   State *st = D.st;
   const bool append = !st->stop && !st->stop_pending && st->search && !st->search_abort;
   sweep_finalize(D, st, append, h, use_cond);
+}
+
+// ---------------------------------------------------------------------------
+// Sequential sweep (Alg. 5): the interfaces' steps one after another, each
+// step's superblock built from the left set the previous step just extended.
+// A step is the staged search with only interface k searching (k_seq_begin
+// sets it), then k_seq_end: the cores are marked evaluated for the current
+// ranks (the evaluation before this step covered them), the pivot appended at
+// once, r_k raised; the last step of the sweep applies the stopping rules and
+// counts the sweep.  The next step's new core slabs and the QR update of
+// interface k follow in the ordinary kernels.
+__global__ void k_seq_begin(Dev *const *Dps, int k) {
+  if (threadIdx.x == 0) Dps[blockIdx.z]->st->seq_k = k;
+}
+
+__global__ void __launch_bounds__(256) k_seq_end(Dev *const *Dps, int k, int last) {
+  const Dev &D = *Dps[blockIdx.z];
+  State *st = D.st;
+  const bool live = !st->stop && !st->stop_pending && st->search && k <= D.d - 1;
+  if (live) sweep_append(D, st, k);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (live) {
+      for (int q = 0; q <= D.d; ++q) st->ro[q] = st->r[q];
+      IfaceState &I = st->it[k];
+      st->search_evals += (long long)I.evals;
+      if (I.active && I.accepted) { st->r[k] += 1; st->seq_nacc++; }
+    }
+    if (last) {
+      if (st->stop) {
+      } else if (st->stop_pending) {
+        st->stop = 1;
+        st->status = st->pending_status;
+      } else if (!st->search) {
+        st->sweep++;
+      } else {
+        if (st->rules && st->seq_nacc == 0) { st->stop = 1; st->status = ST_NO_PIVOT; }
+        st->sweep++;
+      }
+      st->seq_k = 0;
+      st->seq_nacc = 0;
+    }
+  }
 }
 
 // The tensor train of one instance copied out to a caller's buffer in the

@@ -70,3 +70,25 @@ def test_batch_plain_launches_match_graph():
     a = b.run()
     b.set_graphs(False)
     assert b.run() == a
+
+
+def test_full_mix_against_stored_oracle_runs():
+    """The 256-instance mix of the batched workload (C/D/E, n 4..24, N 65..513,
+    rank caps 8..128) in one batch: the 24 instances the oracle was run on
+    (tests/golden/batch_oracle.json) agree with it to 1e-12, with the same
+    status."""
+    import json
+    import os
+    from paper_1903_11554_gb300 import binding
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch_oracle.json")))
+    probs = inputs.batched_mix(256)
+    got = binding.Batch(probs).run()
+    worst = 0.0
+    for key, ref in gold.items():
+        g = got[int(key)]
+        assert probs[int(key)].name == ref["workload"]
+        assert g["status"] == ref["status"], (key, g, ref)
+        err = abs(g["value"] - float(ref["value"])) / abs(float(ref["value"]))
+        worst = max(worst, err)
+        assert err <= 1e-12, (key, g["value"], ref["value"])
+    print("256-instance batch: %d instances against the oracle, worst relative error %.2e" % (len(gold), worst))

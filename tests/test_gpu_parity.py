@@ -302,3 +302,23 @@ def test_persistent_search_times_out_and_recovers():
     assert r["status_name"] == "timeout", r
     plan.set_wait_limit(10 ** 9)
     assert plan.run() == ref
+
+
+@pytest.mark.parametrize("case", ["C_rn", "D_rn", "D_cube", "E_cube", "TEST"])
+def test_sequential_sweep_matches_oracle(case):
+    """Alg. 5 on the GPU (interfaces one after another, each pivot appended at
+    once) against the oracle's sequential sweep: the same run, and the same
+    final nested sets."""
+    p = FULL[case]()
+    ora = ttcross.integrate(p, sequential=True)
+    plan = B().Plan(p)
+    plan.set_sequential(True)
+    got = plan.run()
+    assert got["status"] == ora["status"]
+    assert rel(got["value"], ora["value"]) < 1e-12
+    assert (got["sweeps"], got["n_eval"], got["ranks"]) == (ora["sweeps"], ora["n_eval"], ora["ranks"])
+    st = plan.get_state()
+    par = ttcross.to_parents(p, ora["state"])
+    for key in ("lpar", "lnode", "rpar", "rnode"):
+        for a, b in zip(st[key], par[key]):
+            assert np.array_equal(a, b), key
