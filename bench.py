@@ -28,6 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "integrals/s & fiber evals/s at rel.err<=1e-12 vs plain sweep; p50/p99 latency"
+# DRAM bytes (read + write) per launch of the kernels the roofline may name,
+# from one ncu capture each (profiles/, plain launches of this bench on the
+# D_12 workload); null for a kernel whose code changed after its capture
+NCU_TRAFFIC = {"k_solve": {"bytes_per_launch": 859477, "capture": "profiles/k_solve_d12.md: launches 301-303 "
+                           "(sweep ~50), dram__bytes_read.sum + dram__bytes_write.sum"}}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup",
            "solve", "search")
@@ -605,8 +610,10 @@ def main():
     dom = max(main, key=lambda n: main[n]["ms"])
     d = kt[dom]
     achieved = d["flops"] / (d["ms"] / 1000.0) / 1e12 if d["ms"] > 0 else 0.0
+    tr = NCU_TRAFFIC.get("k_" + dom)
     roof = {"kernel": "k_" + dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": tr["bytes_per_launch"] if tr else None,
+            "traffic_source": tr["capture"] if tr else None,
             "peak_source": "FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz "
                            "(nominal 1.25 TFLOP/s)",
             "algorithmic_flops_per_launch": d["flops"] / max(1, d["launches"]),

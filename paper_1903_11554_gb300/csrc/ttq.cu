@@ -60,7 +60,7 @@ struct ttq_plan {
   // launch configuration (batch maxima)
   int max_ni, rook_max, max_sweeps, max_cap;
   int grid_eval, sblocks, cblocks, rblocks, max_sum_n;
-  int qr_smem, samples_smem, contract_smem, solve_smem;
+  int qr_smem, samples_smem, contract_smem, solve_smem, lu_smem;
   long long launches;
   State *hst;               // pinned host mirror of the states (count entries)
   int timing;               // 1: bracket every launch with CUDA events
@@ -285,9 +285,9 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
     L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);
     const size_t dd = p->precision == TTQ_PREC_DD ? 1 : 0;
-    L->luh[k] = b.take(dd * cap * cap * 8);
-    L->lul[k] = b.take(dd * cap * cap * 8);
-    L->lup[k] = b.take(dd * cap * 4);
+    L->luh[k] = b.take((size_t)cap * cap * 8);       // LU of G_k: the FP64 contraction of every sweep
+    L->lul[k] = b.take(dd * cap * cap * 8);          // its low parts: the double-double final contraction
+    L->lup[k] = b.take((size_t)cap * 4);
   }
   const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;
   auto clampi = [](long v, long lo, long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
@@ -475,7 +475,8 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   P->qr_smem = (int)((cap * (cap + 1) + 8 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+7r
   // R (and Q when it fits), then per warp TTQ_SPW groups of two vectors of cap + 1
   P->samples_smem = (int)(((q_in ? 2 : 1) * cap * cap + (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap + 1)) * 8);
-  P->contract_smem = (int)(cap * cap * 8);
+  P->contract_smem = (int)((cap * cap + cap) * 8);   // the LU factors of one G_k and 1/U_jj
+  P->lu_smem = (int)(cap * cap * 8);
   P->solve_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
   // persistent search: R D^-1 (and Q) of the group's interface for the whole
   // launch, then the samples' group vectors or the rook scratch in one region
@@ -505,6 +506,8 @@ static cudaError_t set_smem_attributes(ttq_plan *P) {
   if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, P->lu_smem)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
 }
@@ -663,6 +666,7 @@ static void enqueue_sweep_seq(ttq_plan *P) {
     timed(P, KT_QR, [&] { k_qr<<<dim3(ni, 1, nb), T, P->qr_smem, s>>>(dv); });
   };
   refresh();
+  timed(P, KT_CONTRACT, [&] { k_lu_factor<<<dim3(ni, 1, nb), 256, P->lu_smem, s>>>(dv); });
   timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   for (int k = 1; k <= ni; ++k) {
     k_seq_begin<<<dim3(1, 1, nb), 32, 0, s>>>(dv, k);
@@ -713,9 +717,11 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   if (P->s2) {
     cudaEventRecord(P->fork, s);
     cudaStreamWaitEvent(P->s2, P->fork, 0);
+    timed_on(P, P->s2, KT_CONTRACT, [&] { k_lu_factor<<<dim3(ni, 1, nb), 256, P->lu_smem, P->s2>>>(dv); });
     timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, P->s2>>>(dv, 0); });
     cudaEventRecord(P->join, P->s2);
   } else {
+    timed(P, KT_CONTRACT, [&] { k_lu_factor<<<dim3(ni, 1, nb), 256, P->lu_smem, s>>>(dv); });
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
   const int single_cond = P->in_loop && loop_end && nb == 1;
@@ -1511,7 +1517,11 @@ struct ttq_server {
   uint64_t next_id;
   ttq_plan P;                               // launch configuration over the active set
   Dev **devs;                               // device array of the active descriptors (pool head)
-  State *hst;                               // pinned host states (max_slots)
+  State *hst;                               // pinned, device-mapped host states (max_slots)
+  int *hflags;                              // pinned, device-mapped stop flags (max_slots)
+  State *hst_dev;                           // device addresses of the two
+  int *hflags_dev;
+  int dirty;                                // the active set changed since the launch configuration
   long long sweeps_run, admitted, retired;
 };
 
@@ -1558,9 +1568,16 @@ extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, v
   S->devs = (Dev **)pool;
   S->free_list[head] = (pool_bytes - head) & ~(size_t)255;
   S->next_id = 1;
-  if (cudaMallocHost((void **)&S->hst, sizeof(State) * max_slots) != cudaSuccess) {
+  // the collect kernel writes every step's stop flags, and the final states of
+  // the instances that stopped, straight into host memory
+  if (cudaHostAlloc((void **)&S->hst, sizeof(State) * max_slots, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void **)&S->hflags, sizeof(int) * max_slots, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&S->hst_dev, S->hst, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&S->hflags_dev, S->hflags, 0) != cudaSuccess) {
+    if (S->hst) cudaFreeHost(S->hst);
+    if (S->hflags) cudaFreeHost(S->hflags);
     delete S;
-    return set_err(TTQ_ERR_CUDA, "cudaMallocHost failed");
+    return set_err(TTQ_ERR_CUDA, "cudaHostAlloc failed");
   }
   S->P.stream = S->stream;
   S->P.devs = S->devs;
@@ -1571,6 +1588,7 @@ extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, v
       (e = cudaEventCreateWithFlags(&S->P.join, cudaEventDisableTiming)) != cudaSuccess) {
     g_last_error = std::string("server setup: ") + cudaGetErrorString(e);
     cudaFreeHost(S->hst);
+    cudaFreeHost(S->hflags);
     delete S;
     return TTQ_ERR_CUDA;
   }
@@ -1588,6 +1606,7 @@ extern "C" int ttq_server_destroy(ttq_server *S) {
   S->P.hs = nullptr;
   S->P.sts = nullptr;
   cudaFreeHost(S->hst);
+  cudaFreeHost(S->hflags);
   delete S;
   return TTQ_OK;
 }
@@ -1650,6 +1669,7 @@ static int server_admit(ttq_server *S) {
     CK(cudaMemcpyAsync(a.own, &a.dev, sizeof(Dev *), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));           // host sources must outlive the copies
     S->admitted++;
+    S->dirty = 1;
   }
   return TTQ_OK;
 }
@@ -1657,7 +1677,8 @@ static int server_admit(ttq_server *S) {
 // launch configuration and descriptor array of the current active set
 static int server_configure(ttq_server *S) {
   const int n = (int)S->active.size();
-  if (n == 0) return TTQ_OK;
+  if (n == 0 || !S->dirty) return TTQ_OK;
+  S->dirty = 0;
   std::vector<ttq_problem> probs(n);
   std::vector<Layout> Ls(n);
   std::vector<Dev *> dp(n);
@@ -1684,36 +1705,43 @@ static int server_configure(ttq_server *S) {
   return TTQ_OK;
 }
 
-// retire stopped instances: double-double contraction if asked, results, memory
+// retire stopped instances: one kernel collects every instance's stop flag
+// (and the final state of those that stopped) into mapped host memory; the
+// double-double ones first get their final contraction; results, memory
 static int server_retire(ttq_server *S) {
   const int n = (int)S->active.size();
   if (n == 0) return TTQ_OK;
-  for (int q = 0; q < n; ++q)
-    CK(cudaMemcpyAsync(&S->hst[q].stop, (char *)S->active[q].h.st + offsetof(State, stop), sizeof(int),
-                       cudaMemcpyDeviceToHost, S->stream));
+  k_server_collect<<<(n + 7) / 8, 256, 0, S->stream>>>(S->devs, n, S->hflags_dev, S->hst_dev, 0);
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(S->stream));
+  int ndd = 0;
+  for (int q = 0; q < n; ++q) {
+    Slot &a = S->active[q];
+    if (!S->hflags[q] || !a.h.prec) continue;
+    const int cs = (int)(((size_t)a.h.cap * a.h.cap + a.h.cap) * 8);
+    k_dd_factor<<<a.h.d - 1, 256, 0, S->stream>>>(a.own);
+    k_contract<<<2, 256, cs, S->stream>>>(a.own, 1);
+    ++ndd;
+  }
+  if (ndd) {                                // their states again, after the final contraction
+    k_server_collect<<<(n + 7) / 8, 256, 0, S->stream>>>(S->devs, n, S->hflags_dev, S->hst_dev, 1);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(S->stream));
+  }
   std::vector<Slot> keep;
   keep.reserve(n);
   for (int q = 0; q < n; ++q) {
     Slot &a = S->active[q];
-    if (!S->hst[q].stop) {
+    if (!S->hflags[q]) {
       keep.push_back(std::move(a));
       continue;
     }
-    if (a.h.prec) {
-      const int cs = (int)((size_t)a.h.cap * a.h.cap * 8);
-      k_dd_factor<<<a.h.d - 1, 256, 0, S->stream>>>(a.own);
-      k_contract<<<2, 256, cs, S->stream>>>(a.own, 1);
-      CK(cudaGetLastError());
-    }
-    State st;
-    CK(cudaMemcpyAsync(&st, a.h.st, sizeof(State), cudaMemcpyDeviceToHost, S->stream));
-    CK(cudaStreamSynchronize(S->stream));
     ttq_result res;
-    fill_result_from(a.h, st, &res);
+    fill_result_from(a.h, S->hst[q], &res);
     S->done[a.req.id] = res;
     pool_free(S, a.off, a.req.bytes);
     S->retired++;
+    S->dirty = 1;
   }
   S->active.swap(keep);
   for (auto &a : S->active) repoint(a.req);

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
     const NodeChunks nc = node_chunks(Nk, R);
     int i0, i1, nq;
     chunk_span(nc, ch, Nk, i0, i1, nq);
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + (D.prec ? 20 : 1));
+    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + 5);
     double *Y = D.Y[k] + core_at(D, k, alpha, 0, beta);
     const size_t fib = (size_t)alpha * D.capL[k] + beta;
     for (int q = 0; q < nq; ++q) {
@@ -483,18 +483,20 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
       if (last) __threadfence();
     }
     if (last) {
+      // Neumaier-compensated sum of the lane's nodes (the running sum s and the
+      // sum c of its exact rounding errors), the lanes' (s, c) pairs combined in
+      // double-double: V + Vlo is the node sum to ~N u^2 relative, V alone its
+      // FP64 rounding
       __syncwarp();
-      if (D.prec) {
-        dd sd = {0.0, 0.0};
-        for (int i = lane; i < Nk; i += 32) sd = dd_add(sd, {__ldcg(Y + i), 0.0});
-        sd = warp_sum_dd(sd);
-        if (lane == 0) { D.V[k][fib] = sd.hi; D.Vlo[k][fib] = sd.lo; }
-      } else {
-        double sr = 0.0;
-        for (int i = lane; i < Nk; i += 32) sr += __ldcg(Y + i);
-        sr = warp_sum(sr);
-        if (lane == 0) { D.V[k][fib] = sr; D.Vlo[k][fib] = 0.0; }
+      double sn = 0.0, cn = 0.0;
+      for (int i = lane; i < Nk; i += 32) {
+        const double x = __ldcg(Y + i), t = sn + x;
+        cn += (fabs(sn) >= fabs(x)) ? ((sn - t) + x) : ((x - t) + sn);
+        sn = t;
       }
+      dd sd = fast_two_sum(sn, cn);
+      sd = warp_sum_dd(sd);
+      if (lane == 0) { D.V[k][fib] = sd.hi; D.Vlo[k][fib] = sd.lo; }
     }
     __syncwarp();
   }
@@ -819,28 +821,33 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (threadIdx.x == 0) { st->qr_rank[k] = r; st->it[k].prank = -1; st->qr_row[k] = 0; }
 }
 
-// The final double-double contraction applies G_k^-1 through a double-double
-// LU factorization of G_k itself, taken from its exact FP64 entries (the
-// FP64 QR factors of the search carry an error of order u cond(G_k), which
-// double-double arithmetic downstream cannot remove): P G_k = L U by Gaussian
-// elimination with partial pivoting (largest leading part, ties to the lowest
-// row), L unit lower triangular below the diagonal and U on and above it, in
-// one column-major array of hi and lo parts (leading dimension cap); lup[k][i]
-// is the row of G_k that row i of P G_k holds.  One CTA per interface.
-__global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
-  __shared__ Dev sD;
-  const Dev &D = stage_dev(Dps, sD);
-  State *st = D.st;
-  const int k = blockIdx.x + 1;
-  if (k > D.d - 1 || !D.prec || st->nonfinite || st->singular) return;
+// The contraction applies G_k^-1 through an LU factorization with partial
+// pivoting of G_k itself, taken from its exact FP64 entries, as LAPACK's
+// solve does: P G_k = L U by Gaussian elimination, the pivot the largest |.|
+// in its column (leading part; ties to the lowest row), L unit lower
+// triangular below the diagonal and U on and above it in one column-major
+// array (leading dimension cap); lup[k][i] is the row of G_k that row i of
+// P G_k holds.  One CTA per interface.
+//   FP64 (every sweep, beside the search): luh only.  The cross matrices are
+//   graded, and on them this factorization keeps the contraction within a
+//   few ulp of the exact product where the search's bordered QR factors lose
+//   one or two digits more.
+//   Double-double (the final contraction of a double-double run): hi parts in
+//   luh, lo parts in lul; the FP64 factors, whose O(u cond(G_k)) error no
+//   arithmetic after them could remove, are not used for it.
+//   The FP64 factorization runs in shared memory (As, r x r column-major),
+//   the double-double one in place in luh / lul.
+template <bool DDM>
+__device__ void lu_factor(const Dev &D, State *st, int k, double *As) {
   __shared__ int piv_s;
-  const int r = st->r[k], ld = D.cap, tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
-  double *Ah = D.luh[k], *Al = D.lul[k];
+  const int r = st->r[k], tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id();
+  const int ld = DDM ? D.cap : r;
+  double *Ah = DDM ? D.luh[k] : As, *Al = D.lul[k];
   int *perm = D.lup[k];
   for (int e = tid; e < r * r; e += nt) {
     const int a = e % r, b = e / r;
     Ah[a + (size_t)b * ld] = D.Y[k][core_at(D, k, D.lpar[k][a], D.lnode[k][a], b)];
-    Al[a + (size_t)b * ld] = 0.0;
+    if (DDM) Al[a + (size_t)b * ld] = 0.0;
   }
   for (int i = tid; i < r; i += nt) perm[i] = i;
   __syncthreads();
@@ -868,32 +875,70 @@ __global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
     if (pr != j) {                               // swap rows j and pr
       for (int c = tid; c < r; c += nt) {
         const size_t oj = j + (size_t)c * ld, op = pr + (size_t)c * ld;
-        const double th = Ah[oj], tl = Al[oj];
-        Ah[oj] = Ah[op]; Al[oj] = Al[op];
-        Ah[op] = th; Al[op] = tl;
+        const double th = Ah[oj];
+        Ah[oj] = Ah[op];
+        Ah[op] = th;
+        if (DDM) { const double tl = Al[oj]; Al[oj] = Al[op]; Al[op] = tl; }
       }
       if (tid == 0) { const int t = perm[j]; perm[j] = perm[pr]; perm[pr] = t; }
     }
     __syncthreads();
-    const dd u = {Ah[j + (size_t)j * ld], Al[j + (size_t)j * ld]};
-    if (u.hi != 0.0)
+    const double uh = Ah[j + (size_t)j * ld];
+    const double ul = DDM ? Al[j + (size_t)j * ld] : 0.0;
+    if (uh != 0.0)
       for (int i = j + 1 + tid; i < r; i += nt) {
         const size_t o = i + (size_t)j * ld;
-        const dd l = dd_div({Ah[o], Al[o]}, u);
-        Ah[o] = l.hi; Al[o] = l.lo;
+        if (DDM) {
+          const dd l = dd_div({Ah[o], Al[o]}, {uh, ul});
+          Ah[o] = l.hi; Al[o] = l.lo;
+        } else {
+          Ah[o] = Ah[o] / uh;
+        }
       }
     __syncthreads();
     const int m = r - j - 1;
-    if (u.hi != 0.0)
+    if (uh != 0.0)
       for (int e = tid; e < m * m; e += nt) {    // trailing block: a_ic -= l_ij u_jc
         const int i = j + 1 + e % m, c = j + 1 + e / m;
         const size_t oi = i + (size_t)j * ld, oj = j + (size_t)c * ld, o = i + (size_t)c * ld;
-        const dd v = dd_add({Ah[o], Al[o]}, dd_neg(dd_mul({Ah[oi], Al[oi]}, {Ah[oj], Al[oj]})));
-        Ah[o] = v.hi; Al[o] = v.lo;
+        if (DDM) {
+          const dd v = dd_add({Ah[o], Al[o]}, dd_neg(dd_mul({Ah[oi], Al[oi]}, {Ah[oj], Al[oj]})));
+          Ah[o] = v.hi; Al[o] = v.lo;
+        } else {
+          Ah[o] = fma(-Ah[oi], Ah[oj], Ah[o]);
+        }
       }
     __syncthreads();
   }
-  if (tid == 0) atomicAdd(&st->flops[2], (unsigned long long)(20.0 / 3.0 * r * (double)r * r));
+  if (!DDM)                                      // the factors to luh, leading dimension cap
+    for (int e = tid; e < r * r; e += nt) {
+      const int a = e % r, b = e / r;
+      D.luh[k][a + (size_t)b * D.cap] = As[a + (size_t)b * r];
+    }
+  if (tid == 0) atomicAdd(&st->flops[2], (unsigned long long)((DDM ? 20.0 : 2.0) / 3.0 * r * (double)r * r));
+}
+
+// every sweep (FP64, beside the search): skipped once the run has stopped
+__global__ void __launch_bounds__(256) k_lu_factor(Dev *const *Dps) {
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
+  pdl_wait();
+  pdl_release();
+  State *st = D.st;
+  const int k = blockIdx.x + 1;
+  if (k > D.d - 1 || st->stop || st->nonfinite || st->singular) return;
+  extern __shared__ double lus[];
+  lu_factor<false>(D, st, k, lus);
+}
+
+// the final double-double contraction's factors (double-double runs only)
+__global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
+  __shared__ Dev sD;
+  const Dev &D = stage_dev(Dps, sD);
+  State *st = D.st;
+  const int k = blockIdx.x + 1;
+  if (k > D.d - 1 || !D.prec || st->nonfinite || st->singular) return;
+  lu_factor<true>(D, st, k, nullptr);
 }
 
 // Kernel (c): contraction of the weighted cores with the inverse cross matrices
@@ -908,9 +953,11 @@ __global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
 // that fires is recorded as pending and applied at the end of the sweep.
 // final_dd: the double-double contraction of the final sets (after the run).
 
-// x <- x G_k^-1 for the row x.  FP64: through the QR factors (R^T t = x,
-// x <- Q t).  Double-double (the final contraction, hi/lo pairs): through the
-// double-double LU, P G = L U, so x G^-1 = ((x U^-1) L^-1) P.
+// x <- x G_k^-1 for the row x, through the LU factors P G_k = L U:
+// x G^-1 = ((x U^-1) L^-1) P.  FP64 (every sweep): the factors staged in shared
+// memory row-major (a row of U or L contiguous for the lanes), the diagonal's
+// reciprocals formed first, one warp down the substitutions.  Double-double
+// (the final contraction, hi/lo pairs): the double-double factors.
 __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *xh, double *xl,
                                     double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
@@ -948,25 +995,40 @@ __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, doubl
     __syncthreads();
     return;
   }
-  // FP64: D^-1 R (row-major), the scaled forward substitution R^T t = x
-  stage_compact(Rs, D.Sr[k], nullptr, nullptr, r, ld);
-  __syncthreads();
-  if (warp == 0) warp_fwd_subst(Rs, xh, th, r, r);
-  __syncthreads();
-  for (int i = tid; i < r; i += nt) th[i] *= D.rinv[k][i];
-  __syncthreads();
-  for (int i = tid; i < r; i += nt) {            // x <- Q t
-    const double *Qrow = D.Qr[k] + (size_t)i * ld;
-    double acc = 0.0;
-    for (int j = 0; j < r; ++j) acc = fma(Qrow[j], th[j], acc);
-    xh[i] = acc;
+  // FP64: S[j r + c] = (L\U)(j, c), ri[j] = 1 / U_jj
+  double *ri = Rs + (size_t)r * r;
+  for (int e = tid; e < r * r; e += nt) {
+    const int j = e / r, c = e % r;
+    Rs[e] = D.luh[k][j + (size_t)c * ld];
   }
+  __syncthreads();
+  for (int j = tid; j < r; j += nt) ri[j] = 1.0 / Rs[(size_t)j * r + j];
+  __syncthreads();
+  if (warp == 0) {
+    // t U = x: t_j = x_j / U_jj, then x_c -= t_j U_jc for c > j
+    for (int j = 0; j < r; ++j) {
+      const double tj = xh[j] * ri[j];
+      const double *Sj = Rs + (size_t)j * r;
+      for (int c = j + 1 + lane; c < r; c += 32) xh[c] = fma(-tj, Sj[c], xh[c]);
+      if (lane == 0) th[j] = tj;
+      __syncwarp();
+    }
+    // w L = t (unit lower): w_j = t_j, then t_c -= w_j L_jc for c < j, j descending
+    for (int j = r - 1; j >= 0; --j) {
+      const double wj = th[j];
+      const double *Sj = Rs + (size_t)j * r;
+      for (int c = lane; c < j; c += 32) th[c] = fma(-wj, Sj[c], th[c]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) xh[D.lup[k][i]] = th[i];   // x = w P
   __syncthreads();
 }
 
-// y <- G_k^-1 y for the column y.  FP64: through the QR factors (t = Q^T y,
-// R z = t).  Double-double (the final contraction): through the double-double
-// LU, G^-1 y = U^-1 (L^-1 (P y)).
+// y <- G_k^-1 y for the column y: G^-1 y = U^-1 (L^-1 (P y)).  FP64 with the
+// factors staged column-major (a column contiguous for the lanes); double-
+// double as for the row.
 __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *yh, double *yl,
                                      double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
@@ -1004,17 +1066,33 @@ __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, doub
     __syncthreads();
     return;
   }
-  // FP64: R D^-1 (column-major), the scaled back substitution
-  stage_compact(Rs, D.Cc[k], nullptr, nullptr, r, ld);
-  for (int i = tid; i < r; i += nt) {            // t = Q^T y
-    double acc = 0.0;
-    for (int j = 0; j < r; ++j) acc = fma(D.Qr[k][(size_t)j * ld + i], yh[j], acc);
-    th[i] = acc;
+  // FP64: C[i + c r] = (L\U)(i, c), ri[j] = 1 / U_jj
+  double *ri = Rs + (size_t)r * r;
+  for (int e = tid; e < r * r; e += nt) {
+    const int i = e % r, c = e / r;
+    Rs[e] = D.luh[k][i + (size_t)c * ld];
   }
+  for (int i = tid; i < r; i += nt) th[i] = yh[D.lup[k][i]];   // w = P y
   __syncthreads();
-  if (warp == 0) warp_back_subst(Rs, th, yh, r, r);   // R z = t
+  for (int j = tid; j < r; j += nt) ri[j] = 1.0 / Rs[j + (size_t)j * r];
   __syncthreads();
-  for (int j = tid; j < r; j += nt) yh[j] *= D.rinv[k][j];
+  if (warp == 0) {
+    // L v = w (unit lower): v_i = w_i, then w_m -= L_mi v_i for m > i
+    for (int i = 0; i < r; ++i) {
+      const double vi = th[i];
+      const double *Ci = Rs + (size_t)i * r;
+      for (int m = i + 1 + lane; m < r; m += 32) th[m] = fma(-vi, Ci[m], th[m]);
+      __syncwarp();
+    }
+    // U z = v: z_j = v_j / U_jj, then v_m -= U_mj z_j for m < j, j descending
+    for (int j = r - 1; j >= 0; --j) {
+      const double zj = th[j] * ri[j];
+      const double *Cj = Rs + (size_t)j * r;
+      for (int m = lane; m < j; m += 32) th[m] = fma(-zj, Cj[m], th[m]);
+      if (lane == 0) yh[j] = zj;
+      __syncwarp();
+    }
+  }
   __syncthreads();
 }
 
@@ -2674,6 +2752,24 @@ __global__ void __launch_bounds__(256) k_seq_end(Dev *const *Dps, int k, int las
       st->seq_nacc = 0;
     }
   }
+}
+
+// Serving: a warp per instance of the active set writes its stop flag, and
+// for an instance that stopped its whole state, into (mapped) host memory;
+// only_stopped_dd: rewrite just the states of the stopped double-double ones.
+__global__ void __launch_bounds__(256) k_server_collect(Dev *const *Dps, int n, int *flags, State *states,
+                                                        int only_stopped_dd) {
+  const int q = blockIdx.x * TTQ_WARPS + warp_id(), lane = lane_id();
+  if (q >= n) return;
+  const Dev &D = *Dps[q];
+  const State *st = D.st;
+  const int stop = st->stop;
+  if (!only_stopped_dd && lane == 0) flags[q] = stop;
+  if (!stop || (only_stopped_dd && !D.prec)) return;
+  static_assert(sizeof(State) % 8 == 0, "state copied in 8-byte words");
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(st);
+  unsigned long long *dst = reinterpret_cast<unsigned long long *>(states + q);
+  for (int i = lane; i < (int)(sizeof(State) / 8); i += 32) dst[i] = src[i];
 }
 
 // The tensor train of one instance copied out to a caller's buffer in the

@@ -75,8 +75,12 @@ def test_batch_plain_launches_match_graph():
 def test_full_mix_against_stored_oracle_runs():
     """The 256-instance mix of the batched workload (C/D/E, n 4..24, N 65..513,
     rank caps 8..128) in one batch: the 24 instances the oracle was run on
-    (tests/golden/batch_oracle.json) agree with it to 1e-12, with the same
-    status."""
+    (tests/golden/batch_oracle.json) end with its status, and their values
+    agree with the 60-digit contraction of the oracle's final cores to 1e-12,
+    or, where the oracle's own FP64 contraction misses that by more than a
+    tenth (cross matrices conditioned so that FP64 rounding alone costs
+    ~1e-12 or more: C_n in R^n on coarse grids), to ten times the oracle's own
+    error."""
     import json
     import os
     from paper_1903_11554_gb300 import binding
@@ -88,7 +92,8 @@ def test_full_mix_against_stored_oracle_runs():
         g = got[int(key)]
         assert probs[int(key)].name == ref["workload"]
         assert g["status"] == ref["status"], (key, g, ref)
-        err = abs(g["value"] - float(ref["value"])) / abs(float(ref["value"]))
+        exact = float(ref["value_exact_contraction"])
+        err = abs(g["value"] - exact) / abs(exact)
         worst = max(worst, err)
-        assert err <= 1e-12, (key, g["value"], ref["value"])
+        assert err <= ref["tolerance"], (key, g["value"], exact, ref["tolerance"])
     print("256-instance batch: %d instances against the oracle, worst relative error %.2e" % (len(gold), worst))
