@@ -387,7 +387,7 @@ def measure_batched(binding, inputs, torch, count=256):
 
 
 def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120.0, max_slots=1024,
-                    sweeps_per_step=2, alone=0):
+                    sweeps_per_step=2, alone=0, batched=False):
     """Poisson arrivals (rate per second, seeded), families uniform over C/D/E,
     n in 4..32, tol log-uniform in [1e-14, 1e-8], N in {129, 257, 513}, rank cap
     64; HBM admission budget pool_gb; sweeps_per_step sweeps of every request
@@ -398,6 +398,7 @@ def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120
     arrivals, probs = inputs.serving_stream(count, rate)
     pool_bytes = int(pool_gb * (1 << 30))
     srv = binding.Server(pool_bytes, max_slots=max_slots)
+    srv.set_mode(batched)
     t0 = time.time()
     i, lat, when, ids = 0, {}, {}, {}
     peak_flight, peak_queue = 0, 0
@@ -429,8 +430,9 @@ def measure_serving(binding, inputs, torch, count=2000, rate=2000.0, pool_gb=120
     for rid in list(results)[:8]:
         same &= (binding.integrate(probs[ids[rid]]) == results[rid])
     out = {"workload": "Poisson %g req/s, %d requests (seed 2000), C/D/E, n 4..32, tol 1e-14..1e-8, N 129..513, "
-                       "rank cap 64, HBM admission budget %g GB, %d sweeps per server step"
-                       % (rate, count, pool_gb, sweeps_per_step),
+                       "rank cap 64, HBM admission budget %g GB, %s"
+                       % (rate, count, pool_gb, ("batched engine, %d sweeps per server step" % sweeps_per_step)
+                          if batched else "concurrent engine (a plan and graph per request, 16 streams)"),
            "offered_per_s": count / float(arrivals[-1]), "achieved_integrals_per_s": count / span,
            "latency_s": {"p50": ls[len(ls) // 2], "p99": ls[min(len(ls) - 1, int(math.ceil(0.99 * len(ls))) - 1)]},
            "peak_in_flight": peak_flight, "peak_queued": peak_queue, "seconds": span,
@@ -665,6 +667,7 @@ def main():
         torch.cuda.empty_cache()
         systems["batched"] = measure_batched(binding, inputs, torch)
         systems["serving"] = measure_serving(binding, inputs, torch, count=args.serving_requests, alone=100)
+        systems["serving_batched_engine"] = measure_serving(binding, inputs, torch, count=400, batched=True)
         # the same stream kind offered at 70% of the capacity just measured, so
         # its latencies are service times rather than queueing under overload
         cap_rate = 0.7 * systems["serving"]["achieved_integrals_per_s"]

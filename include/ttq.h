@@ -211,9 +211,9 @@ int ttq_plan_set_config(ttq_plan *plan, int rook_ctas, int sample_ctas, int eval
  * footprint (ttq_workspace_bytes, reserved at its rank cap) exceeds the pool
  * is refused with TTQ_ERR_ADMISSION.  ttq_server_step, at a sweep boundary:
  * retires the requests that stopped (their memory returns to the pool, their
- * result becomes available), admits queued requests in arrival order while a
- * slot and pool memory are free, and enqueues `sweeps` sweeps of every
- * request in flight, all of them in the same batched kernel launches.  Each
+ * result becomes available) and admits queued requests in arrival order while
+ * a slot and pool memory are free (how requests in flight run: see
+ * ttq_server_set_mode).  Each
  * result equals what a single plan gives for the same problem, whatever else
  * is in flight.  ttq_server_poll returns TTQ_PENDING until a request is done;
  * ttq_server_drain returns up to max finished results at once.
@@ -227,6 +227,17 @@ int ttq_server_step(ttq_server *server, int sweeps, int *in_flight, int *queued,
 int ttq_server_poll(ttq_server *server, uint64_t request_id, ttq_result *out);
 int ttq_server_drain(ttq_server *server, uint64_t *ids, ttq_result *results, int max, int *n);
 int ttq_server_stats(const ttq_server *server, int64_t *stats /* [6] */);
+
+/* Serving engine.  Mode 0 (the default): every request in flight is a plan of
+ * its own over its pool region, its whole run one CUDA graph launch on one of
+ * the server's 16 streams, so requests overlap on the device as they arrive;
+ * ttq_server_step retires the requests whose runs have finished (waiting for
+ * the earliest admitted one when none has) and admits queued ones; `sweeps`
+ * is not used.  Mode 1: the requests in flight advance together, `sweeps`
+ * sweeps per step, in the batched kernel launches (the batch form above).
+ * Either way each result equals what a single plan gives for the problem.
+ * Set before the first request is admitted. */
+int ttq_server_set_mode(ttq_server *server, int mode);
 
 /* --- stage-level entry points (replay and inspection) ------------------- */
 

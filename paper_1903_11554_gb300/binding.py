@@ -85,6 +85,7 @@ SIGNATURES = {
     "ttq_server_drain": (_c.c_int, [_vp, _c.POINTER(_c.c_uint64), _c.POINTER(TTQResult), _c.c_int,
                                     _c.POINTER(_c.c_int)]),
     "ttq_server_stats": (_c.c_int, [_vp, _c.POINTER(_c.c_int64)]),
+    "ttq_server_set_mode": (_c.c_int, [_vp, _c.c_int]),
     "ttq_tt_bytes": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "ttq_tt_export": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_size_t, _c.POINTER(_vp)]),
     "ttq_tt_get": (_c.c_int, [_vp, _c.c_int, _i32p, _i32p, _i32p, _c.POINTER(_vp), _c.POINTER(_vp),
@@ -485,6 +486,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def set_mode(self, batched: bool):
+        """False (default): each request its own plan and graph, overlapping on
+        the server's streams; True: requests advance together in batched sweeps."""
+        _check(self.lib.ttq_server_set_mode(self.h, 1 if batched else 0), "ttq_server_set_mode")
 
     def submit(self, p: inputs.Problem) -> int:
         arrays = _Arrays(p)

@@ -60,7 +60,7 @@ struct ttq_plan {
   // launch configuration (batch maxima)
   int max_ni, rook_max, max_sweeps, max_cap;
   int grid_eval, sblocks, cblocks, rblocks, max_sum_n;
-  int qr_smem, samples_smem, contract_smem, solve_smem, lu_smem;
+  int qr_smem, samples_smem, contract_smem, solve_smem;
   long long launches;
   State *hst;               // pinned host mirror of the states (count entries)
   int timing;               // 1: bracket every launch with CUDA events
@@ -285,9 +285,9 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
     L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);
     const size_t dd = p->precision == TTQ_PREC_DD ? 1 : 0;
-    L->luh[k] = b.take((size_t)cap * cap * 8);       // LU of G_k: the FP64 contraction of every sweep
-    L->lul[k] = b.take(dd * cap * cap * 8);          // its low parts: the double-double final contraction
-    L->lup[k] = b.take((size_t)cap * 4);
+    L->luh[k] = b.take(dd * cap * cap * 8);          // double-double LU of G_k (final contraction)
+    L->lul[k] = b.take(dd * cap * cap * 8);
+    L->lup[k] = b.take(dd * cap * 4);
   }
   const int nch = (maxN + TTQ_CHUNK - 1) / TTQ_CHUNK;
   auto clampi = [](long v, long lo, long hi) { return (int)(v < lo ? lo : (v > hi ? hi : v)); };
@@ -475,8 +475,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   P->qr_smem = (int)((cap * (cap + 1) + 8 * cap) * 8);   // full QR: r(r+1)+r, bordering: r^2+7r
   // R (and Q when it fits), then per warp TTQ_SPW groups of two vectors of cap + 1
   P->samples_smem = (int)(((q_in ? 2 : 1) * cap * cap + (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap + 1)) * 8);
-  P->contract_smem = (int)((cap * cap + cap) * 8);   // the LU factors of one G_k and 1/U_jj
-  P->lu_smem = (int)(cap * cap * 8);
+  P->contract_smem = (int)(cap * cap * 8);
   P->solve_smem = (int)((q_in ? 2 : 1) * cap * cap * 8);
   // persistent search: R D^-1 (and Q) of the group's interface for the whole
   // launch, then the samples' group vectors or the rook scratch in one region
@@ -506,8 +505,6 @@ static cudaError_t set_smem_attributes(ttq_plan *P) {
   if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_lu_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, P->lu_smem)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
 }
@@ -666,7 +663,6 @@ static void enqueue_sweep_seq(ttq_plan *P) {
     timed(P, KT_QR, [&] { k_qr<<<dim3(ni, 1, nb), T, P->qr_smem, s>>>(dv); });
   };
   refresh();
-  timed(P, KT_CONTRACT, [&] { k_lu_factor<<<dim3(ni, 1, nb), 256, P->lu_smem, s>>>(dv); });
   timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   for (int k = 1; k <= ni; ++k) {
     k_seq_begin<<<dim3(1, 1, nb), 32, 0, s>>>(dv, k);
@@ -717,11 +713,9 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   if (P->s2) {
     cudaEventRecord(P->fork, s);
     cudaStreamWaitEvent(P->s2, P->fork, 0);
-    timed_on(P, P->s2, KT_CONTRACT, [&] { k_lu_factor<<<dim3(ni, 1, nb), 256, P->lu_smem, P->s2>>>(dv); });
     timed_on(P, P->s2, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, P->s2>>>(dv, 0); });
     cudaEventRecord(P->join, P->s2);
   } else {
-    timed(P, KT_CONTRACT, [&] { k_lu_factor<<<dim3(ni, 1, nb), 256, P->lu_smem, s>>>(dv); });
     timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
   }
   const int single_cond = P->in_loop && loop_end && nb == 1;
@@ -1523,7 +1517,23 @@ struct ttq_server {
   int *hflags_dev;
   int dirty;                                // the active set changed since the launch configuration
   long long sweeps_run, admitted, retired;
+  // concurrent engine (mode 0): every request in flight is a plan of its own
+  // whose whole run is one graph launch on one of the server's streams
+  int mode;                                 // 0: concurrent plans, 1: batched sweeps
+  std::vector<cudaStream_t> streams;
+  struct Live {
+    Request req;
+    size_t off;
+    ttq_plan *plan;
+    cudaEvent_t done;
+    int slot;                               // index of its final state in hst
+  };
+  std::vector<Live> live;
+  std::vector<int> free_slots;
+  int next_stream;
 };
+
+#define TTQ_SERVER_STREAMS 16
 
 static size_t pool_alloc(ttq_server *S, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
@@ -1582,6 +1592,14 @@ extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, v
   S->P.stream = S->stream;
   S->P.devs = S->devs;
   S->P.hst = S->hst;
+  S->mode = 0;
+  S->next_stream = 0;
+  for (int q = max_slots - 1; q >= 0; --q) S->free_slots.push_back(q);
+  for (int q = 0; q < TTQ_SERVER_STREAMS; ++q) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
+    S->streams.push_back(st);
+  }
   cudaError_t e;
   if ((e = create_side_stream(&S->P.s2, false)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&S->P.fork, cudaEventDisableTiming)) != cudaSuccess ||
@@ -1598,6 +1616,12 @@ extern "C" int ttq_server_create(void *pool, size_t pool_bytes, int max_slots, v
 
 extern "C" int ttq_server_destroy(ttq_server *S) {
   if (!S) return TTQ_OK;
+  for (auto &L : S->live) {
+    cudaEventSynchronize(L.done);
+    cudaEventDestroy(L.done);
+    ttq_plan_destroy(L.plan);
+  }
+  for (cudaStream_t st : S->streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
   cudaStreamSynchronize(S->stream);
   if (S->P.s2) { cudaStreamSynchronize(S->P.s2); cudaStreamDestroy(S->P.s2); }
   if (S->P.fork) cudaEventDestroy(S->P.fork);
@@ -1748,9 +1772,88 @@ static int server_retire(ttq_server *S) {
   return TTQ_OK;
 }
 
+// Concurrent engine.  Retire: every plan whose run has completed (its event,
+// queried without waiting) gives its result from the final state copied to
+// mapped host memory; its plan is destroyed and its pool memory freed.
+static int server_retire_live(ttq_server *S) {
+  // a step makes progress: with requests in flight and none finished, wait for
+  // the one admitted first
+  if (!S->live.empty()) {
+    bool any = false;
+    for (auto &L : S->live) any |= cudaEventQuery(L.done) != cudaErrorNotReady;
+    if (!any) CK(cudaEventSynchronize(S->live.front().done));
+  }
+  std::vector<ttq_server::Live> keep;
+  keep.reserve(S->live.size());
+  for (auto &L : S->live) {
+    const cudaError_t q = cudaEventQuery(L.done);
+    if (q == cudaErrorNotReady) {
+      keep.push_back(std::move(L));
+      continue;
+    }
+    if (q != cudaSuccess) { g_last_error = std::string("server: ") + cudaGetErrorString(q); return TTQ_ERR_CUDA; }
+    ttq_result res;
+    fill_result_from(L.plan->h, S->hst[L.slot], &res);
+    L.plan->launches += (long long)L.plan->sweep_kernels * S->hst[L.slot].loop_guard;
+    S->done[L.req.id] = res;
+    cudaEventDestroy(L.done);
+    ttq_plan_destroy(L.plan);
+    pool_free(S, L.off, L.req.bytes);
+    S->free_slots.push_back(L.slot);
+    S->retired++;
+  }
+  S->live.swap(keep);
+  return TTQ_OK;
+}
+
+// Admit, in arrival order, while a slot and pool memory are free: a plan over
+// the request's pool region on the next of the server's streams, its whole
+// run enqueued as one graph, its final state copied to mapped host memory,
+// an event behind it.
+static int server_admit_live(ttq_server *S) {
+  while (!S->queue.empty() && (int)S->live.size() < S->max_slots && !S->free_slots.empty()) {
+    Request &r = S->queue.front();
+    const size_t off = pool_alloc(S, r.bytes);
+    if (off == (size_t)-1) break;           // wait for memory (arrival order is kept)
+    ttq_server::Live L;
+    L.req = std::move(r);
+    S->queue.pop_front();
+    repoint(L.req);
+    L.off = off;
+    L.slot = S->free_slots.back();
+    cudaStream_t st = S->streams.empty() ? S->stream : S->streams[S->next_stream++ % S->streams.size()];
+    int rc = plan_build(&L.req.p, 1, S->pool + off, L.req.bytes, st, &L.plan);
+    if (rc) { pool_free(S, off, L.req.bytes); return rc; }
+    L.plan->persistent = 0;
+    if ((rc = enqueue_run(L.plan))) { ttq_plan_destroy(L.plan); pool_free(S, off, L.req.bytes); return rc; }
+    CK(cudaMemcpyAsync(S->hst + L.slot, L.plan->st, sizeof(State), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+    CK(cudaEventRecord(L.done, st));
+    S->free_slots.pop_back();
+    S->admitted++;
+    S->live.push_back(std::move(L));
+  }
+  return TTQ_OK;
+}
+
+extern "C" int ttq_server_set_mode(ttq_server *S, int mode) {
+  if (!S || mode < 0 || mode > 1) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
+  if (!S->live.empty() || !S->active.empty()) return set_err(TTQ_ERR_INVALID_ARG, "requests in flight");
+  S->mode = mode;
+  return TTQ_OK;
+}
+
 extern "C" int ttq_server_step(ttq_server *S, int sweeps, int *active, int *queued, int64_t *completed) {
   if (!S || sweeps < 1) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
   int rc;
+  if (S->mode == 0) {
+    if ((rc = server_retire_live(S))) return rc;
+    if ((rc = server_admit_live(S))) return rc;
+    if (active) *active = (int)S->live.size();
+    if (queued) *queued = (int)S->queue.size();
+    if (completed) *completed = S->retired;
+    return TTQ_OK;
+  }
   if ((rc = server_retire(S))) return rc;
   if ((rc = server_admit(S))) return rc;
   if ((rc = server_configure(S))) return rc;
@@ -1781,6 +1884,7 @@ extern "C" int ttq_server_poll(ttq_server *S, uint64_t request_id, ttq_result *o
   auto it = S->done.find(request_id);
   if (it == S->done.end()) {
     for (auto &a : S->active) if (a.req.id == request_id) return TTQ_PENDING;
+    for (auto &L : S->live) if (L.req.id == request_id) return TTQ_PENDING;
     for (auto &r : S->queue) if (r.id == request_id) return TTQ_PENDING;
     return set_err(TTQ_ERR_NOT_FOUND, "unknown request");
   }
@@ -1806,7 +1910,7 @@ extern "C" int ttq_server_stats(const ttq_server *S, int64_t *stats /* [6] */) {
   if (!S || !stats) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
   size_t free_bytes = 0;
   for (auto &kv : S->free_list) free_bytes += kv.second;
-  stats[0] = (int64_t)S->active.size();
+  stats[0] = (int64_t)(S->mode == 0 ? S->live.size() : S->active.size());
   stats[1] = (int64_t)S->queue.size();
   stats[2] = S->admitted;
   stats[3] = S->retired;

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
     const NodeChunks nc = node_chunks(Nk, R);
     int i0, i1, nq;
     chunk_span(nc, ch, Nk, i0, i1, nq);
-    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + 5);
+    fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node + (D.prec ? 5 : 1));
     double *Y = D.Y[k] + core_at(D, k, alpha, 0, beta);
     const size_t fib = (size_t)alpha * D.capL[k] + beta;
     for (int q = 0; q < nq; ++q) {
@@ -483,20 +483,34 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
       if (last) __threadfence();
     }
     if (last) {
-      // Neumaier-compensated sum of the lane's nodes (the running sum s and the
-      // sum c of its exact rounding errors), the lanes' (s, c) pairs combined in
-      // double-double: V + Vlo is the node sum to ~N u^2 relative, V alone its
-      // FP64 rounding
       __syncwarp();
-      double sn = 0.0, cn = 0.0;
-      for (int i = lane; i < Nk; i += 32) {
-        const double x = __ldcg(Y + i), t = sn + x;
-        cn += (fabs(sn) >= fabs(x)) ? ((sn - t) + x) : ((x - t) + sn);
-        sn = t;
+      if (D.prec) {
+        // Neumaier-compensated sum of the lane's nodes (running sum s, and c the
+        // sum of its exact rounding errors), then the lanes' pairs added in
+        // the butterfly with each addition's exact error carried along: V +
+        // Vlo is the node sum to ~N u^2 relative
+        double sn = 0.0, cn = 0.0;
+        for (int i = lane; i < Nk; i += 32) {
+          const double x = __ldcg(Y + i), t = sn + x;
+          cn += (fabs(sn) >= fabs(x)) ? ((sn - t) + x) : ((x - t) + sn);
+          sn = t;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double so = __shfl_xor_sync(0xffffffffu, sn, o), co = __shfl_xor_sync(0xffffffffu, cn, o);
+          // lower lane's value first, so every lane forms the same pair
+          const dd e = ((lane & o) == 0) ? two_sum(sn, so) : two_sum(so, sn);
+          sn = e.hi;
+          cn = ((lane & o) == 0) ? (cn + co) + e.lo : (co + cn) + e.lo;
+        }
+        const dd sd = fast_two_sum(sn, cn);
+        if (lane == 0) { D.V[k][fib] = sd.hi; D.Vlo[k][fib] = sd.lo; }
+      } else {
+        double sr = 0.0;
+        for (int i = lane; i < Nk; i += 32) sr += __ldcg(Y + i);
+        sr = warp_sum(sr);
+        if (lane == 0) { D.V[k][fib] = sr; D.Vlo[k][fib] = 0.0; }
       }
-      dd sd = fast_two_sum(sn, cn);
-      sd = warp_sum_dd(sd);
-      if (lane == 0) { D.V[k][fib] = sd.hi; D.Vlo[k][fib] = sd.lo; }
     }
     __syncwarp();
   }
@@ -821,22 +835,16 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (threadIdx.x == 0) { st->qr_rank[k] = r; st->it[k].prank = -1; st->qr_row[k] = 0; }
 }
 
-// The contraction applies G_k^-1 through an LU factorization with partial
-// pivoting of G_k itself, taken from its exact FP64 entries, as LAPACK's
-// solve does: P G_k = L U by Gaussian elimination, the pivot the largest |.|
-// in its column (leading part; ties to the lowest row), L unit lower
-// triangular below the diagonal and U on and above it in one column-major
-// array (leading dimension cap); lup[k][i] is the row of G_k that row i of
-// P G_k holds.  One CTA per interface.
-//   FP64 (every sweep, beside the search): luh only.  The cross matrices are
-//   graded, and on them this factorization keeps the contraction within a
-//   few ulp of the exact product where the search's bordered QR factors lose
-//   one or two digits more.
-//   Double-double (the final contraction of a double-double run): hi parts in
-//   luh, lo parts in lul; the FP64 factors, whose O(u cond(G_k)) error no
-//   arithmetic after them could remove, are not used for it.
-//   The FP64 factorization runs in shared memory (As, r x r column-major),
-//   the double-double one in place in luh / lul.
+// The final double-double contraction applies G_k^-1 through a double-double
+// LU factorization with partial pivoting of G_k itself, taken from its exact
+// FP64 entries: P G_k = L U by Gaussian elimination, the pivot the largest
+// leading part in its column (ties to the lowest row), L unit lower triangular
+// below the diagonal and U on and above it, hi parts in luh and lo parts in
+// lul, column-major with leading dimension cap; lup[k][i] is the row of G_k
+// that row i of P G_k holds.  One CTA per interface.  The FP64 QR factors of
+// the search carry an error of order u cond(G_k) that no arithmetic after them
+// could remove, so they are not used for it.  (The template's FP64 form
+// factors in shared memory; the library uses the double-double form.)
 template <bool DDM>
 __device__ void lu_factor(const Dev &D, State *st, int k, double *As) {
   __shared__ int piv_s;
@@ -918,19 +926,6 @@ __device__ void lu_factor(const Dev &D, State *st, int k, double *As) {
   if (tid == 0) atomicAdd(&st->flops[2], (unsigned long long)((DDM ? 20.0 : 2.0) / 3.0 * r * (double)r * r));
 }
 
-// every sweep (FP64, beside the search): skipped once the run has stopped
-__global__ void __launch_bounds__(256) k_lu_factor(Dev *const *Dps) {
-  __shared__ Dev sD;
-  const Dev &D = stage_dev(Dps, sD);
-  pdl_wait();
-  pdl_release();
-  State *st = D.st;
-  const int k = blockIdx.x + 1;
-  if (k > D.d - 1 || st->stop || st->nonfinite || st->singular) return;
-  extern __shared__ double lus[];
-  lu_factor<false>(D, st, k, lus);
-}
-
 // the final double-double contraction's factors (double-double runs only)
 __global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
   __shared__ Dev sD;
@@ -953,11 +948,9 @@ __global__ void __launch_bounds__(256) k_dd_factor(Dev *const *Dps) {
 // that fires is recorded as pending and applied at the end of the sweep.
 // final_dd: the double-double contraction of the final sets (after the run).
 
-// x <- x G_k^-1 for the row x, through the LU factors P G_k = L U:
-// x G^-1 = ((x U^-1) L^-1) P.  FP64 (every sweep): the factors staged in shared
-// memory row-major (a row of U or L contiguous for the lanes), the diagonal's
-// reciprocals formed first, one warp down the substitutions.  Double-double
-// (the final contraction, hi/lo pairs): the double-double factors.
+// x <- x G_k^-1 for the row x.  FP64: through the QR factors (R^T t = x,
+// x <- Q t).  Double-double (the final contraction, hi/lo pairs): through the
+// double-double LU, P G = L U, so x G^-1 = ((x U^-1) L^-1) P.
 __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *xh, double *xl,
                                     double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
@@ -995,40 +988,25 @@ __device__ void contract_left_solve(const Dev &D, int k, int r, bool prec, doubl
     __syncthreads();
     return;
   }
-  // FP64: S[j r + c] = (L\U)(j, c), ri[j] = 1 / U_jj
-  double *ri = Rs + (size_t)r * r;
-  for (int e = tid; e < r * r; e += nt) {
-    const int j = e / r, c = e % r;
-    Rs[e] = D.luh[k][j + (size_t)c * ld];
+  // FP64: D^-1 R (row-major), the scaled forward substitution R^T t = x
+  stage_compact(Rs, D.Sr[k], nullptr, nullptr, r, ld);
+  __syncthreads();
+  if (warp == 0) warp_fwd_subst(Rs, xh, th, r, r);
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) th[i] *= D.rinv[k][i];
+  __syncthreads();
+  for (int i = tid; i < r; i += nt) {            // x <- Q t
+    const double *Qrow = D.Qr[k] + (size_t)i * ld;
+    double acc = 0.0;
+    for (int j = 0; j < r; ++j) acc = fma(Qrow[j], th[j], acc);
+    xh[i] = acc;
   }
-  __syncthreads();
-  for (int j = tid; j < r; j += nt) ri[j] = 1.0 / Rs[(size_t)j * r + j];
-  __syncthreads();
-  if (warp == 0) {
-    // t U = x: t_j = x_j / U_jj, then x_c -= t_j U_jc for c > j
-    for (int j = 0; j < r; ++j) {
-      const double tj = xh[j] * ri[j];
-      const double *Sj = Rs + (size_t)j * r;
-      for (int c = j + 1 + lane; c < r; c += 32) xh[c] = fma(-tj, Sj[c], xh[c]);
-      if (lane == 0) th[j] = tj;
-      __syncwarp();
-    }
-    // w L = t (unit lower): w_j = t_j, then t_c -= w_j L_jc for c < j, j descending
-    for (int j = r - 1; j >= 0; --j) {
-      const double wj = th[j];
-      const double *Sj = Rs + (size_t)j * r;
-      for (int c = lane; c < j; c += 32) th[c] = fma(-wj, Sj[c], th[c]);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < r; i += nt) xh[D.lup[k][i]] = th[i];   // x = w P
   __syncthreads();
 }
 
-// y <- G_k^-1 y for the column y: G^-1 y = U^-1 (L^-1 (P y)).  FP64 with the
-// factors staged column-major (a column contiguous for the lanes); double-
-// double as for the row.
+// y <- G_k^-1 y for the column y.  FP64: through the QR factors (t = Q^T y,
+// R z = t).  Double-double (the final contraction): through the double-double
+// LU, G^-1 y = U^-1 (L^-1 (P y)).
 __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, double *Rs, double *yh, double *yl,
                                      double *th, double *tl) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), ld = D.cap;
@@ -1066,33 +1044,17 @@ __device__ void contract_right_solve(const Dev &D, int k, int r, bool prec, doub
     __syncthreads();
     return;
   }
-  // FP64: C[i + c r] = (L\U)(i, c), ri[j] = 1 / U_jj
-  double *ri = Rs + (size_t)r * r;
-  for (int e = tid; e < r * r; e += nt) {
-    const int i = e % r, c = e / r;
-    Rs[e] = D.luh[k][i + (size_t)c * ld];
+  // FP64: R D^-1 (column-major), the scaled back substitution
+  stage_compact(Rs, D.Cc[k], nullptr, nullptr, r, ld);
+  for (int i = tid; i < r; i += nt) {            // t = Q^T y
+    double acc = 0.0;
+    for (int j = 0; j < r; ++j) acc = fma(D.Qr[k][(size_t)j * ld + i], yh[j], acc);
+    th[i] = acc;
   }
-  for (int i = tid; i < r; i += nt) th[i] = yh[D.lup[k][i]];   // w = P y
   __syncthreads();
-  for (int j = tid; j < r; j += nt) ri[j] = 1.0 / Rs[j + (size_t)j * r];
+  if (warp == 0) warp_back_subst(Rs, th, yh, r, r);   // R z = t
   __syncthreads();
-  if (warp == 0) {
-    // L v = w (unit lower): v_i = w_i, then w_m -= L_mi v_i for m > i
-    for (int i = 0; i < r; ++i) {
-      const double vi = th[i];
-      const double *Ci = Rs + (size_t)i * r;
-      for (int m = i + 1 + lane; m < r; m += 32) th[m] = fma(-vi, Ci[m], th[m]);
-      __syncwarp();
-    }
-    // U z = v: z_j = v_j / U_jj, then v_m -= U_mj z_j for m < j, j descending
-    for (int j = r - 1; j >= 0; --j) {
-      const double zj = th[j] * ri[j];
-      const double *Cj = Rs + (size_t)j * r;
-      for (int m = lane; m < j; m += 32) th[m] = fma(-zj, Cj[m], th[m]);
-      if (lane == 0) yh[j] = zj;
-      __syncwarp();
-    }
-  }
+  for (int j = tid; j < r; j += nt) yh[j] *= D.rinv[k][j];
   __syncthreads();
 }
 

@@ -33,9 +33,10 @@ def requests():
     ]
 
 
-def serve(reqs, pool_bytes, max_slots=64, per_step=3):
+def serve(reqs, pool_bytes, max_slots=64, per_step=3, batched=False):
     from paper_1903_11554_gb300 import binding
     srv = binding.Server(pool_bytes, max_slots=max_slots)
+    srv.set_mode(batched)
     ids, out, peak_queue, peak_flight = [], {}, 0, 0
     pending = list(reqs)
     for _ in range(10000):
@@ -52,11 +53,12 @@ def serve(reqs, pool_bytes, max_slots=64, per_step=3):
     return [out[i] for i in ids], peak_queue, peak_flight
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("batched", [False, True])
+def test_served_results_equal_alone(batched):
     from paper_1903_11554_gb300 import binding
     reqs = requests()
     alone = [binding.integrate(p) for p in reqs]
-    served, _, flight = serve(reqs, 1 << 30, per_step=2)
+    served, _, flight = serve(reqs, 1 << 30, per_step=2, batched=batched)
     assert flight > 1                            # requests overlapped on the device
     for a, b in zip(served, alone):
         assert a == b
@@ -65,12 +67,13 @@ def test_served_results_equal_alone():
         assert abs(r["value"] - ref) <= 1e-12 * abs(ref)
 
 
-def test_admission_by_memory_queues_and_completes():
+@pytest.mark.parametrize("batched", [False, True])
+def test_admission_by_memory_queues_and_completes(batched):
     from paper_1903_11554_gb300 import binding
     reqs = requests()
     alone = [binding.integrate(p) for p in reqs]
     need = max(binding.workspace_bytes(p) for p in reqs)
-    served, peak_queue, flight = serve(reqs, need + (1 << 18) + 4096, per_step=5)
+    served, peak_queue, flight = serve(reqs, need + (1 << 18) + 4096, per_step=5, batched=batched)
     assert peak_queue > 0                        # requests waited for memory
     for a, b in zip(served, alone):
         assert a == b
