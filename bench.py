@@ -156,7 +156,7 @@ for s in %(sweeps)r:
     value, cores, scale, piv = ttcross.sweep(p, st, s, search=s < len(ranks_at) - 1)
     st = ttcross.apply_pivots(p, st, piv)
     dt = time.perf_counter() - t
-    out.append([s, max(rk), dt, repr(value) == g["history"][s]])
+    out.append([s, max(rk), dt, abs(value / float(g["history"][s]) - 1.0)])
     print(json.dumps(out[-1]), flush=True)
 """
 
@@ -207,14 +207,14 @@ def cpu_baseline(wl, k_sweeps=3):
         secs = sum(r[2] for r in rows)
         res[label] = {"value": (len(rows) / total) / secs, "cores": th, "seconds": round(secs, 2),
                       "sweeps_timed": [r[0] for r in rows], "ranks": [r[1] for r in rows],
-                      "values_equal_stored_run": all(r[3] for r in rows)}
+                      "max_rel_diff_vs_stored_run": max(r[3] for r in rows)}
     one = res["one_core"]
     return {"value": one["value"], "unit": "integrals/s", "cores": 1, "kind": "oracle",
             "sample": "oracle sweeps %s of the %d-sweep %s run (ranks %s), each from that run's own index sets at that "
                       "sweep, timed on one host core in %.1f s; they stand for %d/%d of an integral (stratified "
                       "sample, no fit)" % (one["sweeps_timed"], total, wl, one["ranks"], one["seconds"],
                                            len(one["sweeps_timed"]), total),
-            "all_cores": res["all_cores"], **info}
+            "max_rel_diff_vs_stored_run": one["max_rel_diff_vs_stored_run"], "all_cores": res["all_cores"], **info}
 
 
 # --------------------------------------------------------------------------
@@ -498,7 +498,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(p),
             "cpu_baseline": {"kind": "oracle", "cores": threads, "sample": sample, "value": v, "unit": "integrals/s",
-                             "values_equal_stored_run": all(r[3] for r in timed), **info},
+                             "max_rel_diff_vs_stored_run": max(r[3] for r in timed), **info},
             "e2e": {"value": v, "unit": "integrals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
