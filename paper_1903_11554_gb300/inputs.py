@@ -155,9 +155,10 @@ def config_e16(**kw) -> Problem:
 
 def config_d_cube(n: int, **kw) -> Problem:
     """D_n in the paper's unit-cube form (Eq. 10) with Gauss-Legendre 129 nodes per
-    mode, the rule of the printed D_8 and D_16 values (Sec. 5.5, Fig. 7): D_8 at
-    rank cap 64 (seed 8), D_16 at rank cap 80 (seed 16), tol 1e-12."""
-    caps = {8: 64, 16: 80}
+    mode, the rule of the printed D_8, D_16 and D_32 values (Sec. 5.5, Fig. 7):
+    D_8 at rank cap 64 (seed 8), D_16 at rank cap 80 (seed 16), D_32 at rank cap
+    64 (seed 32), tol 1e-12."""
+    caps = {8: 64, 16: 80, 32: 64}
     args = dict(rank_cap=caps.get(n, 64), tol=1e-12, seed=n, name="D%d_cube_N129" % n)
     args.update(kw)
     return make_problem("D", "cube", n, 129, **args)

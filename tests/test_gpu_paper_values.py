@@ -1,9 +1,10 @@
 """The paper's own values and the double-double bar, on the GPU (needs a GB300).
 
-  * D_8 and D_16 in the paper's unit-cube form (Eq. 10) with Gauss-Legendre 129
-    nodes per mode: the printed values of Sec. 5.5 (Fig. 7) to 5e-12, and the
-    stored oracle runs of the same problems (tests/golden/oracle_full.json,
-    written by tests/golden/make_oracle_values.py) to 1e-12.
+  * D_8, D_16 and D_32 in the paper's unit-cube form (Eq. 10) with
+    Gauss-Legendre 129 nodes per mode: the printed values of Sec. 5.5 (Fig. 7)
+    to 5e-12, and for D_8 and D_16 the stored oracle runs of the same problems
+    (tests/golden/oracle_full.json, written by
+    tests/golden/make_oracle_values.py) to 1e-12.
   * E_16 at full size (d = 15, Gauss-Legendre 128, rank cap 96, tol 1e-14)
     with the double-double final contraction: value + value_lo against a
     60-digit decimal contraction of the GPU's own final cores (the product of
@@ -71,6 +72,20 @@ def test_d_printed_values(n):
     assert abs(got["value"] / ora - 1) < 1e-12, (got["value"], ora)
     print("D_%d: GPU %.17e, printed rel %.2e, oracle rel %.2e"
           % (n, got["value"], abs(got["value"] / ref - 1), abs(got["value"] / ora - 1)))
+
+
+def test_d32_printed_value():
+    """D_32 (d = 31, the largest printed D_d within the library's d <= 32): the
+    cross converges (tol 1e-12, rank 47 of cap 64) and its value meets the
+    printed one; there is no stored oracle run of it (hours in the numpy
+    oracle), the printed value is the pin."""
+    p = inputs.config_d_cube(32)
+    got = B().integrate(p)
+    assert got["status_name"] == "converged", got
+    ref = printed("D_32")
+    err = abs(got["value"] / ref - 1)
+    print("D_32: GPU %.17e, printed rel %.2e, rank %d, sweeps %d" % (got["value"], err, got["max_rank"], got["sweeps"]))
+    assert err < 5e-12, (got["value"], ref)
 
 
 def test_e16_double_double_at_full_size():
