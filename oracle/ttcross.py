@@ -36,6 +36,11 @@ Readings where the paper is silent:
     D_n) then pick the same pivot whatever the rounding;
   * a pivot is accepted when |E*| > tol * scale, scale = largest |entry| of the
     current cores, and r_k < rank cap;
+  * several pivots per interface per sweep (npiv > 1, a rank-adaptive variant
+    of Alg. 6, which adds one): the npiv best samples with distinct rows and
+    columns start rook searches on the old residual, and greedy complete
+    pivoting on the residual matrix of their rows and columns keeps the pairs
+    whose Schur pivot passes the acceptance threshold (pivot_search_multi);
   * stopping: relative internal convergence |I_s - I_{s-1}| <= tol |I_s|, or
     no pivot accepted in a sweep, or every interface at the rank cap, or the
     sweep limit.
@@ -317,11 +322,19 @@ class Pivot:
     evals: int
 
 
-def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarray,
-                 sweep: int, scale: float) -> Optional[Pivot]:
-    """Alg. 2 on superblock k with the index sets of the previous sweep (Alg. 6).
-    Residual E(rho, gamma) = A(rho, gamma) - B_k(rho, :) R_{k+1}(:, gamma),
-    R_{k+1} = Y_{k+1} as r_k x (N_{k+1} r_{k+1})."""
+@dataclasses.dataclass
+class _Superblock:
+    """Superblock k of Alg. 6 on the sets of the previous sweep: its sizes, the
+    cross's rows and columns (not eligible: the residual vanishes there), and
+    the residual E(rho, gamma) = A(rho, gamma) - B_k(rho, :) R_{k+1}(:, gamma)."""
+    M: int
+    Ncol: int
+    row_ok: np.ndarray
+    col_ok: np.ndarray
+    residual: object
+
+
+def _superblock(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarray) -> Optional[_Superblock]:
     Nk = problem.N[k - 1]
     rk = st.rank(k)
     M = st.rank(k - 1) * Nk
@@ -329,12 +342,10 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
     Ncol = R.shape[1]
     if M <= rk or Ncol <= rk:
         return None                                       # superblock already fully crossed
-    P = cross_rows(problem, st, k)
-    Q = cross_cols(problem, st, k)
     row_ok = np.ones(M, dtype=bool)
-    row_ok[P] = False
+    row_ok[cross_rows(problem, st, k)] = False
     col_ok = np.ones(Ncol, dtype=bool)
-    col_ok[Q] = False
+    col_ok[cross_cols(problem, st, k)] = False
 
     def residual(rows, cols):
         rows = np.asarray(rows, dtype=np.int64)
@@ -343,52 +354,191 @@ def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarr
         approx = np.einsum("tb,bt->t", B[rows, :], R[:, cols])
         return A - approx
 
-    evals = 0
-    # random samples
+    return _Superblock(M, Ncol, row_ok, col_ok, residual)
+
+
+def _sample_scores(problem, sb: _Superblock, k: int, sweep: int):
+    """Alg. 2, first step: |E| at the interface's seeded random positions
+    (-1 where a sample lies on a cross row or column)."""
     S = problem.samples_for(k)
     stream = rng.stream_id(sweep, k, rng.PURPOSE_SAMPLE)
-    srows = np.array([rng.draw_index(problem.seed, stream, 2 * t, M) for t in range(S)], dtype=np.int64)
-    scols = np.array([rng.draw_index(problem.seed, stream, 2 * t + 1, Ncol) for t in range(S)], dtype=np.int64)
-    ok = row_ok[srows] & col_ok[scols]
+    srows = np.array([rng.draw_index(problem.seed, stream, 2 * t, sb.M) for t in range(S)], dtype=np.int64)
+    scols = np.array([rng.draw_index(problem.seed, stream, 2 * t + 1, sb.Ncol) for t in range(S)], dtype=np.int64)
+    ok = sb.row_ok[srows] & sb.col_ok[scols]
     score = np.full(S, -1.0)
     if ok.any():
-        score[ok] = np.abs(residual(srows[ok], scols[ok]))
-        evals += int(ok.sum())
-    t = tie_argmax(score, scale)
-    if t < 0:
-        return None
-    row, col = int(srows[t]), int(scols[t])
+        score[ok] = np.abs(sb.residual(srows[ok], scols[ok]))
+    return srows, scols, score, int(ok.sum())
 
-    # rook pivoting: alternate column and row searches until the rook condition,
-    # Eq. (2), holds.  It is tested after each search: a column search that
-    # returns the row searched in the previous round ends the search, since that
-    # row search returned the current column (the pivot already dominates its
-    # row and its column, and a repeated row search would return the same pivot).
-    rows_all = np.arange(M)
-    cols_all = np.arange(Ncol)
+
+def _rook(problem, sb: _Superblock, row: int, col: int, scale: float):
+    """Rook pivoting from the start (row, col): alternate column and row
+    searches until the rook condition, Eq. (2), holds or the round budget is
+    spent.  The condition is tested after each search: a column search that
+    returns the row searched in the previous round ends the search, since that
+    row search returned the current column (the pivot already dominates its
+    row and its column, and a repeated row search would return the same
+    pivot).  Returns (row, col, E at the pivot, rounds, evaluations)."""
+    rows_all = np.arange(sb.M)
+    cols_all = np.arange(sb.Ncol)
     err = 0.0
     rounds = 0
+    evals = 0
     prev_row = -1
     for _ in range(max(1, problem.rook_max)):
         rounds += 1
-        cscore = np.full(M, -1.0)
-        cscore[row_ok] = np.abs(residual(rows_all[row_ok], np.full(int(row_ok.sum()), col)))
-        evals += int(row_ok.sum())
+        cscore = np.full(sb.M, -1.0)
+        cscore[sb.row_ok] = np.abs(sb.residual(rows_all[sb.row_ok], np.full(int(sb.row_ok.sum()), col)))
+        evals += int(sb.row_ok.sum())
         row = tie_argmax(cscore, scale)
         if row == prev_row:
             break
-        rres = np.zeros(Ncol)
-        rres[col_ok] = residual(np.full(int(col_ok.sum()), row), cols_all[col_ok])
-        evals += int(col_ok.sum())
-        rscore = np.where(col_ok, np.abs(rres), -1.0)
+        rres = np.zeros(sb.Ncol)
+        rres[sb.col_ok] = sb.residual(np.full(int(sb.col_ok.sum()), row), cols_all[sb.col_ok])
+        evals += int(sb.col_ok.sum())
+        rscore = np.where(sb.col_ok, np.abs(rres), -1.0)
         new_col = tie_argmax(rscore, scale)
         err = float(rres[new_col])
         if new_col == col:
             break
         prev_row = row
         col = new_col
-    accepted = abs(err) > problem.pivot_tol * scale and rk < problem.rank_cap
-    return Pivot(k=k, row=row, col=col, err=err, accepted=bool(accepted), rounds=rounds, evals=evals)
+    return row, col, err, rounds, evals
+
+
+def pivot_search(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarray,
+                 sweep: int, scale: float) -> Optional[Pivot]:
+    """Alg. 2 on superblock k with the index sets of the previous sweep (Alg. 6).
+    Residual E(rho, gamma) = A(rho, gamma) - B_k(rho, :) R_{k+1}(:, gamma),
+    R_{k+1} = Y_{k+1} as r_k x (N_{k+1} r_{k+1}): the best random sample starts
+    the rook pivoting; its pivot is accepted when |E| > pivot_tol * scale and
+    r_k < rank cap."""
+    sb = _superblock(problem, st, k, B, Ynext)
+    if sb is None:
+        return None
+    srows, scols, score, evals = _sample_scores(problem, sb, k, sweep)
+    t = tie_argmax(score, scale)
+    if t < 0:
+        return None
+    row, col, err, rounds, ev = _rook(problem, sb, int(srows[t]), int(scols[t]), scale)
+    accepted = abs(err) > problem.pivot_tol * scale and st.rank(k) < problem.rank_cap
+    return Pivot(k=k, row=row, col=col, err=err, accepted=bool(accepted), rounds=rounds, evals=evals + ev)
+
+
+def schur_step(Mx: np.ndarray, a: int, c: int, rows_left: List[int], cols_left: List[int]) -> None:
+    """Replace the rows and columns left of Mx by the Schur complement of the
+    pivot Mx[a, c]: M_be <- M_be - M_bc M_ae / M_ac."""
+    piv = Mx[a, c]
+    for b in rows_left:
+        for e in cols_left:
+            Mx[b, e] = Mx[b, e] - (Mx[b, c] * Mx[a, e]) / piv
+
+
+def greedy_cross(Mx: np.ndarray, scale: float, pivot_tol: float, room: int):
+    """Greedy complete pivoting on the square residual matrix Mx (modified in
+    place): the largest |M_ac| over the rows and columns left (tie window,
+    first in row-major order) while it exceeds pivot_tol * scale and fewer than
+    `room` pivots were taken; each taken pivot is followed by schur_step.
+    Returns [(a, c, pivot)] in order; the product of the pivots is the
+    determinant of Mx restricted to the taken rows and columns, in that order."""
+    m = Mx.shape[0]
+    rows_left = list(range(m))
+    cols_left = list(range(m))
+    out = []
+    while rows_left and len(out) < room:
+        score = np.full((m, m), -1.0)
+        for a in rows_left:
+            for c in cols_left:
+                if np.isfinite(Mx[a, c]):
+                    score[a, c] = abs(Mx[a, c])
+        t = tie_argmax(score.ravel(), scale)
+        if t < 0:
+            break
+        a, c = divmod(t, m)
+        piv = float(Mx[a, c])
+        if not abs(piv) > pivot_tol * scale:
+            break
+        out.append((a, c, piv))
+        rows_left.remove(a)
+        cols_left.remove(c)
+        schur_step(Mx, a, c, rows_left, cols_left)
+    return out
+
+
+@dataclasses.dataclass
+class MultiPivot:
+    """Interface k's outcome with several pivots per sweep: the rook searches
+    run (one Pivot each, with its own residual), the residual matrix of their
+    rows and columns, and the pivots accepted from it in acceptance order (err:
+    the Schur pivot)."""
+    k: int
+    searches: List[Pivot]
+    cross: np.ndarray
+    pivots: List[Pivot]
+    evals: int
+
+    @property
+    def accepted(self) -> bool:
+        return len(self.pivots) > 0
+
+
+def pivot_search_multi(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarray,
+                       sweep: int, scale: float, npiv: int) -> Optional[MultiPivot]:
+    """Up to npiv pivots on superblock k in one sweep (a rank-adaptive variant;
+    Alg. 6 itself adds one).  On the residual of the sweep's old cross:
+      1. starts: the npiv best random samples, taken one at a time as the
+         tie-window argmax among the samples whose row and column differ from
+         those of the starts already taken;
+      2. rook pivoting (Alg. 2) from each start;
+      3. a search whose row or column equals that of an earlier search is
+         dropped;
+      4. the residuals at the remaining searches' rows x_a and columns y_c
+         form the matrix M (M_aa: search a's own residual; the others fresh
+         evaluations);
+      5. greedy complete pivoting on M (cross approximation of the candidates'
+         block): the largest |M_ac| over the rows and columns left (tie
+         window, first in row-major order) is accepted while it exceeds
+         pivot_tol * scale and the rank stays below the cap; x_a and y_c are
+         appended, and M is replaced by its Schur complement
+         M_bd - M_bc M_ad / M_ac.
+    Each accepted pair extends the cross by a row and a column whose Schur
+    pivot is nonzero, so the new cross matrix stays nonsingular:
+    det G_k' = det G_k times the product of the accepted pivots.  With
+    npiv = 1 this is exactly pivot_search."""
+    sb = _superblock(problem, st, k, B, Ynext)
+    if sb is None:
+        return None
+    srows, scols, score, evals = _sample_scores(problem, sb, k, sweep)
+    starts: List[int] = []
+    sc = score.copy()
+    while len(starts) < npiv:
+        t = tie_argmax(sc, scale)
+        if t < 0:
+            break
+        starts.append(t)
+        sc[(srows == srows[t]) | (scols == scols[t])] = -1.0
+    if not starts:
+        return None
+    searches: List[Pivot] = []
+    for t in starts:
+        row, col, err, rounds, ev = _rook(problem, sb, int(srows[t]), int(scols[t]), scale)
+        evals += ev
+        searches.append(Pivot(k=k, row=row, col=col, err=err, accepted=False, rounds=rounds, evals=ev))
+    kept: List[Pivot] = []
+    for pv in searches:
+        if not any(pv.row == q.row or pv.col == q.col for q in kept):
+            kept.append(pv)
+    m = len(kept)
+    Mx = np.empty((m, m))
+    for a in range(m):
+        for c in range(m):
+            Mx[a, c] = kept[a].err if a == c else float(sb.residual([kept[a].row], [kept[c].col])[0])
+    evals += m * (m - 1)
+    cross = Mx.copy()
+    room = problem.rank_cap - st.rank(k)
+    pivots = [Pivot(k=k, row=kept[a].row, col=kept[c].col, err=piv, accepted=True, rounds=kept[a].rounds, evals=0)
+              for a, c, piv in greedy_cross(Mx, scale, problem.pivot_tol, room)]
+    return MultiPivot(k=k, searches=searches, cross=cross, pivots=pivots, evals=evals)
 
 
 # ---------------------------------------------------------------------------
@@ -432,8 +582,14 @@ def apply_pivots(problem, st: CrossState, pivots: List[Pivot]) -> CrossState:
     (alpha*, i*) extends I_<=k, the new column (j*, beta*) extends I_>k; both are
     nested in the previous sweep's neighbours by construction."""
     new = st.copy()
+    flat: List[Pivot] = []
     for pv in pivots:
-        if pv is None or not pv.accepted:
+        if isinstance(pv, MultiPivot):
+            flat.extend(pv.pivots)                        # in acceptance order
+        elif pv is not None:
+            flat.append(pv)
+    for pv in flat:
+        if not pv.accepted:
             continue
         k = pv.k
         Nk = problem.N[k - 1]
@@ -455,16 +611,22 @@ class SweepRecord:
     scale: float
 
 
-def search_all(problem, st: CrossState, s: int, cores: List[np.ndarray], scale: float) -> List[Optional[Pivot]]:
+def search_all(problem, st: CrossState, s: int, cores: List[np.ndarray], scale: float) -> list:
     """Alg. 6 with one superblock per interface: Alg. 2 on every interface k
-    (independently, on the sets of this sweep); interfaces at the cap skip."""
-    pivots: List[Optional[Pivot]] = []
+    (independently, on the sets of this sweep); interfaces at the cap skip.
+    With problem.npiv > 1 every interface runs pivot_search_multi (a
+    MultiPivot per interface instead of a Pivot)."""
+    npiv = getattr(problem, "npiv", 1)
+    pivots: list = []
     for k in range(1, problem.d):
         if st.rank(k) >= problem.rank_cap:
             pivots.append(None)
             continue
         B = maxvol_coefficients(cores[k - 1], cross_rows(problem, st, k))
-        pivots.append(pivot_search(problem, st, k, B, cores[k], s, scale))
+        if npiv > 1:
+            pivots.append(pivot_search_multi(problem, st, k, B, cores[k], s, scale, npiv))
+        else:
+            pivots.append(pivot_search(problem, st, k, B, cores[k], s, scale))
     return pivots
 
 
@@ -512,6 +674,8 @@ def integrate(problem, state: Optional[CrossState] = None, record: bool = True, 
     d = problem.d
     if d < 2:
         raise ValueError("the cross needs d >= 2")
+    if sequential and getattr(problem, "npiv", 1) > 1:
+        raise ValueError("the sequential sweep takes one pivot per step")
     st = state.copy() if state is not None else initial_state(problem)
     history: List[SweepRecord] = []
     search_evals = 0

@@ -69,6 +69,7 @@ class Problem:
     rook_max: int = 3           # column/row rounds of rook pivoting
     init_samples: int = 64      # random points scanned for the initial multi-indices
     r0: int = 1                 # initial multi-indices (rank of every interface before the first sweep)
+    npiv: int = 1               # pivots an interface may add per sweep (1: Alg. 6 as printed)
     precision: str = "fp64"     # "fp64" or "dd" (double-double final contraction)
     name: str = ""
 
