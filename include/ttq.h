@@ -73,6 +73,7 @@ typedef enum {
 #define TTQ_MAX_RANK 128      /* rank cap <= 128 */
 #define TTQ_MAX_NODES 2048    /* N_k <= 2048 */
 #define TTQ_MAX_INIT_SAMPLES 1024
+#define TTQ_MAX_PIVOTS 4      /* pivots an interface may add per sweep (npiv) */
 
 /* The problem statement (Sec. 4.1: integrand, per-mode nodes and weights;
  * Alg. 6 inputs: rank cap and stopping tolerance). */
@@ -97,6 +98,13 @@ typedef struct ttq_problem {
   int32_t precision;          /* ttq_precision */
   int32_t r0;                 /* initial multi-indices (the rank of every interface before the first sweep),
                                  1..rank_cap and at most min(N_1, N_d, init_samples); 0 is taken as 1 */
+  int32_t npiv;               /* pivots an interface may add per sweep, 0..TTQ_MAX_PIVOTS; 0 or 1: one, as
+                                 Alg. 6.  More (a rank-adaptive variant): the npiv best random samples with
+                                 distinct rows and columns start rook searches (Alg. 2) on the sweep's old
+                                 residual, and greedy complete pivoting on the residual matrix of their rows
+                                 and columns keeps the pairs whose Schur pivot passes the acceptance
+                                 threshold, appended in that order.  Single plans of the staged search only
+                                 (not batches, servers, the persistent or the sequential search). */
 } ttq_problem;
 
 typedef struct ttq_result {

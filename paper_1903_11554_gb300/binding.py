@@ -32,7 +32,8 @@ class TTQProblem(_c.Structure):
                 ("inputs_on_device", _c.c_int32), ("rank_cap", _c.c_int32), ("tol", _c.c_double),
                 ("pivot_tol", _c.c_double), ("conv_window", _c.c_int32), ("max_sweeps", _c.c_int32),
                 ("seed", _c.c_uint64), ("n_samples", _c.c_int32), ("rook_max", _c.c_int32),
-                ("init_samples", _c.c_int32), ("precision", _c.c_int32), ("r0", _c.c_int32)]
+                ("init_samples", _c.c_int32), ("precision", _c.c_int32), ("r0", _c.c_int32),
+                ("npiv", _c.c_int32)]
 
 
 class TTQResult(_c.Structure):
@@ -168,6 +169,7 @@ def make_struct(p: inputs.Problem, arrays: _Arrays) -> TTQProblem:
     s.rook_max = p.rook_max
     s.init_samples = p.init_samples
     s.r0 = p.r0
+    s.npiv = getattr(p, "npiv", 1)
     s.precision = inputs.PREC_CODE[p.precision]
     return s
 

@@ -81,6 +81,7 @@ struct ttq_plan {
   int sequential;           // sweeps of Alg. 5 (interfaces one after another) instead of Alg. 6
   int persistent;           // one instance: the search of a sweep as one cooperative launch (k_search)
   int search_grid, search_smem;
+  int npiv;                 // searches per interface (several pivots per sweep): the decisions kernels' grid y
 };
 
 static cudaEvent_t ev_get(ttq_plan *P) {
@@ -193,8 +194,11 @@ static int validate(const ttq_problem *p) {
   }
   if (p->n_samples < 0 || p->n_samples > (1 << 20)) return set_err(TTQ_ERR_INVALID_ARG, "bad n_samples");
   if (p->precision < 0 || p->precision > 1) return set_err(TTQ_ERR_INVALID_ARG, "bad precision");
+  if (p->npiv < 0 || p->npiv > TTQ_MAX_PIVOTS) return set_err(TTQ_ERR_INVALID_ARG, "npiv must be in 0..4");
   return TTQ_OK;
 }
+
+static int npiv_of(const ttq_problem *p) { return p->npiv < 1 ? 1 : p->npiv; }
 
 struct Bump {
   size_t off = 0;
@@ -213,6 +217,9 @@ struct Layout {
   size_t Qr[TTQ_MAXD], Qc[TTQ_MAXD], Rc[TTQ_MAXD], Rr[TTQ_MAXD], Cc[TTQ_MAXD], Sr[TTQ_MAXD], rinv[TTQ_MAXD],
       zvec[TTQ_MAXD], pvec[TTQ_MAXD], ptab[TTQ_MAXD];
   size_t cs[TTQ_MAXD], ce[TTQ_MAXD], im[TTQ_MAXD], zs[TTQ_MAXD];
+  size_t itx;                // states of searches 1 .. npiv-1 (several pivots per sweep)
+  size_t cs_st, im_st;       // scratch strides between the searches of an interface
+  int pt_st;
   size_t luh[TTQ_MAXD], lul[TTQ_MAXD], lup[TTQ_MAXD];   // double-double LU of G_k (precision DD only)
   size_t devs;               // this instance's own one-entry descriptor array
   size_t total;
@@ -231,6 +238,23 @@ static void make_layout(const ttq_problem *p, Layout *L) {
   for (int k = 1; k < d; ++k) maxS = samples_for(p, k) > maxS ? samples_for(p, k) : maxS;
   int capL[TTQ_MAXD + 1];
   for (int k = 0; k <= d; ++k) capL[k] = (k == 0 || k == d) ? 1 : cap;
+  // several pivots per sweep: every interface holds npiv searches' scratch,
+  // search j's j strides (the largest of any interface) past search 0's
+  const int np = npiv_of(p);
+  size_t cs_st = 0, im_st = 0;
+  for (int k = 1; k < d; ++k) {
+    size_t nc = (size_t)samples_for(p, k);
+    const size_t ncol = (size_t)cap * p->nodes_per_mode[k - 1], nrow = (size_t)p->nodes_per_mode[k] * cap;
+    nc = nc > ncol ? nc : ncol;
+    nc = nc > nrow ? nc : nrow;
+    cs_st = nc > cs_st ? nc : cs_st;
+    const size_t nchk = (p->nodes_per_mode[k - 1] + 31) / 32, nchk1 = (p->nodes_per_mode[k] + 31) / 32;
+    const size_t ni = (size_t)cap * (nchk > nchk1 ? nchk : nchk1);
+    im_st = ni > im_st ? ni : im_st;
+  }
+  L->cs_st = cs_st;
+  L->im_st = im_st;
+  L->pt_st = maxN;
   Bump b;
   L->dev = b.take(sizeof(Dev));
   L->st = b.take(sizeof(State));
@@ -270,20 +294,21 @@ static void make_layout(const ttq_problem *p, Layout *L) {
     L->Cc[k] = b.take((size_t)cap * cap * 8);
     L->Sr[k] = b.take((size_t)cap * cap * 8);
     L->rinv[k] = b.take((size_t)cap * 8);
-    L->zvec[k] = b.take((size_t)cap * 8);
+    L->zvec[k] = b.take((size_t)cap * np * 8);
     L->pvec[k] = b.take((size_t)cap * 8);
-    L->ptab[k] = b.take((size_t)(p->nodes_per_mode[k - 1] > p->nodes_per_mode[k] ? p->nodes_per_mode[k - 1] : p->nodes_per_mode[k]) * 8);
+    L->ptab[k] = b.take(((size_t)(np - 1) * maxN +
+                         (p->nodes_per_mode[k - 1] > p->nodes_per_mode[k] ? p->nodes_per_mode[k - 1] : p->nodes_per_mode[k])) * 8);
     size_t nc = (size_t)samples_for(p, k);
     size_t ncol = (size_t)cap * p->nodes_per_mode[k - 1], nrow = (size_t)p->nodes_per_mode[k] * cap;
     nc = nc > ncol ? nc : ncol;
     nc = nc > nrow ? nc : nrow;
-    L->cs[k] = b.take(nc * 8);
-    L->ce[k] = b.take(nc * 8);
+    L->cs[k] = b.take((nc + (size_t)(np - 1) * cs_st) * 8);
+    L->ce[k] = b.take((nc + (size_t)(np - 1) * cs_st) * 8);
     L->zs[k] = b.take((size_t)samples_for(p, k) * cap * 8);
     // per-row maxima of a rook step: one slot per outer index and row of 32 nodes
     const size_t nchk = (p->nodes_per_mode[k - 1] + 31) / 32;
     const size_t nchk1 = (p->nodes_per_mode[k] + 31) / 32;
-    L->im[k] = b.take((size_t)cap * (nchk > nchk1 ? nchk : nchk1) * 8);
+    L->im[k] = b.take(((size_t)cap * (nchk > nchk1 ? nchk : nchk1) + (size_t)(np - 1) * im_st) * 8);
     const size_t dd = p->precision == TTQ_PREC_DD ? 1 : 0;
     L->luh[k] = b.take(dd * cap * cap * 8);          // double-double LU of G_k (final contraction)
     L->lul[k] = b.take(dd * cap * cap * 8);
@@ -296,6 +321,7 @@ static void make_layout(const ttq_problem *p, Layout *L) {
   L->cblocks = clampi(((long)(d - 1) * cap * nch + TTQ_WARPS - 1) / TTQ_WARPS, 1, 456);
   L->rblocks = L->cblocks;
   L->cbuf = b.take((size_t)4 * cap * 8);
+  L->itx = b.take((size_t)(np - 1) * TTQ_MAXD * sizeof(IfaceState));
   L->devs = b.take(sizeof(Dev *));
   L->total = (b.off + 255) & ~(size_t)255;
 }
@@ -363,6 +389,10 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
     cudaGetLastError();
   }
   D.q_in_smem = q_in_smem;
+  D.npiv = npiv_of(p);
+  D.cs_st = L.cs_st;
+  D.im_st = L.im_st;
+  D.pt_st = L.pt_st;
   int off = 0;
   for (int k = 0; k < d; ++k) { D.N[k] = p->nodes_per_mode[k]; D.off[k] = off; off += D.N[k]; }
   for (int k = 1; k < d; ++k) D.S[k] = samples_for(p, k);
@@ -391,6 +421,7 @@ static void fill_descriptor(const ttq_problem *p, const double *hx, char *base, 
   }
   D.st = (State *)(base + L.st);
   D.cbuf = (double *)(base + L.cbuf);
+  D.itx = (IfaceState *)(base + L.itx);
 }
 
 // host copies of a problem's nodes and weights (checked finite)
@@ -414,7 +445,7 @@ static int host_inputs(const ttq_problem *p, cudaStream_t s, std::vector<double>
 
 // launch configuration from the instances' problems (maxima over the set)
 static void configure(ttq_plan *P, const ttq_problem *probs, int count, const Layout *Ls) {
-  P->max_ni = 0; P->rook_max = 1; P->max_sweeps = 1; P->max_cap = 1; P->max_sum_n = 1;
+  P->max_ni = 0; P->rook_max = 1; P->max_sweeps = 1; P->max_cap = 1; P->max_sum_n = 1; P->npiv = 1;
   P->sblocks = P->cblocks = P->rblocks = 1;
   size_t maxfib = 0;
   for (int q = 0; q < count; ++q) {
@@ -424,6 +455,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     P->rook_max = p->rook_max > P->rook_max ? p->rook_max : P->rook_max;
     P->max_sweeps = p->max_sweeps > P->max_sweeps ? p->max_sweeps : P->max_sweeps;
     P->max_cap = cap > P->max_cap ? cap : P->max_cap;
+    P->npiv = npiv_of(p) > P->npiv ? npiv_of(p) : P->npiv;
     int sn = 0;
     for (int k = 0; k < p->d; ++k) sn += p->nodes_per_mode[k];
     P->max_sum_n = sn > P->max_sum_n ? sn : P->max_sum_n;
@@ -540,6 +572,8 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
   for (int q = 0; q < count; ++q) {
     int rc = validate(probs + q);
     if (rc) return rc;
+    if (count > 1 && npiv_of(probs + q) > 1)
+      return set_err(TTQ_ERR_INVALID_ARG, "several pivots per sweep: single-instance plans only");
     make_layout(probs + q, &Ls[q]);
     offs[q] = need;
     need += Ls[q].total;
@@ -735,11 +769,14 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   for (int q = 0; q < P->rook_max; ++q) {
     const bool fin = q == P->rook_max - 1;
     timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
-    timed(P, KT_SOLVE, [&] { launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 1, 0, P->cond, 0); });
+    timed(P, KT_SOLVE, [&] {
+      launch_k(P, k_solve, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 1, 0, P->cond, 0);
+    });
     timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv); });
     if (fin && P->s2) cudaStreamWaitEvent(s, P->join, 0);
     timed(P, fin ? KT_UPDATE : KT_SOLVE, [&] {
-      launch_k(P, k_solve, dim3(ni, 1, nb), T, P->solve_smem, s, dv, 2, fin ? 1 : 0, P->cond, fin ? single_cond : 0);
+      launch_k(P, k_solve, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 2, fin ? 1 : 0, P->cond,
+               fin ? single_cond : 0);
     });
   }
   if (P->in_loop && loop_end && nb > 1) {
@@ -1307,6 +1344,7 @@ extern "C" int ttq_plan_set_search(ttq_plan *P, int mode) {
   if (mode < 0 || mode > 1) return set_err(TTQ_ERR_INVALID_ARG, "search mode must be 0 (staged) or 1 (persistent)");
   if (mode == 1 && (P->count != 1 || P->search_grid < P->max_ni))
     return set_err(TTQ_ERR_INVALID_ARG, "the persistent search needs a single-instance plan that fits the device");
+  if (mode == 1 && P->npiv > 1) return set_err(TTQ_ERR_INVALID_ARG, "the persistent search takes one pivot per sweep");
   P->persistent = mode;
   if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
   if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
@@ -1316,6 +1354,7 @@ extern "C" int ttq_plan_set_search(ttq_plan *P, int mode) {
 extern "C" int ttq_plan_set_sequential(ttq_plan *P, int enable) {
   if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
   if (enable && P->count != 1) return set_err(TTQ_ERR_INVALID_ARG, "sequential sweeps need a single-instance plan");
+  if (enable && P->npiv > 1) return set_err(TTQ_ERR_INVALID_ARG, "the sequential sweep takes one pivot per step");
   P->sequential = enable ? 1 : 0;
   if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
   if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
@@ -1639,6 +1678,7 @@ extern "C" int ttq_server_submit(ttq_server *S, const ttq_problem *p, uint64_t *
   if (!S || !p) return set_err(TTQ_ERR_INVALID_ARG, "null argument");
   int rc = validate(p);
   if (rc) return rc;
+  if (npiv_of(p) > 1) return set_err(TTQ_ERR_INVALID_ARG, "several pivots per sweep: single plans only, not servers");
   Layout L;
   make_layout(p, &L);
   size_t head = ((size_t)S->max_slots * sizeof(Dev *) + 255) & ~(size_t)255;

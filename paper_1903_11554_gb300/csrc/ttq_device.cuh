@@ -26,6 +26,7 @@
 #define TTQ_TIE_ABS 1e-14
 #define TTQ_MAXPAIR 288                  // varying pairs of one cube-form fiber, <= (n/2)^2 for n <= 33
 #define TTQ_MAX_INIT 1024                // initial random points scanned (include/ttq.h TTQ_MAX_INIT_SAMPLES)
+#define TTQ_MAXP 4                       // pivots an interface may add per sweep (include/ttq.h TTQ_MAX_PIVOTS)
 
 namespace ttq {
 
@@ -51,6 +52,7 @@ struct IfaceState {
   int fix[TTQ_MAXD];              // node indices the next rook step fixes: modes k.. of gamma
                                   // (column step), modes ..k-1 of rho (row step)
   unsigned epoch;                 // persistent search: stages of this sweep finished so far
+  unsigned acc_arrive;            // several pivots per sweep: searches of the interface that ended (last decisions)
 };
 
 struct State {
@@ -114,8 +116,24 @@ struct Dev {
   double *im[TTQ_MAXD];     // per interface: max score of each row of 32 rook candidates (-1: none eligible)
   double *luh[TTQ_MAXD], *lul[TTQ_MAXD];   // double-double mode: P G_k = L U, column-major (hi, lo parts)
   int *lup[TTQ_MAXD];       // double-double mode: row i of P G_k is row lup[k][i] of G_k
+  // several pivots per interface per sweep: npiv searches per interface; search
+  // j's scratch lies j strides past search 0's (zvec: cap, ptab: pt_st, cs and
+  // ce: cs_st, im: im_st entries) and its state is itx[(j - 1) TTQ_MAXD + k]
+  int npiv, pt_st;
+  size_t cs_st, im_st;
+  IfaceState *itx;
   State *st;
 };
+
+// search j (0 .. npiv-1) of interface k: state and scratch
+__device__ __forceinline__ IfaceState &search_state(const Dev &D, State *st, int k, int j) {
+  return j == 0 ? st->it[k] : D.itx[(j - 1) * TTQ_MAXD + k];
+}
+__device__ __forceinline__ double *zvec_of(const Dev &D, int k, int j) { return D.zvec[k] + (size_t)j * D.cap; }
+__device__ __forceinline__ double *ptab_of(const Dev &D, int k, int j) { return D.ptab[k] + (size_t)j * D.pt_st; }
+__device__ __forceinline__ double *cs_of(const Dev &D, int k, int j) { return D.cs[k] + (size_t)j * D.cs_st; }
+__device__ __forceinline__ double *ce_of(const Dev &D, int k, int j) { return D.ce[k] + (size_t)j * D.cs_st; }
+__device__ __forceinline__ double *im_of(const Dev &D, int k, int j) { return D.im[k] + (size_t)j * D.im_st; }
 
 // ---------------------------------------------------------------------------
 // warp helpers (fixed butterfly order: every lane gets the same, reproducible result)

@@ -814,19 +814,31 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   pdl_release();
   if (stop || !mine) return;
   extern __shared__ double sm[];
-  if (threadIdx.x == 0) {
-    IfaceState &I = st->it[k];
+  if (threadIdx.x < D.npiv) {
+    IfaceState &I = search_state(D, st, k, threadIdx.x);
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
     I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0; I.items_done = 0; I.epoch = 0;
+    I.acc_arrive = 0;
   }
   if (have == r) {
     if (threadIdx.x == 0) st->it[k].prank = -1;
     return;
   }
+  __shared__ double part[4 * TTQ_MAXR];
   if (have >= 1 && have == r - 1 && rowdone == r) {
-    __shared__ double part[4 * TTQ_MAXR];
     qr_border_col(D, k, r, sm, part);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * r * (double)r));
+  } else if (have >= 1 && D.npiv > 1) {
+    // several pivots appended in the last sweep: one bordering update per new
+    // row and column, in append order (the rows' entries over the new columns
+    // come from this sweep's kernel (a), which precedes this kernel)
+    for (int t = have + 1; t <= r; ++t) {
+      qr_border_row(D, k, t, sm);
+      __syncthreads();
+      qr_border_col(D, k, t, sm, part);
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * t * (double)t));
+    }
   } else {
     qr_full(D, k, r, sm);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(8.0 / 3.0 * r * (double)r * r));
@@ -1221,16 +1233,16 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 // (stage 2 marks the qualifying items there, TTQ_MAXR * TTQ_MAX_NODES / 32 bits
 // at most).  vrow (stage 1, may be null): L_k(rho*, :) (r entries) is read into
 // it by the warp that finds rho*, before the block learns the result.
-__device__ int stage_pick(const Dev &D, int k, int stage, double *e_out, unsigned *qbits, double *vrow = nullptr,
-                          int r = 0) {
+__device__ int stage_pick(const Dev &D, int k, int j, int stage, double *e_out, unsigned *qbits,
+                          double *vrow = nullptr, int r = 0) {
   __shared__ int si[TTQ_WARPS];
   __shared__ double se[TTQ_WARPS];
   State *st = D.st;
-  IfaceState &I = st->it[k];
+  IfaceState &I = search_state(D, st, k, j);
   const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), nw = nt >> 5;
-  const long long *csb = reinterpret_cast<const long long *>(D.cs[k]);
-  const double *ce = D.ce[k];
-  const long long *imb = reinterpret_cast<const long long *>(D.im[k]);
+  const long long *csb = reinterpret_cast<const long long *>(cs_of(D, k, j));
+  const double *ce = ce_of(D, k, j);
+  const long long *imb = reinterpret_cast<const long long *>(im_of(D, k, j));
   const long long *src = stage == 0 ? csb : imb;
   const int Nm = stage == 1 ? D.N[k - 1] : D.N[k];           // nodes of the searched mode
   const int lim = stage == 0 ? D.S[k] : D.cap * ((Nm + 31) >> 5);
@@ -1406,7 +1418,7 @@ __device__ __forceinline__ bool uses_ptab(const Dev &D, int rk) {
 // modes k.. of gamma* = (j, beta), a row step (free mode k) the modes ..k-1 of
 // rho* = (alpha, i).  Built by warps 1.. of the CTA while warp 0 runs the
 // substitution; fm: the fixed node indices of those modes (shared memory).
-__device__ __forceinline__ void build_ptab(const Dev &D, int k, bool col, const int *fm, int nfm) {
+__device__ __forceinline__ void build_ptab(const Dev &D, int k, int j, bool col, const int *fm, int nfm) {
   // only warps on the other three schedulers (warp w runs on scheduler w % 4),
   // so the FP64 unit of warp 0's substitution chain is not shared
   const int w = warp_id(), nw = blockDim.x >> 5;
@@ -1414,13 +1426,14 @@ __device__ __forceinline__ void build_ptab(const Dev &D, int k, bool col, const 
   const int slot = (w - 1 - w / 4) * 32 + lane_id();            // 0 .. (3/4 nw - 1) * 32 + 31
   const int nslots = (nw - (nw + 3) / 4) * 32;
   const int Nf = col ? D.N[k - 1] : D.N[k];
+  double *tab = ptab_of(D, k, j);
   for (int i = slot; i < Nf; i += nslots) {
     double p = 1.0;
     for (int q = 0; q < nfm; ++q) {
       const int dm = i - fm[q];
       p *= D.T[dm < 0 ? -dm : dm];
     }
-    D.ptab[k][i] = p;
+    tab[i] = p;
   }
 }
 
@@ -1434,16 +1447,20 @@ __device__ __forceinline__ void build_ptab(const Dev &D, int k, bool col, const 
 //           the previous round's row (the rook test, Eq. 2, then ends the search).
 //   mode 2, after a row step: gamma_new = argmax over E(rho*, :); the rook test
 //           (Eq. 2) or the round limit ends the search, else the next column solve.
-// The solve's result goes to zvec[k]; the row solve also keeps R^-T l in pvec[k]
-// for the QR update of the pivot's row.  Fs: the scaled triangle the solve needs
+// The solve's result goes to the search's zvec; the row solve of search 0 also
+// keeps R^-T l in pvec[k] for the QR update of the pivot's row.  j: the search
+// of interface k (0 .. npiv-1); pick_in >= 0 (mode 0): the sample that starts
+// it, with residual e_in, instead of the stage's argmax.  Fs: the scaled triangle the solve needs
 // (R D^-1 column-major for modes 0 and 2, D^-1 R row-major for mode 1) and Qs
 // (Q row-major / column-major), both compact with leading dimension r, when the
 // caller has them in shared memory; nullptr reads them from global memory.
 // ri: 1/R_jj in shared memory, or nullptr.
-__device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, const double *Qs, const double *ri_s,
-                             SolveSmem &sc, bool staging_in_flight = false) {
+__device__ void stage_finish(const Dev &D, int k, int j, int mode, const double *Fs, const double *Qs,
+                             const double *ri_s, SolveSmem &sc, bool staging_in_flight = false, int pick_in = -1,
+                             double e_in = 0.0) {
   State *st = D.st;
-  IfaceState &I = st->it[k];
+  IfaceState &I = search_state(D, st, k, j);
+  double *zv = zvec_of(D, k, j);
   const int r = st->r[k], ld = D.cap, tid = threadIdx.x, nt = blockDim.x;
   double *v = sc.v, *t = sc.t;
   const double *ri = ri_s;
@@ -1457,7 +1474,9 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   double e;
   int col = -1, row = -1, spick = -1;
   if (mode == 0) {
-    const int pick = stage_pick(D, k, 0, &e, qb);
+    int pick = pick_in;
+    if (pick_in >= 0) e = e_in;
+    else pick = stage_pick(D, k, j, 0, &e, qb);
     spick = pick;
     if (pick >= 0) {
       const int Nk = D.N[k - 1], Nk1 = D.N[k], rn = st->r[k + 1];
@@ -1467,7 +1486,7 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
       if (tid == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
     }
   } else if (mode == 1) {
-    const int pick = stage_pick(D, k, 1, &e, qb, v, r);   // L_k(rho*, :) lands in v
+    const int pick = stage_pick(D, k, j, 1, &e, qb, v, r);   // L_k(rho*, :) lands in v
     const int prev = __ldcg(&I.row), done_rounds = __ldcg(&I.rounds);
     __syncthreads();                             // every thread has read the previous row
     // Eq. 2 already holds when the column search returns the row searched in the
@@ -1481,7 +1500,7 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
     }
     row = rook ? -1 : pick;
   } else {
-    const int pick = stage_pick(D, k, 2, &e, qb);
+    const int pick = stage_pick(D, k, j, 2, &e, qb);
     if (pick < 0) {
       if (tid == 0) I.active = 0;
     } else {
@@ -1518,27 +1537,30 @@ __device__ void stage_finish(const Dev &D, int k, int mode, const double *Fs, co
   if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
   if (colsolve && mode == 0) {
-    for (int b = tid; b < r; b += nt) D.zvec[k][b] = __ldcg(D.zs[k] + (size_t)spick * D.cap + b);
-    if (tab) build_ptab(D, k, true, fm, nfm);
+    for (int b = tid; b < r; b += nt) zv[b] = __ldcg(D.zs[k] + (size_t)spick * D.cap + b);
+    if (tab) build_ptab(D, k, j, true, fm, nfm);
   } else if (colsolve) {
     // t = Q^T y (Q row-major: Q[b][i] at Q[b ld + i]), then R z = t
     if (Qs) cta_gemv(Qs, 1, r, v, r, sc.part, t);
     else cta_gemv(D.Qr[k], 1, ld, v, r, sc.part, t);
     if (warp_id() == 0) warp_back_subst(F, t, v, r, fld);
-    else if (tab) build_ptab(D, k, true, fm, nfm);
+    else if (tab) build_ptab(D, k, j, true, fm, nfm);
     __syncthreads();
-    for (int b = tid; b < r; b += nt) D.zvec[k][b] = v[b] * ri[b];
+    for (int b = tid; b < r; b += nt) zv[b] = v[b] * ri[b];
   } else if (rowsolve) {
     // R^T t = l, then b = Q t (Q column-major: Q[i][c] at Q[i + c ld])
     if (warp_id() == 0) warp_fwd_subst(F, v, t, r, fld);
-    else if (tab) build_ptab(D, k, false, fm, nfm);
+    else if (tab) build_ptab(D, k, j, false, fm, nfm);
     __syncthreads();
     for (int b = tid; b < r; b += nt) t[b] *= ri[b];
     __syncthreads();
     if (Qs) cta_gemv(Qs, 1, r, t, r, sc.part, v);
     else cta_gemv(D.Qc[k], 1, ld, t, r, sc.part, v);
-    for (int b = tid; b < r; b += nt) { D.zvec[k][b] = v[b]; D.pvec[k][b] = t[b]; }
-    if (tid == 0) { I.prow = row; I.prank = r; }
+    for (int b = tid; b < r; b += nt) {
+      zv[b] = v[b];
+      if (j == 0) D.pvec[k][b] = t[b];
+    }
+    if (tid == 0 && j == 0) { I.prow = row; I.prank = r; }
   }
   if (((colsolve && mode != 0) || rowsolve) && tid == 0)
     atomicAdd(&st->flops[9], (unsigned long long)(3 * r * r) +
@@ -1597,11 +1619,23 @@ __device__ void sweep_finalize(const Dev &D, State *st, bool append, cudaGraphCo
   if (append) {
     // a thread per interface: its rank, the sweep's evaluations, the accepted count
     for (int q = tid + 1; q <= d - 1; q += blockDim.x) {
-      const IfaceState &I = st->it[q];
-      atomicAdd(&ev_s, I.evals);
-      if (I.active && I.accepted) {
-        st->r[q] += 1;
-        atomicAdd(&nacc_s, 1);
+      IfaceState &I = st->it[q];
+      if (D.npiv > 1) {
+        // several pivots per sweep: the count multi_accept kept, every search's evaluations
+        unsigned long long ev = 0;
+        for (int j = 0; j < D.npiv; ++j) ev += __ldcg(&search_state(D, st, q, j).evals);
+        atomicAdd(&ev_s, ev);
+        const int na = __ldcg(&I.accepted);
+        if (na > 0) {
+          st->r[q] += na;
+          atomicAdd(&nacc_s, 1);
+        }
+      } else {
+        atomicAdd(&ev_s, I.evals);
+        if (I.active && I.accepted) {
+          st->r[q] += 1;
+          atomicAdd(&nacc_s, 1);
+        }
       }
     }
     __syncthreads();
@@ -1630,6 +1664,151 @@ __device__ void sweep_finalize(const Dev &D, State *st, bool append, cudaGraphCo
   }
 }
 
+// Several pivots per interface per sweep (a rank-adaptive variant; Alg. 6
+// adds one): interface k's pivots from the rook searches of its npiv starts,
+// by the last CTA of its searches in the sweep's last decisions kernel (whole
+// CTA).  On the residual E of the sweep's old cross:
+//   1. searches that found a pivot, in start order; one whose row or column
+//      equals that of an earlier kept search is dropped;
+//   2. M(a, c) = E(x_a, y_c) over the kept rows x_a and columns y_c: M(a, a)
+//      is search a's residual, the others A(x_a, y_c) - L_k(x_a, :) z_c, z_c =
+//      G_k^-1 R_{k+1}(:, y_c) (a warp each: Q^T y, back substitution) and A
+//      evaluated at the points (groups of 8 lanes);
+//   3. greedy complete pivoting: the largest |M| over the rows and columns
+//      left (tie window, first in row-major order) while it exceeds
+//      pivot_tol * scale and the rank stays below the cap; its row and column
+//      are appended (nested by construction, as sweep_append) and M becomes
+//      its Schur complement M_be - M_bc M_ae / M_ac.
+// The count kept goes to it[k].accepted.
+__device__ void multi_accept(const Dev &D, State *st, int k, bool append) {
+  __shared__ int kr[TTQ_MAXP], kc[TTQ_MAXP], km_s, acc_a[TTQ_MAXP], acc_c[TTQ_MAXP], nacc_s;
+  __shared__ double ke[TTQ_MAXP], Mx[TTQ_MAXP][TTQ_MAXP], Av[TTQ_MAXP][TTQ_MAXP];
+  __shared__ double zc[TTQ_MAXP][TTQ_MAXR], tv[TTQ_MAXP][TTQ_MAXR], yv[TTQ_MAXP][TTQ_MAXR];
+  __shared__ int mxp[TTQ_MAXD][TTQ_MAXP * TTQ_MAXP];   // node indices of point q = a m + c in column q
+  const int tid = threadIdx.x, lane = lane_id(), warp = warp_id(), nw = blockDim.x >> 5, d = D.d;
+  IfaceState &I0 = st->it[k];
+  if (!append) {
+    if (tid == 0) I0.accepted = 0;
+    return;
+  }
+  const int r = st->r[k], ld = D.cap, Nk = D.N[k - 1], rn = st->r[k + 1];
+  const double scale = __longlong_as_double((long long)__ldcg(&st->scale_bits));
+  if (tid == 0) {
+    int m = 0;
+    for (int j = 0; j < D.npiv; ++j) {
+      IfaceState &I = search_state(D, st, k, j);
+      if (!__ldcg(&I.active)) continue;
+      const int rw = __ldcg(&I.row), cl = __ldcg(&I.col);
+      bool dup = false;
+      for (int q = 0; q < m; ++q) dup |= (kr[q] == rw) || (kc[q] == cl);
+      if (dup) continue;
+      kr[m] = rw;
+      kc[m] = cl;
+      ke[m] = __ldcg(&I.err);
+      ++m;
+    }
+    km_s = m;
+  }
+  __syncthreads();
+  const int m = km_s;
+  if (m >= 2) {
+    // z_c = G^-1 R_{k+1}(:, y_c): t = Q^T y (Q row-major), R D^-1 back substitution, D^-1
+    if (warp < m) {
+      const int jc = kc[warp] / rn, bc = kc[warp] % rn;
+      for (int b = lane; b < r; b += 32) yv[warp][b] = D.Y[k + 1][core_at(D, k + 1, b, jc, bc)];
+      __syncwarp();
+      for (int i = lane; i < r; i += 32) {
+        double acc = 0.0;
+        for (int b = 0; b < r; ++b) acc = fma(D.Qr[k][(size_t)b * ld + i], yv[warp][b], acc);
+        tv[warp][i] = acc;
+      }
+      __syncwarp();
+      warp_back_subst(D.Cc[k], tv[warp], zc[warp], r, ld);
+      __syncwarp();
+      for (int b = lane; b < r; b += 32) zc[warp][b] *= D.rinv[k][b];
+    }
+    // the points (x_a, y_c): modes ..k-2 from I<=k-1, i_a, j_c, modes k+1.. from I>k+1
+    const int mm = m * m;
+    for (int e = tid; e < d * mm; e += blockDim.x) {
+      const int v = e / mm, q = e % mm, a = q / m, c = q % m;
+      const int alpha = kr[a] / Nk, i = kr[a] % Nk, jj = kc[c] / rn, beta = kc[c] % rn;
+      int mv;
+      if (v < k - 1) mv = D.lidx[k - 1][alpha * d + v];
+      else if (v == k - 1) mv = i;
+      else if (v == k) mv = jj;
+      else mv = D.ridx[k + 1][beta * d + v];
+      mxp[v][q] = mv;
+    }
+    __syncthreads();
+    if (warp < (mm + 3) / 4) {                   // four points per warp, a group of 8 lanes each
+      const int g = lane >> 3, gl = lane & 7, q = warp * 4 + g;
+      const double A = group_point_value<8>(D, &mxp[0][q < mm ? q : 0], TTQ_MAXP * TTQ_MAXP, gl);
+      if (gl == 0 && q < mm) Av[q / m][q % m] = A;
+    }
+    __syncthreads();
+    for (int q = warp; q < mm; q += nw) {
+      const int a = q / m, c = q % m;
+      if (a == c) continue;
+      const int alpha = kr[a] / Nk, i = kr[a] % Nk;
+      double acc = 0.0;
+      for (int b = lane; b < r; b += 32) acc = fma(D.Y[k][core_at(D, k, alpha, i, b)], zc[c][b], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) Mx[a][c] = Av[a][c] - acc;
+    }
+  }
+  if (tid < m) Mx[tid][tid] = ke[tid];
+  __syncthreads();
+  if (tid == 0) {
+    unsigned rows_left = (1u << m) - 1u, cols_left = (1u << m) - 1u;
+    int n = 0;
+    while (rows_left && n < D.cap - r) {
+      double smax = -1.0;
+      for (int a = 0; a < m; ++a)
+        for (int c = 0; c < m; ++c)
+          if (((rows_left >> a) & 1u) && ((cols_left >> c) & 1u) && isfinite(Mx[a][c])) smax = fmax(smax, fabs(Mx[a][c]));
+      if (smax < 0.0) break;
+      const double thr = __dadd_rn(smax, -__dadd_rn(__dmul_rn(TTQ_TIE_REL, smax), __dmul_rn(TTQ_TIE_ABS, scale)));
+      int fa = -1, fc = -1;
+      for (int a = 0; a < m && fa < 0; ++a)
+        for (int c = 0; c < m; ++c)
+          if (((rows_left >> a) & 1u) && ((cols_left >> c) & 1u) && isfinite(Mx[a][c]) && fabs(Mx[a][c]) >= thr) {
+            fa = a;
+            fc = c;
+            break;
+          }
+      const double piv = Mx[fa][fc];
+      if (!(fabs(piv) > D.pivot_tol * scale)) break;
+      acc_a[n] = fa;
+      acc_c[n] = fc;
+      ++n;
+      rows_left &= ~(1u << fa);
+      cols_left &= ~(1u << fc);
+      for (int b = 0; b < m; ++b)
+        for (int e = 0; e < m; ++e)
+          if (((rows_left >> b) & 1u) && ((cols_left >> e) & 1u))
+            Mx[b][e] = __dsub_rn(Mx[b][e], __ddiv_rn(__dmul_rn(Mx[b][fc], Mx[fa][e]), piv));
+    }
+    nacc_s = n;
+    I0.accepted = n;
+    if (m > 1) atomicAdd(&I0.evals, (unsigned long long)(m * (m - 1)));
+  }
+  __syncthreads();
+  const int n = nacc_s;
+  if (warp == 0)
+    for (int t = 0; t < n; ++t) {
+      const int prow = kr[acc_a[t]], pcol = kc[acc_c[t]], pos = r + t;
+      const int alpha = prow / Nk, i = prow % Nk, jj = pcol / rn, beta = pcol % rn;
+      if (lane < d) {
+        D.lidx[k][(size_t)pos * d + lane] = (lane < k - 1) ? D.lidx[k - 1][alpha * d + lane] : (lane == k - 1 ? i : -1);
+        D.ridx[k][(size_t)pos * d + lane] = (lane == k) ? jj : (lane > k ? D.ridx[k + 1][beta * d + lane] : -1);
+      }
+      if (lane == 0) {
+        D.lpar[k][pos] = alpha; D.lnode[k][pos] = i;
+        D.rpar[k][pos] = beta; D.rnode[k][pos] = jj;
+      }
+    }
+}
+
 // End of the sweep (Alg. 6) in the last decisions kernel of the staged search:
 // every CTA appends its interface's accepted pivot, then the last CTA of the
 // instance to arrive finalizes the sweep.
@@ -1637,10 +1816,25 @@ __device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHa
   State *st = D.st;
   __shared__ int last_s;
   const bool append = !st->stop && !st->stop_pending && st->search && !st->search_abort;
-  if (append && mine) sweep_append(D, st, k);
+  if (D.npiv > 1) {
+    // one CTA per search of the interface (grid y): the last of them to
+    // arrive takes the interface's pivots from all of its searches
+    if (mine) {
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) last_s = (atomicAdd(&st->it[k].acc_arrive, 1u) == gridDim.y - 1) ? 1 : 0;
+      __syncthreads();
+      if (last_s) {
+        __threadfence();
+        multi_accept(D, st, k, append);
+      }
+    }
+  } else if (append && mine) {
+    sweep_append(D, st, k);
+  }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last_s = (atomicAdd(&st->end_arrive, 1u) == gridDim.x - 1) ? 1 : 0;
+  if (threadIdx.x == 0) last_s = (atomicAdd(&st->end_arrive, 1u) == gridDim.x * gridDim.y - 1) ? 1 : 0;
   __syncthreads();
   if (!last_s) return;
   __threadfence();
@@ -1658,27 +1852,31 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fi
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
   State *st = D.st;
-  const int k = blockIdx.x + 1;
+  const int k = blockIdx.x + 1, j = blockIdx.y;  // interface, search (grid y: the searches per interface)
   const bool mine = k <= D.d - 1;
   extern __shared__ double sm[];
   __shared__ SolveSmem sc;
   const int r = mine ? st->r[k] : 0, ld = D.cap;
   double *Fs = sm;
   double *Qs = D.q_in_smem ? sm + (size_t)r * r : nullptr;   // Q staged too when it fits
-  if (r > 0) {
+  // the run flags and the search's state were last written two or more
+  // launches back (the previous decisions kernel, the samples' finisher, the
+  // end of the previous sweep), which had completed before the preceding rook
+  // step passed its own wait: they are read before this kernel's wait
+  bool work = false;
+  if (mine) {
+    const IfaceState &I = search_state(D, st, k, j);
+    work = !st->stop && st->search && I.active && !I.rook_done;
+  }
+  if (r > 0 && (j == 0 || work)) {
     if (mode == 1) stage_compact_async(Fs, D.Sr[k], Qs, D.Qc[k], r, ld);   // D^-1 R row-major, Q col-major
     else stage_compact_async(Fs, D.Cc[k], Qs, D.Qr[k], r, ld);             // R D^-1 col-major, Q row-major
     for (int b = threadIdx.x; b < r; b += blockDim.x) cp_async8(sc.ri + b, D.rinv[k] + b);
   }
-  // the run flags and the interface's search state were last written two or
-  // more launches back (the previous decisions kernel, the samples' finisher,
-  // the end of the previous sweep), which had completed before the preceding
-  // rook step passed its own wait: they are read before this kernel's wait
-  const bool work = mine && !st->stop && st->search && st->it[k].active && !st->it[k].rook_done;
   pdl_wait();
   pdl_release();
   if (work)
-    stage_finish(D, k, mode, Fs, Qs, sc.ri, sc, true);
+    stage_finish(D, k, j, mode, Fs, Qs, sc.ri, sc, true);
   else
     cp_async_wait_all();                         // no copy outlives the CTA
   if (fin) sweep_end(D, k, mine, h, use_cond);
@@ -1895,6 +2093,88 @@ __device__ __forceinline__ void sample_task(const Dev &D, const SampleCtx &c, in
   __syncwarp();
 }
 
+// Several pivots per sweep: the starts of interface k's searches, up to npiv
+// samples taken one at a time as the tie-window argmax of the sample scores
+// among the samples whose row and column differ from those of the starts
+// already taken (the first is the sample stage_pick takes).  Whole CTA; clears
+// the stage reduction; returns the count, with each start's residual.
+__device__ int sample_starts(const Dev &D, int k, int *pick, double *perr) {
+  __shared__ long long red[TTQ_WARPS];
+  __shared__ int redi[TTQ_WARPS];
+  __shared__ double rede[TTQ_WARPS];
+  __shared__ int srow[TTQ_MAXP], scol[TTQ_MAXP], n_s;
+  State *st = D.st;
+  IfaceState &I = st->it[k];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = lane_id(), warp = warp_id(), nw = nt >> 5;
+  const int S = D.S[k];
+  const unsigned long long M = (unsigned long long)st->r[k - 1] * D.N[k - 1];
+  const unsigned long long Ncol = (unsigned long long)D.N[k] * st->r[k + 1];
+  const unsigned long long sid = stream_id(st->sweep, k, 1);
+  const double scale = __longlong_as_double((long long)__ldcg(&st->scale_bits));
+  const long long *csb = reinterpret_cast<const long long *>(D.cs[k]);
+  const double *ce = D.ce[k];
+  __syncthreads();
+  if (tid == 0) { I.smax_bits = 0ULL; I.stage_count = 0; n_s = 0; }
+  __syncthreads();
+  for (int n = 0; n < D.npiv; ++n) {
+    // pass 1: the largest eligible score; pass 2: the first eligible sample in the window
+    long long best = -1;
+    for (int t = tid; t < S; t += nt) {
+      const long long v = __ldcg(csb + t);
+      if (v < 0) continue;
+      const int rw = (int)draw_index(D.seed, sid, 2ULL * t, M), cl = (int)draw_index(D.seed, sid, 2ULL * t + 1, Ncol);
+      bool ex = false;
+      for (int q = 0; q < n; ++q) ex |= (srow[q] == rw) || (scol[q] == cl);
+      if (!ex && v > best) best = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ob > best ? ob : best;
+    }
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    best = red[0];
+    for (int w = 1; w < nw; ++w) best = red[w] > best ? red[w] : best;
+    __syncthreads();
+    if (best < 0) break;                         // uniform: every thread saw the same maximum
+    const double smax = __longlong_as_double(best);
+    const double thr = __dadd_rn(smax, -__dadd_rn(__dmul_rn(TTQ_TIE_REL, smax), __dmul_rn(TTQ_TIE_ABS, scale)));
+    const long long thrb = thr > 0.0 ? __double_as_longlong(thr) : 0LL;
+    int first = 0x7fffffff;
+    double ef = 0.0;
+    for (int t = tid; t < S; t += nt) {
+      const long long v = __ldcg(csb + t);
+      if (v < thrb || t >= first) continue;
+      const int rw = (int)draw_index(D.seed, sid, 2ULL * t, M), cl = (int)draw_index(D.seed, sid, 2ULL * t + 1, Ncol);
+      bool ex = false;
+      for (int q = 0; q < n; ++q) ex |= (srow[q] == rw) || (scol[q] == cl);
+      if (!ex) { first = t; ef = __ldcg(ce + t); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int of = __shfl_xor_sync(0xffffffffu, first, o);
+      const double oe = __shfl_xor_sync(0xffffffffu, ef, o);
+      if (of < first) { first = of; ef = oe; }
+    }
+    if (lane == 0) { redi[warp] = first; rede[warp] = ef; }
+    __syncthreads();
+    if (tid == 0) {
+      int f = redi[0];
+      double e = rede[0];
+      for (int w = 1; w < nw; ++w)
+        if (redi[w] < f) { f = redi[w]; e = rede[w]; }
+      pick[n] = f;
+      perr[n] = e;
+      srow[n] = (int)draw_index(D.seed, sid, 2ULL * f, M);
+      scol[n] = (int)draw_index(D.seed, sid, 2ULL * f + 1, Ncol);
+      n_s = n + 1;
+    }
+    __syncthreads();
+  }
+  return n_s;
+}
+
 __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) {
   // descriptor read in place: its shared-memory copy would cost the kernel its
   // second resident CTA per SM (R, Q and the group vectors fill the rest)
@@ -1960,7 +2240,14 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, 2) k_samples(Dev *const *Dps) 
   __syncthreads();
   if (!sc.is_last) return;
   __threadfence();
-  stage_finish(D, k, 0, Rs, Qs, ri, sc);
+  if (D.npiv == 1) {
+    stage_finish(D, k, 0, 0, Rs, Qs, ri, sc);
+  } else {
+    __shared__ int picks[TTQ_MAXP];
+    __shared__ double perrs[TTQ_MAXP];
+    const int n = sample_starts(D, k, picks, perrs);
+    for (int j = 0; j < n; ++j) stage_finish(D, k, j, 0, Rs, Qs, ri, sc, false, picks[j], perrs[j]);
+  }
 }
 
 // Work list of a rook step over every interface of the instance: lane k-1
@@ -2001,10 +2288,11 @@ __device__ __forceinline__ bool score_bits(double E, unsigned long long &bits) {
 // One work item of the column step: rows rho = (alpha, i), i in [i0, i1) with
 // NQ rows of 32 nodes per lane.  E = A(rho, gamma*) - L_k(rho, :) z.
 template <int NQ>
-__device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0, int i1, int rk, const int *ms,
+__device__ __forceinline__ void col_item(const Dev &D, int k, int j, int alpha, int i0, int i1, int rk, const int *ms,
                                          const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
                                          unsigned long long (&bq)[NQ], unsigned &nel, unsigned &nev) {
-  const double *tab = uses_ptab(D, rk) ? D.ptab[k] : nullptr;
+  const double *tab = uses_ptab(D, rk) ? ptab_of(D, k, j) : nullptr;
+  double *csj = cs_of(D, k, j), *cej = ce_of(D, k, j);
   const int lane = lane_id(), Nk = D.N[k - 1];
   int iq[NQ];
   bool ok[NQ];
@@ -2038,12 +2326,12 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
     bq[q] = 0ULL;                                  // score bits + 1 of the row's eligible candidate, 0: none
     if (iq[q] >= i1) continue;
     const int rho = alpha * Nk + iq[q];
-    if (!ok[q]) { D.cs[k][rho] = -1.0; D.ce[k][rho] = 0.0; continue; }
+    if (!ok[q]) { csj[rho] = -1.0; cej[rho] = 0.0; continue; }
     const double E = A[q] - acc[q];
     unsigned long long sb;
     const bool fin = score_bits(E, sb);
-    D.cs[k][rho] = fin ? __longlong_as_double((long long)sb) : -1.0;
-    D.ce[k][rho] = E;
+    csj[rho] = fin ? __longlong_as_double((long long)sb) : -1.0;
+    cej[rho] = E;
     ++nev;
     if (fin) { bq[q] = sb + 1ULL; ++nel; }
   }
@@ -2052,10 +2340,11 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int alpha, int i0,
 // One work item of the row step: columns gamma = (j, beta), j in [j0, j1).
 // E = A(rho*, gamma) - l^T R_{k+1}(:, gamma) with z = G^-T l.
 template <int NQ>
-__device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, int j1, int rk, int rn, const int *ms,
-                                         const FiberU &u, const double *pl, const int *exc, int nex, const double *z,
-                                         unsigned long long (&bq)[NQ], unsigned &nel, unsigned &nev) {
-  const double *tab = uses_ptab(D, rk) ? D.ptab[k] : nullptr;
+__device__ __forceinline__ void row_item(const Dev &D, int k, int j, int beta, int j0, int j1, int rk, int rn,
+                                         const int *ms, const FiberU &u, const double *pl, const int *exc, int nex,
+                                         const double *z, unsigned long long (&bq)[NQ], unsigned &nel, unsigned &nev) {
+  const double *tab = uses_ptab(D, rk) ? ptab_of(D, k, j) : nullptr;
+  double *csj = cs_of(D, k, j), *cej = ce_of(D, k, j);
   const int lane = lane_id(), Nk1 = D.N[k];
   int jq[NQ];
   bool ok[NQ];
@@ -2087,12 +2376,12 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, 
     bq[q] = 0ULL;
     if (jq[q] >= j1) continue;
     const int g = jq[q] * rn + beta;
-    if (!ok[q]) { D.cs[k][g] = -1.0; D.ce[k][g] = 0.0; continue; }
+    if (!ok[q]) { csj[g] = -1.0; cej[g] = 0.0; continue; }
     const double E = A[q] - acc[q];
     unsigned long long sb;
     const bool fin = score_bits(E, sb);
-    D.cs[k][g] = fin ? __longlong_as_double((long long)sb) : -1.0;
-    D.ce[k][g] = E;
+    csj[g] = fin ? __longlong_as_double((long long)sb) : -1.0;
+    cej[g] = E;
     ++nev;
     if (fin) { bq[q] = sb + 1ULL; ++nel; }
   }
@@ -2102,7 +2391,7 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int beta, int j0, 
 // at its slot outer * rows + row, the order of the candidate indices, -1 when
 // the row has no eligible candidate) and the stage reduction (pass 1 of the argmax)
 template <int NQ>
-__device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k, int slot0,
+__device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k, int j, int slot0,
                                              unsigned long long (&bq)[NQ], unsigned nel, unsigned nev) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -2118,7 +2407,7 @@ __device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k,
     unsigned long long best = 0ULL;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      D.im[k][slot0 + q] = bq[q] ? __longlong_as_double((long long)(bq[q] - 1ULL)) : -1.0;
+      im_of(D, k, j)[slot0 + q] = bq[q] ? __longlong_as_double((long long)(bq[q] - 1ULL)) : -1.0;
       best = bq[q] > best ? bq[q] : best;
     }
     if (nev) atomicAdd(&I.evals, (unsigned long long)nev);
@@ -2143,6 +2432,25 @@ __device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k,
 //    no sparse second wave of items trails the first.
 // Lane k-1 of the warp holds interface k's outer rank and nodes; pieces come
 // out as (interface, outer index, first row, rows).
+// the searches of interface k that still run a rook step (bit j: search j)
+__device__ __forceinline__ unsigned running_searches(const Dev &D, State *st, int k) {
+  unsigned m = 0;
+  for (int j = 0; j < D.npiv; ++j) {
+    const IfaceState &I = search_state(D, st, k, j);
+    if (I.active && !I.rook_done) m |= 1u << j;
+  }
+  return m;
+}
+// the n-th (from 0) set bit of m
+__device__ __forceinline__ int nth_search(unsigned m, int n) {
+  for (int j = 0; j < TTQ_MAXP; ++j)
+    if ((m >> j) & 1u) {
+      if (n == 0) return j;
+      --n;
+    }
+  return 0;
+}
+
 struct RookDeal {
   ItemMap im;
   int R, pos, end;
@@ -2190,19 +2498,21 @@ __device__ __forceinline__ void rook_piece(RookDeal &q, int k, int ok, int N, in
 // shared vector when zk != k), candidates and per-row maxima stored, pass 1 of
 // the argmax.  The piece's loads form one round: z, the fiber's left indices,
 // the fixed right indices (I.fix), the cross's parent pointers.
-__device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh, int k, int alpha, int q0, int nq,
-                                          int rk, int &zk, unsigned long long &fl) {
+__device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh, int k, int j, int alpha, int q0,
+                                          int nq, int rk, int &zk, unsigned long long &fl) {
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  IfaceState &I = st->it[k];
+  IfaceState &I = search_state(D, st, k, j);
+  const int zkey = k + 64 * j;
   const int Nk = D.N[k - 1], rows = (Nk + 31) >> 5;
   const int i0 = 32 * q0, i1 = min(Nk, 32 * (q0 + nq)), slot0 = alpha * rows + q0;
   double zr[TTQ_MAXR / 32];
   int lp[TTQ_MAXR / 32], ln[TTQ_MAXR / 32];
-  const bool newz = k != zk;
+  const bool newz = zkey != zk;
+  const double *zsrc = zvec_of(D, k, j);
 #pragma unroll
   for (int q = 0; q < TTQ_MAXR / 32; ++q) {
     const int a = lane + 32 * q;
-    zr[q] = (newz && a < rk) ? __ldcg(D.zvec[k] + a) : 0.0;
+    zr[q] = (newz && a < rk) ? __ldcg(zsrc + a) : 0.0;
     lp[q] = a < rk ? D.lpar[k][a] : -1;
     ln[q] = a < rk ? D.lnode[k][a] : 0;
   }
@@ -2212,7 +2522,7 @@ __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh,
 #pragma unroll
     for (int q = 0; q < TTQ_MAXR / 32; ++q)
       if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
-    zk = k;
+    zk = zkey;
   }
   if (lane < d) sh.ms[warp][lane] = (lane < k - 1) ? vl : vr;
   // rows of the cross with this parent alpha: excluded nodes i
@@ -2233,9 +2543,9 @@ __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh,
 #define TTQ_COL_PIECE(Q)                                                                                      \
   {                                                                                                           \
     unsigned long long bq[Q];                                                                                 \
-    col_item<Q>(D, k, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
-                nev);                                                                                         \
-    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                            \
+    col_item<Q>(D, k, j, alpha, i0, i1, rk, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq,   \
+                nel, nev);                                                                                    \
+    rows_publish<Q>(D, I, k, j, slot0, bq, nel, nev);                                                         \
   }
   switch (nq) {
     case 4: TTQ_COL_PIECE(4) break;
@@ -2260,26 +2570,28 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   // one round of loads: the run's flags and, lane k-1, interface k's search
   // state and the ranks around it
   const int stop = st->stop, search = st->search;
-  int act = 0, r0 = 0, r1 = 0, Nl = 1;
+  unsigned act = 0;
+  int r0 = 0, r1 = 0, Nl = 1;
   if (lane < d - 1) {
-    const IfaceState &I = st->it[lane + 1];
-    act = I.active && !I.rook_done;
+    act = running_searches(D, st, lane + 1);
     r0 = st->r[lane];
     r1 = st->r[lane + 1];
     Nl = D.N[lane];
   }
   if (stop || !search) return;
-  const int outer = act ? r0 : 0;
+  // an interface's running searches take consecutive blocks of its outer indices
+  const int outer = __popc(act) * r0;
   RookDeal dl = rook_deal(D, outer, Nl);
   unsigned long long fl = 0;
-  int zk = 0;                                   // interface whose z sits in sh.z[warp]
+  int zk = 0;                                   // interface and search whose z sits in sh.z[warp]
   while (dl.pos < dl.end) {
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);                  // interface (1-based)
     const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rl = __shfl_sync(0xffffffffu, r0, k - 1);
-    int alpha, q0, nq;
-    rook_piece(dl, k, rl, D.N[k - 1], alpha, q0, nq);
-    col_piece(D, st, sh, k, alpha, q0, nq, rk, zk, fl);
+    const unsigned am = __shfl_sync(0xffffffffu, act, k - 1);
+    int o, q0, nq;
+    rook_piece(dl, k, __popc(am) * rl, D.N[k - 1], o, q0, nq);
+    col_piece(D, st, sh, k, nth_search(am, o / rl), o % rl, q0, nq, rk, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
 }
@@ -2287,19 +2599,21 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
 // One piece of the row step of interface k (one warp): columns gamma = (j,
 // beta) for the nq rows of 32 nodes j from q0 of fiber beta, E = A(rho*, gamma)
 // - l^T R_{k+1}(:, gamma) with z = G_k^-T l; as col_piece.
-__device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh, int k, int beta, int q0, int nq,
-                                          int rk, int rn, int &zk, unsigned long long &fl) {
+__device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh, int k, int j, int beta, int q0,
+                                          int nq, int rk, int rn, int &zk, unsigned long long &fl) {
   const int lane = lane_id(), warp = warp_id(), d = D.d;
-  IfaceState &I = st->it[k];
+  IfaceState &I = search_state(D, st, k, j);
+  const int zkey = k + 64 * j;
   const int Nk1 = D.N[k], rows = (Nk1 + 31) >> 5;
   const int j0 = 32 * q0, j1 = min(Nk1, 32 * (q0 + nq)), slot0 = beta * rows + q0;
   double zr[TTQ_MAXR / 32];
   int rp[TTQ_MAXR / 32], rnd[TTQ_MAXR / 32];
-  const bool newz = k != zk;
+  const bool newz = zkey != zk;
+  const double *zsrc = zvec_of(D, k, j);
 #pragma unroll
   for (int q = 0; q < TTQ_MAXR / 32; ++q) {
     const int b = lane + 32 * q;
-    zr[q] = (newz && b < rk) ? __ldcg(D.zvec[k] + b) : 0.0;
+    zr[q] = (newz && b < rk) ? __ldcg(zsrc + b) : 0.0;
     rp[q] = b < rk ? D.rpar[k][b] : -1;
     rnd[q] = b < rk ? D.rnode[k][b] : 0;
   }
@@ -2309,7 +2623,7 @@ __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh,
 #pragma unroll
     for (int q = 0; q < TTQ_MAXR / 32; ++q)
       if (lane + 32 * q < rk) sh.z[warp][lane + 32 * q] = zr[q];
-    zk = k;
+    zk = zkey;
   }
   if (lane < d) sh.ms[warp][lane] = (lane < k) ? vl : vr;
   int nex = 0;
@@ -2328,9 +2642,9 @@ __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh,
 #define TTQ_ROW_PIECE(Q)                                                                                           \
   {                                                                                                                \
     unsigned long long bq[Q];                                                                                      \
-    row_item<Q>(D, k, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq, nel, \
-                nev);                                                                                              \
-    rows_publish<Q>(D, I, k, slot0, bq, nel, nev);                                                                 \
+    row_item<Q>(D, k, j, beta, j0, j1, rk, rn, sh.ms[warp], u, sh.pl[warp], sh.exc[warp], nex, sh.z[warp], bq,     \
+                nel, nev);                                                                                         \
+    rows_publish<Q>(D, I, k, j, slot0, bq, nel, nev);                                                              \
   }
   switch (nq) {
     case 4: TTQ_ROW_PIECE(4) break;
@@ -2354,16 +2668,16 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   __shared__ RookSmem sh;
   const int lane = lane_id(), d = D.d;
   const int stop = st->stop, search = st->search;
-  int act = 0, r1 = 0, r2 = 0, Nl = 1;
+  unsigned act = 0;
+  int r1 = 0, r2 = 0, Nl = 1;
   if (lane < d - 1) {
-    const IfaceState &I = st->it[lane + 1];
-    act = I.active && !I.rook_done;
+    act = running_searches(D, st, lane + 1);
     r1 = st->r[lane + 1];
     r2 = st->r[lane + 2];
     Nl = D.N[lane + 1];
   }
   if (stop || !search) return;
-  const int outer = act ? r2 : 0;
+  const int outer = __popc(act) * r2;
   RookDeal dl = rook_deal(D, outer, Nl);
   unsigned long long fl = 0;
   int zk = 0;
@@ -2371,9 +2685,10 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     const unsigned ball = __ballot_sync(0xffffffffu, lane < d - 1 && dl.im.pre > dl.pos);
     const int k = __ffs(ball);
     const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rn = __shfl_sync(0xffffffffu, r2, k - 1);
-    int beta, q0, nq;
-    rook_piece(dl, k, rn, D.N[k], beta, q0, nq);
-    row_piece(D, st, sh, k, beta, q0, nq, rk, rn, zk, fl);
+    const unsigned am = __shfl_sync(0xffffffffu, act, k - 1);
+    int o, q0, nq;
+    rook_piece(dl, k, __popc(am) * rn, D.N[k], o, q0, nq);
+    row_piece(D, st, sh, k, nth_search(am, o / rn), o % rn, q0, nq, rk, rn, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
 }
@@ -2612,7 +2927,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_search(Dev *c
     }
   }
   if (group_arrive(st, k, g)) {
-    stage_finish(D, k, 0, Rs, Qs, ri, sc);
+    stage_finish(D, k, 0, 0, Rs, Qs, ri, sc);
     if (!iface_running(I)) sweep_append(D, st, k);
     group_publish(st, k, 1u);
   }
@@ -2628,12 +2943,12 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_search(Dev *c
       while (q.pos < q.end) {
         int alpha, q0, nq;
         group_piece(q, rl, Nk, alpha, q0, nq);
-        col_piece(D, st, sh, k, alpha, q0, nq, rk, zk, fl_col);
+        col_piece(D, st, sh, k, 0, alpha, q0, nq, rk, zk, fl_col);
       }
     }
     ++e;
     if (group_arrive(st, k, g)) {
-      stage_finish(D, k, 1, nullptr, nullptr, ri, sc);
+      stage_finish(D, k, 0, 1, nullptr, nullptr, ri, sc);
       if (!iface_running(I)) sweep_append(D, st, k);
       group_publish(st, k, e);
     }
@@ -2646,12 +2961,12 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_search(Dev *c
       while (q.pos < q.end) {
         int beta, q0, nq;
         group_piece(q, rn, Nk1, beta, q0, nq);
-        row_piece(D, st, sh, k, beta, q0, nq, rk, rn, zk, fl_row);
+        row_piece(D, st, sh, k, 0, beta, q0, nq, rk, rn, zk, fl_row);
       }
     }
     ++e;
     if (group_arrive(st, k, g)) {
-      stage_finish(D, k, 2, Rs, Qs, ri, sc);
+      stage_finish(D, k, 0, 2, Rs, Qs, ri, sc);
       if (!iface_running(I)) sweep_append(D, st, k);
       group_publish(st, k, e);
     }
