@@ -41,13 +41,14 @@ KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "u
 def workload(name):
     from paper_1903_11554_gb300 import inputs
     return {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16,
-            "d12_r4": inputs.config_d12_r4}[name]()
+            "d12_r4": inputs.config_d12_r4, "d12_p4": inputs.config_d12_p4}[name]()
 
 
 def workload_config(p):
     return {"workload": "%s: %s_%d, %s form, N=%d/mode, d=%d, rank cap %d, tol %g, %s contraction, seed %d"
             % (p.name, p.family, p.n, "R^n trapezoid" if p.form == "rn" else "unit-cube Gauss-Legendre",
-               p.N[0], p.d, p.rank_cap, p.tol, p.precision, p.seed),
+               p.N[0], p.d, p.rank_cap, p.tol, p.precision, p.seed)
+            + (", up to %d pivots per interface per sweep" % p.npiv if p.npiv > 1 else ""),
             "family": p.family, "n": p.n, "d": p.d, "nodes_per_mode": p.N[0], "rank_cap": p.rank_cap,
             "tol": p.tol, "precision": p.precision, "l2": "flushed between steps (256 MB write)"}
 
@@ -287,7 +288,7 @@ def measure_workload(binding, torch, name, steps, flush):
             ex = float(g["value_exact_contraction"])
             out["rel_err_vs_oracle_cores_at_60_digits"] = abs(res[-1]["value"] + res[-1]["value_lo"] - ex) / abs(ex)
         out["same_trajectory_as_oracle"] = (res[-1]["sweeps"], res[-1]["n_eval"]) == (g["sweeps"], g["n_eval"])
-        if name == "d12_r4":
+        if name in ("d12_r4", "d12_p4"):
             pass
         elif name == "c4":
             env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
@@ -658,7 +659,7 @@ def main():
 
     others = {}
     if args.workload == "d12" and args.launch_mode == "graph":
-        for name in ("c4", "e16", "d12_r4"):
+        for name in ("c4", "e16", "d12_r4", "d12_p4"):
             others[name] = measure_workload(binding, torch, name, max(3, min(args.steps, 20)), flush)
         others["d12_search_variants"] = measure_search_variants(binding, torch, flush)
     systems = {}

@@ -1868,7 +1868,7 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fi
     const IfaceState &I = search_state(D, st, k, j);
     work = !st->stop && st->search && I.active && !I.rook_done;
   }
-  if (r > 0 && (j == 0 || work)) {
+  if (r > 0 && work) {
     if (mode == 1) stage_compact_async(Fs, D.Sr[k], Qs, D.Qc[k], r, ld);   // D^-1 R row-major, Q col-major
     else stage_compact_async(Fs, D.Cc[k], Qs, D.Qr[k], r, ld);             // R D^-1 col-major, Q row-major
     for (int b = threadIdx.x; b < r; b += blockDim.x) cp_async8(sc.ri + b, D.rinv[k] + b);

@@ -146,6 +146,14 @@ def config_d12_r4(**kw) -> Problem:
     return config_d12(**args)
 
 
+def config_d12_p4(**kw) -> Problem:
+    """D_12 as config_d12 with up to four pivots per interface per sweep (the
+    rank-adaptive variant; Alg. 6 adds one)."""
+    args = dict(npiv=4, name="D12_rn_N385_r64_p4")
+    args.update(kw)
+    return config_d12(**args)
+
+
 def config_e16(**kw) -> Problem:
     """E_16 on [0,1]^15, Gauss-Legendre 128 nodes/mode, rank cap 96, tol 1e-14,
     double-double final contraction."""

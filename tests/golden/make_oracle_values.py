@@ -6,7 +6,7 @@ ranks and nested sets, per sweep the integral and the ranks, and the final
 cross contracted at 60 digits (oracle.ttcross.contract_decimal).  Calls only
 the oracle; takes ~40 min.
 
-    python tests/golden/make_oracle_values.py [c4 d12 e16 d8 d16 c8_cube c16_cube c24_cube c32_cube]
+    python tests/golden/make_oracle_values.py [c4 d12 d12_r4 d12_p4 e16 d8 d16 c8_cube c16_cube c24_cube c32_cube]
 """
 import json
 import os
@@ -20,6 +20,7 @@ from oracle import ttcross  # noqa: E402
 from paper_1903_11554_gb300 import inputs  # noqa: E402
 
 CONFIGS = {"c4": inputs.config_c4, "d12": inputs.config_d12, "d12_r4": inputs.config_d12_r4,
+           "d12_p4": inputs.config_d12_p4,
            "e16": inputs.config_e16,
            "d8": lambda: inputs.config_d_cube(8), "d16": lambda: inputs.config_d_cube(16),
            "c8_cube": lambda: inputs.config_c_cube(8), "c16_cube": lambda: inputs.config_c_cube(16),

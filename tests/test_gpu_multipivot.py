@@ -5,7 +5,8 @@ pivot_search_multi (needs a GB300).
     and the nested sets after every sweep identical (the accepted pivots, their
     order and count);
   * whole runs: status, sweeps, evaluations and final ranks equal, value within
-    1e-12;
+    1e-12; the D_12 workload with four pivots per sweep at full size against
+    its stored oracle run;
   * D_8 in the unit-cube form with four pivots per sweep against its printed
     value (Sec. 5.5, Fig. 7);
   * the modes that take one pivot per sweep refuse a problem with several.
@@ -96,6 +97,26 @@ def test_d8_printed_value_with_four_pivots():
     assert rel(got["value"], ref) < 5e-12
     print("D_8, four pivots per sweep: %d sweeps (one pivot: 29), rank %d, printed rel %.2e"
           % (got["sweeps"], got["max_rank"], rel(got["value"], ref)))
+
+
+def test_d12_four_pivots_full_size():
+    """The D_12 workload with up to four pivots per sweep at full size against
+    the stored oracle run (tests/golden/oracle_full.json, "d12_p4"): the same
+    sweeps, evaluations and final nested sets, the value within 1e-12 of the
+    oracle's and of its 60-digit contraction of the oracle's final cores."""
+    g = json.load(open(os.path.join(GOLDEN, "oracle_full.json")))["d12_p4"]
+    p = inputs.config_d12_p4()
+    plan = B().Plan(p)
+    got = plan.run()
+    assert (got["status"], got["sweeps"], got["n_eval"], got["ranks"]) == (g["status"], g["sweeps"], g["n_eval"], g["ranks"])
+    st = plan.get_state()
+    for key in ("lpar", "lnode", "rpar", "rnode"):
+        for a, b in zip(st[key], g["parents"][key]):
+            assert list(map(int, a)) == b, key
+    assert rel(got["value"], float(g["value"])) < 1e-12
+    assert rel(got["value"], float(g["value_exact_contraction"])) < 1e-12
+    print("D_12, four pivots: %d sweeps (one pivot: 64), value rel %.2e to the oracle"
+          % (got["sweeps"], rel(got["value"], float(g["value"]))))
 
 
 def test_one_pivot_modes_refuse_several():
