@@ -202,14 +202,17 @@ int ttq_batch_create(const ttq_problem *probs, int count, void *workspace, size_
 int ttq_batch_run(ttq_plan *batch, ttq_result *results /* [count] */);
 
 /* Autotuner: times the evaluation, sample and rook kernels over `sweeps`
- * sweeps for candidate grid shapes (CTAs per instance of the rook kernels, which
- * spread all interfaces' work over one grid; CTAs per interface of the sample
- * kernel; CTAs per instance of the evaluation kernel), keeps the fastest and
- * writes them to chosen[0..2] (rook, sample, eval) if chosen != NULL.  Grid
- * shapes never change results.  ttq_plan_set_config sets them directly (each
- * in 1..65535, else TTQ_ERR_INVALID_ARG). */
-int ttq_batch_autotune(ttq_plan *plan, int sweeps, int32_t *chosen);
+ * sweeps for candidate launch shapes (CTAs per instance of the rook kernels,
+ * which spread all interfaces' work over one grid; CTAs per interface of the
+ * sample kernel; CTAs per instance of the evaluation kernel; the largest rook
+ * work item, 1, 2 or 4 rows of 32 candidates), keeps the fastest and writes
+ * them to chosen[0..3] (rook, sample, eval, rook rows) if chosen != NULL.
+ * Launch shapes never change results.  ttq_plan_set_config sets the CTA
+ * counts directly (each in 1..65535) and ttq_plan_set_rook_rows the item size
+ * (1, 2 or 4), else TTQ_ERR_INVALID_ARG. */
+int ttq_batch_autotune(ttq_plan *plan, int sweeps, int32_t *chosen /* [4] */);
 int ttq_plan_set_config(ttq_plan *plan, int rook_ctas, int sample_ctas, int eval_ctas);
+int ttq_plan_set_rook_rows(ttq_plan *plan, int rows);
 
 /* --- serving: continuous batching -----------------------------------------
  * A server owns a caller-allocated device pool (`pool`, pool_bytes, 256-byte

@@ -77,6 +77,7 @@ SIGNATURES = {
     "ttq_batch_run": (_c.c_int, [_vp, _c.POINTER(TTQResult)]),
     "ttq_batch_autotune": (_c.c_int, [_vp, _c.c_int, _i32p]),
     "ttq_plan_set_config": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
+    "ttq_plan_set_rook_rows": (_c.c_int, [_vp, _c.c_int]),
     "ttq_server_create": (_c.c_int, [_vp, _c.c_size_t, _c.c_int, _vp, _c.POINTER(_vp)]),
     "ttq_server_destroy": (_c.c_int, [_vp]),
     "ttq_server_submit": (_c.c_int, [_vp, _c.POINTER(TTQProblem), _c.POINTER(_c.c_uint64)]),
@@ -432,12 +433,13 @@ class Batch:
         return [_result_dict(r) for r in res]
 
     def autotune(self, sweeps: int = 3):
-        chosen = (_c.c_int32 * 3)()
+        chosen = (_c.c_int32 * 4)()
         _check(self.lib.ttq_batch_autotune(self.h, sweeps, chosen), "ttq_batch_autotune")
-        return {"rook_ctas": chosen[0], "sample_ctas": chosen[1], "eval_ctas": chosen[2]}
+        return {"rook_ctas": chosen[0], "sample_ctas": chosen[1], "eval_ctas": chosen[2], "rook_rows": chosen[3]}
 
-    def set_config(self, rook_ctas: int, sample_ctas: int, eval_ctas: int):
+    def set_config(self, rook_ctas: int, sample_ctas: int, eval_ctas: int, rook_rows: int = 4):
         _check(self.lib.ttq_plan_set_config(self.h, rook_ctas, sample_ctas, eval_ctas), "ttq_plan_set_config")
+        _check(self.lib.ttq_plan_set_rook_rows(self.h, rook_rows), "ttq_plan_set_rook_rows")
 
     def set_graphs(self, on: bool):
         _check(self.lib.ttq_plan_set_graphs(self.h, 1 if on else 0), "ttq_plan_set_graphs")

@@ -82,6 +82,7 @@ struct ttq_plan {
   int persistent;           // one instance: the search of a sweep as one cooperative launch (k_search)
   int search_grid, search_smem;
   int npiv;                 // searches per interface (several pivots per sweep): the decisions kernels' grid y
+  int rook_rmax;            // largest rook work item, rows of 32 candidates (1, 2 or 4)
 };
 
 static cudaEvent_t ev_get(ttq_plan *P) {
@@ -446,6 +447,7 @@ static int host_inputs(const ttq_problem *p, cudaStream_t s, std::vector<double>
 // launch configuration from the instances' problems (maxima over the set)
 static void configure(ttq_plan *P, const ttq_problem *probs, int count, const Layout *Ls) {
   P->max_ni = 0; P->rook_max = 1; P->max_sweeps = 1; P->max_cap = 1; P->max_sum_n = 1; P->npiv = 1;
+  P->rook_rmax = 4;
   P->sblocks = P->cblocks = P->rblocks = 1;
   size_t maxfib = 0;
   for (int q = 0; q < count; ++q) {
@@ -703,9 +705,9 @@ static void enqueue_sweep_seq(ttq_plan *P) {
     P->launches++;
     timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), W, P->samples_smem, s>>>(dv); });
     for (int q = 0; q < P->rook_max; ++q) {
-      timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv); });
+      timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
       timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 1, 0, P->cond, 0); });
-      timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv); });
+      timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
       timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 2, 0, P->cond, 0); });
     }
     timed(P, KT_UPDATE, [&] { k_seq_end<<<dim3(1, 1, nb), T, 0, s>>>(dv, k, k == ni ? 1 : 0); });
@@ -768,11 +770,11 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   // rules, the WHILE condition), after the contraction has joined
   for (int q = 0; q < P->rook_max; ++q) {
     const bool fin = q == P->rook_max - 1;
-    timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv); });
+    timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv, P->rook_rmax); });
     timed(P, KT_SOLVE, [&] {
       launch_k(P, k_solve, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 1, 0, P->cond, 0);
     });
-    timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv); });
+    timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv, P->rook_rmax); });
     if (fin && P->s2) cudaStreamWaitEvent(s, P->join, 0);
     timed(P, fin ? KT_UPDATE : KT_SOLVE, [&] {
       launch_k(P, k_solve, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 2, fin ? 1 : 0, P->cond,
@@ -1009,6 +1011,7 @@ extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
   const int cand_c[] = {4, 16, 38, 76, 152, 304, 456};
   const int cand_s[] = {8, 16, 32, 64, 128};
   const int cand_e[] = {152, 304, 608, 1216};
+  const int cand_r[] = {1, 2, 4};
   const int save_timing = P->timing;
   P->timing = 1;
   auto time_cfg = [&](double *ms_out) -> int {
@@ -1052,12 +1055,24 @@ extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
   P->sblocks = bs;
   if (!rc) be = pick(cand_e, 4, &P->grid_eval, nullptr);
   P->grid_eval = be;
+  int br = P->rook_rmax;
+  if (!rc) br = pick(cand_r, 3, &P->rook_rmax, nullptr);
+  P->rook_rmax = br;
   P->timing = save_timing;
   for (int k = 0; k < KT_N; ++k) { P->kt_ms[k] = 0.0; P->kt_n[k] = 0; }
   if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
   if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
-  if (chosen) { chosen[0] = P->cblocks; chosen[1] = P->sblocks; chosen[2] = P->grid_eval; }
+  if (chosen) { chosen[0] = P->cblocks; chosen[1] = P->sblocks; chosen[2] = P->grid_eval; chosen[3] = P->rook_rmax; }
   return rc;
+}
+
+extern "C" int ttq_plan_set_rook_rows(ttq_plan *P, int rmax) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (rmax != 1 && rmax != 2 && rmax != 4) return set_err(TTQ_ERR_INVALID_ARG, "rook item rows must be 1, 2 or 4");
+  P->rook_rmax = rmax;
+  if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
+  if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
+  return TTQ_OK;
 }
 
 extern "C" int ttq_plan_set_config(ttq_plan *P, int rook_ctas, int sample_ctas, int eval_ctas) {

@@ -2456,10 +2456,10 @@ struct RookDeal {
   int R, pos, end;
   bool items;
 };
-__device__ __forceinline__ RookDeal rook_deal(const Dev &D, int outer, int Nl) {
+__device__ __forceinline__ RookDeal rook_deal(const Dev &D, int outer, int Nl, int rmax) {
   const long long W = (long long)gridDim.x * TTQ_WARPS;
   RookDeal q;
-  q.R = rows_per_item(outer, Nl);
+  q.R = rows_per_item(outer, Nl, rmax);
   q.im = item_map(outer ? outer * node_chunks(Nl, q.R).nch : 0);
   q.items = q.im.total <= W;
   if (!q.items) q.im = item_map(outer ? outer * ((Nl + 31) >> 5) : 0);
@@ -2559,7 +2559,8 @@ __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh,
 
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i) of every
 // searching interface; pass 1 of the argmax per interface (pass 2 in k_solve).
-__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps) {
+// rmax: the largest item (rows of 32 candidates) of the item deal (1, 2 or 4)
+__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps, int rmax) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
@@ -2581,7 +2582,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   if (stop || !search) return;
   // an interface's running searches take consecutive blocks of its outer indices
   const int outer = __popc(act) * r0;
-  RookDeal dl = rook_deal(D, outer, Nl);
+  RookDeal dl = rook_deal(D, outer, Nl, rmax);
   unsigned long long fl = 0;
   int zk = 0;                                   // interface and search whose z sits in sh.z[warp]
   while (dl.pos < dl.end) {
@@ -2659,7 +2660,7 @@ __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh,
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
 // searching interface, rows of 32 nodes j of the fibers beta, dealt like the
 // column step's; pass 1 of the argmax.
-__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps) {
+__global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps, int rmax) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
   pdl_wait();
@@ -2678,7 +2679,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   }
   if (stop || !search) return;
   const int outer = __popc(act) * r2;
-  RookDeal dl = rook_deal(D, outer, Nl);
+  RookDeal dl = rook_deal(D, outer, Nl, rmax);
   unsigned long long fl = 0;
   int zk = 0;
   while (dl.pos < dl.end) {

@@ -58,7 +58,11 @@ def test_grid_shapes_and_autotune_do_not_change_results():
     ref = b.run()
     b.set_config(7, 5, 33)
     assert b.run() == ref
+    for rows in (1, 2):
+        b.set_config(19, 3, 77, rook_rows=rows)
+        assert b.run() == ref
     chosen = b.autotune(sweeps=2)
+    assert chosen["rook_rows"] in (1, 2, 4)
     assert all(v >= 1 for v in chosen.values())
     assert b.run() == ref
 
