@@ -472,7 +472,8 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   {
     int dev = 0, sms = 152, occ = 3;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col, TTQ_WARPS * 32, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col<false>, TTQ_WARPS * 32, 0) != cudaSuccess ||
+        occ < 1)
       occ = 1;
     const int slots = sms * occ;
     // one instance: the resident slots less the two of the contraction chains,
@@ -531,7 +532,13 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
 
 static cudaError_t set_smem_attributes(ttq_plan *P) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_qr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem)) !=
+      cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(k_qr_row, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
@@ -540,7 +547,7 @@ static cudaError_t set_smem_attributes(ttq_plan *P) {
     return e;
   if ((e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
+  return cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
 }
 
 static void plan_free(ttq_plan *P) {
@@ -696,7 +703,7 @@ static void enqueue_sweep_seq(ttq_plan *P) {
   auto refresh = [&] {
     timed(P, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
     timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, 0, s>>>(dv); });
-    timed(P, KT_QR, [&] { k_qr<<<dim3(ni, 1, nb), T, P->qr_smem, s>>>(dv); });
+    timed(P, KT_QR, [&] { k_qr<false><<<dim3(ni, 1, nb), T, P->qr_smem, s>>>(dv); });
   };
   refresh();
   timed(P, KT_CONTRACT, [&] { k_contract<<<dim3(2, 1, nb), 256, P->contract_smem, s>>>(dv, 0); });
@@ -705,10 +712,10 @@ static void enqueue_sweep_seq(ttq_plan *P) {
     P->launches++;
     timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), W, P->samples_smem, s>>>(dv); });
     for (int q = 0; q < P->rook_max; ++q) {
-      timed(P, KT_ROOK_COL, [&] { k_rook_col<<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
-      timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 1, 0, P->cond, 0); });
-      timed(P, KT_ROOK_ROW, [&] { k_rook_row<<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
-      timed(P, KT_SOLVE, [&] { k_solve<<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 2, 0, P->cond, 0); });
+      timed(P, KT_ROOK_COL, [&] { k_rook_col<false><<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
+      timed(P, KT_SOLVE, [&] { k_solve<false><<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 1, 0, P->cond, 0); });
+      timed(P, KT_ROOK_ROW, [&] { k_rook_row<false><<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
+      timed(P, KT_SOLVE, [&] { k_solve<false><<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 2, 0, P->cond, 0); });
     }
     timed(P, KT_UPDATE, [&] { k_seq_end<<<dim3(1, 1, nb), T, 0, s>>>(dv, k, k == ni ? 1 : 0); });
     if (k < ni) refresh();
@@ -745,7 +752,8 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   else
     timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, 0, s, dv); });
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
-  timed(P, KT_QR, [&] { launch_k(P, k_qr, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
+  const bool multi = P->npiv > 1;
+  timed(P, KT_QR, [&] { launch_k(P, multi ? k_qr<true> : k_qr<false>, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
   if (P->s2) {
     cudaEventRecord(P->fork, s);
     cudaStreamWaitEvent(P->s2, P->fork, 0);
@@ -770,14 +778,20 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   // rules, the WHILE condition), after the contraction has joined
   for (int q = 0; q < P->rook_max; ++q) {
     const bool fin = q == P->rook_max - 1;
-    timed(P, KT_ROOK_COL, [&] { launch_k(P, k_rook_col, dim3(P->cblocks, 1, nb), W, 0, s, dv, P->rook_rmax); });
-    timed(P, KT_SOLVE, [&] {
-      launch_k(P, k_solve, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 1, 0, P->cond, 0);
+    timed(P, KT_ROOK_COL, [&] {
+      launch_k(P, multi ? k_rook_col<true> : k_rook_col<false>, dim3(P->cblocks, 1, nb), W, 0, s, dv, P->rook_rmax);
     });
-    timed(P, KT_ROOK_ROW, [&] { launch_k(P, k_rook_row, dim3(P->rblocks, 1, nb), W, 0, s, dv, P->rook_rmax); });
+    timed(P, KT_SOLVE, [&] {
+      launch_k(P, multi ? k_solve<true> : k_solve<false>, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 1, 0,
+               P->cond, 0);
+    });
+    timed(P, KT_ROOK_ROW, [&] {
+      launch_k(P, multi ? k_rook_row<true> : k_rook_row<false>, dim3(P->rblocks, 1, nb), W, 0, s, dv, P->rook_rmax);
+    });
     if (fin && P->s2) cudaStreamWaitEvent(s, P->join, 0);
     timed(P, fin ? KT_UPDATE : KT_SOLVE, [&] {
-      launch_k(P, k_solve, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 2, fin ? 1 : 0, P->cond,
+      launch_k(P, multi ? k_solve<true> : k_solve<false>, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 2,
+               fin ? 1 : 0, P->cond,
                fin ? single_cond : 0);
     });
   }

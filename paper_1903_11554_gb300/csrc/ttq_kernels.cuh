@@ -797,6 +797,7 @@ __global__ void __launch_bounds__(256) k_qr_row(Dev *const *Dps) {
   if (threadIdx.x == 0) st->qr_row[k] = r;
 }
 
+template <bool MULTI>
 __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
@@ -814,7 +815,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   pdl_release();
   if (stop || !mine) return;
   extern __shared__ double sm[];
-  if (threadIdx.x < D.npiv) {
+  if (threadIdx.x < (MULTI ? D.npiv : 1)) {
     IfaceState &I = search_state(D, st, k, threadIdx.x);
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
     I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0; I.items_done = 0; I.epoch = 0;
@@ -828,7 +829,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
   if (have >= 1 && have == r - 1 && rowdone == r) {
     qr_border_col(D, k, r, sm, part);
     if (threadIdx.x == 0) atomicAdd(&st->flops[1], (unsigned long long)(12.0 * r * (double)r));
-  } else if (have >= 1 && D.npiv > 1) {
+  } else if (MULTI && have >= 1) {
     // several pivots appended in the last sweep: one bordering update per new
     // row and column, in append order (the rows' entries over the new columns
     // come from this sweep's kernel (a), which precedes this kernel)
@@ -1812,11 +1813,12 @@ __device__ void multi_accept(const Dev &D, State *st, int k, bool append) {
 // End of the sweep (Alg. 6) in the last decisions kernel of the staged search:
 // every CTA appends its interface's accepted pivot, then the last CTA of the
 // instance to arrive finalizes the sweep.
+template <bool MULTI>
 __device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHandle h, int use_cond) {
   State *st = D.st;
   __shared__ int last_s;
   const bool append = !st->stop && !st->stop_pending && st->search && !st->search_abort;
-  if (D.npiv > 1) {
+  if constexpr (MULTI) {
     // one CTA per search of the interface (grid y): the last of them to
     // arrive takes the interface's pivots from all of its searches
     if (mine) {
@@ -1847,12 +1849,15 @@ __device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHa
 // the preceding rook step: they overlap its tail (the rook step streams the
 // cores through L2, so the factors come from DRAM) instead of delaying the argmax.
 // fin: the search's last decisions kernel, which also ends the sweep (sweep_end).
+// MULTI: several pivots per sweep (one CTA per search, grid y); the one-pivot
+// instance is the same code with the search index 0
+template <bool MULTI>
 __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fin, cudaGraphConditionalHandle h,
                                                int use_cond) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
   State *st = D.st;
-  const int k = blockIdx.x + 1, j = blockIdx.y;  // interface, search (grid y: the searches per interface)
+  const int k = blockIdx.x + 1, j = MULTI ? (int)blockIdx.y : 0;  // interface, search (grid y: its searches)
   const bool mine = k <= D.d - 1;
   extern __shared__ double sm[];
   __shared__ SolveSmem sc;
@@ -1879,7 +1884,7 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fi
     stage_finish(D, k, j, mode, Fs, Qs, sc.ri, sc, true);
   else
     cp_async_wait_all();                         // no copy outlives the CTA
-  if (fin) sweep_end(D, k, mine, h, use_cond);
+  if (fin) sweep_end<MULTI>(D, k, mine, h, use_cond);
 }
 
 // per-warp scratch of the rook kernels (no solve buffers: the solves run in k_solve)
@@ -2433,9 +2438,10 @@ __device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k,
 // Lane k-1 of the warp holds interface k's outer rank and nodes; pieces come
 // out as (interface, outer index, first row, rows).
 // the searches of interface k that still run a rook step (bit j: search j)
+template <bool MULTI>
 __device__ __forceinline__ unsigned running_searches(const Dev &D, State *st, int k) {
   unsigned m = 0;
-  for (int j = 0; j < D.npiv; ++j) {
+  for (int j = 0; j < (MULTI ? D.npiv : 1); ++j) {
     const IfaceState &I = search_state(D, st, k, j);
     if (I.active && !I.rook_done) m |= 1u << j;
   }
@@ -2560,6 +2566,7 @@ __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh,
 // Alg. 2, column step: E(:, gamma*) over all rows rho = (alpha, i) of every
 // searching interface; pass 1 of the argmax per interface (pass 2 in k_solve).
 // rmax: the largest item (rows of 32 candidates) of the item deal (1, 2 or 4)
+template <bool MULTI>
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps, int rmax) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
@@ -2574,7 +2581,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   unsigned act = 0;
   int r0 = 0, r1 = 0, Nl = 1;
   if (lane < d - 1) {
-    act = running_searches(D, st, lane + 1);
+    act = running_searches<MULTI>(D, st, lane + 1);
     r0 = st->r[lane];
     r1 = st->r[lane + 1];
     Nl = D.N[lane];
@@ -2591,8 +2598,9 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rl = __shfl_sync(0xffffffffu, r0, k - 1);
     const unsigned am = __shfl_sync(0xffffffffu, act, k - 1);
     int o, q0, nq;
-    rook_piece(dl, k, __popc(am) * rl, D.N[k - 1], o, q0, nq);
-    col_piece(D, st, sh, k, nth_search(am, o / rl), o % rl, q0, nq, rk, zk, fl);
+    rook_piece(dl, k, MULTI ? __popc(am) * rl : rl, D.N[k - 1], o, q0, nq);
+    if constexpr (MULTI) col_piece(D, st, sh, k, nth_search(am, o / rl), o % rl, q0, nq, rk, zk, fl);
+    else col_piece(D, st, sh, k, 0, o, q0, nq, rk, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
 }
@@ -2660,6 +2668,7 @@ __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh,
 // Alg. 2, row step: E(rho*, :) over all columns gamma = (j, beta) of every
 // searching interface, rows of 32 nodes j of the fibers beta, dealt like the
 // column step's; pass 1 of the argmax.
+template <bool MULTI>
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps, int rmax) {
   __shared__ Dev sD;
   const Dev &D = stage_dev(Dps, sD);
@@ -2672,7 +2681,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   unsigned act = 0;
   int r1 = 0, r2 = 0, Nl = 1;
   if (lane < d - 1) {
-    act = running_searches(D, st, lane + 1);
+    act = running_searches<MULTI>(D, st, lane + 1);
     r1 = st->r[lane + 1];
     r2 = st->r[lane + 2];
     Nl = D.N[lane + 1];
@@ -2688,8 +2697,9 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     const int rk = __shfl_sync(0xffffffffu, r1, k - 1), rn = __shfl_sync(0xffffffffu, r2, k - 1);
     const unsigned am = __shfl_sync(0xffffffffu, act, k - 1);
     int o, q0, nq;
-    rook_piece(dl, k, __popc(am) * rn, D.N[k], o, q0, nq);
-    row_piece(D, st, sh, k, nth_search(am, o / rn), o % rn, q0, nq, rk, rn, zk, fl);
+    rook_piece(dl, k, MULTI ? __popc(am) * rn : rn, D.N[k], o, q0, nq);
+    if constexpr (MULTI) row_piece(D, st, sh, k, nth_search(am, o / rn), o % rn, q0, nq, rk, rn, zk, fl);
+    else row_piece(D, st, sh, k, 0, o, q0, nq, rk, rn, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
 }
