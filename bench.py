@@ -41,7 +41,8 @@ KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "u
 def workload(name):
     from paper_1903_11554_gb300 import inputs
     return {"d12": inputs.config_d12, "c4": inputs.config_c4, "e16": inputs.config_e16,
-            "d12_r4": inputs.config_d12_r4, "d12_p4": inputs.config_d12_p4}[name]()
+            "d12_r4": inputs.config_d12_r4, "d12_p4": inputs.config_d12_p4,
+            "d8": lambda: inputs.config_d_cube(8), "d32": lambda: inputs.config_d_cube(32)}[name]()
 
 
 def workload_config(p):
@@ -288,7 +289,7 @@ def measure_workload(binding, torch, name, steps, flush):
             ex = float(g["value_exact_contraction"])
             out["rel_err_vs_oracle_cores_at_60_digits"] = abs(res[-1]["value"] + res[-1]["value_lo"] - ex) / abs(ex)
         out["same_trajectory_as_oracle"] = (res[-1]["sweeps"], res[-1]["n_eval"]) == (g["sweeps"], g["n_eval"])
-        if name in ("d12_r4", "d12_p4"):
+        if name in ("d12_r4", "d12_p4", "d8"):
             pass
         elif name == "c4":
             env = dict(os.environ, CUDA_VISIBLE_DEVICES="", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
@@ -309,7 +310,21 @@ def measure_workload(binding, torch, name, steps, flush):
                                  "sample": "oracle sweeps %s of the %d-sweep run on one host core, %.1f s; they stand "
                                            "for %d/%d of an integral" % ([r[0] for r in rows], g["sweeps"], secs,
                                                                          len(rows), g["sweeps"])}
+    printed = paper_value(name)
+    if printed is not None:
+        out["rel_err_vs_printed_value"] = abs(res[-1]["value"] + res[-1]["value_lo"] - printed["value"]) / printed["value"]
+        out["printed_value"] = printed
     return out
+
+
+def paper_value(name):
+    """The paper's printed value of a workload (tests/golden/paper_values.json), if any."""
+    key = {"d8": "D_8", "d32": "D_32"}.get(name)
+    path = os.path.join(ROOT, "tests", "golden", "paper_values.json")
+    if key is None or not os.path.exists(path):
+        return None
+    e = json.load(open(path))[key]
+    return {"value": float(e["value"]), "source": e["source"]}
 
 
 def measure_search_variants(binding, torch, flush, steps=3):
@@ -659,7 +674,7 @@ def main():
 
     others = {}
     if args.workload == "d12" and args.launch_mode == "graph":
-        for name in ("c4", "e16", "d12_r4", "d12_p4"):
+        for name in ("c4", "e16", "d12_r4", "d12_p4", "d8", "d32"):
             others[name] = measure_workload(binding, torch, name, max(3, min(args.steps, 20)), flush)
         others["d12_search_variants"] = measure_search_variants(binding, torch, flush)
     systems = {}
