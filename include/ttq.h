@@ -272,7 +272,10 @@ int ttq_plan_get_state(ttq_plan *plan, int32_t *ranks, int32_t *lpar, int32_t *l
  * sweep's integral to *value and, if pivots != NULL, d-1 ttq_pivot records.
  * In double-double mode with search == 0, *value / *value_lo are the
  * double-double contraction; with search != 0 the FP64 one.  No stopping rule
- * is applied. */
+ * is applied.  With several pivots per sweep (npiv > 1) each record describes
+ * the interface's first search and `accepted` is the number of pivots the
+ * interface appended; the pivots themselves are the new rows of the nested
+ * sets (ttq_plan_get_state). */
 int ttq_plan_sweep(ttq_plan *plan, int sweep_index, int search, double *value, double *value_lo,
                    ttq_pivot *pivots);
 
