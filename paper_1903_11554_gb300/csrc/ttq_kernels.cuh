@@ -530,7 +530,9 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32) k_eval_slabs(Dev *const *Dps) 
 // rotations fold the new row into R (Q gains a row and a column), and the new
 // column of R is Q'^T times the new column of G.  A full Householder QR
 // (O(r^3), LAPACK dgeqr2/dorg2r conventions) runs when no factors are stored
-// (first sweep, or index sets replaced from outside).
+// (first sweep, or index sets replaced from outside).  With several pivots per
+// sweep (MULTI) an interface may append m > 1 rows and columns: one bordering
+// update (row, then column) per appended pair, in append order.
 // Stored: Q column-major (Qc) and row-major (Qr), R column- and row-major,
 // 1/R_jj, and R with its diagonal divided out for the FP64 substitutions:
 // Cc = R D^-1 column-major (entries R_ij / R_jj, back substitution) and
@@ -1844,7 +1846,7 @@ __device__ void sweep_end(const Dev &D, int k, bool mine, cudaGraphConditionalHa
 }
 
 // The decisions after a rook step (modes 1 and 2 of stage_finish), one CTA per
-// interface.  The rank and the factors are fixed from kernel (b) to the end of
+// interface and search.  The rank and the factors are fixed from kernel (b) to the end of
 // the search, so their copies to shared memory are issued before the wait for
 // the preceding rook step: they overlap its tail (the rook step streams the
 // cores through L2, so the factors come from DRAM) instead of delaying the argmax.

@@ -83,6 +83,12 @@ def test_workspace_size_and_validation(lib):
     bad.weights = bad.weights[:3]
     with pytest.raises(binding.TTQError):
         binding.workspace_bytes(bad)          # R^n form needs d == n
+    for npiv in (-1, 5):                      # 0..TTQ_MAX_PIVOTS pivots per sweep
+        with pytest.raises(binding.TTQError):
+            binding.workspace_bytes(inputs.config_c4(npiv=npiv))
+    # several pivots per sweep: each search's scratch beside the first's
+    assert binding.workspace_bytes(inputs.config_c4(npiv=4)) > binding.workspace_bytes(inputs.config_c4())
+    assert binding.workspace_bytes(inputs.config_c4(npiv=0)) == binding.workspace_bytes(inputs.config_c4())
 
 
 def test_status_strings(lib):
