@@ -394,6 +394,7 @@ def measure_batched(binding, inputs, torch, count=256):
     return {"workload": "%d mixed instances (C/D/E cyclic, n 4..24, N 65..513, rank cap 8..128, tol 1e-12, "
                         "seed 256+i)" % count,
             "integrals_per_s": count / dt, "seconds": dt, "autotuned": tuned,
+            "concurrent_groups": min(8, max(1, count // 32)),
             "statuses": {k: sum(1 for r in res if r["status_name"] == k) for k in set(r["status_name"] for r in res)},
             "fiber_evals_per_s": sum(r["n_eval"] for r in res) / dt,
             "one_at_a_time": {"integrals_per_s": count / st, "seconds": st,

@@ -211,6 +211,16 @@ int ttq_batch_run(ttq_plan *batch, ttq_result *results /* [count] */);
  * counts directly (each in 1..65535) and ttq_plan_set_rook_rows the item size
  * (1, 2 or 4), else TTQ_ERR_INVALID_ARG. */
 int ttq_batch_autotune(ttq_plan *plan, int sweeps, int32_t *chosen /* [4] */);
+
+/* Concurrent groups of a batch run: the instances sorted by cost (rank cap^2
+ * times the nodes of all modes, ties in instance order) are split into
+ * `groups` contiguous groups of near-equal count, each a WHILE loop of its own
+ * in the batch's run graph with no dependence on the others, so a group of
+ * small instances does not wait for the sweeps of the large ones.  1..min(8,
+ * count / 2); the default is min(8, count / 32) (at least 1).  Results are the
+ * same for every grouping (each instance's kernels are the same). */
+#define TTQ_MAX_BATCH_GROUPS 8
+int ttq_batch_set_groups(ttq_plan *batch, int groups);
 int ttq_plan_set_config(ttq_plan *plan, int rook_ctas, int sample_ctas, int eval_ctas);
 int ttq_plan_set_rook_rows(ttq_plan *plan, int rows);
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "ttq_batch_autotune": (_c.c_int, [_vp, _c.c_int, _i32p]),
     "ttq_plan_set_config": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
     "ttq_plan_set_rook_rows": (_c.c_int, [_vp, _c.c_int]),
+    "ttq_batch_set_groups": (_c.c_int, [_vp, _c.c_int]),
     "ttq_server_create": (_c.c_int, [_vp, _c.c_size_t, _c.c_int, _vp, _c.POINTER(_vp)]),
     "ttq_server_destroy": (_c.c_int, [_vp]),
     "ttq_server_submit": (_c.c_int, [_vp, _c.POINTER(TTQProblem), _c.POINTER(_c.c_uint64)]),
@@ -436,6 +437,10 @@ class Batch:
         chosen = (_c.c_int32 * 4)()
         _check(self.lib.ttq_batch_autotune(self.h, sweeps, chosen), "ttq_batch_autotune")
         return {"rook_ctas": chosen[0], "sample_ctas": chosen[1], "eval_ctas": chosen[2], "rook_rows": chosen[3]}
+
+    def set_groups(self, groups: int):
+        """Concurrent groups of the run graph (instances sorted by cost)."""
+        _check(self.lib.ttq_batch_set_groups(self.h, groups), "ttq_batch_set_groups")
 
     def set_config(self, rook_ctas: int, sample_ctas: int, eval_ctas: int, rook_rows: int = 4):
         _check(self.lib.ttq_plan_set_config(self.h, rook_ctas, sample_ctas, eval_ctas), "ttq_plan_set_config")

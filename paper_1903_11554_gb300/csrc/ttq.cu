@@ -83,6 +83,16 @@ struct ttq_plan {
   int search_grid, search_smem;
   int npiv;                 // searches per interface (several pivots per sweep): the decisions kernels' grid y
   int rook_rmax;            // largest rook work item, rows of 32 candidates (1, 2 or 4)
+  // batches: the instances sorted by cost (rank cap^2 x nodes), split into
+  // ngroups contiguous groups that run as concurrent WHILE loops of one graph
+  Dev **devs_sorted;        // device array, count entries, in cost order
+  int ngroups;
+  std::vector<int> order;   // instance of each sorted position
+  std::vector<int> glo, gcnt, gkernels;   // per group: first sorted position, instances, kernels per iteration
+  // the group being enqueued (the whole batch when cur_dv is null)
+  Dev *const *cur_dv;
+  int cur_nb;
+  unsigned *cur_guard;
 };
 
 static cudaEvent_t ev_get(ttq_plan *P) {
@@ -200,6 +210,18 @@ static int validate(const ttq_problem *p) {
 }
 
 static int npiv_of(const ttq_problem *p) { return p->npiv < 1 ? 1 : p->npiv; }
+
+// a batch's workspace head: its descriptor array, then the same sorted by cost
+static size_t batch_head_bytes(int count) {
+  return count > 1 ? 2 * (((size_t)count * sizeof(Dev *) + 255) & ~(size_t)255) : 0;
+}
+
+// cost of an instance for the grouping of a batch: rank cap^2 x nodes
+static double instance_cost(const ttq_problem *p) {
+  double n = 0.0;
+  for (int k = 0; k < p->d; ++k) n += p->nodes_per_mode[k];
+  return (double)p->rank_cap * p->rank_cap * n;
+}
 
 struct Bump {
   size_t off = 0;
@@ -576,7 +598,7 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
   if (count < 1 || count > 65535) return set_err(TTQ_ERR_INVALID_ARG, "count must be in 1..65535");
   if (!out) return set_err(TTQ_ERR_INVALID_ARG, "null out");
   std::vector<Layout> Ls(count);
-  size_t need = count > 1 ? (((size_t)count * sizeof(Dev *) + 255) & ~(size_t)255) : 0;
+  size_t need = batch_head_bytes(count);
   std::vector<size_t> offs(count);
   for (int q = 0; q < count; ++q) {
     int rc = validate(probs + q);
@@ -632,6 +654,19 @@ static int plan_build(const ttq_problem *probs, int count, void *workspace, size
     P->devs = (Dev **)base0;
     e = cudaMemcpyAsync(P->devs, devp.data(), count * sizeof(Dev *), cudaMemcpyHostToDevice, s);
     P->h2d += (long long)(count * sizeof(Dev *));
+    // the same descriptors in cost order, for the concurrent groups of the run graph
+    P->order.resize(count);
+    for (int q = 0; q < count; ++q) P->order[q] = q;
+    std::stable_sort(P->order.begin(), P->order.end(),
+                     [&](int a, int b) { return instance_cost(probs + a) < instance_cost(probs + b); });
+    std::vector<Dev *> sorted(count);
+    for (int q = 0; q < count; ++q) sorted[q] = devp[P->order[q]];
+    P->devs_sorted = (Dev **)(base0 + batch_head_bytes(count) / 2);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P->devs_sorted, sorted.data(), count * sizeof(Dev *), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    P->h2d += (long long)(count * sizeof(Dev *));
+    P->ngroups = std::min(8, count / 32 > 1 ? count / 32 : 1);
   }
   if (!rc && e == cudaSuccess) {
     P->h = P->hs[0];
@@ -672,7 +707,7 @@ extern "C" int ttq_plan_destroy(ttq_plan *P) {
 
 extern "C" int ttq_batch_workspace_bytes(const ttq_problem *probs, int count, size_t *bytes) {
   if (!probs || !bytes || count < 1 || count > 65535) return set_err(TTQ_ERR_INVALID_ARG, "bad argument");
-  size_t need = count > 1 ? (((size_t)count * sizeof(Dev *) + 255) & ~(size_t)255) : 0;
+  size_t need = batch_head_bytes(count);
   for (int q = 0; q < count; ++q) {
     int rc = validate(probs + q);
     if (rc) return rc;
@@ -732,8 +767,8 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
     return;
   }
   cudaStream_t s = P->stream;
-  const int ni = P->max_ni, nb = P->count;
-  Dev *const *dv = P->devs;
+  const int ni = P->max_ni, nb = P->cur_dv ? P->cur_nb : P->count;
+  Dev *const *dv = P->cur_dv ? P->cur_dv : P->devs;
   const dim3 W(TTQ_WARPS * 32), T(256);
   // the QR row append (old entries only) beside the evaluation of the new slabs
   if (P->s2) {
@@ -796,7 +831,7 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
     });
   }
   if (P->in_loop && loop_end && nb > 1) {
-    launch_k(P, k_batch_cond, dim3(1), T, 0, s, dv, nb, P->max_sweeps, P->guard, P->cond);
+    launch_k(P, k_batch_cond, dim3(1), T, 0, s, dv, nb, P->max_sweeps, P->cur_dv ? P->cur_guard : P->guard, P->cond);
     P->launches++;
   }
 }
@@ -805,45 +840,73 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
 // the condition is set on the device (the last decisions kernel of the sweep for one instance, k_batch_cond
 // for a batch), so a run needs no host round trip per sweep.
 static int build_run_graph(ttq_plan *P) {
+  // a batch split into groups: one WHILE node per group, with no edges between
+  // them, so the groups' sweeps run concurrently; each group's condition
+  // kernel watches its own instances and counts its iterations in the
+  // batch_guard of its first instance's state
+  const int G = (P->count > 1 && P->devs_sorted && P->ngroups > 1) ? P->ngroups : 1;
+  P->glo.assign(G, 0);
+  P->gcnt.assign(G, P->count);
+  P->gkernels.assign(G, 0);
+  if (G > 1)
+    for (int g = 0; g < G; ++g) {
+      P->glo[g] = (int)((long long)g * P->count / G);
+      P->gcnt[g] = (int)((long long)(g + 1) * P->count / G) - P->glo[g];
+    }
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
-  cudaGraphConditionalHandle h;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) { cudaGraphDestroy(g); g_last_error = std::string("conditional handle: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
-  alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
-  memset(npbuf, 0, sizeof(npbuf));
-  cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
-  np.type = cudaGraphNodeTypeConditional;
-  np.conditional.handle = h;
-  np.conditional.type = cudaGraphCondTypeWhile;
-  np.conditional.size = 1;
-  cudaGraphNode_t node;
-  e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
-  if (e != cudaSuccess) { cudaGraphDestroy(g); g_last_error = std::string("while node: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
-  cudaGraph_t body = np.conditional.phGraph_out[0];
   const long long l0 = P->launches;
   long long n0[KT_N];
   memcpy(n0, P->kt_n, sizeof(n0));
-  P->cond = h;
-  P->in_loop = 1;
-  // four sweeps per iteration: the condition is evaluated (and the body
-  // relaunched, ~5 us) a quarter as often; a sweep that follows the stop finds
-  // it set and its kernels return at once
-  e = cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    enqueue_sweep(P, false, true);
-    enqueue_sweep(P, false);
-    enqueue_sweep(P, false);
-    enqueue_sweep(P, true);
-    e = cudaStreamEndCapture(P->stream, &body);
+  cudaError_t e = cudaSuccess;
+  for (int grp = 0; grp < G && e == cudaSuccess; ++grp) {
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { g_last_error = std::string("conditional handle: ") + cudaGetErrorString(e); break; }
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) { g_last_error = std::string("while node: ") + cudaGetErrorString(e); break; }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    P->cond = h;
+    P->in_loop = 1;
+    if (G > 1) {
+      P->cur_dv = P->devs_sorted + P->glo[grp];
+      P->cur_nb = P->gcnt[grp];
+      P->cur_guard = (unsigned *)((char *)P->sts[P->order[P->glo[grp]]] + offsetof(State, batch_guard));
+    }
+    const long long lg = P->launches;
+    // four sweeps per iteration: the condition is evaluated (and the body
+    // relaunched, ~5 us) a quarter as often; a sweep that follows the stop
+    // finds it set and its kernels return at once
+    e = cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      enqueue_sweep(P, false, true);
+      enqueue_sweep(P, false);
+      enqueue_sweep(P, false);
+      enqueue_sweep(P, true);
+      e = cudaStreamEndCapture(P->stream, &body);
+    }
+    P->gkernels[grp] = (int)(P->launches - lg);
+    P->in_loop = 0;
+    P->cur_dv = nullptr;
+    if (e != cudaSuccess) g_last_error = std::string("run graph: ") + cudaGetErrorString(e);
   }
-  P->in_loop = 0;
   P->sweep_kernels = (int)(P->launches - l0);
   P->launches = l0;
   memcpy(P->kt_n, n0, sizeof(n0));
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->run_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(&P->run_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (e != cudaSuccess) g_last_error = std::string("run graph: ") + cudaGetErrorString(e);
+  }
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) { g_last_error = std::string("run graph: ") + cudaGetErrorString(e); return TTQ_ERR_CUDA; }
+  if (e != cudaSuccess) return TTQ_ERR_CUDA;
   return TTQ_OK;
 }
 
@@ -922,8 +985,14 @@ static int enqueue_run(ttq_plan *P) {
   k_begin<<<dim3(1, 1, P->count), 1, 0, P->stream>>>(P->devs, 0, 1, 1);
   P->launches++;
   CK(cudaGetLastError());
-  if (P->count > 1) CK(cudaMemsetAsync(P->guard, 0, sizeof(unsigned), P->stream));
   if (!P->run_exec && (rc = build_run_graph(P))) return rc;
+  if (P->count > 1 && P->glo.size() > 1) {
+    for (size_t g = 0; g < P->glo.size(); ++g)
+      CK(cudaMemsetAsync((char *)P->sts[P->order[P->glo[g]]] + offsetof(State, batch_guard), 0, sizeof(unsigned),
+                         P->stream));
+  } else if (P->count > 1) {
+    CK(cudaMemsetAsync(P->guard, 0, sizeof(unsigned), P->stream));
+  }
   CK(cudaGraphLaunch(P->run_exec, P->stream));
   if (any_prec(P)) {                        // double-double contraction of the final sets
     timed(P, KT_CONTRACT, [&] { k_dd_factor<<<dim3(P->max_ni, 1, P->count), 256, 0, P->stream>>>(P->devs); });
@@ -939,6 +1008,16 @@ static int run_all(ttq_plan *P) {
   if (P->use_graph && !P->timing && !P->sequential) {
     if ((rc = enqueue_run(P))) return rc;
     if ((rc = read_states(P))) return rc;
+    if (P->count > 1) {
+      // each WHILE loop of the batch: its iterations (its condition kernel's
+      // count) times the kernels of one iteration
+      const bool grouped = P->glo.size() > 1;
+      for (size_t g = 0; g < P->gkernels.size(); ++g) {
+        const State &S0 = P->hst[grouped ? P->order[P->glo[g]] : 0];
+        P->launches += (long long)P->gkernels[g] * S0.batch_guard;
+      }
+      return TTQ_OK;
+    }
     int mx = 0;
     for (int q = 0; q < P->count; ++q) mx = P->hst[q].loop_guard > mx ? P->hst[q].loop_guard : mx;
     P->launches += (long long)P->sweep_kernels * mx;
@@ -1078,6 +1157,16 @@ extern "C" int ttq_batch_autotune(ttq_plan *P, int sweeps, int32_t *chosen) {
   if (P->sweep_exec) { cudaGraphExecDestroy(P->sweep_exec); P->sweep_exec = nullptr; }
   if (chosen) { chosen[0] = P->cblocks; chosen[1] = P->sblocks; chosen[2] = P->grid_eval; chosen[3] = P->rook_rmax; }
   return rc;
+}
+
+extern "C" int ttq_batch_set_groups(ttq_plan *P, int groups) {
+  if (!P) return set_err(TTQ_ERR_INVALID_ARG, "null plan");
+  if (P->count < 2 || !P->devs_sorted) return set_err(TTQ_ERR_INVALID_ARG, "groups need a batch of two or more instances");
+  if (groups < 1 || groups > TTQ_MAX_BATCH_GROUPS || groups > P->count / 2 + (groups == 1 ? 1 : 0))
+    return set_err(TTQ_ERR_INVALID_ARG, "groups must be in 1..min(8, count / 2)");
+  P->ngroups = groups;
+  if (P->run_exec) { cudaGraphExecDestroy(P->run_exec); P->run_exec = nullptr; }
+  return TTQ_OK;
 }
 
 extern "C" int ttq_plan_set_rook_rows(ttq_plan *P, int rmax) {

@@ -67,6 +67,21 @@ def test_grid_shapes_and_autotune_do_not_change_results():
     assert b.run() == ref
 
 
+def test_concurrent_groups_do_not_change_results():
+    """The batch's run graph as 1, 2 or 4 concurrent groups of cost-sorted
+    instances: the same results bit for bit."""
+    from paper_1903_11554_gb300 import binding
+    probs = mix()
+    b = binding.Batch(probs)
+    b.set_groups(1)
+    ref = b.run()
+    for groups in (2, 4):
+        b.set_groups(groups)
+        assert b.run() == ref
+    with pytest.raises(binding.TTQError):
+        b.set_groups(len(probs))
+
+
 def test_batch_plain_launches_match_graph():
     from paper_1903_11554_gb300 import binding
     probs = mix()[:4]
