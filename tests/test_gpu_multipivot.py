@@ -48,6 +48,7 @@ CASES = {
     "D_rn_4": lambda: inputs.make_problem("D", "rn", 6, 49, L=12.0, rank_cap=16, npiv=4),
     "D_cube_2": lambda: inputs.make_problem("D", "cube", 7, 33, rank_cap=16, npiv=2),
     "E_cube_4": lambda: inputs.make_problem("E", "cube", 9, 33, rank_cap=16, npiv=4),
+    "E_cube_3_r0_2_dd": lambda: inputs.make_problem("E", "cube", 7, 33, rank_cap=14, npiv=3, r0=2, precision="dd"),
 }
 
 
