@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "integrals/s & fiber evals/s at rel.err<=1e-12 vs plain sweep; p50/p99 latency"
 # DRAM bytes (read + write) per launch of the kernels the roofline may name,
-# from one ncu capture each (profiles/, plain launches of this bench on the
+# from one ncu capture each (plain launches of this bench on the
 # D_12 workload); null for a kernel whose code changed after its capture
 NCU_TRAFFIC = {"k_solve": {"bytes_per_launch": 858453, "capture": "profiles/k_solve_d12.md: launches 301-303 "
                            "(sweep ~50), dram__bytes_read.sum + dram__bytes_write.sum"}}

@@ -547,7 +547,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
       occ = 0;
     // the resident CTA slots less two for the contraction's chains on the second stream
     P->search_grid = occ >= 1 ? sms * occ - 2 : 0;
-    P->persistent = 0;                      // opt in with ttq_plan_set_search (measured slower, see DESIGN)
+    P->persistent = 0;                      // opt in with ttq_plan_set_search: measured slower than the staged launches
     cudaGetLastError();
   }
 }
