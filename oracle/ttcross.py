@@ -38,9 +38,11 @@ Readings where the paper is silent:
     current cores, and r_k < rank cap;
   * several pivots per interface per sweep (npiv > 1, a rank-adaptive variant
     of Alg. 6, which adds one): the npiv best samples with distinct rows and
-    columns start rook searches on the old residual, and greedy complete
-    pivoting on the residual matrix of their rows and columns keeps the pairs
-    whose Schur pivot passes the acceptance threshold (pivot_search_multi);
+    columns start rook searches on the old residual (a search that meets an
+    earlier one at the same step stops there, its end being the earlier one's),
+    and greedy complete pivoting on the residual matrix of their rows and
+    columns keeps the pairs whose Schur pivot passes the acceptance threshold
+    (pivot_search_multi);
   * stopping: relative internal convergence |I_s - I_{s-1}| <= tol |I_s|, or
     no pivot accepted in a sweep, or every interface at the rank cap, or the
     sweep limit.
@@ -320,6 +322,7 @@ class Pivot:
     accepted: bool
     rounds: int
     evals: int
+    merged: bool = False   # several pivots per sweep: stopped where it met an earlier search
 
 
 @dataclasses.dataclass
@@ -371,14 +374,18 @@ def _sample_scores(problem, sb: _Superblock, k: int, sweep: int):
     return srows, scols, score, int(ok.sum())
 
 
-def _rook(problem, sb: _Superblock, row: int, col: int, scale: float):
+def _rook(problem, sb: _Superblock, row: int, col: int, scale: float, trace: Optional[list] = None):
     """Rook pivoting from the start (row, col): alternate column and row
     searches until the rook condition, Eq. (2), holds or the round budget is
     spent.  The condition is tested after each search: a column search that
     returns the row searched in the previous round ends the search, since that
     row search returned the current column (the pivot already dominates its
     row and its column, and a repeated row search would return the same
-    pivot).  Returns (row, col, E at the pivot, rounds, evaluations)."""
+    pivot).  Returns (row, col, E at the pivot, rounds, evaluations).
+    trace (a list, or None): gets one entry per search run, in order,
+    (kind, row, col, evaluations): kind "c" for a column search (along col,
+    row the current row), "r" for a row search (along row, col the current
+    column)."""
     rows_all = np.arange(sb.M)
     cols_all = np.arange(sb.Ncol)
     err = 0.0
@@ -390,12 +397,16 @@ def _rook(problem, sb: _Superblock, row: int, col: int, scale: float):
         cscore = np.full(sb.M, -1.0)
         cscore[sb.row_ok] = np.abs(sb.residual(rows_all[sb.row_ok], np.full(int(sb.row_ok.sum()), col)))
         evals += int(sb.row_ok.sum())
+        if trace is not None:
+            trace.append(("c", row, col, int(sb.row_ok.sum())))
         row = tie_argmax(cscore, scale)
         if row == prev_row:
             break
         rres = np.zeros(sb.Ncol)
         rres[sb.col_ok] = sb.residual(np.full(int(sb.col_ok.sum()), row), cols_all[sb.col_ok])
         evals += int(sb.col_ok.sum())
+        if trace is not None:
+            trace.append(("r", row, col, int(sb.col_ok.sum())))
         rscore = np.where(sb.col_ok, np.abs(rres), -1.0)
         new_col = tie_argmax(rscore, scale)
         err = float(rres[new_col])
@@ -483,7 +494,7 @@ class MultiPivot:
 
 
 def pivot_search_multi(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np.ndarray,
-                       sweep: int, scale: float, npiv: int) -> Optional[MultiPivot]:
+                       sweep: int, scale: float, npiv: int, meet: bool = True) -> Optional[MultiPivot]:
     """Up to npiv pivots on superblock k in one sweep (a rank-adaptive variant;
     Alg. 6 itself adds one).  On the residual of the sweep's old cross:
       1. starts: the npiv best random samples, taken one at a time as the
@@ -491,7 +502,12 @@ def pivot_search_multi(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np
          those of the starts already taken;
       2. rook pivoting (Alg. 2) from each start;
       3. a search whose row or column equals that of an earlier search is
-         dropped;
+         dropped; a search that meets an earlier search still running at the
+         same stage (the same column to search in a column step, the same row
+         in a row step) stops there: from that stage on both searches take the
+         same steps and end on the same pivot (only the round that ends them
+         may differ by a half, and then the later one ends on the earlier
+         one's pivot), which this rule would drop;
       4. the residuals at the remaining searches' rows x_a and columns y_c
          form the matrix M (M_aa: search a's own residual; the others fresh
          evaluations);
@@ -504,7 +520,8 @@ def pivot_search_multi(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np
     Each accepted pair extends the cross by a row and a column whose Schur
     pivot is nonzero, so the new cross matrix stays nonsingular:
     det G_k' = det G_k times the product of the accepted pivots.  With
-    npiv = 1 this is exactly pivot_search."""
+    npiv = 1 this is exactly pivot_search.  meet=False runs every search to
+    its end (for the tests of the meeting rule)."""
     sb = _superblock(problem, st, k, B, Ynext)
     if sb is None:
         return None
@@ -520,13 +537,33 @@ def pivot_search_multi(problem, st: CrossState, k: int, B: np.ndarray, Ynext: np
     if not starts:
         return None
     searches: List[Pivot] = []
+    ran: List[int] = []                  # per search: the stages it ran before it ended or met another
+    traces: List[list] = []
     for t in starts:
-        row, col, err, rounds, ev = _rook(problem, sb, int(srows[t]), int(scols[t]), scale)
+        tr: list = []
+        row, col, err, rounds, ev = _rook(problem, sb, int(srows[t]), int(scols[t]), scale, tr)
+        # stage s of every search is the same step of the sweep (column and row
+        # searches alternate from the first column search on)
+        n = len(tr)
+        for s_, (kind, r_, c_, _) in enumerate(tr if meet else []):
+            pos = c_ if kind == "c" else r_
+            if any(s_ < ran[q] and (traces[q][s_][2] if kind == "c" else traces[q][s_][1]) == pos
+                   for q in range(len(searches))):
+                n = s_
+                break
+        if n < len(tr):
+            ev = sum(e for *_, e in tr[:n])
+            _, row, col, _ = tr[n]
+            searches.append(Pivot(k=k, row=row, col=col, err=0.0, accepted=False, rounds=n // 2 + 1, evals=ev,
+                                  merged=True))
+        else:
+            searches.append(Pivot(k=k, row=row, col=col, err=err, accepted=False, rounds=rounds, evals=ev))
         evals += ev
-        searches.append(Pivot(k=k, row=row, col=col, err=err, accepted=False, rounds=rounds, evals=ev))
+        ran.append(n)
+        traces.append(tr)
     kept: List[Pivot] = []
     for pv in searches:
-        if not any(pv.row == q.row or pv.col == q.col for q in kept):
+        if not pv.merged and not any(pv.row == q.row or pv.col == q.col for q in kept):
             kept.append(pv)
     m = len(kept)
     Mx = np.empty((m, m))

@@ -53,6 +53,8 @@ struct IfaceState {
                                   // (column step), modes ..k-1 of rho (row step)
   unsigned epoch;                 // persistent search: stages of this sweep finished so far
   unsigned acc_arrive;            // several pivots per sweep: searches of the interface that ended (last decisions)
+  int merged;                     // several pivots per sweep: stopped where it met an earlier search (its end
+                                  // is that search's pivot)
 };
 
 struct State {

@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(256) k_qr(Dev *const *Dps) {
     IfaceState &I = search_state(D, st, k, threadIdx.x);
     I.active = 0; I.rook_done = 0; I.row = I.col = -1; I.rounds = 0; I.accepted = 0;
     I.err = 0.0; I.evals = 0; I.smax_bits = 0ULL; I.stage_count = 0; I.items_done = 0; I.epoch = 0;
-    I.acc_arrive = 0;
+    I.acc_arrive = 0; I.merged = 0;
   }
   if (have == r) {
     if (threadIdx.x == 0) st->it[k].prank = -1;
@@ -1700,7 +1700,7 @@ __device__ void multi_accept(const Dev &D, State *st, int k, bool append) {
     int m = 0;
     for (int j = 0; j < D.npiv; ++j) {
       IfaceState &I = search_state(D, st, k, j);
-      if (!__ldcg(&I.active)) continue;
+      if (!__ldcg(&I.active) || __ldcg(&I.merged)) continue;
       const int rw = __ldcg(&I.row), cl = __ldcg(&I.col);
       bool dup = false;
       for (int q = 0; q < m; ++q) dup |= (kr[q] == rw) || (kc[q] == cl);
@@ -1882,6 +1882,9 @@ __global__ void __launch_bounds__(256) k_solve(Dev *const *Dps, int mode, int fi
   }
   pdl_wait();
   pdl_release();
+  // a search that met an earlier one in the preceding rook step stops (set by
+  // that step, so read after the wait and through L2)
+  if (MULTI && work && __ldcg(&search_state(D, st, k, j).merged)) work = false;
   if (work)
     stage_finish(D, k, j, mode, Fs, Qs, sc.ri, sc, true);
   else
@@ -2439,15 +2442,40 @@ __device__ __forceinline__ void rows_publish(const Dev &D, IfaceState &I, int k,
 //    no sparse second wave of items trails the first.
 // Lane k-1 of the warp holds interface k's outer rank and nodes; pieces come
 // out as (interface, outer index, first row, rows).
-// the searches of interface k that still run a rook step (bit j: search j)
+// the searches of interface k that run the rook step (bit j: search j).  With
+// several searches, one that meets an earlier running search at this step
+// (stage 1, a column step: the same column to search; stage 2, a row step:
+// the same row) stops: from here both take the same steps and end on the same
+// pivot, which the acceptance would drop as a repeat.  Those go to *newly.
 template <bool MULTI>
-__device__ __forceinline__ unsigned running_searches(const Dev &D, State *st, int k) {
-  unsigned m = 0;
+__device__ __forceinline__ unsigned running_searches(const Dev &D, State *st, int k, int stage,
+                                                     unsigned *newly = nullptr) {
+  unsigned m = 0, mg = 0;
+  int pos[TTQ_MAXP] = {-1, -1, -1, -1};
   for (int j = 0; j < (MULTI ? D.npiv : 1); ++j) {
     const IfaceState &I = search_state(D, st, k, j);
-    if (I.active && !I.rook_done) m |= 1u << j;
+    if (!I.active || I.rook_done) continue;
+    if constexpr (MULTI) {
+      if (I.merged) continue;
+      const int p = stage == 1 ? I.col : I.row;
+      bool meet = false;
+      for (int q = 0; q < j; ++q) meet |= ((m >> q) & 1u) && pos[q] == p;
+      pos[j] = p;
+      if (meet) {
+        mg |= 1u << j;
+        continue;
+      }
+    }
+    m |= 1u << j;
   }
+  if (newly) *newly = mg;
   return m;
+}
+// the searches of interface k that met an earlier one (bits of m) stop: the
+// decisions kernel after this step and the acceptance skip them
+__device__ __forceinline__ void mark_met(const Dev &D, State *st, int k, unsigned m) {
+  for (int j = 0; j < TTQ_MAXP; ++j)
+    if ((m >> j) & 1u) search_state(D, st, k, j).merged = 1;
 }
 // the n-th (from 0) set bit of m
 __device__ __forceinline__ int nth_search(unsigned m, int n) {
@@ -2582,13 +2610,15 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
   const int stop = st->stop, search = st->search;
   unsigned act = 0;
   int r0 = 0, r1 = 0, Nl = 1;
+  unsigned met = 0;
   if (lane < d - 1) {
-    act = running_searches<MULTI>(D, st, lane + 1);
+    act = running_searches<MULTI>(D, st, lane + 1, 1, &met);
     r0 = st->r[lane];
     r1 = st->r[lane + 1];
     Nl = D.N[lane];
   }
   if (stop || !search) return;
+  if (MULTI && met && blockIdx.x == 0 && warp_id() == 0) mark_met(D, st, lane + 1, met);
   // an interface's running searches take consecutive blocks of its outer indices
   const int outer = __popc(act) * r0;
   RookDeal dl = rook_deal(D, outer, Nl, rmax);
@@ -2682,13 +2712,15 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
   const int stop = st->stop, search = st->search;
   unsigned act = 0;
   int r1 = 0, r2 = 0, Nl = 1;
+  unsigned met = 0;
   if (lane < d - 1) {
-    act = running_searches<MULTI>(D, st, lane + 1);
+    act = running_searches<MULTI>(D, st, lane + 1, 2, &met);
     r1 = st->r[lane + 1];
     r2 = st->r[lane + 2];
     Nl = D.N[lane + 1];
   }
   if (stop || !search) return;
+  if (MULTI && met && blockIdx.x == 0 && warp_id() == 0) mark_met(D, st, lane + 1, met);
   const int outer = __popc(act) * r2;
   RookDeal dl = rook_deal(D, outer, Nl, rmax);
   unsigned long long fl = 0;

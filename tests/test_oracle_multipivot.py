@@ -13,7 +13,10 @@ Checked against what the mathematics fixes, not against a restatement:
     residual built from Eq. (1);
   * Thm. 2 (exact recovery of a separable tensor of known rank) and the
     printed D_8 (Sec. 5.5, Fig. 7);
-  * a planted mistake in the Schur update fails the determinant identity.
+  * a planted mistake in the Schur update fails the determinant identity;
+  * the meeting rule (a search that meets an earlier running search at the
+    same step stops there) changes no accepted pivot: run to their ends, the
+    searches it stops end on the pivot of the search they met.
 """
 import json
 import os
@@ -142,6 +145,8 @@ def test_rook_condition_of_every_search():
         J = ttcross.cross_cols(p, st, k)
         E = S - S[:, J] @ np.linalg.solve(S[np.ix_(I, J)], S[I, :])
         for pv in mp.searches:
+            if pv.merged:
+                continue
             if pv.rounds < p.rook_max:
                 assert abs(E[pv.row, pv.col]) >= np.max(np.abs(E[pv.row, :])) * (1 - 1e-9)
                 assert abs(E[pv.row, pv.col]) >= np.max(np.abs(E[:, pv.col])) * (1 - 1e-9)
@@ -150,7 +155,7 @@ def test_rook_condition_of_every_search():
         # the residual matrix of the kept searches is E on their rows and columns
         kept = []
         for pv in mp.searches:
-            if not any(pv.row == q.row or pv.col == q.col for q in kept):
+            if not pv.merged and not any(pv.row == q.row or pv.col == q.col for q in kept):
                 kept.append(pv)
         sub = E[np.ix_([q.row for q in kept], [q.col for q in kept])]
         assert np.allclose(mp.cross, sub, rtol=0, atol=1e-10 * abs(E).max())
@@ -205,3 +210,37 @@ def test_planted_schur_sign_fails_the_identity(monkeypatch):
                 broken = True
         st = new
     assert broken
+
+
+@pytest.mark.parametrize("case", [("C", "rn", 5, 41, 10.0, 4), ("D", "rn", 5, 33, 8.0, 4), ("D", "cube", 7, 25, 0.0, 3),
+                                  ("E", "cube", 6, 21, 0.0, 4)])
+def test_meeting_rule_keeps_the_pivots(case):
+    fam, form, n, N, L, npiv = case
+    kw = dict(rank_cap=14, seed=5, npiv=npiv)
+    p = inputs.make_problem(fam, form, n, N, L=L, **kw) if form == "rn" else inputs.make_problem(fam, form, n, N, **kw)
+    st = ttcross.initial_state(p)
+    merged = 0
+    for s in range(5):
+        cores, scale = _prepare(p, st)
+        for k in range(1, p.d):
+            B = ttcross.maxvol_coefficients(cores[k - 1], ttcross.cross_rows(p, st, k))
+            a = ttcross.pivot_search_multi(p, st, k, B, cores[k], s, scale, npiv)
+            b = ttcross.pivot_search_multi(p, st, k, B, cores[k], s, scale, npiv, meet=False)
+            if a is None:
+                assert b is None
+                continue
+            assert [(q.row, q.col, q.err) for q in a.pivots] == [(q.row, q.col, q.err) for q in b.pivots]
+            assert np.array_equal(a.cross, b.cross)
+            assert a.evals <= b.evals
+            full = b.searches
+            for j, pv in enumerate(a.searches):
+                if not pv.merged:
+                    assert (pv.row, pv.col, pv.err, pv.evals) == (full[j].row, full[j].col, full[j].err, full[j].evals)
+                    continue
+                merged += 1
+                assert pv.evals < full[j].evals
+                # run to its end it stops on the pivot of an earlier search
+                assert any((full[q].row, full[q].col) == (full[j].row, full[j].col) for q in range(j))
+        pv_all = ttcross.search_all(p, st, s, cores, scale)
+        st = ttcross.apply_pivots(p, st, pv_all)
+    assert merged > 0
