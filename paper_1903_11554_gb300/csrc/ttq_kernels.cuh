@@ -1235,9 +1235,11 @@ __global__ void __launch_bounds__(256) k_contract(Dev *const *Dps, int final_dd)
 // dependent rounds of global reads.  qbits: blockDim.x words of shared scratch
 // (stage 2 marks the qualifying items there, TTQ_MAXR * TTQ_MAX_NODES / 32 bits
 // at most).  vrow (stage 1, may be null): L_k(rho*, :) (r entries) is read into
-// it by the warp that finds rho*, before the block learns the result.
+// it by the warp that finds rho*, before the block learns the result, and with
+// it, into fm, the node indices of rho*'s modes 0 .. k-1 (the next row step's
+// fixed modes), in the same round of loads.
 __device__ int stage_pick(const Dev &D, int k, int j, int stage, double *e_out, unsigned *qbits,
-                          double *vrow = nullptr, int r = 0) {
+                          double *vrow = nullptr, int r = 0, int *fm = nullptr) {
   __shared__ int si[TTQ_WARPS];
   __shared__ double se[TTQ_WARPS];
   State *st = D.st;
@@ -1362,7 +1364,9 @@ __device__ int stage_pick(const Dev &D, int k, int j, int stage, double *e_out, 
         }
         if (f != 0x7fffffff) {
           const int ai = f / Nm, ii = f % Nm;
+          const int fmv = lane < k - 1 ? D.lidx[k - 1][ai * D.d + lane] : ii;
           for (int b = lane; b < r; b += 32) vrow[b] = D.Y[k][core_at(D, k, ai, ii, b)];
+          if (fm && lane < k) fm[lane] = fmv;
         }
       }
     }
@@ -1474,8 +1478,13 @@ __device__ void stage_finish(const Dev &D, int k, int j, int mode, const double 
   const double *F = Fs ? Fs : (mode == 1 ? D.Sr[k] : D.Cc[k]);
   const int fld = Fs ? r : ld;
   unsigned *qb = reinterpret_cast<unsigned *>(sc.part);   // free until the solve's products
+  __shared__ int fm[TTQ_MAXD];
   double e;
   int col = -1, row = -1, spick = -1;
+  // the search state the rook test reads, loaded with the argmax's first round
+  // (nothing writes it before the argmax's barriers)
+  const int prev_row = mode == 1 ? __ldcg(&I.row) : 0, prev_col = mode == 2 ? __ldcg(&I.col) : 0;
+  const int done_rounds = mode != 0 ? __ldcg(&I.rounds) : 0;
   if (mode == 0) {
     int pick = pick_in;
     if (pick_in >= 0) e = e_in;
@@ -1489,9 +1498,8 @@ __device__ void stage_finish(const Dev &D, int k, int j, int mode, const double 
       if (tid == 0) { I.row = row; I.col = col; I.err = e; I.active = 1; }
     }
   } else if (mode == 1) {
-    const int pick = stage_pick(D, k, j, 1, &e, qb, v, r);   // L_k(rho*, :) lands in v
-    const int prev = __ldcg(&I.row), done_rounds = __ldcg(&I.rounds);
-    __syncthreads();                             // every thread has read the previous row
+    const int pick = stage_pick(D, k, j, 1, &e, qb, v, r, fm);   // L_k(rho*, :) lands in v, its modes in fm
+    const int prev = prev_row;
     // Eq. 2 already holds when the column search returns the row searched in the
     // previous round: that search returned the current column, so the pivot
     // dominates its row and its column and the search ends without a row search
@@ -1507,16 +1515,14 @@ __device__ void stage_finish(const Dev &D, int k, int j, int mode, const double 
     if (pick < 0) {
       if (tid == 0) I.active = 0;
     } else {
-      const int rounds = __ldcg(&I.rounds) + 1;
-      const bool done = (pick == __ldcg(&I.col)) || rounds >= D.rook_max;
-      __syncthreads();                           // every thread has read I.col
+      const int rounds = done_rounds + 1;
+      const bool done = (pick == prev_col) || rounds >= D.rook_max;
       if (tid == 0) { I.rounds = rounds; I.col = pick; I.err = e; I.rook_done = done ? 1 : 0; }
       if (!done) col = pick;
     }
   }
   const bool colsolve = mode != 1 && col >= 0, rowsolve = mode == 1 && row >= 0;
   const bool tab = uses_ptab(D, r) && (colsolve || rowsolve) && blockDim.x > 32;
-  __shared__ int fm[TTQ_MAXD];
   int nfm = 0;
   // the node indices the next rook step fixes go to I.fix, so that its work
   // items read them in their first round of loads
@@ -1530,12 +1536,8 @@ __device__ void stage_finish(const Dev &D, int k, int j, int mode, const double 
       I.fix[k + tid] = fm[tid];
     }
   } else if (rowsolve) {
-    const int Nk = D.N[k - 1], alpha = row / Nk, i0 = row % Nk;
-    nfm = k;                                     // modes 0 .. k-1
-    if (tid < nfm) {
-      fm[tid] = tid == k - 1 ? i0 : D.lidx[k - 1][alpha * D.d + tid];
-      I.fix[tid] = fm[tid];
-    }
+    nfm = k;                                     // modes 0 .. k-1, read with L_k(rho*, :) by the argmax
+    if (tid < nfm) I.fix[tid] = fm[tid];
   }
   if (staging_in_flight) cp_async_wait_all();   // factors copied under the argmax
   __syncthreads();
