@@ -61,6 +61,7 @@ struct ttq_plan {
   int max_ni, rook_max, max_sweeps, max_cap;
   int grid_eval, sblocks, cblocks, rblocks, max_sum_n;
   int qr_smem, samples_smem, contract_smem, solve_smem;
+  int tsm_smem;             // kernel (a) and rook steps: room for the pair table of D in R^n (N doubles)
   long long launches;
   State *hst;               // pinned host mirror of the states (count entries)
   int timing;               // 1: bracket every launch with CUDA events
@@ -467,8 +468,23 @@ static int host_inputs(const ttq_problem *p, cudaStream_t s, std::vector<double>
 }
 
 // launch configuration from the instances' problems (maxima over the set)
+// The dynamic shared memory a kernel may take is a property of the function,
+// shared by every plan of the process: it is only ever raised, so a plan made
+// later with smaller factors does not lower it under one made earlier.
+static std::mutex g_smem_mu;
+template <typename K>
+static cudaError_t allow_smem(K kern, int bytes) {
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if (bytes <= fa.maxDynamicSharedSizeBytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 static void configure(ttq_plan *P, const ttq_problem *probs, int count, const Layout *Ls) {
   P->max_ni = 0; P->rook_max = 1; P->max_sweeps = 1; P->max_cap = 1; P->max_sum_n = 1; P->npiv = 1;
+  P->tsm_smem = 0;
   P->rook_rmax = 4;
   P->sblocks = P->cblocks = P->rblocks = 1;
   size_t maxfib = 0;
@@ -483,6 +499,12 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     int sn = 0;
     for (int k = 0; k < p->d; ++k) sn += p->nodes_per_mode[k];
     P->max_sum_n = sn > P->max_sum_n ? sn : P->max_sum_n;
+    if (p->family == TTQ_FAMILY_D && p->form == TTQ_FORM_RN) {
+      bool eqN = true;
+      for (int k = 1; k < p->d; ++k) eqN = eqN && p->nodes_per_mode[k] == p->nodes_per_mode[0];
+      const int tb = eqN ? p->nodes_per_mode[0] * 8 : 0;
+      P->tsm_smem = tb > P->tsm_smem ? tb : P->tsm_smem;
+    }
     size_t fib = 0;
     for (int k = 1; k <= p->d; ++k) fib += (size_t)((k == 1) ? 1 : cap) * ((k == p->d) ? 1 : cap);
     maxfib = fib > maxfib ? fib : maxfib;
@@ -494,7 +516,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   {
     int dev = 0, sms = 152, occ = 3;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col<false>, TTQ_WARPS * 32, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col<false>, TTQ_WARPS * 32, P->tsm_smem) != cudaSuccess ||
         occ < 1)
       occ = 1;
     const int slots = sms * occ;
@@ -507,7 +529,8 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     // (one CTA per interface, on the second stream) find room beside it at once
     // instead of waiting for its CTAs to retire
     int occe = 3;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occe, k_eval_slabs, TTQ_WARPS * 32, 0) != cudaSuccess || occe < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occe, k_eval_slabs, TTQ_WARPS * 32, P->tsm_smem) != cudaSuccess ||
+        occe < 1)
       occe = 1;
     size_t ge = (maxfib + TTQ_WARPS - 1) / TTQ_WARPS;
     ge = ge < 1 ? 1 : ge;
@@ -519,7 +542,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     int occs = 1;
     const size_t cap0 = P->max_cap;
     const size_t ssm = (((cap0 <= 96) ? 2 : 1) * cap0 * cap0 + (size_t)TTQ_WARPS * TTQ_SPW * 2 * (cap0 + 1)) * 8;
-    cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+    allow_smem(k_samples, (int)ssm);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occs, k_samples, TTQ_WARPS * 32, ssm) != cudaSuccess || occs < 1)
       occs = 1;
     const int per = (sms * occs) / std::max(1, P->max_ni * count);
@@ -542,7 +565,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
     P->search_smem = (int)((q_in ? 2 : 1) * cap * cap * 8 + scr);
     int dev = 0, sms = 152, occ = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem);
+    allow_smem(k_search, P->search_smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, TTQ_WARPS * 32, P->search_smem) != cudaSuccess)
       occ = 0;
     // the resident CTA slots less two for the contraction's chains on the second stream
@@ -554,22 +577,20 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
 
 static cudaError_t set_smem_attributes(ttq_plan *P) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_qr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_qr_row, cudaFuncAttributeMaxDynamicSharedMemorySize, P->qr_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_samples, cudaFuncAttributeMaxDynamicSharedMemorySize, P->samples_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, P->contract_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, P->search_smem)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, P->solve_smem);
+  if ((e = allow_smem(k_qr<false>, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_qr<true>, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_qr_row, P->qr_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_solve<false>, P->solve_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_solve<true>, P->solve_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_samples, P->samples_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_contract, P->contract_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_search, P->search_smem)) != cudaSuccess) return e;
+  // the pair table's room (beside the rook steps' 39 KB of static shared memory)
+  if ((e = allow_smem(k_eval_slabs, P->tsm_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_rook_col<false>, P->tsm_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_rook_col<true>, P->tsm_smem)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_rook_row<false>, P->tsm_smem)) != cudaSuccess) return e;
+  return allow_smem(k_rook_row<true>, P->tsm_smem);
 }
 
 static void plan_free(ttq_plan *P) {
@@ -737,7 +758,7 @@ static void enqueue_sweep_seq(ttq_plan *P) {
   const dim3 W(TTQ_WARPS * 32), T(256);
   auto refresh = [&] {
     timed(P, KT_QR, [&] { k_qr_row<<<dim3(ni, 1, nb), 256, P->qr_smem, s>>>(dv); });
-    timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, 0, s>>>(dv); });
+    timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, P->tsm_smem, s>>>(dv); });
     timed(P, KT_QR, [&] { k_qr<false><<<dim3(ni, 1, nb), T, P->qr_smem, s>>>(dv); });
   };
   refresh();
@@ -747,9 +768,13 @@ static void enqueue_sweep_seq(ttq_plan *P) {
     P->launches++;
     timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), W, P->samples_smem, s>>>(dv); });
     for (int q = 0; q < P->rook_max; ++q) {
-      timed(P, KT_ROOK_COL, [&] { k_rook_col<false><<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
+      timed(P, KT_ROOK_COL, [&] {
+        k_rook_col<false><<<dim3(P->cblocks, 1, nb), W, P->tsm_smem, s>>>(dv, P->rook_rmax);
+      });
       timed(P, KT_SOLVE, [&] { k_solve<false><<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 1, 0, P->cond, 0); });
-      timed(P, KT_ROOK_ROW, [&] { k_rook_row<false><<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax); });
+      timed(P, KT_ROOK_ROW, [&] {
+        k_rook_row<false><<<dim3(P->rblocks, 1, nb), W, P->tsm_smem, s>>>(dv, P->rook_rmax);
+      });
       timed(P, KT_SOLVE, [&] { k_solve<false><<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 2, 0, P->cond, 0); });
     }
     timed(P, KT_UPDATE, [&] { k_seq_end<<<dim3(1, 1, nb), T, 0, s>>>(dv, k, k == ni ? 1 : 0); });
@@ -783,9 +808,9 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   // except as the first node of the run graph's body, where nothing precedes it
   // and a plain launch lets the QR row kernel beside it start at once
   if (P->in_loop && head)
-    timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, 0, s>>>(dv); });
+    timed(P, KT_EVAL, [&] { k_eval_slabs<<<dim3(P->grid_eval, 1, nb), W, P->tsm_smem, s>>>(dv); });
   else
-    timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, 0, s, dv); });
+    timed(P, KT_EVAL, [&] { launch_k(P, k_eval_slabs, dim3(P->grid_eval, 1, nb), W, P->tsm_smem, s, dv); });
   if (P->s2) cudaStreamWaitEvent(s, P->join, 0);
   const bool multi = P->npiv > 1;
   timed(P, KT_QR, [&] { launch_k(P, multi ? k_qr<true> : k_qr<false>, dim3(ni, 1, nb), T, P->qr_smem, s, dv); });
@@ -814,14 +839,16 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   for (int q = 0; q < P->rook_max; ++q) {
     const bool fin = q == P->rook_max - 1;
     timed(P, KT_ROOK_COL, [&] {
-      launch_k(P, multi ? k_rook_col<true> : k_rook_col<false>, dim3(P->cblocks, 1, nb), W, 0, s, dv, P->rook_rmax);
+      launch_k(P, multi ? k_rook_col<true> : k_rook_col<false>, dim3(P->cblocks, 1, nb), W, P->tsm_smem, s, dv,
+               P->rook_rmax);
     });
     timed(P, KT_SOLVE, [&] {
       launch_k(P, multi ? k_solve<true> : k_solve<false>, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 1, 0,
                P->cond, 0);
     });
     timed(P, KT_ROOK_ROW, [&] {
-      launch_k(P, multi ? k_rook_row<true> : k_rook_row<false>, dim3(P->rblocks, 1, nb), W, 0, s, dv, P->rook_rmax);
+      launch_k(P, multi ? k_rook_row<true> : k_rook_row<false>, dim3(P->rblocks, 1, nb), W, P->tsm_smem, s, dv,
+               P->rook_rmax);
     });
     if (fin && P->s2) cudaStreamWaitEvent(s, P->join, 0);
     timed(P, fin ? KT_UPDATE : KT_SOLVE, [&] {

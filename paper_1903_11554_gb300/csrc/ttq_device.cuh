@@ -328,7 +328,20 @@ struct FiberU {
   int npair;      // unit-cube A_n: number of pairs (i, j) whose product contains x_F
   int fl_node;    // FP64 operations per node of this fiber (the lane-local part)
   int fl_uniform; // FP64 operations of the fiber's shared part
+  const double *T;  // D in R^n on one uniform grid: the pair table (the CTA's shared copy, else D.T)
 };
+
+// The pair table T of D in R^n on one uniform grid copied to the CTA's shared
+// memory (dyn: the launch's dynamic shared memory); null when the problem has
+// none or the launch gave it less than N doubles.  Constant for the plan, so it is copied before the
+// kernel's wait; the caller's barrier orders the copy before its reads.
+__device__ __forceinline__ const double *stage_pair_table(const Dev &D, double *dyn) {
+  unsigned bytes;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(bytes));
+  if (!D.uniformT || D.N[0] > (int)(bytes / 8)) return nullptr;
+  for (int t = threadIdx.x; t < D.N[0]; t += blockDim.x) dyn[t] = D.T[t];
+  return dyn;
+}
 
 // q-th pair (a, b), a < b, of d modes in row order: the row from the
 // triangular-number inverse a = d - 2 - floor((sqrt(4 d (d-1) - 7 - 8 q) - 1) / 2)
@@ -341,12 +354,16 @@ __device__ __forceinline__ void pair_of(int q, int d, int &a, int &b) {
   b = q + a + 1 - d * (d - 1) / 2 + (d - a) * (d - a - 1) / 2;
 }
 
-// m: warp-uniform node indices (shared memory); plist: per-warp scratch of TTQ_MAXPAIR doubles
-__device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m, double *plist) {
+// m: warp-uniform node indices (shared memory); plist: per-warp scratch of TTQ_MAXPAIR doubles;
+// Ts: the CTA's shared-memory copy of the pair table T, or null (T read from global memory)
+__device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m, double *plist,
+                                              const double *Ts = nullptr) {
   const int lane = threadIdx.x & 31;
   const int d = D.d;
   FiberU u;
   u.P = 1.0; u.S = 0.0; u.aL = u.bL = u.aR = u.bR = 0.0; u.npair = 0;
+  u.T = Ts ? Ts : D.T;
+  const double *T = u.T;
   double wj = 1.0;
   const bool mine = lane < d && lane != f;
   const int oj = mine ? D.off[lane] + m[lane] : 0;
@@ -367,7 +384,7 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
         pair_of(q, d, a, b);
         if (a != f && b != f) {
           const int dm = m[a] - m[b];
-          tp[qq] = D.T[dm < 0 ? -dm : dm];
+          tp[qq] = T[dm < 0 ? -dm : dm];
         }
       }
     }
@@ -405,7 +422,7 @@ __device__ __forceinline__ FiberU fiber_setup(const Dev &D, int f, const int *m,
         double t2;
         if (D.uniformT) {
           int dm = m[a] - m[b];
-          t2 = D.T[dm < 0 ? -dm : dm];
+          t2 = T[dm < 0 ? -dm : dm];
         } else {
           double t = tanh((D.x[D.off[a] + m[a]] - D.x[D.off[b] + m[b]]) * 0.5);
           t2 = t * t;
@@ -484,7 +501,7 @@ __device__ __forceinline__ double fiber_value_tab(const Dev &D, int f, const int
   for (int j = jlo; j < jhi; ++j) {
     if (j == f) continue;
     const int dm = i - m[j];
-    p *= D.T[dm < 0 ? -dm : dm];
+    p *= u.T[dm < 0 ? -dm : dm];
   }
   return p * (rs * rs);
 }
@@ -511,7 +528,7 @@ __device__ __forceinline__ double fiber_value(const Dev &D, int f, const int *m,
         for (int j = 0; j < d; ++j) {
           if (j == f) continue;
           int dm = i - m[j];
-          p *= D.T[dm < 0 ? -dm : dm];
+          p *= u.T[dm < 0 ? -dm : dm];
         }
       } else {
         const double si = D.x[o];
