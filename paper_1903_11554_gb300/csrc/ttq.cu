@@ -61,7 +61,7 @@ struct ttq_plan {
   int max_ni, rook_max, max_sweeps, max_cap;
   int grid_eval, sblocks, cblocks, rblocks, max_sum_n;
   int qr_smem, samples_smem, contract_smem, solve_smem;
-  int tsm_smem;             // kernel (a) and rook steps: room for the pair table of D in R^n (N doubles)
+  int tsm_smem;             // kernel (a): room for the pair table of D in R^n (N doubles)
   long long launches;
   State *hst;               // pinned host mirror of the states (count entries)
   int timing;               // 1: bracket every launch with CUDA events
@@ -516,7 +516,7 @@ static void configure(ttq_plan *P, const ttq_problem *probs, int count, const La
   {
     int dev = 0, sms = 152, occ = 3;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col<false>, TTQ_WARPS * 32, P->tsm_smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rook_col<false>, TTQ_WARPS * 32, 0) != cudaSuccess ||
         occ < 1)
       occ = 1;
     const int slots = sms * occ;
@@ -585,12 +585,7 @@ static cudaError_t set_smem_attributes(ttq_plan *P) {
   if ((e = allow_smem(k_samples, P->samples_smem)) != cudaSuccess) return e;
   if ((e = allow_smem(k_contract, P->contract_smem)) != cudaSuccess) return e;
   if ((e = allow_smem(k_search, P->search_smem)) != cudaSuccess) return e;
-  // the pair table's room (beside the rook steps' 39 KB of static shared memory)
-  if ((e = allow_smem(k_eval_slabs, P->tsm_smem)) != cudaSuccess) return e;
-  if ((e = allow_smem(k_rook_col<false>, P->tsm_smem)) != cudaSuccess) return e;
-  if ((e = allow_smem(k_rook_col<true>, P->tsm_smem)) != cudaSuccess) return e;
-  if ((e = allow_smem(k_rook_row<false>, P->tsm_smem)) != cudaSuccess) return e;
-  return allow_smem(k_rook_row<true>, P->tsm_smem);
+  return allow_smem(k_eval_slabs, P->tsm_smem);   // the pair table's room
 }
 
 static void plan_free(ttq_plan *P) {
@@ -769,11 +764,11 @@ static void enqueue_sweep_seq(ttq_plan *P) {
     timed(P, KT_SAMPLES, [&] { k_samples<<<dim3(P->sblocks, ni, nb), W, P->samples_smem, s>>>(dv); });
     for (int q = 0; q < P->rook_max; ++q) {
       timed(P, KT_ROOK_COL, [&] {
-        k_rook_col<false><<<dim3(P->cblocks, 1, nb), W, P->tsm_smem, s>>>(dv, P->rook_rmax);
+        k_rook_col<false><<<dim3(P->cblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax);
       });
       timed(P, KT_SOLVE, [&] { k_solve<false><<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 1, 0, P->cond, 0); });
       timed(P, KT_ROOK_ROW, [&] {
-        k_rook_row<false><<<dim3(P->rblocks, 1, nb), W, P->tsm_smem, s>>>(dv, P->rook_rmax);
+        k_rook_row<false><<<dim3(P->rblocks, 1, nb), W, 0, s>>>(dv, P->rook_rmax);
       });
       timed(P, KT_SOLVE, [&] { k_solve<false><<<dim3(ni, 1, nb), T, P->solve_smem, s>>>(dv, 2, 0, P->cond, 0); });
     }
@@ -839,16 +834,14 @@ static void enqueue_sweep(ttq_plan *P, bool loop_end = true, bool head = false) 
   for (int q = 0; q < P->rook_max; ++q) {
     const bool fin = q == P->rook_max - 1;
     timed(P, KT_ROOK_COL, [&] {
-      launch_k(P, multi ? k_rook_col<true> : k_rook_col<false>, dim3(P->cblocks, 1, nb), W, P->tsm_smem, s, dv,
-               P->rook_rmax);
+      launch_k(P, multi ? k_rook_col<true> : k_rook_col<false>, dim3(P->cblocks, 1, nb), W, 0, s, dv, P->rook_rmax);
     });
     timed(P, KT_SOLVE, [&] {
       launch_k(P, multi ? k_solve<true> : k_solve<false>, dim3(ni, P->npiv, nb), T, P->solve_smem, s, dv, 1, 0,
                P->cond, 0);
     });
     timed(P, KT_ROOK_ROW, [&] {
-      launch_k(P, multi ? k_rook_row<true> : k_rook_row<false>, dim3(P->rblocks, 1, nb), W, P->tsm_smem, s, dv,
-               P->rook_rmax);
+      launch_k(P, multi ? k_rook_row<true> : k_rook_row<false>, dim3(P->rblocks, 1, nb), W, 0, s, dv, P->rook_rmax);
     });
     if (fin && P->s2) cudaStreamWaitEvent(s, P->join, 0);
     timed(P, fin ? KT_UPDATE : KT_SOLVE, [&] {

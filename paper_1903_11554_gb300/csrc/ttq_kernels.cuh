@@ -2540,7 +2540,7 @@ __device__ __forceinline__ void rook_piece(RookDeal &q, int k, int ok, int N, in
 // the argmax.  The piece's loads form one round: z, the fiber's left indices,
 // the fixed right indices (I.fix), the cross's parent pointers.
 __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh, int k, int j, int alpha, int q0,
-                                          int nq, int rk, int &zk, unsigned long long &fl, const double *Ts = nullptr) {
+                                          int nq, int rk, int &zk, unsigned long long &fl) {
   const int lane = lane_id(), warp = warp_id(), d = D.d;
   IfaceState &I = search_state(D, st, k, j);
   const int zkey = k + 64 * j;
@@ -2576,7 +2576,7 @@ __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh,
     nex += __popc(bal);
   }
   __syncwarp();
-  FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp], Ts);
+  FiberU u = fiber_setup(D, k - 1, sh.ms[warp], sh.pl[warp]);
   // per node: the entry (the shared right-mode factors come from the step's table), the product, the residual
   const int tabbed = uses_ptab(D, rk) ? (d - k) - 1 : 0;
   fl += (unsigned long long)u.fl_uniform + (unsigned long long)(i1 - i0) * (u.fl_node - tabbed + 2 * rk + 1);
@@ -2604,10 +2604,7 @@ __device__ __forceinline__ void col_piece(const Dev &D, State *st, RookSmem &sh,
 template <bool MULTI>
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev *const *Dps, int rmax) {
   __shared__ Dev sD;
-  extern __shared__ double dyn_t[];
   const Dev &D = stage_dev(Dps, sD);
-  const double *Ts = stage_pair_table(D, dyn_t);
-  __syncthreads();
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -2639,8 +2636,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
     const unsigned am = __shfl_sync(0xffffffffu, act, k - 1);
     int o, q0, nq;
     rook_piece(dl, k, MULTI ? __popc(am) * rl : rl, D.N[k - 1], o, q0, nq);
-    if constexpr (MULTI) col_piece(D, st, sh, k, nth_search(am, o / rl), o % rl, q0, nq, rk, zk, fl, Ts);
-    else col_piece(D, st, sh, k, 0, o, q0, nq, rk, zk, fl, Ts);
+    if constexpr (MULTI) col_piece(D, st, sh, k, nth_search(am, o / rl), o % rl, q0, nq, rk, zk, fl);
+    else col_piece(D, st, sh, k, 0, o, q0, nq, rk, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[4], fl);
 }
@@ -2649,8 +2646,7 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_col(Dev 
 // beta) for the nq rows of 32 nodes j from q0 of fiber beta, E = A(rho*, gamma)
 // - l^T R_{k+1}(:, gamma) with z = G_k^-T l; as col_piece.
 __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh, int k, int j, int beta, int q0,
-                                          int nq, int rk, int rn, int &zk, unsigned long long &fl,
-                                          const double *Ts = nullptr) {
+                                          int nq, int rk, int rn, int &zk, unsigned long long &fl) {
   const int lane = lane_id(), warp = warp_id(), d = D.d;
   IfaceState &I = search_state(D, st, k, j);
   const int zkey = k + 64 * j;
@@ -2685,7 +2681,7 @@ __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh,
     nex += __popc(bal);
   }
   __syncwarp();
-  FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp], Ts);
+  FiberU u = fiber_setup(D, k, sh.ms[warp], sh.pl[warp]);
   const int tabbed = uses_ptab(D, rk) ? k - 1 : 0;
   fl += (unsigned long long)u.fl_uniform + (unsigned long long)(j1 - j0) * (u.fl_node - tabbed + 2 * rk + 1);
   unsigned nel = 0, nev = 0;
@@ -2712,10 +2708,7 @@ __device__ __forceinline__ void row_piece(const Dev &D, State *st, RookSmem &sh,
 template <bool MULTI>
 __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev *const *Dps, int rmax) {
   __shared__ Dev sD;
-  extern __shared__ double dyn_t[];
   const Dev &D = stage_dev(Dps, sD);
-  const double *Ts = stage_pair_table(D, dyn_t);
-  __syncthreads();
   pdl_wait();
   pdl_release();
   State *st = D.st;
@@ -2744,8 +2737,8 @@ __global__ void __launch_bounds__(TTQ_WARPS * 32, TTQ_ROOK_CTAS) k_rook_row(Dev 
     const unsigned am = __shfl_sync(0xffffffffu, act, k - 1);
     int o, q0, nq;
     rook_piece(dl, k, MULTI ? __popc(am) * rn : rn, D.N[k], o, q0, nq);
-    if constexpr (MULTI) row_piece(D, st, sh, k, nth_search(am, o / rn), o % rn, q0, nq, rk, rn, zk, fl, Ts);
-    else row_piece(D, st, sh, k, 0, o, q0, nq, rk, rn, zk, fl, Ts);
+    if constexpr (MULTI) row_piece(D, st, sh, k, nth_search(am, o / rn), o % rn, q0, nq, rk, rn, zk, fl);
+    else row_piece(D, st, sh, k, 0, o, q0, nq, rk, rn, zk, fl);
   }
   if (lane == 0 && fl) atomicAdd(&st->flops[5], fl);
 }
