@@ -31,7 +31,7 @@ METRIC = "integrals/s & fiber evals/s at rel.err<=1e-12 vs plain sweep; p50/p99 
 # DRAM bytes (read + write) per launch of the kernels the roofline may name,
 # from one ncu capture each (plain launches of this bench on the
 # D_12 workload); null for a kernel whose code changed after its capture
-NCU_TRAFFIC = {"k_solve": {"bytes_per_launch": 858453, "capture": "profiles/k_solve_d12.md: launches 301-303 "
+NCU_TRAFFIC = {"k_solve": {"bytes_per_launch": 859733, "capture": "profiles/k_solve_d12.md: launches 301-303 "
                            "(sweep ~50), dram__bytes_read.sum + dram__bytes_write.sum"}}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 KERNELS = ("eval_slabs", "qr", "contract", "samples", "rook_col", "rook_row", "update", "init", "setup",
