@@ -94,3 +94,21 @@ def test_r0_beyond_the_initial_samples_is_rejected():
     p = inputs.make_problem("C", "rn", 4, 41, L=10.0, rank_cap=8, r0=9, init_samples=8)
     with pytest.raises(B().TTQError):
         B().Plan(p)
+
+
+def test_plan_runs_after_a_plan_with_smaller_factors_was_made():
+    """Kernel shared-memory limits are per function for the whole process: a
+    plan made after another with smaller factors (rank cap 8) must not lower
+    the limits the first plan's launches need (rank cap 64: the samples'
+    factors alone take 64 KB).  Both run, in either order, and give the
+    values they give alone."""
+    big = inputs.make_problem("D", "rn", 8, 65, L=12.0, rank_cap=64, max_sweeps=6)
+    small = inputs.make_problem("C", "rn", 4, 41, L=10.0, rank_cap=8)
+    alone_big = B().Plan(big).run()
+    alone_small = B().Plan(small).run()
+    pb = B().Plan(big)
+    ps = B().Plan(small)                         # made after the larger plan
+    rb = pb.run()
+    rs = ps.run()
+    assert (rb["value"], rb["sweeps"], rb["n_eval"]) == (alone_big["value"], alone_big["sweeps"], alone_big["n_eval"])
+    assert (rs["value"], rs["sweeps"], rs["n_eval"]) == (alone_small["value"], alone_small["sweeps"], alone_small["n_eval"])
