@@ -1902,7 +1902,7 @@ struct RookSmem {
   int ms[TTQ_WARPS][TTQ_MAXD];
   double pl[TTQ_WARPS][TTQ_MAXPAIR];
   int exc[TTQ_WARPS][TTQ_MAXR];
-  double z[TTQ_WARPS][TTQ_MAXR];
+  __align__(16) double z[TTQ_WARPS][TTQ_MAXR];   // read two entries at a time
 };
 
 // a stage's candidates of one warp feed the interface's maximum (pass 1 of the
@@ -2291,6 +2291,7 @@ __device__ __forceinline__ ItemMap item_map(int cnt) {
 #define TTQ_ROOK_UNROLL 8
 #endif
 constexpr int kRookUnroll = TTQ_ROOK_UNROLL;
+constexpr int kRookUnroll2 = TTQ_ROOK_UNROLL / 2;   // the same depth in pairs of rank steps
 
 // Score of a residual for the argmax, as IEEE bits: |E| for finite E (non-negative
 // doubles order like their bit patterns), else none.  Integer operations only.
@@ -2328,8 +2329,18 @@ __device__ __forceinline__ void col_item(const Dev &D, int k, int j, int alpha, 
     int c[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) c[q] = min(iq[q], Nk - 1);
-#pragma unroll kRookUnroll
-    for (int b = 0; b < rk; ++b) {
+    // z two entries per shared-memory load; the products still added in rank order
+    int b = 0;
+#pragma unroll kRookUnroll2
+    for (; b + 1 < rk; b += 2) {
+      const double2 zz = *reinterpret_cast<const double2 *>(z + b);
+      const double *row = Yc + b * cst;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(row[c[q]], zz.x, acc[q]);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(row[cst + c[q]], zz.y, acc[q]);
+    }
+    if (b < rk) {
       const double zb = z[b];
       const double *row = Yc + b * cst;
 #pragma unroll
@@ -2378,8 +2389,17 @@ __device__ __forceinline__ void row_item(const Dev &D, int k, int j, int beta, i
     int c[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) c[q] = min(jq[q], Nk1 - 1);
-#pragma unroll kRookUnroll
-    for (int a = 0; a < rk; ++a) {
+    int a = 0;
+#pragma unroll kRookUnroll2
+    for (; a + 1 < rk; a += 2) {
+      const double2 zz = *reinterpret_cast<const double2 *>(z + a);
+      const double *row = Yr + (size_t)a * Nk1;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(row[c[q]], zz.x, acc[q]);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[q] = fma(row[Nk1 + c[q]], zz.y, acc[q]);
+    }
+    if (a < rk) {
       const double za = z[a];
       const double *row = Yr + (size_t)a * Nk1;
 #pragma unroll
