@@ -101,10 +101,12 @@ typedef struct ttq_problem {
   int32_t npiv;               /* pivots an interface may add per sweep, 0..TTQ_MAX_PIVOTS; 0 or 1: one, as
                                  Alg. 6.  More (a rank-adaptive variant): the npiv best random samples with
                                  distinct rows and columns start rook searches (Alg. 2) on the sweep's old
-                                 residual, and greedy complete pivoting on the residual matrix of their rows
-                                 and columns keeps the pairs whose Schur pivot passes the acceptance
-                                 threshold, appended in that order.  Single plans of the staged search only
-                                 (not batches, servers, the persistent or the sequential search). */
+                                 residual (a search that meets an earlier one at the same step stops there:
+                                 its end would be the earlier one's pivot), and greedy complete pivoting on
+                                 the residual matrix of their rows and columns keeps the pairs whose Schur
+                                 pivot passes the acceptance threshold, appended in that order.  Single
+                                 plans of the staged search only (not batches, servers, the persistent or
+                                 the sequential search). */
 } ttq_problem;
 
 typedef struct ttq_result {
