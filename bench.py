@@ -651,6 +651,16 @@ def main():
                             "tflops": (v["flops"] / (v["ms"] / 1000.0) / 1e12) if v["ms"] > 0 else 0.0}
                         for k, v in kt.items() if v["launches"]}}
 
+    # ---- the whole integral's algorithmic FP64 operations (the device
+    # counters over the ROOF_STEPS integrals above) against its graph-timed
+    # duration: how much of the FP64 peak one integral uses end to end
+    per_int_flops = sum(v["flops"] for n, v in kt.items() if n != "search") / ROOF_STEPS
+    whole = per_int_flops / (ms / args.steps / 1000.0) / 1e12
+    fp64_whole = {"algorithmic_flops_per_integral": per_int_flops, "tflops": whole, "peak": FP64_PEAK_TFLOPS,
+                  "frac": whole / FP64_PEAK_TFLOPS,
+                  "note": "every kernel's counted FP64 operations of one integral / the integral's graph-timed "
+                          "duration (ms_per_step)"}
+
     # ---- kernel (a) on whole cores: the final index sets set back on the plan
     # (every fiber new), one sweep without search; the evaluation kernel alone
     eval_full = measure_eval_full(plan, p, flush)
@@ -718,7 +728,8 @@ def main():
         "result": {"value": results[-1]["value"], "value_lo": results[-1]["value_lo"], "sweeps": results[-1]["sweeps"],
                    "max_rank": results[-1]["max_rank"], "status": results[-1]["status_name"],
                    "n_eval": results[-1]["n_eval"], "internal_conv": results[-1]["internal_conv"], **check},
-        "roofline": roof, "eval_full_cores": eval_full, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof, "fp64_whole_integral": fp64_whole, "eval_full_cores": eval_full, "cpu_baseline": cpu,
+        "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
         **others,
         **systems,
