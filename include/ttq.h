@@ -361,10 +361,11 @@ int ttq_plan_kernel_times(ttq_plan *plan, double *ms, int64_t *launches, double 
  *    until the process exits.  A problem whose plan needs more
  *    (ttq_workspace_bytes) is rejected with TTQ_ERR_WORKSPACE.
  *  - nodes/weights must be host arrays (inputs_on_device == 0).
- *  - The first call on a device looks up the scratch's device address
- *    (cudaGetSymbolAddress) with that device current, once per device for
- *    the life of the process; make that first call before any stream capture
- *    starts, and do not reset the device (cudaDeviceReset) between calls.
+ *  - Every call looks up the scratch's device address (cudaGetSymbolAddress,
+ *    which allocates nothing) with the caller's device current, so calls
+ *    after a device reset or on another device find their own scratch; make
+ *    the first call of the process before any stream capture starts (the
+ *    first lookup may load the library's device code).
  *  - The call waits for its stream and copies from host memory on its own
  *    stack; on a stream that is capturing it returns TTQ_ERR_INVALID_ARG
  *    before doing any CUDA work, so the caller's capture is left intact.

@@ -1572,12 +1572,10 @@ extern "C" const char *ttq_last_error(void) { return g_last_error.c_str(); }
 // scratch is this array.
 // size: TTQ_NOALLOC_SCRATCH_BYTES (16 MiB), include/ttq.h
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TTQ_NOALLOC_SCRATCH_BYTES];
-// Device address of the scratch, per device id, looked up once per device with
-// that device current (host code cannot use the symbol's own address: it names
-// a host-side stand-in).  The lookup is guarded so that host threads calling
-// for the first time at once take the same, finished value.
-static void *g_noalloc_ptr[256];
-static std::mutex g_noalloc_mu;
+// The scratch's device address is looked up on every call, with the caller's
+// device current (host code cannot use the symbol's own address: it names a
+// host-side stand-in); the lookup allocates nothing, and no address outlives
+// the context it was taken in (a device reset or a new primary context).
 
 extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_result *out) {
   int rc = validate(p);
@@ -1595,18 +1593,9 @@ extern "C" int ttq_integrate_noalloc(const ttq_problem *p, void *stream, ttq_res
   CK(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
   if (cap != cudaStreamCaptureStatusNone)
     return set_err(TTQ_ERR_INVALID_ARG, "ttq_integrate_noalloc called on a capturing stream");
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) return set_err(TTQ_ERR_INVALID_ARG, "device id out of range");
-  {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {              // first call on this device: look up the scratch address
-      void *ptr = nullptr;
-      CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-      g_noalloc_ptr[dev] = ptr;
-    }
-  }
-  char *base = (char *)g_noalloc_ptr[dev];
+  void *scratch = nullptr;
+  CK(cudaGetSymbolAddress(&scratch, g_noalloc_scratch));
+  char *base = (char *)scratch;
   const int d = p->d;
   size_t sumN = 0;
   for (int k = 0; k < d; ++k) sumN += p->nodes_per_mode[k];
